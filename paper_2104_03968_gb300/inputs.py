@@ -1,0 +1,286 @@
+"""Seeded synthetic inputs for the FLD radiation-energy update.
+
+This module is the only code shared by the CUDA path's tests/benchmark and the
+CPU oracle's tests.  It holds workload recipes (fields, grids, units, time steps)
+and none of the method's arithmetic: no limiter, no diffusion coefficient, no
+operator, no exchange.  Every array is float64 and C-contiguous, x fastest.
+
+Recipes (numpy ``default_rng``; the seeds are the workloads' names):
+
+* ``gaussian_pulse_2d``  64x64 periodic, rho=1, kappa=1e3, c=1: a Gaussian E pulse
+  (sigma=4 cells, amplitude 1 on a 1e-6 floor), dt = 10x the explicit limit.
+* ``lognormal_3d``       n^3 periodic, lognormal density (sigma_ln=1, P(k) ~ k^-4
+  Gaussian field), smooth T_gas and T_rad fields, Kramers opacity
+  kappa = kappa0 rho T^-3.5, dt = 100x the explicit limit.
+* ``batched_2d``         many square periodic grids, n log-uniform in [64, 512]
+  (multiples of 16), kappa0 = 10^U(-2,4), dt = 10^U(1,3) x the explicit limit.
+* ``wind_columns``       spherically symmetric wind-like columns on a geometric
+  radial grid r = R*..100 R*, rho ~ r^-2 beyond a seeded sonic point, E from the
+  inward diffusion integral, a synthetic 128x128 (log rho, log T) opacity table.
+* ``heating_cooling``    uniform static gas out of radiative equilibrium.
+* ``thin_front``         1-D optically thin slab lit by an erf profile.
+
+The "explicit limit" is dx^2 / (2 d D_thick) with D_thick = c / (3 kappa rho), the
+optically thick diffusion coefficient; the flux limiter only lowers D below it.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# CODATA-style cgs constants
+C_LIGHT = 2.99792458e10       # cm/s
+K_B = 1.380649e-16            # erg/K
+M_P = 1.67262192e-24          # g
+SIGMA_SB = 5.670374419e-5     # erg/cm^2/s/K^4
+A_RAD = 4.0 * SIGMA_SB / C_LIGHT
+R_SUN = 6.957e10              # cm
+L_SUN = 3.828e33              # erg/s
+M_SUN = 1.98847e33            # g
+YEAR = 3.15576e7              # s
+
+SEED_BASE = 2104039680
+
+
+def code_units(limiter: str = "lp") -> dict:
+    """Dimensionless units: c = 1, a_r = 1, k_b/(mu m_p) = 1, gamma = 5/3."""
+    return {"c": 1.0, "a_rad": 1.0, "gamma": 5.0 / 3.0, "gas_R": 1.0, "limiter": limiter,
+            "opacity": "const", "kappa0": 1.0, "kr_a": 1.0, "kr_b": -3.5}
+
+
+def cgs_units(mu: float, gamma: float = 5.0 / 3.0, limiter: str = "lp") -> dict:
+    return {"c": C_LIGHT, "a_rad": A_RAD, "gamma": gamma, "gas_R": K_B / (mu * M_P),
+            "limiter": limiter, "opacity": "const", "kappa0": 1.0, "kr_a": 1.0, "kr_b": -3.5}
+
+
+def periodic_grid(shape, dx: float = 1.0) -> dict:
+    """shape is (nx,), (nx, ny) or (nx, ny, nz); arrays are stored x fastest."""
+    nd = len(shape)
+    n = list(shape) + [1] * (3 - nd)
+    return {"ndim": nd, "n": n, "dx": [dx] * 3, "bc": ["periodic"] * 6, "bc_val": [0.0] * 6}
+
+
+def _array_shape(grid: dict):
+    nx, ny, nz = grid["n"]
+    return {1: (nx,), 2: (ny, nx), 3: (nz, ny, nx)}[grid["ndim"]]
+
+
+def equilibrium_eps(phys: dict, rho, T):
+    """Gas internal energy density at temperature T (ideal gas)."""
+    return rho * phys["gas_R"] * T / (phys["gamma"] - 1.0)
+
+
+def rad_energy(phys: dict, T):
+    return phys["a_rad"] * T ** 4
+
+
+def rad_temperature(phys: dict, E):
+    return (E / phys["a_rad"]) ** 0.25
+
+
+def thick_explicit_dt(dx2_min, ndim: int, c: float, kr_min: float) -> float:
+    """dx^2 / (2 d D_thick) with the largest optically thick D = c / (3 min(kappa rho))."""
+    return float(dx2_min / (2.0 * ndim * c / (3.0 * kr_min)))
+
+
+# ----------------------------------------------------------------------------- fields
+
+def _kgrid(shape):
+    ks = np.meshgrid(*[np.fft.fftfreq(s) * s for s in shape], indexing="ij")
+    return np.sqrt(sum(k * k for k in ks))
+
+
+def gaussian_random_field(rng, shape, kmax_frac: float = 0.25) -> np.ndarray:
+    """Unit-variance Gaussian field: white noise filtered to P(k) ~ k^-4, 1 <= |k| <= N/4."""
+    k = _kgrid(shape)
+    amp = np.zeros_like(k)
+    kmax = kmax_frac * min(shape)
+    sel = (k >= 1.0) & (k <= kmax)
+    amp[sel] = k[sel] ** -2.0
+    noise = rng.standard_normal(shape)
+    f = np.real(np.fft.ifftn(np.fft.fftn(noise) * amp))
+    f -= f.mean()
+    return f / f.std()
+
+
+def smooth_field(rng, shape, kmax: float = 4.0) -> np.ndarray:
+    """Sum of the Fourier modes with |k| <= kmax, random phases, scaled to max |S| = 1."""
+    k = _kgrid(shape)
+    sel = (k > 0) & (k <= kmax)
+    coef = np.zeros(shape, dtype=np.complex128)
+    ph = rng.uniform(0, 2 * np.pi, size=int(sel.sum()))
+    coef[sel] = np.exp(1j * ph)
+    f = np.real(np.fft.ifftn(coef))
+    return f / np.abs(f).max()
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def gaussian_pulse_2d(n: int = 64, kappa: float = 1e3, sigma: float = 4.0, floor: float = 1e-6,
+                      dt_factor: float = 10.0, limiter: str = "lp") -> dict:
+    """Gaussian E_r pulse on a uniform static periodic medium (code units)."""
+    grid = periodic_grid((n, n))
+    phys = code_units(limiter)
+    phys["opacity"] = "const"
+    phys["kappa0"] = kappa
+    x = np.arange(n) + 0.5
+    X, Y = np.meshgrid(x, x, indexing="xy")  # arrays (ny, nx), x fastest
+    r2 = (X - n / 2) ** 2 + (Y - n / 2) ** 2
+    E = floor + np.exp(-r2 / (2 * sigma ** 2))
+    rho = np.ones_like(E)
+    eps = equilibrium_eps(phys, rho, rad_temperature(phys, E))
+    dt_exp = thick_explicit_dt(1.0, 2, phys["c"], kappa * 1.0)
+    return {"name": f"gaussian_pulse_2d_{n}", "grid": grid, "phys": phys, "rho": rho, "eps": eps,
+            "E": E, "dt": dt_factor * dt_exp, "dt_exp": dt_exp, "sigma": sigma, "floor": floor,
+            "D_thick": phys["c"] / (3 * kappa)}
+
+
+def lognormal_fields(rng, shape, phys: dict, kappa0: float, sigma_ln: float = 1.0):
+    G = gaussian_random_field(rng, shape)
+    rho = np.exp(sigma_ln * G - sigma_ln ** 2 / 2)
+    Tg = 1.0 + 0.3 * smooth_field(rng, shape)
+    Tr = 1.0 + 0.3 * smooth_field(rng, shape)
+    E = rad_energy(phys, Tr)
+    eps = equilibrium_eps(phys, rho, Tg)
+    kr_min = float((kappa0 * rho * Tg ** -3.5 * rho).min())
+    return rho, eps, E, kr_min
+
+
+def lognormal_3d(n: int = 128, seed: int = 1, kappa0: float = 1.0, dt_factor: float = 100.0,
+                 ndim: int = 3, limiter: str = "lp") -> dict:
+    """Lognormal density with Kramers opacity; periodic n^ndim (code units)."""
+    rng = np.random.default_rng(SEED_BASE + seed)
+    shape = (n,) * ndim
+    grid = periodic_grid(shape)
+    phys = code_units(limiter)
+    phys.update(opacity="kramers", kappa0=kappa0, kr_a=1.0, kr_b=-3.5)
+    rho, eps, E, kr_min = lognormal_fields(rng, shape, phys, kappa0)
+    dt_exp = thick_explicit_dt(1.0, ndim, phys["c"], kr_min)
+    return {"name": f"lognormal_{ndim}d_{n}", "grid": grid, "phys": phys, "rho": rho, "eps": eps,
+            "E": E, "dt": dt_factor * dt_exp, "dt_exp": dt_exp}
+
+
+def batched_2d(ngrids: int = 512, seed: int = 3, nmin: int = 64, nmax: int = 512,
+               limiter: str = "lp") -> list:
+    """Independent square periodic 2-D grids of uneven size, opacity and time step."""
+    rng = np.random.default_rng(SEED_BASE + seed)
+    out = []
+    for g in range(ngrids):
+        n = int(16 * round(math.exp(rng.uniform(math.log(nmin), math.log(nmax))) / 16))
+        n = max(16, n)
+        kappa0 = 10.0 ** rng.uniform(-2, 4)
+        fac = 10.0 ** rng.uniform(1, 3)
+        grid = periodic_grid((n, n))
+        phys = code_units(limiter)
+        phys.update(opacity="kramers", kappa0=kappa0, kr_a=1.0, kr_b=-3.5)
+        rho, eps, E, kr_min = lognormal_fields(rng, (n, n), phys, kappa0)
+        dt_exp = thick_explicit_dt(1.0, 2, phys["c"], kr_min)
+        out.append({"name": f"batched_2d_{g}", "grid": grid, "phys": phys, "rho": rho, "eps": eps,
+                    "E": E, "dt": fac * dt_exp, "dt_exp": dt_exp})
+    return out
+
+
+def opacity_table(nrho: int = 128, nT: int = 128, lrho=(-16.0, -6.0), lT=(3.7, 6.5)):
+    """Synthetic log10 kappa table: electron scattering + Kramers + an iron-like bump at
+    log T = 5.3.  Rows are log10 rho, columns log10 T."""
+    lr = np.linspace(lrho[0], lrho[1], nrho)
+    lt = np.linspace(lT[0], lT[1], nT)
+    R, T = np.meshgrid(10.0 ** lr, 10.0 ** lt, indexing="ij")
+    kK = 0.2 / (1e-10 * (1e5) ** -3.5)
+    bump = 1.0 * np.exp(-(np.log10(T) - 5.3) ** 2 / (2 * 0.15 ** 2)) * (R / 1e-10) ** 0.25
+    kap = 0.2 + kK * R * T ** -3.5 + bump
+    return np.ascontiguousarray(np.log10(kap)), list(lrho), list(lT)
+
+
+def wind_columns(ncol: int = 4096, ncell: int = 2048, seed: int = 4, dt_factor: float = 100.0,
+                 limiter: str = "lp") -> dict:
+    """Spherically symmetric wind-like radial columns (cgs).  Arrays are (ncol, ncell)."""
+    rng = np.random.default_rng(SEED_BASE + seed)
+    mu = 4.0 / 3.0  # fully ionised helium
+    phys = cgs_units(mu, limiter=limiter)
+    tab, tlo, thi = opacity_table()
+    phys.update(opacity="table", table=tab, tlo=tlo, thi=thi)
+    Rs = R_SUN
+    rf = Rs * 100.0 ** (np.arange(ncell + 1) / ncell)
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    dr = rf[1:] - rf[:-1]
+    L = 10 ** 5.416 * L_SUN
+    kappa_es = 0.2
+    Mdot0 = 1.87e-5 * M_SUN / YEAR
+    vinf0 = 1.0e8
+    rho = np.empty((ncol, ncell))
+    E = np.empty((ncol, ncell))
+    Tg = np.empty((ncol, ncell))
+    for j in range(ncol):
+        Mdot = Mdot0 * rng.uniform(0.8, 1.2)
+        vinf = vinf0 * rng.uniform(0.8, 1.2)
+        rs = Rs * rng.uniform(1.02, 1.3)
+        v = np.maximum(vinf * np.sqrt(np.maximum(1 - Rs / rc, 0.0)), 1e-3 * vinf)
+        r_wind = Mdot / (4 * np.pi * rc ** 2 * v)
+        vs = max(vinf * math.sqrt(1 - Rs / rs), 1e-3 * vinf)
+        rho_s = Mdot / (4 * np.pi * rs ** 2 * vs)
+        inner = rho_s * np.exp(np.minimum((rs - rc) / (0.01 * Rs), 10.0))
+        rho[j] = np.where(rc < rs, inner, r_wind)
+        # E from the inward integral of the Eddington-approximation flux, T(r_max) = 5e4 K
+        integrand = 3 * kappa_es * rho[j] * L / (4 * np.pi * rc ** 2 * C_LIGHT) * dr
+        tail = np.cumsum(integrand[::-1])[::-1]
+        E[j] = A_RAD * 5.0e4 ** 4 + tail
+        Tr = (E[j] / A_RAD) ** 0.25
+        noise = np.interp(np.arange(ncell), np.linspace(0, ncell - 1, 17), rng.uniform(-1, 1, 17))
+        Tg[j] = Tr * (1 + 0.05 * noise)
+    eps = rho * phys["gas_R"] * Tg / (phys["gamma"] - 1.0)
+    # electron scattering is the smallest opacity the table holds
+    dt_exp = (dr[None, :] ** 2 * 3 * kappa_es * rho / (2 * C_LIGHT)).min(axis=1)
+    return {"name": f"wind_columns_{ncol}x{ncell}", "phys": phys, "r_faces": rf,
+            "geometry": "spherical", "bc": ["dirichlet", "dirichlet"], "rho": rho, "eps": eps,
+            "E": E, "bc_lo": E[:, 0].copy(), "bc_hi": E[:, -1].copy(), "dt": dt_factor * dt_exp,
+            "dt_exp": dt_exp}
+
+
+def heating_cooling(e_ratio: float, dt: float, ncell: int = 16) -> dict:
+    """Uniform static gas: rho = 1e-7, kappa = 0.4, gamma = 5/3, mu = 0.6, E = 1e12 (cgs);
+    gas energy e_ratio times the equilibrium value set by the radiation temperature."""
+    phys = cgs_units(0.6)
+    phys.update(opacity="const", kappa0=0.4)
+    rho = np.full(ncell, 1e-7)
+    E = np.full(ncell, 1e12)
+    Tr = rad_temperature(phys, E)
+    e_eq = equilibrium_eps(phys, rho, Tr)
+    return {"name": f"heating_cooling_{e_ratio:g}", "phys": phys, "rho": rho, "E": E,
+            "eps": e_ratio * e_eq, "e_equil": e_eq, "dt": dt}
+
+
+def thin_front(ncell: int = 256) -> dict:
+    """Optically thin slab: rho = 0.025, kappa = 0.4 on [-0.5, 1.5] cm, erf-lit from the left."""
+    from math import erf
+    phys = cgs_units(0.6)
+    phys.update(opacity="const", kappa0=0.4)
+    dx = 2.0 / ncell
+    x = -0.5 + (np.arange(ncell) + 0.5) * dx
+    E0, E1, d = 1.4e-11, 1.4e11, 0.05
+    E = E0 + 0.5 * (1 - np.array([erf(v / d) for v in x])) * E1
+    rho = np.full(ncell, 0.025)
+    eps = equilibrium_eps(phys, rho, rad_temperature(phys, np.full(ncell, E0)))
+    grid = {"ndim": 1, "n": [ncell, 1, 1], "dx": [dx, 1.0, 1.0],
+            "bc": ["dirichlet", "dirichlet"] + ["periodic"] * 4, "bc_val": [E0 + E1, E0, 0, 0, 0, 0]}
+    return {"name": "thin_front", "grid": grid, "phys": phys, "rho": rho, "eps": eps, "E": E,
+            "x": x, "dt": 1e-13, "E0": E0, "E1": E1}
+
+
+def random_small(shape, seed: int, bc=None, kappa0: float = 1.0, dt_factor: float = 30.0,
+                 limiter: str = "lp") -> dict:
+    """Small heterogeneous grid for brute-force checks (code units, Kramers opacity)."""
+    rng = np.random.default_rng(SEED_BASE + 1000 + seed)
+    nd = len(shape)
+    grid = periodic_grid(shape)
+    if bc is not None:
+        grid["bc"] = list(bc[0])
+        grid["bc_val"] = list(bc[1])
+    phys = code_units(limiter)
+    phys.update(opacity="kramers", kappa0=kappa0)
+    arr_shape = tuple(reversed(shape))
+    rho, eps, E, kr_min = lognormal_fields(rng, arr_shape, phys, kappa0)
+    dt_exp = thick_explicit_dt(1.0, nd, phys["c"], kr_min)
+    return {"name": f"random_{'x'.join(map(str, shape))}_{seed}", "grid": grid, "phys": phys,
+            "rho": rho, "eps": eps, "E": E, "dt": dt_factor * dt_exp, "dt_exp": dt_exp}
