@@ -1,0 +1,196 @@
+/*
+ * fld.h -- C ABI of the GB300 (sm_103a) flux-limited-diffusion radiation-energy update.
+ *
+ * Method: arXiv 2104.03968, "Radiation-hydrodynamics with MPI-AMRVAC: flux-limited
+ * diffusion".  The update advances the radiation energy density E and the gas internal
+ * energy density eps of a static medium (density rho) over one time step dt:
+ *
+ *   fld_coeffs    opacity kappa(rho, T), the 4th-order gradient of E (Sect. 3.2, Eq.
+ *                 ileyk_flux), R = |grad E|/(kappa rho E), the Levermore-Pomraning limiter
+ *                 lambda(R) (Sect. 2.2, Eq. fld_lambda) and D = c lambda/(kappa rho)
+ *                 (Sect. 2.2, Eq. fld_F), per cell.
+ *   fld_diffuse   the backward-Euler diffusion solve E^{n+1}/dt - div(D grad E^{n+1}) =
+ *                 E^n/dt on a uniform Cartesian grid, 5/7/3-point stencil with harmonic-mean
+ *                 face coefficients (Sect. 3.4, Eq. discdiff), by geometric multigrid.
+ *   fld_exchange  the point-implicit gas-radiation energy exchange: the quartic in
+ *                 eps^{n+1} (Sect. 3.3), root in ]0, eps^n + E^n[, then E^{n+1}.
+ *   fld_step      fld_coeffs, fld_diffuse and fld_exchange in the selected order.
+ *   fld_step_batched   many independent 2-D/3-D grids in one call.
+ *   fld_columns_step   many independent 1-D radial columns (spherical or Cartesian finite
+ *                 volumes on a stretched grid), diffusion by a tridiagonal solve.
+ *
+ * Conventions shared by every entry point
+ *   - Arrays are caller-owned DEVICE memory, float64, contiguous, x fastest: cell (i,j,k)
+ *     is element i + n[0]*(j + n[1]*k).  Column arrays are [column][cell].
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work
+ *     is enqueued on it.  Calls that solve to a tolerance (fld_diffuse, fld_step,
+ *     fld_step_batched) wait on the stream between multigrid cycles and return after the
+ *     result is complete; the others return after enqueueing.
+ *   - Inputs are never modified; eps and E are updated in place where documented.
+ *   - Return value: FLD_OK, or an error code for an invalid argument, a CUDA error or a
+ *     solve that did not reach rtol within max_cycles.  The message of the last error is
+ *     available from fld_last_error().  No exception crosses the ABI.
+ *   - A context is bound to one device and is not thread-safe; use one context per host
+ *     thread.  It owns the multigrid hierarchy, scratch buffers and CUDA graphs and keeps
+ *     them between calls of the same shape.
+ */
+#ifndef FLD_H
+#define FLD_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define FLD_API __attribute__((visibility("default")))
+#else
+#define FLD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FLD_OK = 0,
+  FLD_ERR_INVALID_ARG = 1,
+  FLD_ERR_NONPOSITIVE = 2,  /* rho, kappa or E <= 0, or eps < 0, met on the device */
+  FLD_ERR_NONFINITE = 3,    /* a NaN/Inf appeared in a residual norm */
+  FLD_ERR_NOT_CONVERGED = 4,
+  FLD_ERR_CUDA = 5,
+  FLD_ERR_DEVICE_TIMEOUT = 6,
+  FLD_ERR_UNSUPPORTED = 7
+} fld_status;
+
+/* boundary conditions (Sect. 3.4): ghost value, fixed gradient, linear extrapolation */
+enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2, FLD_BC_CONTINUOUS = 3 };
+enum { FLD_LIMITER_LP = 0, FLD_LIMITER_THIRD = 1 };   /* Eq. fld_lambda, or lambda = 1/3 */
+enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_KRAMERS = 1, FLD_OPACITY_TABLE = 2 };
+enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 };
+enum { FLD_ORDER_DIFFUSE_THEN_EXCHANGE = 0, FLD_ORDER_EXCHANGE_THEN_DIFFUSE = 1 };
+enum { FLD_GEOM_CARTESIAN = 0, FLD_GEOM_SPHERICAL = 1 };
+
+/* Uniform Cartesian grid.  ndim in {1,2,3}; unused axes have n = 1.  bc[2a] / bc[2a+1] are the
+   lower / upper faces of axis a; bc_val holds the Dirichlet ghost value or the Neumann
+   gradient dE/dx across the boundary face.  Every axis with a non-periodic face needs
+   n >= 2. */
+typedef struct {
+  int ndim;
+  int n[3];
+  double dx[3];
+  int bc[6];
+  double bc_val[6];
+} fld_grid;
+
+typedef struct {
+  /* physics (code units or cgs, consistently) */
+  double c;        /* speed of light */
+  double a_rad;    /* radiation constant a_r = 4 sigma / c */
+  double gamma;    /* adiabatic index */
+  double gas_R;    /* k_b / (mu m_p): T = (gamma-1) eps / (rho gas_R) */
+  int limiter;     /* FLD_LIMITER_* */
+  int opacity;     /* FLD_OPACITY_*: kappa0 | kappa0 rho^kr_a T^kr_b | table */
+  double kappa0, kr_a, kr_b;
+  const double* table; /* DEVICE pointer: log10 kappa on a tn[0] x tn[1] grid, row = log10 rho,
+                          column (fastest) = log10 T, uniform over [tlo, thi], bilinear and
+                          clamped at the edges */
+  int tn[2];
+  double tlo[2], thi[2];
+  /* solver */
+  int precision;   /* FLD_PREC_FP64: FP64 multigrid.  FLD_PREC_MIXED: FP32 V-cycles inside
+                      an FP64 defect-correction loop (FP64 residual, update and norm) */
+  double rtol;     /* stop when ||b - A E||_2 / ||b||_2 <= rtol */
+  int max_cycles;  /* outer iterations (one V-cycle each); 0 = 100 */
+  int nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after coarse correction; 0 = 2 */
+  int exch_maxit;  /* Halley iterations before bisection in the exchange; 0 = 100 */
+  int order;       /* FLD_ORDER_* used by fld_step */
+} fld_params;
+
+typedef struct {
+  int cycles;              /* outer iterations (V-cycles) used */
+  double rel_residual;     /* final ||b - A E||_2 / ||b||_2 in FP64 */
+  int exch_max_iters;      /* largest number of root iterations over the cells */
+  int bisection_fallbacks; /* cells that fell back to bisection */
+  int status;              /* fld_status of this grid / column set */
+} fld_info;
+
+typedef struct fld_ctx fld_ctx;
+
+/* Create a context on `device` (CUDA ordinal).  *out receives the handle. */
+FLD_API fld_status fld_ctx_create(fld_ctx** out, int device);
+FLD_API fld_status fld_ctx_destroy(fld_ctx* ctx);
+/* Message of the last error raised on `ctx` (never NULL; empty when none). */
+FLD_API const char* fld_last_error(const fld_ctx* ctx);
+
+/* Per-cell opacity and diffusion coefficient (Sect. 2.2, Eqs. fld_lambda and fld_F, with the
+   5-point gradient of Sect. 3.2).  In: E, rho, eps (N cells).  Out: kappa_out (N, may be NULL),
+   D_out (N).  Asynchronous. */
+FLD_API fld_status fld_coeffs(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, const double* E,
+                      const double* rho, const double* eps, double* kappa_out, double* D_out,
+                      void* stream);
+
+/* Backward-Euler diffusion (Sect. 3.4, Eq. discdiff): solves
+   E_new + dt*(-div D grad E_new) = E_old (with the boundary terms) to p->rtol.  D_cell is the
+   cell-centred D from fld_coeffs; faces take its harmonic mean.  E_new may alias E_old.
+   `info` (may be NULL) receives cycles and the final relative residual.  Synchronises. */
+FLD_API fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                       const double* D_cell, const double* E_old, double* E_new, fld_info* info,
+                       void* stream);
+
+/* Point-implicit exchange (Sect. 3.3) on n independent cells, in place on eps and E.  kappa may
+   be NULL, in which case it is evaluated from rho and eps with the opacity model of p.
+   Asynchronous; `info` (may be NULL) is filled after a stream synchronisation. */
+FLD_API fld_status fld_exchange(fld_ctx* ctx, size_t n, const fld_params* p, double dt, const double* rho,
+                        const double* kappa, double* eps, double* E, fld_info* info, void* stream);
+
+/* One full radiation-energy update in place on eps and E: coefficients from the state entering
+   the diffusion stage (lagged D), diffusion, exchange; p->order selects the paper's order
+   (exchange first, Sect. 3.1) or diffusion first.  Synchronises. */
+FLD_API fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                    const double* rho, double* eps, double* E, fld_info* info, void* stream);
+
+/* fld_step on `ngrids` independent grids with their own sizes, parameters and time steps.
+   grids, params and dt are HOST arrays of length ngrids; rho/eps/E are HOST arrays of DEVICE
+   pointers; infos (may be NULL) receives one fld_info per grid.  Every grid must have ndim 2
+   or 3.  Synchronises. */
+FLD_API fld_status fld_step_batched(fld_ctx* ctx, int ngrids, const fld_grid* grids,
+                            const fld_params* params, const double* dt, const double* const* rho,
+                            double* const* eps, double* const* E, fld_info* infos, void* stream);
+
+/* One full update of `ncol` independent 1-D radial columns of `ncell` cells sharing the face
+   radii r_faces (DEVICE, ncell+1 values, increasing).  geometry: FLD_GEOM_SPHERICAL (areas r^2,
+   volumes (r_+^3 - r_-^3)/3) or FLD_GEOM_CARTESIAN.  bc_lo/bc_hi: FLD_BC_DIRICHLET, NEUMANN or
+   CONTINUOUS; v_lo/v_hi: DEVICE arrays of ncol boundary values.  dt: DEVICE array of ncol time
+   steps.  rho, eps, E: DEVICE [ncol][ncell]; eps and E are updated in place.  The diffusion is
+   a direct tridiagonal solve per column (exact to round-off, no rtol).  The gradient in R is
+   the 3-point non-uniform central difference.  Asynchronous. */
+FLD_API fld_status fld_columns_step(fld_ctx* ctx, int ncol, int ncell, const double* r_faces, int geometry,
+                            int bc_lo, int bc_hi, const double* v_lo, const double* v_hi,
+                            const fld_params* p, const double* dt, const double* rho,
+                            double* eps, double* E, fld_info* info, void* stream);
+
+/* Diffusion stage only of fld_columns_step, with a caller-given cell-centred D (DEVICE
+   [ncol][ncell]); E_new may alias E_old.  Asynchronous. */
+FLD_API fld_status fld_columns_diffuse(fld_ctx* ctx, int ncol, int ncell, const double* r_faces,
+                               int geometry, int bc_lo, int bc_hi, const double* v_lo,
+                               const double* v_hi, const fld_params* p, const double* dt,
+                               const double* D_cell, const double* E_old, double* E_new,
+                               void* stream);
+
+/* ---- tracing: per-kernel launch timing with CUDA events (library diagnostics; the paper has
+   no counterpart).  While enabled, every kernel launch of the library is bracketed by a pair of
+   events on its stream; fld_trace_report synchronises on them and returns, per kernel name,
+   the number of launches and their summed device time since the last enable. */
+typedef struct {
+  char name[32];
+  int launches;
+  double total_ms;
+} fld_trace_entry;
+
+/* on != 0 clears the record and starts tracing; on == 0 stops it (the record is kept). */
+FLD_API fld_status fld_trace_enable(fld_ctx* ctx, int on);
+/* Writes up to `max` entries to `out` and their count to *n.  Synchronises. */
+FLD_API fld_status fld_trace_report(fld_ctx* ctx, fld_trace_entry* out, int max, int* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLD_H */

@@ -1,0 +1,496 @@
+// C ABI of the GB300 FLD library: argument validation, context-owned buffers and the
+// composition of the kernels into the calls declared in include/fld.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "batched.h"
+#include "columns.h"
+#include "kernels.h"
+#include "mg.h"
+#include "trace.h"
+
+using namespace fld;
+
+struct fld_ctx {
+  int device = 0;
+  std::string err;
+  Multigrid mg;
+  double* D = nullptr;
+  double* kappa = nullptr;
+  size_t cap = 0;  // cells of D and kappa
+  unsigned* d_status = nullptr;  // [0] status bits
+  int* d_info = nullptr;         // [0] max iterations, [1] bisections
+  int* h_info = nullptr;         // pinned: [0..1] info, [2] status
+  BatchedSolver* batched = nullptr;
+  double* geom = nullptr;  // per-cell geometry of the 1-D column calls
+  size_t geom_cap = 0;
+};
+
+namespace {
+
+fld_status fail(fld_ctx* ctx, fld_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return st;
+}
+
+fld_status cuda_fail(fld_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, FLD_ERR_CUDA, "%s: CUDA error %d (%s)", where, (int)e, cudaGetErrorString(e));
+}
+
+// RAII: make the context's device current for the duration of a call
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+fld_status check_grid(fld_ctx* ctx, const fld_grid* g) {
+  if (!g) return fail(ctx, FLD_ERR_INVALID_ARG, "grid is NULL");
+  if (g->ndim < 1 || g->ndim > 3) return fail(ctx, FLD_ERR_INVALID_ARG, "ndim must be 1, 2 or 3 (got %d)", g->ndim);
+  for (int a = 0; a < 3; ++a) {
+    if (g->n[a] < 1) return fail(ctx, FLD_ERR_INVALID_ARG, "n[%d] must be >= 1", a);
+    if (a >= g->ndim && g->n[a] != 1) return fail(ctx, FLD_ERR_INVALID_ARG, "n[%d] must be 1 for ndim=%d", a, g->ndim);
+    if (a < g->ndim) {
+      if (!(g->dx[a] > 0) || !std::isfinite(g->dx[a])) return fail(ctx, FLD_ERR_INVALID_ARG, "dx[%d] must be > 0", a);
+      for (int s = 0; s < 2; ++s) {
+        int bc = g->bc[2 * a + s];
+        if (bc < FLD_BC_PERIODIC || bc > FLD_BC_CONTINUOUS)
+          return fail(ctx, FLD_ERR_INVALID_ARG, "bc[%d] = %d is not a boundary condition", 2 * a + s, bc);
+        if (bc != FLD_BC_PERIODIC && g->n[a] < 2)
+          return fail(ctx, FLD_ERR_INVALID_ARG, "axis %d needs n >= 2 for a non-periodic boundary", a);
+        if (!std::isfinite(g->bc_val[2 * a + s])) return fail(ctx, FLD_ERR_INVALID_ARG, "bc_val[%d] not finite", 2 * a + s);
+      }
+      if ((g->bc[2 * a] == FLD_BC_PERIODIC) != (g->bc[2 * a + 1] == FLD_BC_PERIODIC))
+        return fail(ctx, FLD_ERR_INVALID_ARG, "axis %d: periodic must be set on both faces", a);
+    }
+  }
+  long long n = (long long)g->n[0] * g->n[1] * g->n[2];
+  if (n > (1LL << 34)) return fail(ctx, FLD_ERR_INVALID_ARG, "grid too large (%lld cells)", n);
+  return FLD_OK;
+}
+
+fld_status check_params(fld_ctx* ctx, const fld_params* p, bool solver) {
+  if (!p) return fail(ctx, FLD_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->c > 0) || !(p->a_rad > 0) || !(p->gamma > 1) || !(p->gas_R > 0))
+    return fail(ctx, FLD_ERR_INVALID_ARG, "c, a_rad, gas_R must be > 0 and gamma > 1");
+  if (p->limiter != FLD_LIMITER_LP && p->limiter != FLD_LIMITER_THIRD)
+    return fail(ctx, FLD_ERR_INVALID_ARG, "unknown limiter %d", p->limiter);
+  if (p->opacity < FLD_OPACITY_CONST || p->opacity > FLD_OPACITY_TABLE)
+    return fail(ctx, FLD_ERR_INVALID_ARG, "unknown opacity model %d", p->opacity);
+  if (p->opacity != FLD_OPACITY_TABLE && !(p->kappa0 > 0)) return fail(ctx, FLD_ERR_INVALID_ARG, "kappa0 must be > 0");
+  if (p->opacity == FLD_OPACITY_TABLE) {
+    if (!p->table || p->tn[0] < 2 || p->tn[1] < 2 || !(p->thi[0] > p->tlo[0]) || !(p->thi[1] > p->tlo[1]))
+      return fail(ctx, FLD_ERR_INVALID_ARG, "opacity table needs a device pointer, tn >= 2 and thi > tlo");
+  }
+  if (solver) {
+    if (p->precision != FLD_PREC_FP64 && p->precision != FLD_PREC_MIXED)
+      return fail(ctx, FLD_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+    if (!(p->rtol > 0) || p->rtol >= 1) return fail(ctx, FLD_ERR_INVALID_ARG, "rtol must be in (0, 1)");
+    if (p->max_cycles < 0 || p->nu1 < 0 || p->nu2 < 0 || p->nu1 > 16 || p->nu2 > 16)
+      return fail(ctx, FLD_ERR_INVALID_ARG, "max_cycles, nu1, nu2 out of range");
+    if (p->order != FLD_ORDER_DIFFUSE_THEN_EXCHANGE && p->order != FLD_ORDER_EXCHANGE_THEN_DIFFUSE)
+      return fail(ctx, FLD_ERR_INVALID_ARG, "unknown order %d", p->order);
+  }
+  if (p->exch_maxit < 0) return fail(ctx, FLD_ERR_INVALID_ARG, "exch_maxit must be >= 0");
+  return FLD_OK;
+}
+
+GridDev to_dev(const fld_grid* g) {
+  GridDev d{};
+  d.ndim = g->ndim;
+  for (int a = 0; a < 3; ++a) {
+    d.n[a] = g->n[a];
+    d.dx[a] = a < g->ndim ? g->dx[a] : 1.0;
+  }
+  for (int f = 0; f < 6; ++f) {
+    d.bc[f] = (f / 2) < g->ndim ? g->bc[f] : FLD_BC_PERIODIC;
+    d.bc_val[f] = (f / 2) < g->ndim ? g->bc_val[f] : 0.0;
+  }
+  d.ncell = (long long)g->n[0] * g->n[1] * g->n[2];
+  return d;
+}
+
+Opacity to_opacity(const fld_params* p) {
+  Opacity o{};
+  o.model = p->opacity;
+  o.kappa0 = p->kappa0;
+  o.kr_a = p->kr_a;
+  o.kr_b = p->kr_b;
+  o.table = p->table;
+  o.tn0 = p->tn[0];
+  o.tn1 = p->tn[1];
+  o.tlo0 = p->tlo[0];
+  o.tlo1 = p->tlo[1];
+  o.thi0 = p->thi[0];
+  o.thi1 = p->thi[1];
+  return o;
+}
+
+ExchangeParams to_exchange(const fld_params* p, double dt) {
+  ExchangeParams e{};
+  e.c = p->c;
+  e.sigma = p->a_rad * p->c / 4.0;
+  e.gamma = p->gamma;
+  e.gas_R = p->gas_R;
+  e.dt = dt;
+  e.maxit = p->exch_maxit > 0 ? p->exch_maxit : 100;
+  return e;
+}
+
+fld_status ensure_scratch(fld_ctx* ctx, long long ncell) {
+  if ((size_t)ncell <= ctx->cap) return FLD_OK;
+  cudaFree(ctx->D);
+  cudaFree(ctx->kappa);
+  ctx->D = ctx->kappa = nullptr;
+  ctx->cap = 0;
+  cudaError_t e = cudaMalloc(&ctx->D, ncell * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->kappa, ncell * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
+  ctx->cap = ncell;
+  return FLD_OK;
+}
+
+fld_status reset_status(fld_ctx* ctx, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_info, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status reset");
+  return FLD_OK;
+}
+
+// copy the device status/info to the host (synchronises)
+fld_status read_status(fld_ctx* ctx, cudaStream_t s, unsigned* status, int* iters, int* bisect) {
+  cudaError_t e = cudaMemcpyAsync(ctx->h_info, ctx->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_info + 2, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
+  if (iters) *iters = ctx->h_info[0];
+  if (bisect) *bisect = ctx->h_info[1];
+  if (status) *status = (unsigned)ctx->h_info[2];
+  return FLD_OK;
+}
+
+fld_status run_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* D,
+                       const double* E_old, double* E_new, SolveStats* st, cudaStream_t s) {
+  GridDev g = to_dev(grid);
+  cudaError_t e = ctx->mg.configure(g, p->precision);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid allocation");
+  e = ctx->mg.setup(dt, D, E_old, ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid setup");
+  int maxc = p->max_cycles > 0 ? p->max_cycles : 100;
+  int nu1 = p->nu1 > 0 ? p->nu1 : 2, nu2 = p->nu2 > 0 ? p->nu2 : 2;
+  e = ctx->mg.solve(E_old, E_new, p->rtol, maxc, nu1, nu2, st, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid solve");
+  return FLD_OK;
+}
+
+fld_status ensure_geom(fld_ctx* ctx, int ncell) {
+  size_t need = 4 * (size_t)ncell + 4;
+  if (need <= ctx->geom_cap) return FLD_OK;
+  cudaFree(ctx->geom);
+  ctx->geom = nullptr;
+  ctx->geom_cap = 0;
+  cudaError_t e = cudaMalloc(&ctx->geom, need * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "column geometry allocation");
+  ctx->geom_cap = need;
+  return FLD_OK;
+}
+
+fld_status check_coarsest(fld_ctx* ctx, const fld_grid* g) {
+  // the coarsest multigrid level is solved by one thread block
+  int n[3] = {g->n[0], g->n[1], g->n[2]};
+  long long cells = (long long)n[0] * n[1] * n[2];
+  for (;;) {
+    bool ok = cells > 64;
+    for (int a = 0; a < g->ndim && ok; ++a) ok = (n[a] % 2 == 0) && n[a] >= 4;
+    if (!ok) break;
+    for (int a = 0; a < g->ndim; ++a) n[a] /= 2;
+    cells = (long long)n[0] * n[1] * n[2];
+  }
+  if (cells > 4096)
+    return fail(ctx, FLD_ERR_UNSUPPORTED,
+                "grid %dx%dx%d coarsens only to %lld cells (>4096); use axis lengths with more factors of 2", g->n[0],
+                g->n[1], g->n[2], cells);
+  return FLD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fld_status fld_ctx_create(fld_ctx** out, int device) {
+  if (!out) return FLD_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FLD_ERR_INVALID_ARG;
+  fld_ctx* ctx = new (std::nothrow) fld_ctx();
+  if (!ctx) return FLD_ERR_CUDA;
+  ctx->device = device;
+  DeviceGuard dg(device);
+  cudaError_t e = cudaMalloc(&ctx->d_status, 64);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_info, 64);
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_info, 64);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 64);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_info, 0, 64);
+  if (e != cudaSuccess) {
+    fld_ctx_destroy(ctx);
+    return FLD_ERR_CUDA;
+  }
+  *out = ctx;
+  return FLD_OK;
+}
+
+fld_status fld_ctx_destroy(fld_ctx* ctx) {
+  if (!ctx) return FLD_OK;
+  DeviceGuard dg(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->D);
+  cudaFree(ctx->kappa);
+  cudaFree(ctx->geom);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_info);
+  if (ctx->h_info) cudaFreeHost(ctx->h_info);
+  delete ctx->batched;
+  delete ctx;  // releases the multigrid buffers while the device is current
+  return FLD_OK;
+}
+
+const char* fld_last_error(const fld_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fld_status fld_coeffs(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, const double* E, const double* rho,
+                      const double* eps, double* kappa_out, double* D_out, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_grid(ctx, grid);
+  if (st == FLD_OK) st = check_params(ctx, p, false);
+  if (st != FLD_OK) return st;
+  if (!E || !rho || !eps || !D_out) return fail(ctx, FLD_ERR_INVALID_ARG, "E, rho, eps and D_out must be non-NULL");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  GridDev g = to_dev(grid);
+  cudaError_t e = launch_coeffs(g, to_opacity(p), p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, kappa_out, D_out,
+                                ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_coeffs launch");
+  return FLD_OK;
+}
+
+fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* D_cell,
+                       const double* E_old, double* E_new, fld_info* info, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_grid(ctx, grid);
+  if (st == FLD_OK) st = check_params(ctx, p, true);
+  if (st == FLD_OK) st = check_coarsest(ctx, grid);
+  if (st != FLD_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
+  if (!D_cell || !E_old || !E_new) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell, E_old and E_new must be non-NULL");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  SolveStats ss;
+  st = run_diffuse(ctx, grid, p, dt, D_cell, E_old, E_new, &ss, s);
+  if (st != FLD_OK) return st;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->cycles = ss.cycles;
+    info->rel_residual = ss.relres;
+    info->status = ss.status;
+  }
+  if (ss.status != FLD_OK)
+    return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
+                ss.relres, ss.cycles);
+  return FLD_OK;
+}
+
+fld_status fld_exchange(fld_ctx* ctx, size_t n, const fld_params* p, double dt, const double* rho, const double* kappa,
+                        double* eps, double* E, fld_info* info, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_params(ctx, p, false);
+  if (st != FLD_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
+  if (n > 0 && (!rho || !eps || !E)) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and E must be non-NULL");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = reset_status(ctx, s)) != FLD_OK) return st;
+  cudaError_t e = launch_exchange((long long)n, to_exchange(p, dt), to_opacity(p), rho, kappa, eps, E, ctx->d_info,
+                                  ctx->d_info + 1, ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_exchange launch");
+  if (info) {
+    unsigned sbits;
+    memset(info, 0, sizeof(*info));
+    if ((st = read_status(ctx, s, &sbits, &info->exch_max_iters, &info->bisection_fallbacks)) != FLD_OK) return st;
+    info->status = (sbits & kStatNonpositive) ? FLD_ERR_NONPOSITIVE : FLD_OK;
+    if (info->status != FLD_OK) return fail(ctx, FLD_ERR_NONPOSITIVE, "exchange met rho, kappa <= 0 or eps, E < 0");
+  }
+  return FLD_OK;
+}
+
+fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* rho, double* eps,
+                    double* E, fld_info* info, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_grid(ctx, grid);
+  if (st == FLD_OK) st = check_params(ctx, p, true);
+  if (st == FLD_OK) st = check_coarsest(ctx, grid);
+  if (st != FLD_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
+  if (!rho || !eps || !E) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and E must be non-NULL");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  GridDev g = to_dev(grid);
+  if ((st = ensure_scratch(ctx, g.ncell)) != FLD_OK) return st;
+  if ((st = reset_status(ctx, s)) != FLD_OK) return st;
+  Opacity op = to_opacity(p);
+  ExchangeParams xp = to_exchange(p, dt);
+  SolveStats ss;
+  cudaError_t e;
+  if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE) {
+    e = launch_exchange(g.ncell, xp, op, rho, nullptr, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
+  }
+  e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
+  if ((st = run_diffuse(ctx, grid, p, dt, ctx->D, E, E, &ss, s)) != FLD_OK) return st;
+  if (p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE) {
+    // eps is unchanged by the diffusion, so kappa^n from the coefficient stage is current
+    e = launch_exchange(g.ncell, xp, op, rho, ctx->kappa, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
+  }
+  unsigned sbits = 0;
+  fld_info tmp;
+  fld_info* inf = info ? info : &tmp;
+  memset(inf, 0, sizeof(*inf));
+  if ((st = read_status(ctx, s, &sbits, &inf->exch_max_iters, &inf->bisection_fallbacks)) != FLD_OK) return st;
+  inf->cycles = ss.cycles;
+  inf->rel_residual = ss.relres;
+  inf->status = ss.status;
+  if (sbits & kStatNonpositive) {
+    inf->status = FLD_ERR_NONPOSITIVE;
+    return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input state");
+  }
+  if (ss.status != FLD_OK)
+    return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
+                ss.relres, ss.cycles);
+  return FLD_OK;
+}
+
+fld_status fld_step_batched(fld_ctx* ctx, int ngrids, const fld_grid* grids, const fld_params* params, const double* dt,
+                            const double* const* rho, double* const* eps, double* const* E, fld_info* infos,
+                            void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ngrids < 0 || (ngrids > 0 && (!grids || !params || !dt || !rho || !eps || !E)))
+    return fail(ctx, FLD_ERR_INVALID_ARG, "ngrids < 0 or NULL host arrays");
+  for (int i = 0; i < ngrids; ++i) {
+    fld_status st = check_grid(ctx, &grids[i]);
+    if (st == FLD_OK) st = check_params(ctx, &params[i], true);
+    if (st == FLD_OK) st = check_coarsest(ctx, &grids[i]);
+    if (st != FLD_OK) return fail(ctx, st, "grid %d: %s", i, std::string(ctx->err).c_str());
+    if (grids[i].ndim < 2) return fail(ctx, FLD_ERR_INVALID_ARG, "grid %d: batched grids need ndim 2 or 3", i);
+    if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(ctx, FLD_ERR_INVALID_ARG, "grid %d: dt must be > 0", i);
+    if (!rho[i] || !eps[i] || !E[i]) return fail(ctx, FLD_ERR_INVALID_ARG, "grid %d: NULL device array", i);
+  }
+  if (ngrids == 0) return FLD_OK;
+  DeviceGuard dg(ctx->device);
+  if (!ctx->batched) {
+    ctx->batched = new (std::nothrow) BatchedSolver();
+    if (!ctx->batched) return fail(ctx, FLD_ERR_CUDA, "out of host memory");
+  }
+  std::string err;
+  fld_status st = ctx->batched->run(ngrids, grids, params, dt, rho, eps, E, infos, (cudaStream_t)stream, &err);
+  if (st != FLD_OK) return fail(ctx, st, "%s", err.c_str());
+  return FLD_OK;
+}
+
+fld_status fld_columns_step(fld_ctx* ctx, int ncol, int ncell, const double* r_faces, int geometry, int bc_lo,
+                            int bc_hi, const double* v_lo, const double* v_hi, const fld_params* p, const double* dt,
+                            const double* rho, double* eps, double* E, fld_info* info, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_params(ctx, p, false);
+  if (st != FLD_OK) return st;
+  std::string err;
+  st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);
+  if (st != FLD_OK) return fail(ctx, st, "%s", err.c_str());
+  if (!rho || !eps || !E) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and E must be non-NULL");
+  if (ncol == 0) return FLD_OK;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = reset_status(ctx, s)) != FLD_OK) return st;
+  if ((st = ensure_geom(ctx, ncell)) != FLD_OK) return st;
+  cudaError_t e = launch_columns_step(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, *p, dt, rho, eps, E,
+                                      ctx->geom, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_columns_step launch");
+  if (info) {
+    unsigned sbits;
+    memset(info, 0, sizeof(*info));
+    if ((st = read_status(ctx, s, &sbits, &info->exch_max_iters, &info->bisection_fallbacks)) != FLD_OK) return st;
+    info->status = (sbits & kStatNonpositive) ? FLD_ERR_NONPOSITIVE : FLD_OK;
+    if (info->status != FLD_OK) return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in a column");
+  }
+  return FLD_OK;
+}
+
+fld_status fld_columns_diffuse(fld_ctx* ctx, int ncol, int ncell, const double* r_faces, int geometry, int bc_lo,
+                               int bc_hi, const double* v_lo, const double* v_hi, const fld_params* p, const double* dt,
+                               const double* D_cell, const double* E_old, double* E_new, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_params(ctx, p, false);
+  if (st != FLD_OK) return st;
+  std::string err;
+  st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);
+  if (st != FLD_OK) return fail(ctx, st, "%s", err.c_str());
+  if (!D_cell || !E_old || !E_new) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell, E_old and E_new must be non-NULL");
+  if (ncol == 0) return FLD_OK;
+  DeviceGuard dg(ctx->device);
+  if ((st = ensure_geom(ctx, ncell)) != FLD_OK) return st;
+  cudaError_t e = launch_columns_diffuse(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, *p, dt, D_cell,
+                                         E_old, E_new, ctx->geom, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_columns_diffuse launch");
+  return FLD_OK;
+}
+
+fld_status fld_trace_enable(fld_ctx* ctx, int on) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (on) tracer().clear();
+  tracer().on = on != 0;
+  return FLD_OK;
+}
+
+fld_status fld_trace_report(fld_ctx* ctx, fld_trace_entry* out, int max, int* n) {
+  if (!ctx || !n || (max > 0 && !out)) return FLD_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  auto rep = tracer().report();
+  int k = 0;
+  for (auto& e : rep) {
+    if (k >= max) break;
+    memset(&out[k], 0, sizeof(fld_trace_entry));
+    snprintf(out[k].name, sizeof(out[k].name), "%s", e.name.c_str());
+    out[k].launches = e.launches;
+    out[k].total_ms = e.ms;
+    ++k;
+  }
+  *n = k;
+  return FLD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,427 @@
+// Batched 1-D radial columns (arXiv 2104.03968: the Sect. 3.4 diffusion with the spherical
+// geometry its Appendix A treats by source terms, written here directly as finite volumes).
+//
+// One thread block advances one column of n <= 2048 cells entirely on chip:
+//   1. opacity kappa(rho, T) and D = c lambda(R)/(kappa rho) per cell (Sect. 2.2), the gradient
+//      in R by the 3-point non-uniform central difference of the stretched grid;
+//   2. rows of the backward-Euler finite-volume operator
+//        x_i + (dt/V_i) [A_+ D_+ (x_i - x_{i+1})/h_+ + A_- D_- (x_i - x_{i-1})/h_-] = E_i,
+//      D on faces by harmonic mean, A = r^2 and V = (r_+^3 - r_-^3)/3 (or 1 and the width);
+//   3. a direct tridiagonal solve: every thread eliminates its chunk of rows down to two
+//      interface rows, parallel cyclic reduction solves the 2P-row interface system in shared
+//      memory, and the chunks back-substitute;
+//   4. the point-implicit exchange (Sect. 3.3) per cell.
+// HBM traffic is one read of rho, eps, E and one write of eps, E per cell.
+#include <cstdio>
+
+#include "columns.h"
+#include "exchange.cuh"
+#include "trace.h"
+
+namespace fld {
+
+enum { kColStep = 0, kColStepExchangeFirst = 1, kColDiffuse = 2 };
+
+// geometry factors shared by all columns: [gl n][gu n][cm n][cp n][hl hr flo fhi]
+__global__ void k_col_geometry(int n, const double* __restrict__ rf, int geometry, double* __restrict__ geom,
+                               unsigned* __restrict__ status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto rc = [&](int k) -> double {
+    if (k < 0) return 0.5 * (rf[0] + rf[1]) - (rf[1] - rf[0]);
+    if (k >= n) return 0.5 * (rf[n - 1] + rf[n]) + (rf[n] - rf[n - 1]);
+    return 0.5 * (rf[k] + rf[k + 1]);
+  };
+  double rl = rf[i], rr = rf[i + 1];
+  if (!(rr > rl) || (geometry == FLD_GEOM_SPHERICAL && !(rl >= 0.0))) {
+    if (status) atomicOr(status, kStatNonpositive);
+  }
+  double c0 = rc(i);
+  double hm = c0 - rc(i - 1), hp = rc(i + 1) - c0;
+  bool sph = geometry == FLD_GEOM_SPHERICAL;
+  double V = sph ? (rr * rr * rr - rl * rl * rl) / 3.0 : rr - rl;
+  double Al = sph ? rl * rl : 1.0, Ar = sph ? rr * rr : 1.0;
+  geom[i] = Al / (V * hm);
+  geom[n + i] = Ar / (V * hp);
+  geom[2 * n + i] = hp / (hm * (hm + hp));
+  geom[3 * n + i] = hm / (hp * (hm + hp));
+  if (i == 0) {
+    geom[4 * n + 0] = hm;
+    geom[4 * n + 2] = hm / (rc(1) - rc(0));
+  }
+  if (i == n - 1) {
+    geom[4 * n + 1] = hp;
+    geom[4 * n + 3] = hp / (rc(n - 1) - rc(n - 2));
+  }
+}
+
+struct ColArgs {
+  int n;
+  int bc_lo, bc_hi;
+  const double* v_lo;
+  const double* v_hi;
+  const double* dt;
+  const double* geom;
+  const double* rho;
+  const double* Din;
+  const double* Ein;
+  double* eps;
+  double* Eout;
+  double c, gamma, gas_R, sigma;
+  int limiter, maxit;
+  Opacity op;
+  int* info_iters;
+  int* info_bisect;
+  unsigned* status;
+};
+
+__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+
+template <int MODE>
+__global__ void k_columns(ColArgs A) {
+  extern __shared__ double sm[];
+  const int n = A.n, P = blockDim.x, t = threadIdx.x;
+  const int M = (n + P - 1) / P;
+  double* sx = sm;       // E^n, then E^{n+1}
+  double* sr = sx + n;   // rho
+  double* se = sr + n;   // eps
+  double* sk = se + n;   // kappa
+  double* sD = sk + n;   // cell D
+  double* sa = sD + n;   // sub-diagonal, then elimination coefficients
+  double* sb = sa + n;
+  double* sc = sb + n;
+  double* sd = sc + n;
+  double* ra = sd + n;   // interface system, 2P rows
+  double* rb = ra + 2 * P;
+  double* rc = rb + 2 * P;
+  double* rd = rc + 2 * P;
+  const long long base = (long long)blockIdx.x * n;
+  const double dtc = A.dt[blockIdx.x];
+  const double vlo = A.v_lo ? A.v_lo[blockIdx.x] : 0.0, vhi = A.v_hi ? A.v_hi[blockIdx.x] : 0.0;
+  const double *gl = A.geom, *gu = A.geom + n, *cm = A.geom + 2 * n, *cp = A.geom + 3 * n;
+  const double hl = A.geom[4 * n], hr = A.geom[4 * n + 1], flo = A.geom[4 * n + 2], fhi = A.geom[4 * n + 3];
+  ExchangeParams xp{A.c, A.sigma, A.gamma, A.gas_R, dtc, A.maxit};
+  int iters = 0, bis = 0;
+  bool bad = false;
+
+  for (int i = t; i < n; i += P) {
+    sx[i] = A.Ein[base + i];
+    if (MODE == kColDiffuse) {
+      sD[i] = A.Din[base + i];
+    } else {
+      sr[i] = A.rho[base + i];
+      se[i] = A.eps[base + i];
+    }
+  }
+  __syncthreads();
+  const int s0 = t * M, s1 = min(s0 + M, n);
+
+  if (MODE == kColStepExchangeFirst) {
+    for (int i = s0; i < s1; ++i) {
+      double e = se[i], E = sx[i];
+      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e));
+      if (exchange_cell(xp, sr[i], k, e, E, iters, bis)) {
+        se[i] = e;
+        sx[i] = E;
+      } else {
+        bad = true;
+      }
+    }
+    __syncthreads();
+  }
+  if (MODE != kColDiffuse) {
+    for (int i = s0; i < s1; ++i) {
+      double e = sx[i], rh = sr[i];
+      double k = opacity(A.op, rh, temperature(A.gamma, A.gas_R, rh, se[i]));
+      sk[i] = k;
+      if (!(e > 0.0) || !(rh > 0.0) || !(k > 0.0) || !(se[i] >= 0.0)) bad = true;
+      double em, ep;
+      if (i > 0) em = sx[i - 1];
+      else if (A.bc_lo == FLD_BC_DIRICHLET) em = vlo;
+      else if (A.bc_lo == FLD_BC_NEUMANN) em = e - vlo * hl;
+      else em = e - (sx[1] - e) * flo;
+      if (i < n - 1) ep = sx[i + 1];
+      else if (A.bc_hi == FLD_BC_DIRICHLET) ep = vhi;
+      else if (A.bc_hi == FLD_BC_NEUMANN) ep = e + vhi * hr;
+      else ep = e + (e - sx[n - 2]) * fhi;
+      double gm = fabs(cp[i] * (ep - e) + cm[i] * (e - em));
+      double q = k * rh;
+      double D;
+      if (A.limiter == FLD_LIMITER_THIRD) {
+        D = A.c / (3.0 * q);
+      } else {
+        double qe = q * e;
+        D = A.c * e * (2.0 * qe + gm) / (qe * (6.0 * qe + 3.0 * gm) + gm * gm);
+      }
+      sD[i] = D;
+    }
+    __syncthreads();
+  }
+
+  // rows of the dt-scaled operator
+  for (int i = s0; i < s1; ++i) {
+    double Dl = i > 0 ? harm(sD[i - 1], sD[i]) : sD[0];
+    double Du = i < n - 1 ? harm(sD[i], sD[i + 1]) : sD[n - 1];
+    double wl = dtc * Dl * gl[i], wu = dtc * Du * gu[i];
+    double a = 0.0, b = 1.0, c = 0.0, d = sx[i];
+    if (i > 0) {
+      a = -wl;
+      b += wl;
+    } else if (A.bc_lo == FLD_BC_DIRICHLET) {
+      b += wl;
+      d += wl * vlo;
+    } else if (A.bc_lo == FLD_BC_NEUMANN) {
+      d -= wl * vlo * hl;
+    } else {
+      b -= wl * flo;
+      c += wl * flo;
+    }
+    if (i < n - 1) {
+      c -= wu;
+      b += wu;
+    } else if (A.bc_hi == FLD_BC_DIRICHLET) {
+      b += wu;
+      d += wu * vhi;
+    } else if (A.bc_hi == FLD_BC_NEUMANN) {
+      d += wu * vhi * hr;
+    } else {
+      b -= wu * fhi;
+      a += wu * fhi;
+    }
+    sa[i] = a;
+    sb[i] = b;
+    sc[i] = c;
+    sd[i] = d;
+  }
+
+  // chunk elimination down to the interface rows (x_s, x_e) of this thread
+  const int m = s1 - s0;
+  double Ra0 = 0.0, Rb0 = 1.0, Rc0 = 0.0, Rd0 = 0.0;  // row of x_s
+  double Ra1 = 0.0, Rb1 = 1.0, Rc1 = 0.0, Rd1 = 0.0;  // row of x_e
+  if (m == 1) {
+    Ra0 = sa[s0];
+    Rb0 = sb[s0];
+    Rc0 = sc[s0];  // zero: the single-row chunk is the last row
+    Rd0 = sd[s0];
+  } else if (m >= 2) {
+    const int s = s0, e = s1 - 1;
+    // downward: alpha_i x_s + beta_i x_i + c_i x_{i+1} = delta_i  (i = s+1 .. e)
+    for (int i = s + 2; i <= e; ++i) {
+      double f = sa[i] / sb[i - 1];
+      sa[i] = -f * sa[i - 1];
+      sb[i] = sb[i] - f * sc[i - 1];
+      sd[i] = sd[i] - f * sd[i - 1];
+    }
+    Ra1 = sa[e];
+    Rb1 = sb[e];
+    Rc1 = sc[e];
+    Rd1 = sd[e];
+    // upward: x_i = d'_i - a'_i x_s - c'_i x_e  (i = e-1 .. s+1)
+    for (int i = e - 1; i > s; --i) {
+      double inv = 1.0 / sb[i];
+      if (i == e - 1) {
+        sa[i] = sa[i] * inv;
+        sc[i] = sc[i] * inv;
+        sd[i] = sd[i] * inv;
+      } else {
+        double g = sc[i];
+        sa[i] = (sa[i] - g * sa[i + 1]) * inv;
+        sd[i] = (sd[i] - g * sd[i + 1]) * inv;
+        sc[i] = -g * sc[i + 1] * inv;
+      }
+    }
+    Ra0 = sa[s];
+    if (m == 2) {
+      Rb0 = sb[s];
+      Rc0 = sc[s];
+      Rd0 = sd[s];
+    } else {
+      double g = sc[s];
+      Rb0 = sb[s] - g * sa[s + 1];
+      Rc0 = -g * sc[s + 1];
+      Rd0 = sd[s] - g * sd[s + 1];
+    }
+  }
+  ra[2 * t] = Ra0;
+  rb[2 * t] = Rb0;
+  rc[2 * t] = Rc0;
+  rd[2 * t] = Rd0;
+  ra[2 * t + 1] = Ra1;
+  rb[2 * t + 1] = Rb1;
+  rc[2 * t + 1] = Rc1;
+  rd[2 * t + 1] = Rd1;
+  __syncthreads();
+
+  // parallel cyclic reduction on the 2P interface rows
+  const int R = 2 * P;
+  for (int st = 1; st < R; st <<= 1) {
+    double na[2], nb[2], nc[2], nd[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int i = 2 * t + h;
+      double a = ra[i], b = rb[i], c = rc[i], d = rd[i];
+      double am = 0, bm = 1, cm_ = 0, dm = 0, ap = 0, bp = 1, cp_ = 0, dp = 0;
+      if (i - st >= 0) {
+        am = ra[i - st];
+        bm = rb[i - st];
+        cm_ = rc[i - st];
+        dm = rd[i - st];
+      }
+      if (i + st < R) {
+        ap = ra[i + st];
+        bp = rb[i + st];
+        cp_ = rc[i + st];
+        dp = rd[i + st];
+      }
+      double k1 = a / bm, k2 = c / bp;
+      na[h] = -am * k1;
+      nc[h] = -cp_ * k2;
+      nb[h] = b - cm_ * k1 - ap * k2;
+      nd[h] = d - dm * k1 - dp * k2;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int i = 2 * t + h;
+      ra[i] = na[h];
+      rb[i] = nb[h];
+      rc[i] = nc[h];
+      rd[i] = nd[h];
+    }
+    __syncthreads();
+  }
+  const double xs = rd[2 * t] / rb[2 * t];
+  const double xe = rd[2 * t + 1] / rb[2 * t + 1];
+  if (m >= 1) sx[s0] = xs;
+  if (m >= 2) {
+    sx[s1 - 1] = xe;
+    for (int i = s0 + 1; i < s1 - 1; ++i) sx[i] = sd[i] - sa[i] * xs - sc[i] * xe;
+  }
+
+  if (MODE == kColStep) {
+    for (int i = s0; i < s1; ++i) {
+      double e = se[i], E = sx[i];
+      if (exchange_cell(xp, sr[i], sk[i], e, E, iters, bis)) {
+        se[i] = e;
+        sx[i] = E;
+      } else {
+        bad = true;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = t; i < n; i += P) {
+    A.Eout[base + i] = sx[i];
+    if (MODE != kColDiffuse) A.eps[base + i] = se[i];
+  }
+  if (MODE != kColDiffuse) {
+    if (bad) atomicOr(A.status, kStatNonpositive);
+    exchange_report(iters, bis, A.info_iters, A.info_bisect);
+  }
+}
+
+fld_status columns_validate(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo, int bc_hi,
+                            const double* v_lo, const double* v_hi, const double* dt, std::string* err) {
+  char buf[256];
+  auto bad = [&](const char* m) {
+    *err = m;
+    return FLD_ERR_INVALID_ARG;
+  };
+  if (ncol < 0) return bad("ncol must be >= 0");
+  if (ncell < 2 || ncell > kColumnMaxCells) {
+    snprintf(buf, sizeof(buf), "ncell must be in [2, %d] (got %d)", kColumnMaxCells, ncell);
+    *err = buf;
+    return ncell > kColumnMaxCells ? FLD_ERR_UNSUPPORTED : FLD_ERR_INVALID_ARG;
+  }
+  if (!r_faces) return bad("r_faces is NULL");
+  if (geometry != FLD_GEOM_CARTESIAN && geometry != FLD_GEOM_SPHERICAL) return bad("unknown geometry");
+  for (int bc : {bc_lo, bc_hi})
+    if (bc != FLD_BC_DIRICHLET && bc != FLD_BC_NEUMANN && bc != FLD_BC_CONTINUOUS)
+      return bad("column boundaries must be Dirichlet, Neumann or continuous");
+  if ((bc_lo != FLD_BC_CONTINUOUS && !v_lo) || (bc_hi != FLD_BC_CONTINUOUS && !v_hi))
+    return bad("v_lo / v_hi are required for Dirichlet and Neumann boundaries");
+  if (!dt) return bad("dt is NULL");
+  return FLD_OK;
+}
+
+static int col_threads(int n) {
+  int need = (n + 7) / 8;
+  int P = 32;
+  while (P < need && P < 256) P <<= 1;
+  return P;
+}
+
+static size_t col_smem(int n, int P) { return (size_t)(9 * n + 8 * P) * sizeof(double); }
+
+template <int MODE>
+static cudaError_t launch_mode(int ncol, int ncell, const double* r_faces, int geometry, ColArgs& A, unsigned* status,
+                               cudaStream_t s) {
+  k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, const_cast<double*>(A.geom), status);
+  int P = col_threads(ncell);
+  size_t smem = col_smem(ncell, P);
+  cudaError_t e = cudaFuncSetAttribute(k_columns<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  TraceScope ts("columns", s);
+  k_columns<MODE><<<ncol, P, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+static ColArgs col_args(int ncell, int bc_lo, int bc_hi, const double* v_lo, const double* v_hi, const fld_params& p,
+                        const double* dt, double* geom) {
+  ColArgs A{};
+  A.n = ncell;
+  A.bc_lo = bc_lo;
+  A.bc_hi = bc_hi;
+  A.v_lo = v_lo;
+  A.v_hi = v_hi;
+  A.dt = dt;
+  A.geom = geom;
+  A.c = p.c;
+  A.gamma = p.gamma;
+  A.gas_R = p.gas_R;
+  A.sigma = p.a_rad * p.c / 4.0;
+  A.limiter = p.limiter;
+  A.maxit = p.exch_maxit > 0 ? p.exch_maxit : 100;
+  A.op.model = p.opacity;
+  A.op.kappa0 = p.kappa0;
+  A.op.kr_a = p.kr_a;
+  A.op.kr_b = p.kr_b;
+  A.op.table = p.table;
+  A.op.tn0 = p.tn[0];
+  A.op.tn1 = p.tn[1];
+  A.op.tlo0 = p.tlo[0];
+  A.op.tlo1 = p.tlo[1];
+  A.op.thi0 = p.thi[0];
+  A.op.thi1 = p.thi[1];
+  return A;
+}
+
+cudaError_t launch_columns_step(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo, int bc_hi,
+                                const double* v_lo, const double* v_hi, const fld_params& p, const double* dt,
+                                const double* rho, double* eps, double* E, double* geom, int* info_iters,
+                                int* info_bisect, unsigned* status, cudaStream_t s) {
+  ColArgs A = col_args(ncell, bc_lo, bc_hi, v_lo, v_hi, p, dt, geom);
+  A.rho = rho;
+  A.Ein = E;
+  A.Eout = E;
+  A.eps = eps;
+  A.info_iters = info_iters;
+  A.info_bisect = info_bisect;
+  A.status = status;
+  if (p.order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE)
+    return launch_mode<kColStepExchangeFirst>(ncol, ncell, r_faces, geometry, A, status, s);
+  return launch_mode<kColStep>(ncol, ncell, r_faces, geometry, A, status, s);
+}
+
+cudaError_t launch_columns_diffuse(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo, int bc_hi,
+                                   const double* v_lo, const double* v_hi, const fld_params& p, const double* dt,
+                                   const double* D_cell, const double* E_old, double* E_new, double* geom,
+                                   cudaStream_t s) {
+  ColArgs A = col_args(ncell, bc_lo, bc_hi, v_lo, v_hi, p, dt, geom);
+  A.Din = D_cell;
+  A.Ein = E_old;
+  A.Eout = E_new;
+  return launch_mode<kColDiffuse>(ncol, ncell, r_faces, geometry, A, nullptr, s);
+}
+
+}  // namespace fld

@@ -1,0 +1,37 @@
+// Point-implicit gas-radiation energy exchange over independent cells (arXiv 2104.03968,
+// Sect. 3.3); the per-cell solve is in exchange.cuh.
+#include "exchange.cuh"
+#include "kernels.h"
+#include "trace.h"
+
+namespace fld {
+
+__global__ void k_exchange(long long n, ExchangeParams p, Opacity op, const double* __restrict__ rho,
+                           const double* __restrict__ kappa_in, double* __restrict__ eps, double* __restrict__ E,
+                           int* __restrict__ info_iters, int* __restrict__ info_bisect, unsigned* __restrict__ status) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int iters = 0, bis = 0;
+  if (idx < n) {
+    double r = rho[idx], e = eps[idx], En = E[idx];
+    double k = kappa_in ? kappa_in[idx] : opacity(op, r, temperature(p.gamma, p.gas_R, r, e));
+    if (exchange_cell(p, r, k, e, En, iters, bis)) {
+      eps[idx] = e;
+      E[idx] = En;
+    } else {
+      atomicOr(status, kStatNonpositive);
+    }
+  }
+  exchange_report(iters, bis, info_iters, info_bisect);
+}
+
+cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity& op, const double* rho,
+                            const double* kappa, double* eps, double* E, int* info_iters, int* info_bisect,
+                            unsigned* status, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  unsigned blocks = (unsigned)((n + kBlock - 1) / kBlock);
+  TraceScope ts("exchange", s);
+  k_exchange<<<blocks, kBlock, 0, s>>>(n, p, op, rho, kappa, eps, E, info_iters, info_bisect, status);
+  return cudaGetLastError();
+}
+
+}  // namespace fld

@@ -1,0 +1,138 @@
+// Per-cell point-implicit gas-radiation energy exchange (arXiv 2104.03968, Sect. 3.3).
+//
+// Backward Euler on the heating/cooling terms gives the quartic
+//     a1 x^4 + (1 + a2) x - (1 + a2) eps^n - a2 E^n = 0,   x = eps^{n+1} in ]0, eps^n + E^n[,
+// with a2 = c kappa rho dt and a1 = 4 kappa rho sigma dt ((gamma-1)/(rho gas_R))^4 (the gas law
+// turns T^4 into a multiple of eps^4), then E^{n+1} = (a1 x^4 + E^n) / (1 + a2).
+//
+// FP64 is scarce on GB300, so the root is found in two phases: the quartic, rescaled to
+// coefficients in (0, 1], is solved by safeguarded Halley iterations in FP32; FP64 Newton steps
+// (FP64 residual, FP32 reciprocal of the derivative) then polish it to FP64 accuracy.
+// Coefficients outside the FP32-safe range take the paper's FP64 Halley iteration, which falls
+// back to bisection after `maxit` iterations.
+#pragma once
+
+#include "fld_common.cuh"
+
+namespace fld {
+
+// FP64 safeguarded Halley on a y^4 + y - cc = 0 over ]0, 1], bisection after maxit iterations.
+__device__ inline double halley64(double a, double cc, int maxit, int* iters, int* bisected) {
+  double lo = 0.0, hi = 1.0, y = cc;
+  int it = 0;
+  const double tol = 4.0 * 2.220446049250313e-16;
+  while (it < maxit) {
+    double y2 = y * y;
+    double f = fma(a * y2, y2, y - cc);
+    if (f == 0.0) {
+      *iters = it;
+      return y;
+    }
+    if (f < 0) lo = y;
+    else hi = y;
+    double f1 = fma(4.0 * a * y2, y, 1.0);
+    double f2 = 12.0 * a * y2;
+    double yn = y - 2.0 * f * f1 / (2.0 * f1 * f1 - f * f2);
+    if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+    ++it;
+    double dy = fabs(yn - y);
+    y = yn;
+    if (dy <= tol * y) {
+      *iters = it;
+      return y;
+    }
+  }
+  *bisected = 1;
+  for (int k = 0; k < 200 && hi - lo > tol * hi; ++k) {
+    double m = 0.5 * (lo + hi);
+    double m2 = m * m;
+    if (fma(a * m2, m2, m - cc) < 0) lo = m;
+    else hi = m;
+  }
+  *iters = it;
+  return 0.5 * (lo + hi);
+}
+
+// Updates (e, E) of one cell in place.  Returns false (and leaves them) on invalid input.
+__device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k, double& e, double& E, int& iters,
+                                     int& bis) {
+  double e0 = e, E0 = E;
+  if (!(r > 0.0) || !(k > 0.0) || !(e0 >= 0.0) || !(E0 >= 0.0)) return false;
+  double S = e0 + E0;
+  if (!(S > 0.0)) return true;
+  double t = (p.gamma - 1.0) / (r * p.gas_R);
+  double t2 = t * t;
+  double kr = k * r;
+  double a1 = 4.0 * kr * p.sigma * p.dt * t2 * t2;
+  double a2 = p.c * kr * p.dt;
+  double u = 1.0 / (1.0 + a2);
+  double invS = 1.0 / S;
+  // y = x / S solves  a y^4 + y - cc = 0,  a = a1 S^3/(1+a2) >= 0,  cc in (0, 1]
+  double a = a1 * S * S * S * u;
+  double cc = fma(a2 * u, E0, e0) * invS;
+  double y;
+  if (a >= 1e-30 && a <= 1e30 && cc >= 1e-30) {
+    // y = ys z with ys = min(cc, (cc/a)^(1/4)) >= root: alpha z^4 + beta z = 1 with
+    // max(alpha, beta) = 1, so the root z lies in [0.72, 1]
+    float af = (float)a, cf = (float)cc;
+    float ys = fminf(cf, sqrtf(sqrtf(cf / af)));
+    float ys2 = ys * ys;
+    float alpha = af * ys2 * ys2 / cf, beta = ys / cf;
+    float z = 1.0f, lo = 0.0f, hi = 1.0f;
+    for (int it = 0; it < 12; ++it) {
+      float z2 = z * z;
+      float f = fmaf(alpha * z2, z2, fmaf(beta, z, -1.0f));
+      ++iters;
+      if (f < 0.0f) lo = z;
+      else hi = z;
+      float f1 = fmaf(4.0f * alpha * z2, z, beta);
+      float f2 = 12.0f * alpha * z2;
+      float zn = z - 2.0f * f * f1 / (2.0f * f1 * f1 - f * f2);
+      if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
+      float dz = fabsf(zn - z);
+      z = zn;
+      if (dz <= 4e-7f * z) break;
+    }
+    y = (double)ys * (double)z;
+    // FP64 Newton polish: f in FP64, 1/f' in FP32 (f' = 4 a y^3 + 1 >= 1)
+    bool done = false;
+    for (int it = 0; it < 8; ++it) {
+      double y2 = y * y;
+      double f = fma(a * y2, y2, y - cc);
+      double f1 = fma(4.0 * a * y2, y, 1.0);
+      double dy = f * (double)(1.0f / (float)f1);
+      y -= dy;
+      ++iters;
+      if (fabs(dy) <= 8.9e-16 * y) {
+        done = true;
+        break;
+      }
+    }
+    if (!done || !(y > 0.0 && y <= 1.0)) {
+      int it2 = 0;
+      y = halley64(a, cc, p.maxit, &it2, &bis);
+      iters += it2;
+    }
+  } else {
+    y = halley64(a, cc, p.maxit, &iters, &bis);
+  }
+  double x = S * y;
+  double x2 = x * x;
+  e = x;
+  E = fma(a1 * x2, x2, E0) * u;
+  return true;
+}
+
+// warp-aggregated diagnostics: max iterations and bisection count
+__device__ inline void exchange_report(int iters, int bis, int* info_iters, int* info_bisect) {
+  for (int o = 16; o > 0; o >>= 1) {
+    iters = max(iters, __shfl_down_sync(0xffffffffu, iters, o));
+    bis += __shfl_down_sync(0xffffffffu, bis, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (iters) atomicMax(info_iters, iters);
+    if (bis) atomicAdd(info_bisect, bis);
+  }
+}
+
+}  // namespace fld

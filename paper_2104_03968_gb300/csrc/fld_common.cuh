@@ -1,0 +1,84 @@
+// Shared device-side definitions of the GB300 FLD library (sm_103a).
+//
+// Grid convention: cell (i,j,k) is element i + n0*(j + n1*k) (x fastest).  Face arrays of
+// axis a hold the n_a + 1 faces along a for every cross-section cell: the x-face f of row
+// (j,k) is element f + (n0+1)*(j + n1*k), the y-face f of column (i,k) is i + n0*(f + (n1+1)*k),
+// the z-face f is i + n0*(j + n1*f).  Face f of axis a lies between cells f-1 and f.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fld.h"
+
+namespace fld {
+
+constexpr int kBlock = 256;
+
+struct GridDev {
+  int n[3];
+  int ndim;
+  int bc[6];
+  double bc_val[6];
+  double dx[3];
+  long long ncell;
+};
+
+struct ExchangeParams {
+  double c, sigma, gamma, gas_R, dt;
+  int maxit;
+};
+
+struct Opacity {
+  int model;
+  double kappa0, kr_a, kr_b;
+  const double* table;
+  int tn0, tn1;
+  double tlo0, tlo1, thi0, thi1;
+};
+
+// device status word: bit flags OR-ed by kernels, read back by the host
+enum : unsigned { kStatNonpositive = 1u, kStatNonfinite = 2u };
+
+__host__ __device__ inline long long face_count(const int n[3], int a) {
+  long long c = 1;
+  for (int b = 0; b < 3; ++b) c *= (b == a) ? (long long)(n[b] + 1) : (long long)n[b];
+  return c;
+}
+
+// index of face f along axis a for the cross-section coordinates of cell (i,j,k)
+__device__ __forceinline__ long long face_index(const int n[3], int a, int i, int j, int k, int f) {
+  if (a == 0) return (long long)f + (long long)(n[0] + 1) * ((long long)j + (long long)n[1] * k);
+  if (a == 1) return (long long)i + (long long)n[0] * ((long long)f + (long long)(n[1] + 1) * k);
+  return (long long)i + (long long)n[0] * ((long long)j + (long long)n[1] * f);
+}
+
+__device__ __forceinline__ long long cell_index(const int n[3], int i, int j, int k) {
+  return (long long)i + (long long)n[0] * ((long long)j + (long long)n[1] * k);
+}
+
+__device__ __forceinline__ double temperature(double gamma, double gas_R, double rho, double eps) {
+  return (gamma - 1.0) * eps / (rho * gas_R);
+}
+
+// Opacity per cell: constant, Kramers-like power law, or bilinear table in (log10 rho,
+// log10 T) on log10 kappa, clamped to the table edges.
+__device__ inline double opacity(const Opacity& o, double rho, double T) {
+  if (o.model == FLD_OPACITY_CONST) return o.kappa0;
+  if (o.model == FLD_OPACITY_KRAMERS) {
+    if (o.kr_a == 1.0 && o.kr_b == -3.5) return o.kappa0 * rho / (T * T * T * sqrt(T));
+    return o.kappa0 * pow(rho, o.kr_a) * pow(T, o.kr_b);
+  }
+  double u = (log10(rho) - o.tlo0) / (o.thi0 - o.tlo0) * (o.tn0 - 1);
+  double v = (log10(T) - o.tlo1) / (o.thi1 - o.tlo1) * (o.tn1 - 1);
+  u = fmin(fmax(u, 0.0), (double)(o.tn0 - 1));
+  v = fmin(fmax(v, 0.0), (double)(o.tn1 - 1));
+  int i = min((int)u, o.tn0 - 2), j = min((int)v, o.tn1 - 2);
+  double fu = u - i, fv = v - j;
+  const double* t = o.table + (long long)i * o.tn1 + j;
+  double l = (1 - fu) * ((1 - fv) * __ldg(t) + fv * __ldg(t + 1)) +
+             fu * ((1 - fv) * __ldg(t + o.tn1) + fv * __ldg(t + o.tn1 + 1));
+  return exp10(l);
+}
+
+}  // namespace fld

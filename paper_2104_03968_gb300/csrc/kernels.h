@@ -1,0 +1,22 @@
+// Internal launcher declarations of the GB300 FLD library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fld_common.cuh"
+
+namespace fld {
+
+cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
+                          int limiter, const double* E, const double* rho, const double* eps,
+                          double* kappa_out, double* D_out, unsigned* status, cudaStream_t s);
+
+// w64[a] (and w32[a] when non-null) receive the face weights of axis a (layout of fld_common.cuh)
+cudaError_t launch_faces(const GridDev& g, double dt, const double* D, double* const w64[3], float* const w32[3],
+                         cudaStream_t s);
+
+cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity& op, const double* rho,
+                            const double* kappa, double* eps, double* E, int* info_iters, int* info_bisect,
+                            unsigned* status, cudaStream_t s);
+
+}  // namespace fld

@@ -1,0 +1,99 @@
+// Geometric multigrid for the backward-Euler FLD diffusion operator (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <array>
+#include <string>
+#include <vector>
+
+#include "fld_common.cuh"
+
+namespace fld {
+
+// One 256-byte-aligned device allocation carved into sub-buffers.
+class DeviceArena {
+ public:
+  DeviceArena() = default;
+  ~DeviceArena();
+  DeviceArena(const DeviceArena&) = delete;
+  DeviceArena& operator=(const DeviceArena&) = delete;
+  cudaError_t reserve(size_t bytes);
+  void* take(size_t bytes);
+  void release();
+  size_t capacity() const { return cap_; }
+
+ private:
+  char* base_ = nullptr;
+  size_t cap_ = 0, used_ = 0;
+};
+
+template <class T>
+struct LevelDev {
+  int n[3];
+  int ndim;
+  int bc[6];
+  const T* w[3];
+};
+
+struct SolveStats {
+  int cycles = 0;
+  double relres = 0.0;
+  int status = FLD_OK;
+};
+
+// Operator A = I + dt * (-div D grad) on one grid, solved by an outer FP64 defect-correction
+// loop around V-cycles in precision T (double: the plain FP64 solver; float: the mixed form).
+class Multigrid {
+ public:
+  Multigrid() = default;
+  ~Multigrid();
+  Multigrid(const Multigrid&) = delete;
+  Multigrid& operator=(const Multigrid&) = delete;
+
+  // (Re)build the level hierarchy for grid g and precision; keeps buffers when unchanged.
+  cudaError_t configure(const GridDev& g, int precision);
+  // Face weights, diagonals and coarse operators from the cell-centred D; rhs from E_old.
+  cudaError_t setup(double dt, const double* D_cell, const double* E_old, unsigned* status, cudaStream_t s);
+  // Outer iterations until ||b - A x||/||b|| <= rtol or max_cycles V-cycles; writes E_new.
+  cudaError_t solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
+                    SolveStats* st, cudaStream_t s);
+
+  int levels() const { return (int)dims_.size(); }
+  const GridDev& grid() const { return g_; }
+
+ private:
+  template <class T>
+  cudaError_t setup_t(double dt, const double* D_cell, const double* E_old, cudaStream_t s);
+  template <class T>
+  cudaError_t solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
+                      SolveStats* st, cudaStream_t s);
+  template <class T>
+  cudaError_t vcycle(int l, int nu1, int nu2, cudaStream_t s);
+
+  GridDev g_{};
+  int precision_ = -1;
+  bool configured_ = false;
+  std::vector<std::array<int, 3>> dims_;
+  DeviceArena arena_;
+  // FP64 outer operator and iterate
+  double* w64_[3] = {nullptr, nullptr, nullptr};
+  double* b64_ = nullptr;
+  double* xa_ = nullptr;
+  double* xb_ = nullptr;
+  double* partials_ = nullptr;
+  double* scal_ = nullptr;      // [0] = ||r||^2, [1] = ||b||^2
+  double* host_scal_ = nullptr; // pinned mirror
+  int nparts_ = 0;
+  // inner levels (type-erased; cast to T per precision)
+  struct LevelBuf {
+    void* w[3];
+    void* invd;
+    void* x;
+    void* r;
+    void* tmp;
+  };
+  std::vector<LevelBuf> lv_;
+};
+
+}  // namespace fld

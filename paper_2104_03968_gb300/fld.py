@@ -1,0 +1,340 @@
+"""Thin ctypes binding over the C ABI of ``include/fld.h`` (libfld.so, sm_103a).
+
+Argument marshalling only: every step of the update runs in the CUDA library.
+Device arrays are float64, contiguous torch CUDA tensors (x fastest, i.e. a torch
+tensor of shape (nz, ny, nx)); the stream is torch's current stream.  Host arrays
+(numpy or CPU tensors) are accepted by ``step`` / ``columns_step`` / ``step_batched``,
+which then copy them to the device and back around the call.
+
+Parameter dictionaries follow the plain-data schema of ``inputs``: a grid dict
+(ndim, n, dx, bc names, bc_val) and a physics dict (c, a_rad, gamma, gas_R, limiter,
+opacity, kappa0, kr_a, kr_b, table, tlo, thi) extended by solver keys (precision
+"fp64" | "mixed", rtol, max_cycles, nu1, nu2, exch_maxit, order).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3}
+LIMITER = {"lp": 0, "third": 1}
+OPACITY = {"const": 0, "kramers": 1, "table": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+ORDER = {"diffuse_then_exchange": 0, "exchange_then_diffuse": 1}
+GEOMETRY = {"cartesian": 0, "spherical": 1}
+STATUS = {0: "ok", 1: "invalid argument", 2: "non-positive input", 3: "non-finite residual",
+          4: "not converged", 5: "CUDA error", 6: "device timeout", 7: "unsupported"}
+
+
+class FldError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fld status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class Grid(ct.Structure):
+    _fields_ = [("ndim", ct.c_int), ("n", ct.c_int * 3), ("dx", ct.c_double * 3), ("bc", ct.c_int * 6),
+                ("bc_val", ct.c_double * 6)]
+
+
+class Params(ct.Structure):
+    _fields_ = [("c", ct.c_double), ("a_rad", ct.c_double), ("gamma", ct.c_double), ("gas_R", ct.c_double),
+                ("limiter", ct.c_int), ("opacity", ct.c_int), ("kappa0", ct.c_double), ("kr_a", ct.c_double),
+                ("kr_b", ct.c_double), ("table", ct.c_void_p), ("tn", ct.c_int * 2), ("tlo", ct.c_double * 2),
+                ("thi", ct.c_double * 2), ("precision", ct.c_int), ("rtol", ct.c_double),
+                ("max_cycles", ct.c_int), ("nu1", ct.c_int), ("nu2", ct.c_int), ("exch_maxit", ct.c_int),
+                ("order", ct.c_int)]
+
+
+class Info(ct.Structure):
+    _fields_ = [("cycles", ct.c_int), ("rel_residual", ct.c_double), ("exch_max_iters", ct.c_int),
+                ("bisection_fallbacks", ct.c_int), ("status", ct.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+P = ct.c_void_p
+_SIGS = {
+    "fld_ctx_create": [ct.POINTER(ct.c_void_p), ct.c_int],
+    "fld_ctx_destroy": [P],
+    "fld_coeffs": [P, P, P, P, P, P, P, P, P],
+    "fld_diffuse": [P, P, P, ct.c_double, P, P, P, P, P],
+    "fld_exchange": [P, ct.c_size_t, P, ct.c_double, P, P, P, P, P, P],
+    "fld_step": [P, P, P, ct.c_double, P, P, P, P, P],
+    "fld_step_batched": [P, ct.c_int, P, P, P, P, P, P, P, P],
+    "fld_columns_step": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P, P],
+    "fld_columns_diffuse": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libfld.so (building it with nvcc if it is missing or stale).  Raises if the CUDA
+    library cannot be built or loaded: there is no CPU fallback."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing")
+            lib = ct.CDLL(path)
+            for name, args in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = ct.c_int
+            lib.fld_last_error.argtypes = [P]
+            lib.fld_last_error.restype = ct.c_char_p
+            _lib = lib
+    return _lib
+
+
+class Context:
+    """An fld_ctx bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        h = ct.c_void_p()
+        st = self.lib.fld_ctx_create(ct.byref(h), int(device))
+        if st:
+            raise FldError(st, f"fld_ctx_create(device={device}) failed")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fld_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int):
+        if st:
+            raise FldError(st, self.lib.fld_last_error(self.h).decode())
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ct.c_void_p(t.data_ptr())
+
+
+def grid_struct(g: dict) -> Grid:
+    s = Grid()
+    s.ndim = int(g["ndim"])
+    n = list(g["n"]) + [1] * (3 - len(g["n"]))
+    dx = list(g.get("dx", [1.0] * 3))
+    dx = dx + [1.0] * (3 - len(dx))
+    for a in range(3):
+        s.n[a] = int(n[a])
+        s.dx[a] = float(dx[a])
+    bc = list(g.get("bc", ["periodic"] * 6))
+    bv = list(g.get("bc_val", [0.0] * 6))
+    for f in range(6):
+        s.bc[f] = BC[bc[f]] if isinstance(bc[f], str) else int(bc[f])
+        s.bc_val[f] = float(bv[f])
+    return s
+
+
+def params_struct(p: dict, keep: list, device) -> Params:
+    s = Params()
+    s.c, s.a_rad, s.gamma, s.gas_R = (float(p[k]) for k in ("c", "a_rad", "gamma", "gas_R"))
+    s.limiter = LIMITER[p.get("limiter", "lp")]
+    s.opacity = OPACITY[p.get("opacity", "const")]
+    s.kappa0 = float(p.get("kappa0", 1.0))
+    s.kr_a = float(p.get("kr_a", 1.0))
+    s.kr_b = float(p.get("kr_b", -3.5))
+    if s.opacity == OPACITY["table"]:
+        tab = p["table"]
+        if not isinstance(tab, torch.Tensor) or not tab.is_cuda:
+            tab = torch.as_tensor(np.ascontiguousarray(tab), dtype=torch.float64, device=device)
+        tab = tab.contiguous()
+        keep.append(tab)
+        s.table = tab.data_ptr()
+        s.tn[0], s.tn[1] = tab.shape
+        s.tlo[0], s.tlo[1] = (float(v) for v in p["tlo"])
+        s.thi[0], s.thi[1] = (float(v) for v in p["thi"])
+    s.precision = PRECISION[p.get("precision", "fp64")]
+    s.rtol = float(p.get("rtol", 1e-10))
+    s.max_cycles = int(p.get("max_cycles", 0))
+    s.nu1 = int(p.get("nu1", 0))
+    s.nu2 = int(p.get("nu2", 0))
+    s.exch_maxit = int(p.get("exch_maxit", 0))
+    s.order = ORDER[p.get("order", "diffuse_then_exchange")]
+    return s
+
+
+def _device_of(ctx: Context):
+    return torch.device("cuda", ctx.device)
+
+
+def to_device(a, ctx: Context) -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        return a.to(device=_device_of(ctx), dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=_device_of(ctx))
+
+
+# ----------------------------------------------------------------------------- calls
+
+def coeffs(ctx: Context, grid: dict, params: dict, E, rho, eps):
+    """Per-cell (kappa, D) on the device (Sect. 2.2).  Inputs are CUDA tensors."""
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    kappa = torch.empty_like(E)
+    D = torch.empty_like(E)
+    ctx.check(ctx.lib.fld_coeffs(ctx.h, ct.byref(g), ct.byref(p), _dptr(E), _dptr(rho), _dptr(eps), _dptr(kappa),
+                                 _dptr(D), _stream()))
+    return kappa, D
+
+
+def diffuse(ctx: Context, grid: dict, params: dict, dt: float, D, E_old, out=None):
+    """Backward-Euler diffusion solve (Sect. 3.4) by multigrid.  Returns (E_new, info)."""
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    E_new = torch.empty_like(E_old) if out is None else out
+    info = Info()
+    st = ctx.lib.fld_diffuse(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(D), _dptr(E_old), _dptr(E_new),
+                             ct.byref(info), _stream())
+    if st and st != 4:
+        ctx.check(st)
+    return E_new, info.as_dict()
+
+
+def exchange(ctx: Context, params: dict, dt: float, rho, eps, E, kappa=None) -> dict:
+    """Point-implicit exchange (Sect. 3.3), in place on eps and E (CUDA tensors)."""
+    keep = []
+    p = params_struct(params, keep, _device_of(ctx))
+    info = Info()
+    ctx.check(ctx.lib.fld_exchange(ctx.h, E.numel(), ct.byref(p), float(dt), _dptr(rho), _dptr(kappa), _dptr(eps),
+                                   _dptr(E), ct.byref(info), _stream()))
+    return info.as_dict()
+
+
+def step(ctx: Context, grid: dict, params: dict, dt: float, rho, eps, E, allow_unconverged: bool = False) -> dict:
+    """One full update in place on eps and E.  CUDA tensors are updated in place; host arrays
+    are copied to the device, updated, and copied back into the same host buffers."""
+    host = not (isinstance(E, torch.Tensor) and E.is_cuda)
+    if host:
+        hr, he, hE = rho, eps, E
+        rho, eps, E = to_device(rho, ctx), to_device(eps, ctx), to_device(E, ctx)
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    info = Info()
+    st = ctx.lib.fld_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(rho), _dptr(eps), _dptr(E),
+                          ct.byref(info), _stream())
+    if st and not (allow_unconverged and st == 4):
+        ctx.check(st)
+    if host:
+        _copy_back(he, eps)
+        _copy_back(hE, E)
+    return info.as_dict()
+
+
+def _copy_back(host, dev: torch.Tensor):
+    if isinstance(host, torch.Tensor):
+        host.copy_(dev.reshape(host.shape))
+    else:
+        host[...] = dev.cpu().numpy().reshape(host.shape)
+
+
+def step_batched(ctx: Context, grids: list, params: list, dts, rhos: list, epss: list, Es: list) -> list:
+    """fld_step on many independent grids (CUDA tensors, updated in place)."""
+    n = len(grids)
+    keep = []
+    G = (Grid * n)(*[grid_struct(g) for g in grids])
+    Pp = (Params * n)(*[params_struct(p, keep, _device_of(ctx)) for p in params])
+    DT = (ct.c_double * n)(*[float(d) for d in dts])
+    R = (ct.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    EP = (ct.c_void_p * n)(*[e.data_ptr() for e in epss])
+    EE = (ct.c_void_p * n)(*[e.data_ptr() for e in Es])
+    for t in list(rhos) + list(epss) + list(Es):
+        _dptr(t)
+    infos = (Info * n)()
+    ctx.check(ctx.lib.fld_step_batched(ctx.h, n, G, Pp, DT, R, EP, EE, infos, _stream()))
+    return [i.as_dict() for i in infos]
+
+
+def columns_step(ctx: Context, r_faces, geometry: str, bc: tuple, v_lo, v_hi, params: dict, dt, rho, eps, E) -> dict:
+    """Full update of many 1-D radial columns: rho, eps, E of shape (ncol, ncell) updated in place
+    (CUDA tensors) or copied through the device (host arrays)."""
+    host = not (isinstance(E, torch.Tensor) and E.is_cuda)
+    if host:
+        he, hE = eps, E
+        rho, eps, E = to_device(rho, ctx), to_device(eps, ctx), to_device(E, ctx)
+    ncol, ncell = E.shape
+    keep = []
+    rf = to_device(r_faces, ctx)
+    vl = None if v_lo is None else to_device(v_lo, ctx)
+    vh = None if v_hi is None else to_device(v_hi, ctx)
+    dtt = to_device(np.broadcast_to(np.asarray(dt, dtype=np.float64), (ncol,)).copy() if not isinstance(dt, torch.Tensor) else dt, ctx)
+    keep += [rf, vl, vh, dtt]
+    p = params_struct(params, keep, _device_of(ctx))
+    info = Info()
+    ctx.check(ctx.lib.fld_columns_step(ctx.h, ncol, ncell, _dptr(rf), GEOMETRY[geometry], BC[bc[0]], BC[bc[1]],
+                                       _dptr(vl), _dptr(vh), ct.byref(p), _dptr(dtt), _dptr(rho), _dptr(eps),
+                                       _dptr(E), ct.byref(info), _stream()))
+    if host:
+        _copy_back(he, eps)
+        _copy_back(hE, E)
+    return info.as_dict()
+
+
+def columns_diffuse(ctx: Context, r_faces, geometry: str, bc: tuple, v_lo, v_hi, params: dict, dt, D, E_old):
+    """Tridiagonal diffusion stage of many columns with a given cell D.  Returns E_new."""
+    ncol, ncell = E_old.shape
+    keep = []
+    rf = to_device(r_faces, ctx)
+    vl = None if v_lo is None else to_device(v_lo, ctx)
+    vh = None if v_hi is None else to_device(v_hi, ctx)
+    dtt = to_device(np.broadcast_to(np.asarray(dt, dtype=np.float64), (ncol,)).copy() if not isinstance(dt, torch.Tensor) else dt, ctx)
+    keep += [rf, vl, vh, dtt]
+    p = params_struct(params, keep, _device_of(ctx))
+    E_new = torch.empty_like(E_old)
+    ctx.check(ctx.lib.fld_columns_diffuse(ctx.h, ncol, ncell, _dptr(rf), GEOMETRY[geometry], BC[bc[0]], BC[bc[1]],
+                                          _dptr(vl), _dptr(vh), ct.byref(p), _dptr(dtt), _dptr(D), _dptr(E_old),
+                                          _dptr(E_new), _stream()))
+    torch.cuda.current_stream().synchronize()
+    return E_new
+
+
+class TraceEntry(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int), ("total_ms", ct.c_double)]
+
+
+def trace_enable(ctx: Context, on: bool = True):
+    """Start (clearing the record) or stop per-kernel launch timing with CUDA events."""
+    ctx.lib.fld_trace_enable.argtypes = [P, ct.c_int]
+    ctx.check(ctx.lib.fld_trace_enable(ctx.h, 1 if on else 0))
+
+
+def trace_report(ctx: Context) -> dict:
+    """{kernel name: (launches, total device ms)} since the last trace_enable(True)."""
+    ctx.lib.fld_trace_report.argtypes = [P, P, ct.c_int, ct.POINTER(ct.c_int)]
+    buf = (TraceEntry * 256)()
+    n = ct.c_int()
+    ctx.check(ctx.lib.fld_trace_report(ctx.h, buf, 256, ct.byref(n)))
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}

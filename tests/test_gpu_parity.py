@@ -1,0 +1,400 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances: FP64 results within 1e-10 relative (max-norm over the field, so cells at the
+1e-6 floor do not dominate); the mixed form's residual, measured with the oracle's own FP64
+operator, within its rtol.  Integer diagnostics are compared exactly where they are unique.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_03968_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2104_03968_gb300 import fld
+    c = fld.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def relerr(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def solver(phys, **kw):
+    p = dict(phys)
+    p.update(kw)
+    return p
+
+
+BCS = {
+    "periodic": (["periodic"] * 6, [0.0] * 6),
+    "neumann": (["neumann"] * 6, [0.05, -0.02, 0.0, 0.1, 0.03, 0.0]),
+    "dirichlet": (["dirichlet"] * 6, [0.8, 1.2, 0.5, 0.9, 1.1, 0.3]),
+    "mixed": (["dirichlet", "neumann", "periodic", "periodic", "neumann", "dirichlet"], [1.5, 0.2, 0, 0, -0.1, 0.7]),
+    "continuous": (["continuous"] * 4 + ["periodic"] * 2, [0.0] * 6),
+}
+
+
+# ----------------------------------------------------------------------------- coefficients
+
+@pytest.mark.parametrize("shape", [(70, 45), (24, 20, 18), (300,)])
+@pytest.mark.parametrize("bcname", ["periodic", "neumann", "dirichlet", "mixed", "continuous"])
+@pytest.mark.parametrize("limiter", ["lp", "third"])
+def test_coeffs_parity(ctx, shape, bcname, limiter):
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=len(shape) * 7 + len(bcname), bc=BCS[bcname], limiter=limiter)
+    g, p = case["grid"], case["phys"]
+    kap_o = oracle.opacity(p, case["rho"], case["eps"])
+    D_o = oracle.coeffs(g, p, case["E"], case["rho"], kap_o)
+    kap, D = fld.coeffs(ctx, g, p, dev(case["E"]), dev(case["rho"]), dev(case["eps"]))
+    torch.cuda.synchronize()
+    assert relerr(host(kap).reshape(kap_o.shape), kap_o) < 1e-13
+    assert np.abs(host(D).reshape(D_o.shape) / D_o - 1).max() < 1e-12
+
+
+def test_coeffs_table_opacity(ctx):
+    from paper_2104_03968_gb300 import fld
+    case = inputs.wind_columns(ncol=4, ncell=64)
+    p = case["phys"]
+    n = case["rho"].size
+    g = {"ndim": 1, "n": [n, 1, 1], "dx": [1.0, 1, 1], "bc": ["continuous"] * 2 + ["periodic"] * 4,
+         "bc_val": [0.0] * 6}
+    rho, eps, E = case["rho"].ravel(), case["eps"].ravel(), case["E"].ravel()
+    kap_o = oracle.opacity(p, rho, eps)
+    kap, D = fld.coeffs(ctx, g, p, dev(E), dev(rho), dev(eps))
+    torch.cuda.synchronize()
+    assert np.abs(host(kap) / kap_o - 1).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------- exchange
+
+@pytest.mark.parametrize("units", ["code", "cgs"])
+def test_exchange_parity(ctx, units):
+    from paper_2104_03968_gb300 import fld
+    rng = np.random.default_rng(17)
+    n = 100_003  # several blocks and a ragged tail
+    if units == "code":
+        phys = inputs.code_units()
+        rho, kap = 10 ** rng.uniform(-3, 3, n), 10 ** rng.uniform(-3, 3, n)
+        eps, E = 10 ** rng.uniform(-4, 4, n), 10 ** rng.uniform(-4, 4, n)
+        dts = (1e-4, 1.0, 1e4)
+    else:
+        phys = inputs.cgs_units(0.6)
+        rho, kap = 10 ** rng.uniform(-12, -4, n), 10 ** rng.uniform(-1, 2, n)
+        T = 10 ** rng.uniform(3.5, 7, n)
+        eps = inputs.equilibrium_eps(phys, rho, T * 10 ** rng.uniform(-2, 2, n))
+        E = inputs.rad_energy(phys, T)
+        dts = (1e-14, 1e-10, 1e-6)
+    for dt in dts:
+        e_o, E_o, _ = oracle.exchange(phys, dt, rho, kap, eps, E)
+        te, tE = dev(eps), dev(E)
+        info = fld.exchange(ctx, phys, dt, dev(rho), te, tE, kappa=dev(kap))
+        assert np.abs(host(te) / e_o - 1).max() < 1e-12
+        assert np.abs(host(tE) / E_o - 1).max() < 1e-12
+        assert info["bisection_fallbacks"] == 0
+        assert info["status"] == 0
+
+
+def test_exchange_extreme_coefficients_take_fp64_path(ctx):
+    """Coefficients outside the FP32-safe range (very hot gas with a huge dt) still give the
+    root of the quartic."""
+    from paper_2104_03968_gb300 import fld
+    phys = inputs.code_units()
+    rho = np.array([1e-8, 1.0, 1e6, 1.0])
+    kap = np.array([1e8, 1e-9, 1e3, 1.0])
+    eps = np.array([1e10, 1e-20, 1e-12, 0.0])
+    E = np.array([1e-10, 1e20, 1e12, 2.0])
+    for dt in (1e-8, 1e8):
+        e_o, E_o, _ = oracle.exchange(phys, dt, rho, kap, eps, E)
+        te, tE = dev(eps), dev(E)
+        fld.exchange(ctx, phys, dt, dev(rho), te, tE, kappa=dev(kap))
+        assert np.allclose(host(te), e_o, rtol=1e-12, atol=0)
+        assert np.allclose(host(tE), E_o, rtol=1e-12, atol=0)
+
+
+def test_exchange_heating_cooling_setup(ctx):
+    """The paper's heating/cooling relaxation (Sect. 4.1) stepped on the GPU matches the oracle
+    step by step."""
+    from paper_2104_03968_gb300 import fld
+    for ratio in (1e-6, 1e2):
+        for dt in (1e-12, 1e-11):
+            case = inputs.heating_cooling(ratio, dt)
+            p = case["phys"]
+            kap = np.full_like(case["rho"], 0.4)
+            eo, Eo = case["eps"].copy(), case["E"].copy()
+            te, tE = dev(eo), dev(Eo)
+            for _ in range(50):
+                eo, Eo, _ = oracle.exchange(p, dt, case["rho"], kap, eo, Eo)
+                fld.exchange(ctx, p, dt, dev(case["rho"]), te, tE, kappa=dev(kap))
+            assert np.abs(host(te) / eo - 1).max() < 1e-11
+            assert np.abs(host(tE) / Eo - 1).max() < 1e-11
+
+
+# ----------------------------------------------------------------------------- diffusion
+
+@pytest.mark.parametrize("shape", [(64, 48), (32, 24, 16), (256,)])
+@pytest.mark.parametrize("bcname", ["periodic", "neumann", "dirichlet", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_diffuse_parity(ctx, shape, bcname, precision):
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=3 + len(shape), bc=BCS[bcname], dt_factor=100.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    ref = oracle.diffuse(g, case["dt"], D, case["E"], rtol=1e-14)
+    rtol = 1e-13 if precision == "fp64" else 1e-12
+    out, info = fld.diffuse(ctx, g, solver(p, precision=precision, rtol=rtol), case["dt"], dev(D), dev(case["E"]))
+    x = host(out).reshape(ref.shape)
+    assert info["status"] == 0, info
+    assert info["rel_residual"] <= rtol
+    assert oracle.relres(g, case["dt"], D, case["E"], x) < 3 * rtol
+    assert relerr(x, ref) < TOL
+
+
+def test_diffuse_continuous_boundary(ctx):
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small((32, 16), seed=5, bc=BCS["continuous"], dt_factor=2.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    ref = oracle.diffuse(g, case["dt"], D, case["E"], method="dense")
+    out, info = fld.diffuse(ctx, g, solver(p, rtol=1e-13), case["dt"], dev(D), dev(case["E"]))
+    assert info["status"] == 0, info
+    assert relerr(host(out).reshape(ref.shape), ref) < TOL
+
+
+def test_diffuse_fourier_closed_form(ctx):
+    """Uniform D, periodic: the GPU solve hits the Fourier closed form of backward Euler."""
+    from paper_2104_03968_gb300 import fld
+    rng = np.random.default_rng(1)
+    n = (40, 24, 32)
+    g = {"ndim": 3, "n": list(n), "dx": [1.0, 0.5, 2.0], "bc": ["periodic"] * 6, "bc_val": [0.0] * 6}
+    E = 1 + rng.random(tuple(reversed(n)))
+    Dval, dt = 0.37, 3.3
+    out, info = fld.diffuse(ctx, g, solver(inputs.code_units(), rtol=1e-14, max_cycles=200), dt,
+                            dev(np.full(E.shape, Dval)), dev(E))
+    shape = E.shape
+    sym = np.zeros(shape)
+    for ax, dxa in zip(range(3), (2.0, 0.5, 1.0)):
+        k = 2 * np.pi * np.fft.fftfreq(shape[ax])
+        s = (4.0 / dxa ** 2) * np.sin(k / 2) ** 2
+        sl = [None] * 3
+        sl[ax] = slice(None)
+        sym = sym + s[tuple(sl)]
+    ref = np.real(np.fft.ifftn(np.fft.fftn(E) / (1 + dt * Dval * sym)))
+    assert relerr(host(out), ref) < 1e-12
+
+
+def test_diffuse_in_place_alias(ctx):
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small((32, 32), seed=9)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    ref = oracle.diffuse(g, case["dt"], D, case["E"], rtol=1e-14)
+    E = dev(case["E"])
+    fld.diffuse(ctx, g, solver(p, rtol=1e-13), case["dt"], dev(D), E, out=E)
+    assert relerr(host(E), ref) < TOL
+
+
+# ----------------------------------------------------------------------------- full step
+
+@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_parity_lognormal(ctx, order, precision):
+    from paper_2104_03968_gb300 import fld
+    case = inputs.lognormal_3d(n=32, seed=11)
+    g, p = case["grid"], case["phys"]
+    e_o, E_o, _ = oracle.step(g, p, case["dt"], case["rho"], case["eps"], case["E"], order=order, rtol=1e-14)
+    eps, E = dev(case["eps"]), dev(case["E"])
+    rtol = 1e-13 if precision == "fp64" else 1e-12
+    info = fld.step(ctx, g, solver(p, precision=precision, rtol=rtol, order=order), case["dt"], dev(case["rho"]), eps, E)
+    assert info["status"] == 0
+    assert relerr(host(E), E_o) < TOL
+    assert relerr(host(eps), e_o) < TOL
+
+
+def test_gaussian_pulse_twenty_steps(ctx):
+    """64x64 Gaussian pulse: 20 steps at 10x the explicit limit to 1e-12, then 10 exchange steps
+    from T_gas = 2 T_rad; every step against the oracle."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.gaussian_pulse_2d()
+    g, p = case["grid"], case["phys"]
+    sp = solver(p, rtol=1e-12)
+    Eo, eo = case["E"].copy(), case["eps"].copy()
+    E, eps, rho = dev(Eo), dev(eo), dev(case["rho"])
+    for _ in range(20):
+        kap = oracle.opacity(p, case["rho"], eo)
+        D = oracle.coeffs(g, p, Eo, case["rho"], kap)
+        Eo = oracle.diffuse(g, case["dt"], D, Eo, rtol=1e-14)
+        _, D_g = fld.coeffs(ctx, g, p, E, rho, eps)
+        E, info = fld.diffuse(ctx, g, sp, case["dt"], D_g, E)
+        assert info["rel_residual"] <= 1e-12
+    assert relerr(host(E), Eo) < TOL
+    # exchange phase: T_gas = 2 T_rad
+    T = inputs.rad_temperature(p, Eo)
+    eo = inputs.equilibrium_eps(p, case["rho"], 2 * T)
+    eps = dev(eo)
+    E = dev(Eo)
+    kap = np.full_like(Eo, p["kappa0"])
+    for _ in range(10):
+        eo, Eo, _ = oracle.exchange(p, case["dt"], case["rho"], kap, eo, Eo)
+        fld.exchange(ctx, p, case["dt"], rho, eps, E, kappa=dev(kap))
+    assert relerr(host(E), Eo) < TOL and relerr(host(eps), eo) < TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_full_size_128(ctx, precision):
+    """The 128^3 lognormal workload at its full size and rtol: the oracle's FP64 operator applied
+    to the GPU result meets rtol, and sampled cells of the exchange match the oracle."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.lognormal_3d(n=128, seed=1)
+    g, p = case["grid"], case["phys"]
+    rtol = 1e-10 if precision == "fp64" else 1e-8
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    out, info = fld.diffuse(ctx, g, solver(p, precision=precision, rtol=rtol), case["dt"], dev(D), dev(case["E"]))
+    x = host(out).reshape(case["E"].shape)
+    assert info["status"] == 0
+    assert oracle.relres(g, case["dt"], D, case["E"], x) <= 1.01 * rtol
+    # full step: coefficients on the GPU, exchange on sampled cells against the oracle
+    eps, E = dev(case["eps"]), dev(case["E"])
+    info = fld.step(ctx, g, solver(p, precision=precision, rtol=rtol), case["dt"], dev(case["rho"]), eps, E)
+    assert info["status"] == 0
+    rng = np.random.default_rng(0)
+    idx = rng.choice(x.size, 4096, replace=False)
+    e_s, E_s, _ = oracle.exchange(p, case["dt"], case["rho"].ravel()[idx], kap.ravel()[idx],
+                                  case["eps"].ravel()[idx], x.ravel()[idx])
+    # the GPU's diffusion result differs from x by at most the solve tolerance amplification
+    tol = 1e-7 if precision == "fp64" else 1e-5
+    assert np.abs(host(E).ravel()[idx] / E_s - 1).max() < tol
+    assert np.abs(host(eps).ravel()[idx] / e_s - 1).max() < tol
+
+
+# ----------------------------------------------------------------------------- columns
+
+def _column_case(ncol, ncell, seed=0):
+    case = inputs.wind_columns(ncol=ncol, ncell=ncell, seed=seed)
+    return case
+
+
+@pytest.mark.parametrize("ncell", [64, 100, 2048])
+@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
+def test_columns_step_parity(ctx, ncell, order):
+    from paper_2104_03968_gb300 import fld
+    ncol = 6
+    case = _column_case(ncol, ncell)
+    p = solver(case["phys"], order=order)
+    col = {"r_faces": case["r_faces"], "geometry": "spherical", "bc": case["bc"]}
+    eps, E = dev(case["eps"]), dev(case["E"])
+    info = fld.columns_step(ctx, case["r_faces"], "spherical", tuple(case["bc"]), case["bc_lo"], case["bc_hi"], p,
+                            case["dt"], dev(case["rho"]), eps, E)
+    assert info["status"] == 0
+    for j in range(ncol):
+        e_o, E_o, _ = oracle.column_step(col, p, case["dt"][j], case["rho"][j], case["eps"][j], case["E"][j],
+                                         case["bc_lo"][j], case["bc_hi"][j], order=order)
+        assert relerr(host(E)[j], E_o) < TOL
+        assert relerr(host(eps)[j], e_o) < TOL
+
+
+@pytest.mark.parametrize("geometry", ["spherical", "cartesian"])
+@pytest.mark.parametrize("bc", [("dirichlet", "dirichlet"), ("neumann", "dirichlet"), ("continuous", "neumann")])
+def test_columns_diffuse_parity(ctx, geometry, bc):
+    from paper_2104_03968_gb300 import fld
+    rng = np.random.default_rng(2)
+    ncol, n = 5, 333
+    rf = 1.0 * 3.0 ** (np.arange(n + 1) / n)
+    D = 10 ** rng.uniform(-1, 1, (ncol, n))
+    E_old = 1 + rng.random((ncol, n))
+    vlo, vhi = rng.random(ncol) + 0.5, rng.random(ncol)
+    dts = 10 ** rng.uniform(-3, 0, ncol)
+    p = inputs.code_units()
+    out = fld.columns_diffuse(ctx, rf, geometry, bc, vlo, vhi, p, dts, dev(D), dev(E_old))
+    col = {"r_faces": rf, "geometry": geometry, "bc": list(bc)}
+    for j in range(ncol):
+        ref = oracle.column_diffuse(col, dts[j], D[j], E_old[j], vlo[j], vhi[j], method="dense")
+        assert relerr(host(out)[j], ref) < 1e-12
+
+
+def test_columns_thin_front(ctx):
+    """The optically thin front (Sect. 4.4) on a uniform Cartesian column, GPU vs oracle."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.thin_front()
+    p = case["phys"]
+    n = case["E"].size
+    rf = np.linspace(-0.5, 1.5, n + 1)
+    col = {"r_faces": rf, "geometry": "cartesian", "bc": ["dirichlet", "dirichlet"]}
+    vlo, vhi = case["E0"] + case["E1"], case["E0"]
+    Eo, eo = case["E"].copy(), case["eps"].copy()
+    E = dev(Eo[None, :])
+    for _ in range(20):
+        kap = oracle.opacity(p, case["rho"], eo)
+        D = oracle.column_coeffs(col, p, Eo, case["rho"], kap, vlo, vhi)
+        Eo = oracle.column_diffuse(col, case["dt"], D, Eo, vlo, vhi)
+        E = fld.columns_diffuse(ctx, rf, "cartesian", ("dirichlet", "dirichlet"), [vlo], [vhi], p, [case["dt"]],
+                                dev(D[None, :]), E)
+    assert relerr(host(E)[0], Eo) < 1e-12
+
+
+# ----------------------------------------------------------------------------- batched
+
+def test_step_batched_parity(ctx):
+    from paper_2104_03968_gb300 import fld
+    cases = inputs.batched_2d(ngrids=5, nmin=32, nmax=96, seed=21)
+    params = [solver(c["phys"], rtol=1e-13) for c in cases]
+    eps = [dev(c["eps"]) for c in cases]
+    E = [dev(c["E"]) for c in cases]
+    infos = fld.step_batched(ctx, [c["grid"] for c in cases], params, [c["dt"] for c in cases],
+                             [dev(c["rho"]) for c in cases], eps, E)
+    for c, i, te, tE in zip(cases, infos, eps, E):
+        assert i["status"] == 0
+        e_o, E_o, _ = oracle.step(c["grid"], c["phys"], c["dt"], c["rho"], c["eps"], c["E"], rtol=1e-14)
+        assert relerr(host(tE), E_o) < TOL
+        assert relerr(host(te), e_o) < TOL
+
+
+# ----------------------------------------------------------------------------- errors
+
+def test_invalid_arguments_are_rejected(ctx):
+    from paper_2104_03968_gb300 import fld
+    g = inputs.periodic_grid((16, 16))
+    p = solver(inputs.code_units(), rtol=1e-10)
+    t = dev(np.ones((16, 16)))
+    with pytest.raises(fld.FldError) as e:
+        fld.step(ctx, dict(g, ndim=4), p, 1.0, t, t.clone(), t.clone())
+    assert e.value.status == 1
+    with pytest.raises(fld.FldError):
+        fld.step(ctx, g, dict(p, rtol=0.0), 1.0, t, t.clone(), t.clone())
+    with pytest.raises(fld.FldError):
+        fld.step(ctx, g, p, -1.0, t, t.clone(), t.clone())
+    # a state with E <= 0 is reported, not solved
+    bad = dev(np.full((16, 16), -1.0))
+    with pytest.raises(fld.FldError) as e:
+        fld.step(ctx, g, p, 1.0, t, t.clone(), bad)
+    assert e.value.status == 2
+
+
+def test_not_converged_is_reported(ctx):
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small((64, 64), seed=2, dt_factor=300.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    out, info = fld.diffuse(ctx, g, solver(p, rtol=1e-14, max_cycles=1), case["dt"], dev(D), dev(case["E"]))
+    assert info["status"] == 4 and info["cycles"] == 1
