@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the FLD radiation-energy update on GB300.
+
+Workload (default): the 512^3 periodic lognormal-density grid with Kramers opacity,
+dt = 100x the explicit limit, one full update per step (coefficients, multigrid
+diffusion to 1e-8 relative residual, exchange).  `value` is the mixed-precision
+solver (FP32 V-cycles inside the FP64 defect-correction loop); the plain FP64 GPU
+solver on the same inputs and accuracy is reported beside it, with the error of the
+mixed result against it.  Inputs (1 GiB per field) are larger than L2 (129 MB), so no
+explicit flush is needed between steps.
+
+One JSON line on rank 0.  `--impl reference` times the plain CPU oracle instead.
+Multi-GPU: replicas only (one independent grid per GPU, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "implicit FLD cell-updates/s at 1e-8 residual (FP64 vs mixed); % HBM peak"
+UNIT = "cell-updates/s"
+
+# Algorithmic (minimum) bytes per cell of one launch, and the FP64 instruction estimate per
+# cell, for the kernels whose roofline is reported.  "L0" = the finest multigrid level.
+KERNEL_MODEL = {
+    # one colour of a red-black sweep over level 0: the colour's r, 1/diag and x (write), the
+    # other colour's x, the 3 face arrays -- per cell of the level: (0.5+0.5+0.5+0.5)*s + 3*s
+    "smooth_L0": {"bytes_f32": 2 * 4 + 3 * 4, "bytes_f64": 2 * 8 + 3 * 8},
+    "smooth_L0_zero": {"bytes_f32": 3 * 0.5 * 4, "bytes_f64": 3 * 0.5 * 8},
+    # FP64 outer step: x, d, b, 3 face arrays in; x, r out
+    "update_residual": {"bytes_f32": 8 + 4 + 8 + 24 + 8 + 4, "bytes_f64": 8 + 8 + 8 + 24 + 8 + 8},
+    "coeffs": {"bytes_f32": 3 * 8 + 2 * 8, "bytes_f64": 3 * 8 + 2 * 8},
+    "exchange": {"bytes_f32": 4 * 8 + 2 * 8, "bytes_f64": 4 * 8 + 2 * 8},
+    "restrict_L0": {"bytes_f32": 2 * 4 + 3 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 3 * 8 + 8 / 8},
+    "prolong_L0": {"bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
+    "faces": {"bytes_f32": 8 + 3 * (8 + 4), "bytes_f64": 8 + 3 * 8},
+    "fine_setup": {"bytes_f32": 8 + 24 + 8 + 4, "bytes_f64": 8 + 24 + 8 + 8},
+}
+# launches per traced scope (some scopes hold several kernels)
+SCOPE_KERNELS = {"faces": 3, "coarse_setup": 4, "norm_b": 2}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- oracle leg
+
+def oracle_sample(n: int, steps: int, rtol: float):
+    """The CPU oracle on the same recipe at n^3 (a bounded sample of the workload)."""
+    import oracle
+    from paper_2104_03968_gb300 import inputs
+    case = inputs.lognormal_3d(n=n, seed=2)
+    g, p = case["grid"], case["phys"]
+    eps, E = case["eps"], case["E"]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        eps, E, _ = oracle.step(g, p, case["dt"], case["rho"], eps, E, rtol=rtol)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    n = args.oracle_n
+    for _ in range(args.warmup):
+        oracle_sample(n, 1, args.rtol)
+    val, secs = oracle_sample(n, args.steps, args.rtol)
+    sample = f"lognormal {n}^3 (same recipe as the {args.n}^3 workload), {args.steps} steps, rtol {args.rtol:g}"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": f"lognormal-density Kramers-opacity periodic grid {args.n}^3, dt = 100x explicit limit, "
+                        f"full FLD step (coeffs + multigrid diffusion to {args.rtol:g} + exchange)",
+            "grid": [args.n] * 3, "cells": args.n ** 3, "rtol": args.rtol, "precision": args.precision,
+            "nu1": 2, "nu2": 2, "l2_flush": "inputs larger than L2 (1 GiB per field)", "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+def timed_steps(torch, fld, ctx, g, p, dt, rho, eps, E, steps, trace=False):
+    stream = torch.cuda.current_stream()
+    infos = []
+    if trace:
+        fld.trace_enable(ctx, True)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        infos.append(fld.step(ctx, g, p, dt, rho, eps, E))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    rep = None
+    if trace:
+        fld.trace_enable(ctx, False)
+        rep = fld.trace_report(ctx)
+    return t0.elapsed_time(t1), infos, rep
+
+
+def roofline(rep: dict, ncell: int, precision: str, peaks: dict, traffic: dict):
+    if not rep:
+        return None
+    name = max((k for k in rep if k in KERNEL_MODEL), key=lambda k: rep[k][1])
+    launches, ms = rep[name]
+    key = "bytes_f32" if precision == "mixed" else "bytes_f64"
+    per_cell = KERNEL_MODEL[name][key]
+    bytes_launch = per_cell * ncell
+    avg_s = ms / launches * 1e-3
+    achieved = bytes_launch / avg_s / 1e9
+    tr = traffic.get(name)
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+            "traffic": tr, "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": ms / launches,
+            "launches": launches, "share_of_traced_ms": ms / sum(v[1] for v in rep.values())}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--oracle-n", type=int, default=192, dest="oracle_n")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_2104_03968_gb300 import build as _b
+    if rank == 0:
+        _b.build()
+    barrier(world)
+    from paper_2104_03968_gb300 import fld, inputs
+
+    torch.cuda.set_device(local)
+    ctx = fld.Context(local)
+    case = inputs.lognormal_3d(n=args.n, seed=2, device=f"cuda:{local}")
+    g, phys, dt = case["grid"], case["phys"], case["dt"]
+    rho0, eps0, E0 = case["rho"], case["eps"], case["E"]
+    ncell = args.n ** 3
+    p = dict(phys, precision=args.precision, rtol=args.rtol)
+
+    def fresh():
+        return eps0.clone(), E0.clone()
+
+    # ---- main arm: warm-up, then exactly K timed steps
+    eps, E = fresh()
+    for _ in range(args.warmup):
+        fld.step(ctx, g, p, dt, rho0, eps, E)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, infos, rep = timed_steps(torch, fld, ctx, g, p, dt, rho0, eps, E, args.steps, trace=True)
+    clk = clocks.stop()
+    barrier(world)
+    ms = allreduce_max(world, ms)
+    value = world * ncell * args.steps / (ms * 1e-3)
+    launches = sum(v[0] * SCOPE_KERNELS.get(k, 1) for k, v in rep.items())
+    traffic = {}
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tdata = json.load(f)
+        if tdata.get("workload_n") == args.n and tdata.get("precision") == args.precision:
+            traffic = tdata.get("bytes_per_launch", {})
+    peaks = load_peaks()
+    roof = roofline(rep, ncell, args.precision, peaks, traffic)
+
+    # ---- same inputs, one step of each precision, to report the mixed error against FP64
+    extra = {}
+    if not args.no_fp64 and args.precision == "mixed":
+        ctx64 = fld.Context(local)
+        p64 = dict(phys, precision="fp64", rtol=args.rtol)
+        e1, E1 = fresh()
+        fld.step(ctx, g, p, dt, rho0, e1, E1)
+        e2, E2 = fresh()
+        fld.step(ctx64, g, p64, dt, rho0, e2, E2)
+        dE = (E1 - E2)
+        extra["mixed_vs_fp64"] = {"E_max_rel": float(dE.abs().max() / E2.abs().max()),
+                                  "E_l2_rel": float(dE.norm() / E2.norm()),
+                                  "eps_max_rel": float((e1 - e2).abs().max() / e2.abs().max())}
+        del e1, E1, e2, E2, dE
+        eps64, E64 = fresh()
+        for _ in range(args.warmup):
+            fld.step(ctx64, g, p64, dt, rho0, eps64, E64)
+        barrier(world)
+        ms64, infos64, _ = timed_steps(torch, fld, ctx64, g, p64, dt, rho0, eps64, E64, args.steps)
+        ms64 = allreduce_max(world, ms64)
+        extra["fp64"] = {"value": world * ncell * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
+                         "cycles_per_step": [i["cycles"] for i in infos64]}
+        del eps64, E64
+        ctx64.close()
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hr = rho0.cpu().pin_memory()
+        he = eps0.cpu().pin_memory()
+        hE = E0.cpu().pin_memory()
+        fld.step(ctx, g, p, dt, hr, he, hE)  # warm
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fld.step(ctx, g, p, dt, hr, he, hE)
+        torch.cuda.synchronize()
+        secs = allreduce_max(world, time.perf_counter() - t0)
+        e2e = {"value": world * ncell * args.steps / secs, "unit": UNIT, "h2d_bytes_per_step": 3 * ncell * 8,
+               "d2h_bytes_per_step": 2 * ncell * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        val, secs = oracle_sample(args.oracle_n, 1, args.rtol)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full step of the same recipe at {args.oracle_n}^3 ({secs:.1f} s, single thread)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64+f32 (FP32 V-cycles, FP64 residual/update/norm/exchange)" if args.precision == "mixed"
+                else "f64",
+                "data": "synthetic", "config": workload_config(args), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "cycles_per_step": [i["cycles"] for i in infos],
+                "rel_residual": [i["rel_residual"] for i in infos], **extra}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    barrier(world)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -86,33 +86,59 @@ def thick_explicit_dt(dx2_min, ndim: int, c: float, kr_min: float) -> float:
 
 # ----------------------------------------------------------------------------- fields
 
-def _kgrid(shape):
-    ks = np.meshgrid(*[np.fft.fftfreq(s) * s for s in shape], indexing="ij")
-    return np.sqrt(sum(k * k for k in ks))
+def _kgrid(shape, device=None):
+    if device is None:
+        ks = np.meshgrid(*[np.fft.fftfreq(s) * s for s in shape], indexing="ij")
+        return np.sqrt(sum(k * k for k in ks))
+    import torch
+    ks = torch.meshgrid(*[torch.fft.fftfreq(s, device=device, dtype=torch.float64) * s for s in shape],
+                        indexing="ij")
+    return torch.sqrt(sum(k * k for k in ks))
 
 
-def gaussian_random_field(rng, shape, kmax_frac: float = 0.25) -> np.ndarray:
-    """Unit-variance Gaussian field: white noise filtered to P(k) ~ k^-4, 1 <= |k| <= N/4."""
-    k = _kgrid(shape)
-    amp = np.zeros_like(k)
+def gaussian_random_field(rng, shape, kmax_frac: float = 0.25, device=None):
+    """Unit-variance Gaussian field: white noise filtered to P(k) ~ k^-4, 1 <= |k| <= N/4.
+    With a torch ``device`` the same numpy noise is filtered there (large grids)."""
+    k = _kgrid(shape, device)
     kmax = kmax_frac * min(shape)
-    sel = (k >= 1.0) & (k <= kmax)
-    amp[sel] = k[sel] ** -2.0
     noise = rng.standard_normal(shape)
-    f = np.real(np.fft.ifftn(np.fft.fftn(noise) * amp))
-    f -= f.mean()
+    if device is None:
+        amp = np.zeros_like(k)
+        sel = (k >= 1.0) & (k <= kmax)
+        amp[sel] = k[sel] ** -2.0
+        f = np.real(np.fft.ifftn(np.fft.fftn(noise) * amp))
+    else:
+        import torch
+        sel = (k >= 1.0) & (k <= kmax)
+        amp = torch.where(sel, k.clamp(min=1.0) ** -2.0, torch.zeros_like(k))
+        del k, sel
+        f = torch.fft.fftn(torch.from_numpy(noise).to(device))
+        del noise
+        f *= amp
+        del amp
+        f = torch.fft.ifftn(f).real.contiguous()
+        f = f - f.mean()
+        return f / f.std(correction=0)
+    f = f - f.mean()
     return f / f.std()
 
 
-def smooth_field(rng, shape, kmax: float = 4.0) -> np.ndarray:
+def smooth_field(rng, shape, kmax: float = 4.0, device=None) -> np.ndarray:
     """Sum of the Fourier modes with |k| <= kmax, random phases, scaled to max |S| = 1."""
-    k = _kgrid(shape)
+    k = _kgrid(shape)  # host: the selection is tiny
     sel = (k > 0) & (k <= kmax)
-    coef = np.zeros(shape, dtype=np.complex128)
     ph = rng.uniform(0, 2 * np.pi, size=int(sel.sum()))
-    coef[sel] = np.exp(1j * ph)
-    f = np.real(np.fft.ifftn(coef))
-    return f / np.abs(f).max()
+    if device is None:
+        coef = np.zeros(shape, dtype=np.complex128)
+        coef[sel] = np.exp(1j * ph)
+        f = np.real(np.fft.ifftn(coef))
+        return f / np.abs(f).max()
+    import torch
+    coef = torch.zeros(shape, dtype=torch.complex128, device=device)
+    idx = torch.from_numpy(np.nonzero(sel.ravel())[0]).to(device)
+    coef.view(-1)[idx] = torch.from_numpy(np.exp(1j * ph)).to(device)
+    f = torch.fft.ifftn(coef).real.contiguous()
+    return f / f.abs().max()
 
 
 # ----------------------------------------------------------------------------- workloads
@@ -136,26 +162,30 @@ def gaussian_pulse_2d(n: int = 64, kappa: float = 1e3, sigma: float = 4.0, floor
             "D_thick": phys["c"] / (3 * kappa)}
 
 
-def lognormal_fields(rng, shape, phys: dict, kappa0: float, sigma_ln: float = 1.0):
-    G = gaussian_random_field(rng, shape)
-    rho = np.exp(sigma_ln * G - sigma_ln ** 2 / 2)
-    Tg = 1.0 + 0.3 * smooth_field(rng, shape)
-    Tr = 1.0 + 0.3 * smooth_field(rng, shape)
+def lognormal_fields(rng, shape, phys: dict, kappa0: float, sigma_ln: float = 1.0, device=None):
+    G = gaussian_random_field(rng, shape, device=device)
+    xp = np if device is None else __import__("torch")
+    rho = xp.exp(sigma_ln * G - sigma_ln ** 2 / 2)
+    del G
+    Tg = 1.0 + 0.3 * smooth_field(rng, shape, device=device)
+    Tr = 1.0 + 0.3 * smooth_field(rng, shape, device=device)
     E = rad_energy(phys, Tr)
+    del Tr
     eps = equilibrium_eps(phys, rho, Tg)
     kr_min = float((kappa0 * rho * Tg ** -3.5 * rho).min())
     return rho, eps, E, kr_min
 
 
 def lognormal_3d(n: int = 128, seed: int = 1, kappa0: float = 1.0, dt_factor: float = 100.0,
-                 ndim: int = 3, limiter: str = "lp") -> dict:
-    """Lognormal density with Kramers opacity; periodic n^ndim (code units)."""
+                 ndim: int = 3, limiter: str = "lp", device=None) -> dict:
+    """Lognormal density with Kramers opacity; periodic n^ndim (code units).  With a torch
+    ``device`` the fields are built there (same noise and recipe) and returned as tensors."""
     rng = np.random.default_rng(SEED_BASE + seed)
     shape = (n,) * ndim
     grid = periodic_grid(shape)
     phys = code_units(limiter)
     phys.update(opacity="kramers", kappa0=kappa0, kr_a=1.0, kr_b=-3.5)
-    rho, eps, E, kr_min = lognormal_fields(rng, shape, phys, kappa0)
+    rho, eps, E, kr_min = lognormal_fields(rng, shape, phys, kappa0, device=device)
     dt_exp = thick_explicit_dt(1.0, ndim, phys["c"], kr_min)
     return {"name": f"lognormal_{ndim}d_{n}", "grid": grid, "phys": phys, "rho": rho, "eps": eps,
             "E": E, "dt": dt_factor * dt_exp, "dt_exp": dt_exp}
