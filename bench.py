@@ -343,6 +343,7 @@ def main():
                 else "f64",
                 "data": "synthetic", "config": workload_config(args), "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in sorted(rep.items(), key=lambda kv: -kv[1][1])},
                 "cycles_per_step": [i["cycles"] for i in infos],
                 "rel_residual": [i["rel_residual"] for i in infos], **extra}
         print(json.dumps(line), flush=True)
