@@ -175,6 +175,33 @@ FLD_API fld_status fld_columns_diffuse(fld_ctx* ctx, int ncol, int ncell, const 
                                const double* D_cell, const double* E_old, double* E_new,
                                void* stream);
 
+/* ---- allocation-free column update (no counterpart in the paper; a deployment convenience).
+   Some callers cannot allocate device memory when they advance the radiation field: codes whose
+   own memory manager has reserved the whole GPU in advance, runtimes that forbid device
+   allocation inside their time-step loop (for instance while recording work for later replay),
+   or real-time loops where an allocation that may fail or stall is not acceptable.  They cannot
+   create an fld_ctx either, since a context allocates its scratch on first use.
+   fld_columns_step_static takes the arguments of fld_columns_step without the context, does the
+   same computation, and allocates nothing: its scratch (the per-cell geometry factors and three
+   status counters) lives in one statically sized device array of the library, 4 *
+   FLD_STATIC_MAX_CELLS + 8 doubles (about 64 KiB), which every device that loads the library
+   holds until the process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+     - ncell > FLD_STATIC_MAX_CELLS is rejected with FLD_ERR_UNSUPPORTED (nothing is launched);
+       the other argument checks and return codes are those of fld_columns_step.
+     - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+       with that device current, and caches it.  Make that first call before any stream capture.
+     - Every call on a device shares the one array and leaves its contents behind; each call
+       rewrites the geometry and clears the counters before use.  Calls whose work overlaps on
+       the GPU (different streams, or host threads, without ordering between them) race on the
+       array and give undefined results: order them on one stream.
+     - With info == NULL the call returns after enqueueing; otherwise it synchronises on the
+       stream and fills info as fld_columns_step does. */
+#define FLD_STATIC_MAX_CELLS 2048
+FLD_API fld_status fld_columns_step_static(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo,
+                                           int bc_hi, const double* v_lo, const double* v_hi, const fld_params* p,
+                                           const double* dt, const double* rho, double* eps, double* E,
+                                           fld_info* info, void* stream);
+
 /* ---- tracing: per-kernel launch timing with CUDA events (library diagnostics; the paper has
    no counterpart).  While enabled, every kernel launch of the library is bracketed by a pair of
    events on its stream; fld_trace_report synchronises on them and returns, per kernel name,

@@ -13,6 +13,9 @@
 //   4. the point-implicit exchange (Sect. 3.3) per cell.
 // HBM traffic is one read of rho, eps, E and one write of eps, E per cell.
 #include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
 
 #include "columns.h"
 #include "exchange.cuh"
@@ -424,4 +427,106 @@ cudaError_t launch_columns_diffuse(int ncol, int ncell, const double* r_faces, i
   return launch_mode<kColDiffuse>(ncol, ncell, r_faces, geometry, A, nullptr, s);
 }
 
+// ----------------------------------------------------------------------------- no-allocation entry
+
+// Scratch of fld_columns_step_static, resident on every device that loads the library: the
+// per-cell geometry factors of up to FLD_STATIC_MAX_CELLS cells (4 n + 4 doubles) followed by
+// the status word and the two exchange counters (one double slot each).
+constexpr int kStaticGeom = 4 * FLD_STATIC_MAX_CELLS + 4;
+static __device__ __align__(256) double g_static_scratch[kStaticGeom + 4];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_scratch on the current device (looked up once per device).  In
+// host code the symbol name is only a host-side handle, so kernels must receive this address.
+cudaError_t static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+bool static_params_ok(const fld_params* p) {
+  if (!p || !(p->c > 0) || !(p->a_rad > 0) || !(p->gamma > 1) || !(p->gas_R > 0)) return false;
+  if (p->limiter != FLD_LIMITER_LP && p->limiter != FLD_LIMITER_THIRD) return false;
+  if (p->opacity < FLD_OPACITY_CONST || p->opacity > FLD_OPACITY_TABLE) return false;
+  if (p->opacity != FLD_OPACITY_TABLE && !(p->kappa0 > 0)) return false;
+  if (p->opacity == FLD_OPACITY_TABLE &&
+      (!p->table || p->tn[0] < 2 || p->tn[1] < 2 || !(p->thi[0] > p->tlo[0]) || !(p->thi[1] > p->tlo[1])))
+    return false;
+  if (p->exch_maxit < 0) return false;
+  return p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE || p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE;
+}
+
+}  // namespace
+
 }  // namespace fld
+
+extern "C" fld_status fld_columns_step_static(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo,
+                                              int bc_hi, const double* v_lo, const double* v_hi, const fld_params* p,
+                                              const double* dt, const double* rho, double* eps, double* E,
+                                              fld_info* info, void* stream) {
+  using namespace fld;
+  if (ncell > FLD_STATIC_MAX_CELLS) return FLD_ERR_UNSUPPORTED;
+  std::string err;
+  fld_status st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);
+  if (st != FLD_OK) return st;
+  if (!static_params_ok(p) || !rho || !eps || !E) return FLD_ERR_INVALID_ARG;
+  if (info) memset(info, 0, sizeof(*info));
+  if (ncol == 0) return FLD_OK;
+  double* scratch = nullptr;
+  if (static_scratch(&scratch) != cudaSuccess) return FLD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* geom = scratch;
+  unsigned* status = reinterpret_cast<unsigned*>(scratch + kStaticGeom);
+  int* iters = reinterpret_cast<int*>(scratch + kStaticGeom + 1);
+  int* bisect = reinterpret_cast<int*>(scratch + kStaticGeom + 2);
+  // the counters keep the previous call's values: clear them
+  if (cudaMemsetAsync(scratch + kStaticGeom, 0, 3 * sizeof(double), s) != cudaSuccess) return FLD_ERR_CUDA;
+  ColArgs A = col_args(ncell, bc_lo, bc_hi, v_lo, v_hi, *p, dt, geom);
+  A.rho = rho;
+  A.Ein = E;
+  A.Eout = E;
+  A.eps = eps;
+  A.info_iters = iters;
+  A.info_bisect = bisect;
+  A.status = status;
+  k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, geom, status);
+  int P = col_threads(ncell);
+  size_t smem = col_smem(ncell, P);
+  cudaError_t e;
+  if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE) {
+    e = cudaFuncSetAttribute(k_columns<kColStepExchangeFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_columns<kColStepExchangeFirst><<<ncol, P, smem, s>>>(A);
+  } else {
+    e = cudaFuncSetAttribute(k_columns<kColStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_columns<kColStep><<<ncol, P, smem, s>>>(A);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return FLD_ERR_CUDA;
+  if (info) {
+    unsigned sbits = 0;
+    e = cudaMemcpyAsync(&sbits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&info->exch_max_iters, iters, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&info->bisection_fallbacks, bisect, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return FLD_ERR_CUDA;
+    info->status = (sbits & kStatNonpositive) ? FLD_ERR_NONPOSITIVE : FLD_OK;
+    if (info->status != FLD_OK) return FLD_ERR_NONPOSITIVE;
+  }
+  return FLD_OK;
+}

@@ -338,3 +338,29 @@ def trace_report(ctx: Context) -> dict:
     n = ct.c_int()
     ctx.check(ctx.lib.fld_trace_report(ctx.h, buf, 256, ct.byref(n)))
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}
+
+
+STATIC_MAX_CELLS = 2048
+
+
+def columns_step_static(r_faces, geometry: str, bc: tuple, v_lo, v_hi, params: dict, dt, rho, eps, E,
+                        device: int = 0) -> dict:
+    """fld_columns_step_static: the column update without a context and without any device
+    allocation inside the library (its scratch is a static device array).  All array arguments
+    must already be contiguous float64 CUDA tensors; eps and E ([ncol][ncell]) are updated in
+    place.  The caller owns every buffer, including the per-column dt and boundary values."""
+    lib = load()
+    lib.fld_columns_step_static.argtypes = [ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P,
+                                            P, P, P]
+    lib.fld_columns_step_static.restype = ct.c_int
+    ncol, ncell = E.shape
+    keep = []
+    p = params_struct(params, keep, torch.device("cuda", device))
+    info = Info()
+    st = lib.fld_columns_step_static(ncol, ncell, _dptr(r_faces), GEOMETRY[geometry], BC[bc[0]], BC[bc[1]],
+                                     _dptr(v_lo), _dptr(v_hi), ct.byref(p), _dptr(dt), _dptr(rho), _dptr(eps),
+                                     _dptr(E), ct.byref(info), _stream())
+    if st:
+        raise FldError(st, "fld_columns_step_static failed" +
+                       (f" (ncell {ncell} > {STATIC_MAX_CELLS})" if ncell > STATIC_MAX_CELLS else ""))
+    return info.as_dict()
