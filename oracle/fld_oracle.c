@@ -585,14 +585,16 @@ int ora_exchange(size_t n, const ora_phys* p, double dt, const double* rho, cons
       double f1 = 4.0 * A * y * y * y + B;
       double f2 = 12.0 * A * y * y;
       double yn = y - 2.0 * f * f1 / (2.0 * f1 * f1 - f * f2); /* Halley's step */
-      if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
       ++it;
-      double dy = fabs(yn - y);
-      y = yn;
-      if (dy <= tol * y) {
+      /* a converged step can land on the bracket end that was just set from y itself:
+         accept it before the bracket safeguard would turn it into a bisection */
+      if (fabs(yn - y) <= tol * yn) {
+        y = yn;
         converged = 1;
         break;
       }
+      if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+      y = yn;
     }
     if (!converged) { /* bisection fallback */
       ++nbis;
