@@ -119,6 +119,7 @@ GridDev to_dev(const fld_grid* g) {
   for (int a = 0; a < 3; ++a) {
     d.n[a] = g->n[a];
     d.dx[a] = a < g->ndim ? g->dx[a] : 1.0;
+    d.inv_dx2[a] = 1.0 / (d.dx[a] * d.dx[a]);
   }
   for (int f = 0; f < 6; ++f) {
     d.bc[f] = (f / 2) < g->ndim ? g->bc[f] : FLD_BC_PERIODIC;
@@ -145,14 +146,7 @@ Opacity to_opacity(const fld_params* p) {
 }
 
 ExchangeParams to_exchange(const fld_params* p, double dt) {
-  ExchangeParams e{};
-  e.c = p->c;
-  e.sigma = p->a_rad * p->c / 4.0;
-  e.gamma = p->gamma;
-  e.gas_R = p->gas_R;
-  e.dt = dt;
-  e.maxit = p->exch_maxit > 0 ? p->exch_maxit : 100;
-  return e;
+  return make_exchange(p->c, p->a_rad, p->gamma, p->gas_R, dt, p->exch_maxit > 0 ? p->exch_maxit : 100);
 }
 
 fld_status ensure_scratch(fld_ctx* ctx, long long ncell) {

@@ -80,7 +80,133 @@ struct ColArgs {
 
 __device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
 
-template <int MODE>
+constexpr int kColMaxRows = 8;  // rows per thread: n <= 2048 with at most 256 threads per column
+
+// FP32 solve of the tridiagonal system whose rows s0..s0+m-1 this thread holds in registers
+// (sub A, diagonal B, super C, rhs Dv): the chunk is eliminated down to its two interface rows,
+// parallel cyclic reduction solves the 2P interface rows in shared memory (fa..fd), and the
+// chunk back-substitutes into X.  Every thread of the block must call it (it synchronises).
+__device__ __forceinline__ void chunk_solve_f32(int t, int P, int m, const float (&Ain)[kColMaxRows],
+                                                const float (&Bin)[kColMaxRows], const float (&Cin)[kColMaxRows],
+                                                const float (&Din)[kColMaxRows], float* fa, float* fb, float* fc,
+                                                float* fd, float (&X)[kColMaxRows]) {
+  float a[kColMaxRows], b[kColMaxRows], c[kColMaxRows], d[kColMaxRows];
+#pragma unroll
+  for (int k = 0; k < kColMaxRows; ++k) {
+    a[k] = Ain[k];
+    b[k] = Bin[k];
+    c[k] = Cin[k];
+    d[k] = Din[k];
+  }
+  float Ra0 = 0.f, Rb0 = 1.f, Rc0 = 0.f, Rd0 = 0.f, Ra1 = 0.f, Rb1 = 1.f, Rc1 = 0.f, Rd1 = 0.f;
+  if (m == 1) {
+    Ra0 = a[0];
+    Rb0 = b[0];
+    Rc0 = c[0];
+    Rd0 = d[0];
+  } else if (m >= 2) {
+#pragma unroll
+    for (int k = 2; k < kColMaxRows; ++k)
+      if (k < m) {
+        float f = a[k] / b[k - 1];
+        a[k] = -f * a[k - 1];
+        b[k] -= f * c[k - 1];
+        d[k] -= f * d[k - 1];
+      }
+#pragma unroll
+    for (int k = 1; k < kColMaxRows; ++k)
+      if (k == m - 1) {
+        Ra1 = a[k];
+        Rb1 = b[k];
+        Rc1 = c[k];
+        Rd1 = d[k];
+      }
+#pragma unroll
+    for (int k = kColMaxRows - 2; k >= 1; --k)
+      if (k <= m - 2) {
+        float inv = 1.0f / b[k];
+        if (k == m - 2) {
+          a[k] *= inv;
+          c[k] *= inv;
+          d[k] *= inv;
+        } else {
+          float g = c[k];
+          a[k] = (a[k] - g * a[k + 1]) * inv;
+          d[k] = (d[k] - g * d[k + 1]) * inv;
+          c[k] = -g * c[k + 1] * inv;
+        }
+      }
+    Ra0 = a[0];
+    if (m == 2) {
+      Rb0 = b[0];
+      Rc0 = c[0];
+      Rd0 = d[0];
+    } else {
+      float g = c[0];
+      Rb0 = b[0] - g * a[1];
+      Rc0 = -g * c[1];
+      Rd0 = d[0] - g * d[1];
+    }
+  }
+  __syncthreads();  // the interface arrays may still be read by a previous solve
+  fa[2 * t] = Ra0;
+  fb[2 * t] = Rb0;
+  fc[2 * t] = Rc0;
+  fd[2 * t] = Rd0;
+  fa[2 * t + 1] = Ra1;
+  fb[2 * t + 1] = Rb1;
+  fc[2 * t + 1] = Rc1;
+  fd[2 * t + 1] = Rd1;
+  __syncthreads();
+  const int R = 2 * P;
+  for (int st = 1; st < R; st <<= 1) {
+    float na[2], nb[2], nc[2], nd[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int i = 2 * t + h;
+      float am = 0.f, bm = 1.f, cm_ = 0.f, dm = 0.f, ap = 0.f, bp = 1.f, cp_ = 0.f, dp = 0.f;
+      if (i - st >= 0) {
+        am = fa[i - st];
+        bm = fb[i - st];
+        cm_ = fc[i - st];
+        dm = fd[i - st];
+      }
+      if (i + st < R) {
+        ap = fa[i + st];
+        bp = fb[i + st];
+        cp_ = fc[i + st];
+        dp = fd[i + st];
+      }
+      float k1 = fa[i] / bm, k2 = fc[i] / bp;
+      na[h] = -am * k1;
+      nc[h] = -cp_ * k2;
+      nb[h] = fb[i] - cm_ * k1 - ap * k2;
+      nd[h] = fd[i] - dm * k1 - dp * k2;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int i = 2 * t + h;
+      fa[i] = na[h];
+      fb[i] = nb[h];
+      fc[i] = nc[h];
+      fd[i] = nd[h];
+    }
+    __syncthreads();
+  }
+  const float xs = fd[2 * t] / fb[2 * t];
+  const float xe = fd[2 * t + 1] / fb[2 * t + 1];
+#pragma unroll
+  for (int k = 0; k < kColMaxRows; ++k) {
+    float v = 0.f;
+    if (k == 0) v = xs;
+    else if (k == m - 1) v = xe;
+    else if (k < m - 1) v = d[k] - a[k] * xs - c[k] * xe;
+    X[k] = v;
+  }
+}
+
+template <int MODE, bool MIXED>
 __global__ void k_columns(ColArgs A) {
   extern __shared__ double sm[];
   const int n = A.n, P = blockDim.x, t = threadIdx.x;
@@ -103,7 +229,7 @@ __global__ void k_columns(ColArgs A) {
   const double vlo = A.v_lo ? A.v_lo[blockIdx.x] : 0.0, vhi = A.v_hi ? A.v_hi[blockIdx.x] : 0.0;
   const double *gl = A.geom, *gu = A.geom + n, *cm = A.geom + 2 * n, *cp = A.geom + 3 * n;
   const double hl = A.geom[4 * n], hr = A.geom[4 * n + 1], flo = A.geom[4 * n + 2], fhi = A.geom[4 * n + 3];
-  ExchangeParams xp{A.c, A.sigma, A.gamma, A.gas_R, dtc, A.maxit};
+  const ExchangeParams xp = make_exchange(A.c, 4.0 * A.sigma / A.c, A.gamma, A.gas_R, dtc, A.maxit);
   int iters = 0, bis = 0;
   bool bad = false;
 
@@ -197,8 +323,47 @@ __global__ void k_columns(ColArgs A) {
     sd[i] = d;
   }
 
-  // chunk elimination down to the interface rows (x_s, x_e) of this thread
   const int m = s1 - s0;
+  if constexpr (MIXED) {
+    // FP32 solves inside FP64 iterative refinement: x = solve32(d); twice r = d - A x (FP64),
+    // x += solve32(r).  The rows stay in FP64 in shared memory for the residual.
+    float* fa = reinterpret_cast<float*>(ra);
+    float* fb = fa + 2 * P;
+    float* fc = fb + 2 * P;
+    float* fd = fc + 2 * P;
+    float A32[kColMaxRows], B32[kColMaxRows], C32[kColMaxRows], R32[kColMaxRows], X32[kColMaxRows];
+#pragma unroll
+    for (int k = 0; k < kColMaxRows; ++k) {
+      bool in = k < m;
+      A32[k] = in ? (float)sa[s0 + k] : 0.0f;
+      B32[k] = in ? (float)sb[s0 + k] : 1.0f;
+      C32[k] = in ? (float)sc[s0 + k] : 0.0f;
+      R32[k] = in ? (float)sd[s0 + k] : 0.0f;
+    }
+    chunk_solve_f32(t, P, m, A32, B32, C32, R32, fa, fb, fc, fd, X32);
+#pragma unroll
+    for (int k = 0; k < kColMaxRows; ++k)
+      if (k < m) sx[s0 + k] = (double)X32[k];
+    for (int pass = 0; pass < 2; ++pass) {
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kColMaxRows; ++k) {
+        R32[k] = 0.0f;
+        if (k < m) {
+          int i = s0 + k;
+          double r = fma(-sb[i], sx[i], sd[i]);
+          if (i > 0) r = fma(-sa[i], sx[i - 1], r);
+          if (i < n - 1) r = fma(-sc[i], sx[i + 1], r);
+          R32[k] = (float)r;
+        }
+      }
+      chunk_solve_f32(t, P, m, A32, B32, C32, R32, fa, fb, fc, fd, X32);  // synchronises before any update
+#pragma unroll
+      for (int k = 0; k < kColMaxRows; ++k)
+        if (k < m) sx[s0 + k] += (double)X32[k];
+    }
+  } else {
+  // chunk elimination down to the interface rows (x_s, x_e) of this thread
   double Ra0 = 0.0, Rb0 = 1.0, Rc0 = 0.0, Rd0 = 0.0;  // row of x_s
   double Ra1 = 0.0, Rb1 = 1.0, Rc1 = 0.0, Rd1 = 0.0;  // row of x_e
   if (m == 1) {
@@ -300,6 +465,7 @@ __global__ void k_columns(ColArgs A) {
     sx[s1 - 1] = xe;
     for (int i = s0 + 1; i < s1 - 1; ++i) sx[i] = sd[i] - sa[i] * xs - sc[i] * xe;
   }
+  }  // FP64 solve
 
   if (MODE == kColStep) {
     for (int i = s0; i < s1; ++i) {
@@ -356,17 +522,23 @@ static int col_threads(int n) {
 
 static size_t col_smem(int n, int P) { return (size_t)(9 * n + 8 * P) * sizeof(double); }
 
-template <int MODE>
-static cudaError_t launch_mode(int ncol, int ncell, const double* r_faces, int geometry, ColArgs& A, unsigned* status,
-                               cudaStream_t s) {
-  k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, const_cast<double*>(A.geom), status);
+template <int MODE, bool MIXED>
+static cudaError_t launch_kernel(int ncol, int ncell, ColArgs& A, cudaStream_t s) {
   int P = col_threads(ncell);
   size_t smem = col_smem(ncell, P);
-  cudaError_t e = cudaFuncSetAttribute(k_columns<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_columns<MODE, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  TraceScope ts("columns", s);
-  k_columns<MODE><<<ncol, P, smem, s>>>(A);
+  k_columns<MODE, MIXED><<<ncol, P, smem, s>>>(A);
   return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_mode(int ncol, int ncell, const double* r_faces, int geometry, ColArgs& A, unsigned* status,
+                               int precision, cudaStream_t s) {
+  k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, const_cast<double*>(A.geom), status);
+  TraceScope ts(precision == FLD_PREC_MIXED ? "columns_mixed" : "columns", s);
+  return precision == FLD_PREC_MIXED ? launch_kernel<MODE, true>(ncol, ncell, A, s)
+                                     : launch_kernel<MODE, false>(ncol, ncell, A, s);
 }
 
 static ColArgs col_args(int ncell, int bc_lo, int bc_hi, const double* v_lo, const double* v_hi, const fld_params& p,
@@ -412,8 +584,8 @@ cudaError_t launch_columns_step(int ncol, int ncell, const double* r_faces, int 
   A.info_bisect = info_bisect;
   A.status = status;
   if (p.order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE)
-    return launch_mode<kColStepExchangeFirst>(ncol, ncell, r_faces, geometry, A, status, s);
-  return launch_mode<kColStep>(ncol, ncell, r_faces, geometry, A, status, s);
+    return launch_mode<kColStepExchangeFirst>(ncol, ncell, r_faces, geometry, A, status, p.precision, s);
+  return launch_mode<kColStep>(ncol, ncell, r_faces, geometry, A, status, p.precision, s);
 }
 
 cudaError_t launch_columns_diffuse(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo, int bc_hi,
@@ -424,7 +596,7 @@ cudaError_t launch_columns_diffuse(int ncol, int ncell, const double* r_faces, i
   A.Din = D_cell;
   A.Ein = E_old;
   A.Eout = E_new;
-  return launch_mode<kColDiffuse>(ncol, ncell, r_faces, geometry, A, nullptr, s);
+  return launch_mode<kColDiffuse>(ncol, ncell, r_faces, geometry, A, nullptr, p.precision, s);
 }
 
 // ----------------------------------------------------------------------------- no-allocation entry
@@ -505,17 +677,13 @@ extern "C" fld_status fld_columns_step_static(int ncol, int ncell, const double*
   A.info_bisect = bisect;
   A.status = status;
   k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, geom, status);
-  int P = col_threads(ncell);
-  size_t smem = col_smem(ncell, P);
+  const bool mixed = p->precision == FLD_PREC_MIXED;
   cudaError_t e;
-  if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE) {
-    e = cudaFuncSetAttribute(k_columns<kColStepExchangeFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k_columns<kColStepExchangeFirst><<<ncol, P, smem, s>>>(A);
-  } else {
-    e = cudaFuncSetAttribute(k_columns<kColStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k_columns<kColStep><<<ncol, P, smem, s>>>(A);
-  }
-  if (e == cudaSuccess) e = cudaGetLastError();
+  if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE)
+    e = mixed ? launch_kernel<kColStepExchangeFirst, true>(ncol, ncell, A, s)
+              : launch_kernel<kColStepExchangeFirst, false>(ncol, ncell, A, s);
+  else
+    e = mixed ? launch_kernel<kColStep, true>(ncol, ncell, A, s) : launch_kernel<kColStep, false>(ncol, ncell, A, s);
   if (e != cudaSuccess) return FLD_ERR_CUDA;
   if (info) {
     unsigned sbits = 0;

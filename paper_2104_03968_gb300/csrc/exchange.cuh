@@ -33,14 +33,14 @@ __device__ inline double halley64(double a, double cc, int maxit, int* iters, in
     double f1 = fma(4.0 * a * y2, y, 1.0);
     double f2 = 12.0 * a * y2;
     double yn = y - 2.0 * f * f1 / (2.0 * f1 * f1 - f * f2);
-    if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
     ++it;
-    double dy = fabs(yn - y);
-    y = yn;
-    if (dy <= tol * y) {
+    // a converged step may land on the bracket end just set from y: accept it first
+    if (fabs(yn - y) <= tol * yn) {
       *iters = it;
-      return y;
+      return yn;
     }
+    if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+    y = yn;
   }
   *bisected = 1;
   for (int k = 0; k < 200 && hi - lo > tol * hi; ++k) {
@@ -56,25 +56,36 @@ __device__ inline double halley64(double a, double cc, int maxit, int* iters, in
 // Updates (e, E) of one cell in place.  Returns false (and leaves them) on invalid input.
 __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k, double& e, double& E, int& iters,
                                      int& bis) {
-  double e0 = e, E0 = E;
-  if (!(r > 0.0) || !(k > 0.0) || !(e0 >= 0.0) || !(E0 >= 0.0)) return false;
-  double S = e0 + E0;
-  if (!(S > 0.0)) return true;
-  double t = (p.gamma - 1.0) / (r * p.gas_R);
-  double t2 = t * t;
-  double kr = k * r;
-  double a1 = 4.0 * kr * p.sigma * p.dt * t2 * t2;
-  double a2 = p.c * kr * p.dt;
-  double u = 1.0 / (1.0 + a2);
-  double invS = 1.0 / S;
+  const double e0 = e, E0 = E;
+  if (!(gt_zero(r) && gt_zero(k) && ge_zero(e0) && ge_zero(E0))) return false;
+  const double S = e0 + E0;
+  if (!pos_finite(S)) return true;  // eps = E = 0: nothing to exchange
+  const double a2 = p.cdt * k * r;  // c kappa rho dt
+  const double B = 1.0 + a2;
+  const double r3 = r * r * r;
+  const double P = r3 * B;
+  // one reciprocal gives 1/rho^3, 1/(1+a2) and 1/S
+  const double inv = 1.0 / (P * S);
+  double ir3, u, invS;
+  if (pos_finite(inv)) {
+    ir3 = B * S * inv;
+    u = r3 * S * inv;
+    invS = P * inv;
+  } else {
+    ir3 = 1.0 / r3;
+    u = 1.0 / B;
+    invS = 1.0 / S;
+  }
+  // a1 = 4 sigma dt kappa rho ((gamma-1)/(rho gas_R))^4 = k4 kappa / rho^3
+  const double a1 = p.k4 * k * ir3;
   // y = x / S solves  a y^4 + y - cc = 0,  a = a1 S^3/(1+a2) >= 0,  cc in (0, 1]
-  double a = a1 * S * S * S * u;
-  double cc = fma(a2 * u, E0, e0) * invS;
+  const double a = a1 * (S * S) * S * u;
+  const double cc = fma(a2 * u, E0, e0) * invS;
+  const float af = (float)a, cf = (float)cc;
   double y;
-  if (a >= 1e-30 && a <= 1e30 && cc >= 1e-30) {
+  if (af >= 1e-30f && af <= 1e30f && cf >= 1e-30f) {
     // y = ys z with ys = min(cc, (cc/a)^(1/4)) >= root: alpha z^4 + beta z = 1 with
     // max(alpha, beta) = 1, so the root z lies in [0.72, 1]
-    float af = (float)a, cf = (float)cc;
     float ys = fminf(cf, sqrtf(sqrtf(cf / af)));
     float ys2 = ys * ys;
     float alpha = af * ys2 * ys2 / cf, beta = ys / cf;
@@ -88,27 +99,30 @@ __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k
       float f1 = fmaf(4.0f * alpha * z2, z, beta);
       float f2 = 12.0f * alpha * z2;
       float zn = z - 2.0f * f * f1 / (2.0f * f1 * f1 - f * f2);
-      if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
-      float dz = fabsf(zn - z);
-      z = zn;
-      if (dz <= 4e-7f * z) break;
-    }
-    y = (double)ys * (double)z;
-    // FP64 Newton polish: f in FP64, 1/f' in FP32 (f' = 4 a y^3 + 1 >= 1)
-    bool done = false;
-    for (int it = 0; it < 8; ++it) {
-      double y2 = y * y;
-      double f = fma(a * y2, y2, y - cc);
-      double f1 = fma(4.0 * a * y2, y, 1.0);
-      double dy = f * (double)(1.0f / (float)f1);
-      y -= dy;
-      ++iters;
-      if (fabs(dy) <= 8.9e-16 * y) {
-        done = true;
+      // a converged step may land on the bracket end just set from z: accept it before the
+      // safeguard would replace it by a bisection
+      if (fabsf(zn - z) <= 4e-7f * zn) {
+        z = zn;
         break;
       }
+      if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
+      z = zn;
     }
-    if (!done || !(y > 0.0 && y <= 1.0)) {
+    // FP64 Newton polish with the FP64 residual and the FP32 root's reciprocal slope
+    // 1/f'(y) = 1/(4 a y^3 + 1): each step multiplies the error by about 1e-7, so two steps take
+    // the FP32 root (~1e-7) below FP64 rounding.
+    const float y32 = ys * z;
+    const double r1 = (double)__frcp_rn(fmaf(4.0f * af * y32 * y32, y32, 1.0f));
+    y = (double)y32;
+    double d = 0.0;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      double y2 = y * y;
+      d = fma(a * y2, y2, y - cc) * r1;
+      y -= d;
+    }
+    iters += 2;
+    if (!(fabsf((float)d) <= 1e-12f * (float)y) || !(y > 0.0)) {
       int it2 = 0;
       y = halley64(a, cc, p.maxit, &it2, &bis);
       iters += it2;
@@ -116,8 +130,8 @@ __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k
   } else {
     y = halley64(a, cc, p.maxit, &iters, &bis);
   }
-  double x = S * y;
-  double x2 = x * x;
+  const double x = S * y;
+  const double x2 = x * x;
   e = x;
   E = fma(a1 * x2, x2, E0) * u;
   return true;

@@ -21,13 +21,31 @@ struct GridDev {
   int bc[6];
   double bc_val[6];
   double dx[3];
+  double inv_dx2[3];  // 1/dx^2 per axis
   long long ncell;
 };
 
 struct ExchangeParams {
   double c, sigma, gamma, gas_R, dt;
   int maxit;
+  double cdt;  // c dt
+  double k4;   // 4 sigma dt ((gamma-1)/gas_R)^4: a1 = k4 kappa / rho^3
 };
+
+__host__ __device__ inline ExchangeParams make_exchange(double c, double a_rad, double gamma, double gas_R, double dt,
+                                                        int maxit) {
+  ExchangeParams p;
+  p.c = c;
+  p.sigma = a_rad * c / 4.0;  // a_r = 4 sigma / c
+  p.gamma = gamma;
+  p.gas_R = gas_R;
+  p.dt = dt;
+  p.maxit = maxit;
+  p.cdt = c * dt;
+  double t = (gamma - 1.0) / gas_R;
+  p.k4 = 4.0 * p.sigma * dt * t * t * t * t;
+  return p;
+}
 
 struct Opacity {
   int model;
@@ -39,6 +57,22 @@ struct Opacity {
 
 // device status word: bit flags OR-ed by kernels, read back by the host
 enum : unsigned { kStatNonpositive = 1u, kStatNonfinite = 2u };
+
+// Range tests on the bit pattern (integer pipe); FP64 compares would occupy the scarce FP64 pipe.
+// gt_zero(x) == (x > 0.0) and ge_zero(x) == (x >= 0.0), NaN giving false, +inf allowed.
+__device__ __forceinline__ bool gt_zero(double x) {
+  long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7FF0000000000000LL;
+}
+__device__ __forceinline__ bool ge_zero(double x) {
+  long long b = __double_as_longlong(x);
+  return (b >= 0 && b <= 0x7FF0000000000000LL) || b == (long long)0x8000000000000000ULL;
+}
+// x > 0 and finite
+__device__ __forceinline__ bool pos_finite(double x) {
+  long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7FF0000000000000LL;
+}
 
 __host__ __device__ inline long long face_count(const int n[3], int a) {
   long long c = 1;

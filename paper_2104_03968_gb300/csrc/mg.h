@@ -69,7 +69,7 @@ class Multigrid {
   cudaError_t solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                       SolveStats* st, cudaStream_t s);
   template <class T>
-  cudaError_t vcycle(int l, int nu1, int nu2, cudaStream_t s);
+  cudaError_t vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s);
 
   GridDev g_{};
   int precision_ = -1;
@@ -79,8 +79,7 @@ class Multigrid {
   // FP64 outer operator and iterate
   double* w64_[3] = {nullptr, nullptr, nullptr};
   double* b64_ = nullptr;
-  double* xa_ = nullptr;
-  double* xb_ = nullptr;
+  double* diag64_ = nullptr;
   double* partials_ = nullptr;
   double* scal_ = nullptr;      // [0] = ||r||^2, [1] = ||b||^2
   double* host_scal_ = nullptr; // pinned mirror

@@ -296,11 +296,14 @@ def _column_case(ncol, ncell, seed=0):
 
 @pytest.mark.parametrize("ncell", [64, 100, 2048])
 @pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
-def test_columns_step_parity(ctx, ncell, order):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_columns_step_parity(ctx, ncell, order, precision):
+    """The mixed form (FP32 tridiagonal solves inside two FP64 refinement passes) is held to the
+    same FP64 tolerance: the refinement reaches FP64 round-off on these columns."""
     from paper_2104_03968_gb300 import fld
     ncol = 6
     case = _column_case(ncol, ncell)
-    p = solver(case["phys"], order=order)
+    p = solver(case["phys"], order=order, precision=precision)
     col = {"r_faces": case["r_faces"], "geometry": "spherical", "bc": case["bc"]}
     eps, E = dev(case["eps"]), dev(case["E"])
     info = fld.columns_step(ctx, case["r_faces"], "spherical", tuple(case["bc"]), case["bc_lo"], case["bc_hi"], p,
@@ -354,10 +357,13 @@ def test_columns_thin_front(ctx):
 
 # ----------------------------------------------------------------------------- batched
 
-def test_step_batched_parity(ctx):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_batched_parity(ctx, precision):
+    """Five uneven grids in one graph launch (the first call also autotunes), each against the
+    oracle; a second call on the same shape reuses the graph."""
     from paper_2104_03968_gb300 import fld
     cases = inputs.batched_2d(ngrids=5, nmin=32, nmax=96, seed=21)
-    params = [solver(c["phys"], rtol=1e-13) for c in cases]
+    params = [solver(c["phys"], rtol=1e-13 if precision == "fp64" else 1e-12, precision=precision) for c in cases]
     eps = [dev(c["eps"]) for c in cases]
     E = [dev(c["E"]) for c in cases]
     infos = fld.step_batched(ctx, [c["grid"] for c in cases], params, [c["dt"] for c in cases],
@@ -367,6 +373,37 @@ def test_step_batched_parity(ctx):
         e_o, E_o, _ = oracle.step(c["grid"], c["phys"], c["dt"], c["rho"], c["eps"], c["E"], rtol=1e-14)
         assert relerr(host(tE), E_o) < TOL
         assert relerr(host(te), e_o) < TOL
+    # second step through the cached graph, against a second oracle step
+    infos2 = fld.step_batched(ctx, [c["grid"] for c in cases], params, [c["dt"] for c in cases],
+                              [dev(c["rho"]) for c in cases], eps, E)
+    for c, i, te, tE in zip(cases, infos2, eps, E):
+        assert i["status"] == 0
+        e1, E1, _ = oracle.step(c["grid"], c["phys"], c["dt"], c["rho"], c["eps"], c["E"], rtol=1e-14)
+        e2, E2, _ = oracle.step(c["grid"], c["phys"], c["dt"], c["rho"], e1, E1, rtol=1e-14)
+        assert relerr(host(tE), E2) < TOL
+        assert relerr(host(te), e2) < TOL
+
+
+def test_step_batched_mixed_dims_and_boundaries(ctx):
+    """A batch mixing 2-D and 3-D grids, different boundary conditions and both step orders."""
+    from paper_2104_03968_gb300 import fld
+    shapes = [((48, 32), "periodic", "diffuse_then_exchange"), ((16, 16, 8), "dirichlet", "exchange_then_diffuse"),
+              ((40, 24), "mixed", "diffuse_then_exchange"), ((24, 16, 16), "neumann", "diffuse_then_exchange")]
+    cases, params = [], []
+    for k, (shape, bcname, order) in enumerate(shapes):
+        c = inputs.random_small(shape, seed=40 + k, bc=BCS[bcname], dt_factor=50.0)
+        cases.append(c)
+        params.append(solver(c["phys"], rtol=1e-13, order=order))
+    eps = [dev(c["eps"]) for c in cases]
+    E = [dev(c["E"]) for c in cases]
+    infos = fld.step_batched(ctx, [c["grid"] for c in cases], params, [c["dt"] for c in cases],
+                             [dev(c["rho"]) for c in cases], eps, E)
+    for c, p, i, te, tE in zip(cases, params, infos, eps, E):
+        assert i["status"] == 0, i
+        e_o, E_o, _ = oracle.step(c["grid"], c["phys"], c["dt"], c["rho"], c["eps"], c["E"], order=p["order"],
+                                  rtol=1e-14)
+        assert relerr(host(tE).reshape(E_o.shape), E_o) < TOL
+        assert relerr(host(te).reshape(e_o.shape), e_o) < TOL
 
 
 # ----------------------------------------------------------------------------- errors
