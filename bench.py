@@ -29,21 +29,27 @@ sys.path.insert(0, ROOT)
 METRIC = "implicit FLD cell-updates/s at 1e-8 residual (FP64 vs mixed); % HBM peak"
 UNIT = "cell-updates/s"
 
-# Algorithmic (minimum) bytes per cell of one launch, and the FP64 instruction estimate per
-# cell, for the kernels whose roofline is reported.  "L0" = the finest multigrid level.
+# Per-kernel roofline model, per cell of the launch's level.  HBM-bound kernels: algorithmic
+# (minimum) bytes.  FP64-bound kernels: the FP64 operations the formula needs (an FMA counts as
+# 2, a reciprocal or square root as 1), compared with the nominal FP64 rate.
+FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal dense FP64 (1.25 TFLOP/s)
 KERNEL_MODEL = {
-    # one colour of a red-black sweep over level 0: the colour's r, 1/diag and x (write), the
-    # other colour's x, the 3 face arrays -- per cell of the level: (0.5+0.5+0.5+0.5)*s + 3*s
-    "smooth_L0": {"bytes_f32": 2 * 4 + 3 * 4, "bytes_f64": 2 * 8 + 3 * 8},
-    "smooth_L0_zero": {"bytes_f32": 3 * 0.5 * 4, "bytes_f64": 3 * 0.5 * 8},
-    # FP64 outer residual: x, b, diag, 3 face arrays in; r (inner precision) out
-    "residual": {"bytes_f32": 8 + 8 + 8 + 24 + 4, "bytes_f64": 8 + 8 + 8 + 24 + 8},
-    "coeffs": {"bytes_f32": 3 * 8 + 2 * 8, "bytes_f64": 3 * 8 + 2 * 8},
-    "exchange": {"bytes_f32": 4 * 8 + 2 * 8, "bytes_f64": 4 * 8 + 2 * 8},
-    "restrict_L0": {"bytes_f32": 2 * 4 + 3 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 3 * 8 + 8 / 8},
-    "prolong_L0": {"bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
-    "faces": {"bytes_f32": 8 + 3 * (8 + 4), "bytes_f64": 8 + 3 * 8},
-    "fine_setup": {"bytes_f32": 8 + 24 + 8 + 4, "bytes_f64": 8 + 24 + 8 + 8},
+    # one colour of a red-black sweep on the finest level: the colour's r and x (write), the other
+    # colour's x, the 3 face arrays (the FP32 sweep rebuilds 1/diag from them; FP64 reads 1/diag)
+    "smooth_L0": {"bound": "hbm", "bytes_f32": 3 * 0.5 * 4 + 3 * 4, "bytes_f64": 4 * 0.5 * 8 + 3 * 8},
+    "smooth_L0_zero": {"bound": "hbm", "bytes_f32": 3 * 0.5 * 4, "bytes_f64": 3 * 0.5 * 8},
+    "restrict_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 3 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 3 * 8 + 8 / 8},
+    "prolong_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
+    # FP64 outer residual r = b - d x + sum_6 w x_nb, and r^2: 7 FMA + 1 FMA
+    "residual": {"bound": "alu", "flops": 16},
+    # opacity (10), 5-point gradient in 3 axes (21), limiter and D (14)
+    "coeffs": {"bound": "alu", "flops": 45},
+    # three harmonic means sharing one reciprocal, times dt/dx^2
+    "faces": {"bound": "alu", "flops": 27},
+    # coefficients of the rescaled quartic (24), two FP64 polish steps (14), E update (6)
+    "exchange": {"bound": "alu", "flops": 44},
+    # diagonal 1 + sum of 6 faces, rhs copy
+    "fine_setup": {"bound": "alu", "flops": 7},
 }
 # launches per traced scope (some scopes hold several kernels)
 SCOPE_KERNELS = {"faces": 3, "coarse_setup": 4, "norm_b": 2}
@@ -140,9 +146,17 @@ def allreduce_max(world, x: float) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(world: int, cells_per_rank: int, steps: int, local_ms: float):
+    """Replicas: every rank advances its own grid.  The job's time is the slowest rank's; the
+    job's throughput is all ranks' cell-updates over it.  Returns (max_ms, cell-updates/s)."""
+    ms = allreduce_max(world, local_ms)
+    return ms, world * cells_per_rank * steps / (ms * 1e-3)
 
 
 # ----------------------------------------------------------------------------- oracle leg
@@ -208,21 +222,32 @@ def timed_steps(torch, fld, ctx, g, p, dt, rho, eps, E, steps, trace=False):
     return t0.elapsed_time(t1), infos, rep
 
 
-def roofline(rep: dict, ncell: int, precision: str, peaks: dict, traffic: dict):
+def roofline(rep: dict, ncell: int, precision: str, peaks: dict, traffic: dict, bound=None):
+    """Roofline of the modelled kernel with the largest traced time (restricted to one bound
+    when `bound` is given): algorithmic bytes or FP64 flops per launch over its mean launch time."""
     if not rep:
         return None
-    name = max((k for k in rep if k in KERNEL_MODEL), key=lambda k: rep[k][1])
+    cands = [k for k in rep if k in KERNEL_MODEL and (bound is None or KERNEL_MODEL[k]["bound"] == bound)]
+    if not cands:
+        return None
+    name = max(cands, key=lambda k: rep[k][1])
     launches, ms = rep[name]
-    key = "bytes_f32" if precision == "mixed" else "bytes_f64"
-    per_cell = KERNEL_MODEL[name][key]
-    bytes_launch = per_cell * ncell
+    model = KERNEL_MODEL[name]
     avg_s = ms / launches * 1e-3
-    achieved = bytes_launch / avg_s / 1e9
-    tr = traffic.get(name)
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
-            "traffic": tr, "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": ms / launches,
-            "launches": launches, "share_of_traced_ms": ms / sum(v[1] for v in rep.values())}
+    out = {"kernel": name, "bound": model["bound"], "avg_launch_ms": ms / launches, "launches": launches,
+           "share_of_traced_ms": ms / sum(v[1] for v in rep.values())}
+    if model["bound"] == "hbm":
+        per_cell = model["bytes_f32" if precision == "mixed" else "bytes_f64"]
+        achieved = per_cell * ncell / avg_s / 1e9
+        out.update({"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "peak_source": peaks["source"] + " copy bandwidth", "traffic": traffic.get(name),
+                    "algorithmic_bytes_per_launch": per_cell * ncell})
+    else:
+        achieved = model["flops"] * ncell / avg_s / 1e9
+        out.update({"achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                    "frac": achieved / FP64_PEAK_GFLOPS, "peak_source": "nominal FP64 rate of GB300",
+                    "traffic": traffic.get(name), "algorithmic_flops_per_launch": model["flops"] * ncell})
+    return out
 
 
 def main():
@@ -280,8 +305,7 @@ def main():
     ms, infos, rep = timed_steps(torch, fld, ctx, g, p, dt, rho0, eps, E, args.steps, trace=True)
     clk = clocks.stop()
     barrier(world)
-    ms = allreduce_max(world, ms)
-    value = world * ncell * args.steps / (ms * 1e-3)
+    ms, value = replica_throughput(world, ncell, args.steps, ms)
     launches = sum(v[0] * SCOPE_KERNELS.get(k, 1) for k, v in rep.items())
     traffic = {}
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -292,6 +316,7 @@ def main():
             traffic = tdata.get("bytes_per_launch", {})
     peaks = load_peaks()
     roof = roofline(rep, ncell, args.precision, peaks, traffic)
+    roof_hbm = roofline(rep, ncell, args.precision, peaks, traffic, bound="hbm")
 
     # ---- same inputs, one step of each precision, to report the mixed error against FP64
     extra = {}
@@ -347,7 +372,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64+f32 (FP32 V-cycles, FP64 residual/update/norm/exchange)" if args.precision == "mixed"
                 else "f64",
-                "data": "synthetic", "config": workload_config(args), "roofline": roof, "cpu_baseline": cpu,
+                "data": "synthetic", "config": workload_config(args), "roofline": roof, "roofline_hbm": roof_hbm, "cpu_baseline": cpu,
                 "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in sorted(rep.items(), key=lambda kv: -kv[1][1])},
                 "cycles_per_step": [i["cycles"] for i in infos],

@@ -62,7 +62,9 @@ typedef enum {
 
 /* boundary conditions (Sect. 3.4): ghost value, fixed gradient, linear extrapolation */
 enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2, FLD_BC_CONTINUOUS = 3 };
-enum { FLD_LIMITER_LP = 0, FLD_LIMITER_THIRD = 1 };   /* Eq. fld_lambda, or lambda = 1/3 */
+/* Eq. fld_lambda; lambda = 1/3 (the diffusion limit); or the Minerbo limiter, the alternative
+   Sect. 2.2 names: lambda = 2/(3 + sqrt(9 + 12 R^2)) for R <= 3/2, 1/(1 + R + sqrt(1 + 2R)) above */
+enum { FLD_LIMITER_LP = 0, FLD_LIMITER_THIRD = 1, FLD_LIMITER_MINERBO = 2 };
 enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_KRAMERS = 1, FLD_OPACITY_TABLE = 2 };
 enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 };
 enum { FLD_ORDER_DIFFUSE_THEN_EXCHANGE = 0, FLD_ORDER_EXCHANGE_THEN_DIFFUSE = 1 };

@@ -35,7 +35,7 @@ _lock = threading.Lock()
 _lib = None
 
 BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3}
-LIMITER = {"lp": 0, "third": 1}
+LIMITER = {"lp": 0, "third": 1, "minerbo": 2}
 OPACITY = {"const": 0, "kramers": 1, "table": 2}
 GEOMETRY = {"cartesian": 0, "spherical": 1}
 
@@ -76,6 +76,7 @@ def _load():
             P = ct.c_void_p
             sig = {
                 "ora_lambda": (ct.c_double, [ct.c_double]),
+                "ora_lambda_minerbo": (ct.c_double, [ct.c_double]),
                 "ora_temperature": (ct.c_double, [P, ct.c_double, ct.c_double]),
                 "ora_kappa": (ct.c_double, [P, ct.c_double, ct.c_double]),
                 "ora_opacity": (None, [ct.c_size_t, P, _D, _D, _D]),
@@ -161,6 +162,11 @@ def _ref(s):
 def lam(R: float) -> float:
     """Levermore-Pomraning limiter, Sect. 2.2, Eq. (fld_lambda)."""
     return _load().ora_lambda(float(R))
+
+
+def lam_minerbo(R: float) -> float:
+    """Minerbo limiter, the alternative Sect. 2.2 names."""
+    return _load().ora_lambda_minerbo(float(R))
 
 
 def temperature(phys: dict, rho: float, eps: float) -> float:

@@ -8,6 +8,9 @@
  *
  * What each function follows:
  *   ora_lambda            Sect. 2.2, Eq. (fld_lambda): Levermore-Pomraning limiter.
+ *   ora_lambda_minerbo    the Minerbo limiter that Sect. 2.2 names as the alternative (its
+ *                         formula is not printed there; the two-branch form of Minerbo's
+ *                         closure, joined at R = 3/2, is restated here).
  *   ora_coeffs            Sect. 2.2, Eqs. (fld_lambda), (fld_F) and the ratio R; Sect. 3.2,
  *                         Eq. (ileyk_flux): 4th-order 5-point gradient.
  *   face coefficients     Sect. 3.4: harmonic mean of the two cell-centred D.
@@ -43,6 +46,17 @@
 double ora_lambda(double R) {
   /* Sect. 2.2, Eq. (fld_lambda) */
   return (2.0 + R) / (6.0 + 3.0 * R + R * R);
+}
+
+double ora_lambda_minerbo(double R) {
+  if (R <= 1.5) return 2.0 / (3.0 + sqrt(9.0 + 12.0 * R * R));
+  return 1.0 / (1.0 + R + sqrt(1.0 + 2.0 * R));
+}
+
+double ora_limiter(int limiter, double R) {
+  if (limiter == ORA_LIM_THIRD) return 1.0 / 3.0;
+  if (limiter == ORA_LIM_MINERBO) return ora_lambda_minerbo(R);
+  return ora_lambda(R);
 }
 
 double ora_temperature(const ora_phys* p, double rho, double eps) {
@@ -153,7 +167,7 @@ int ora_coeffs(const ora_grid* g, const ora_phys* p, const double* E, const doub
     if (gradmag) gradmag[c] = gm;
     double kr = kappa[c] * rho[c];
     double R = gm / (kr * E[c]);
-    double lam = p->limiter == ORA_LIM_THIRD ? 1.0 / 3.0 : ora_lambda(R);
+    double lam = ora_limiter(p->limiter, R);
     D_cell[c] = p->c * lam / kr; /* Sect. 2.2, Eq. (fld_F): F = -c lambda grad E/(kappa rho) */
   }
   return 0;
@@ -438,7 +452,7 @@ int ora_column_coeffs(int n, const double* rf, int bc_lo, int bc_hi, double v_lo
     double d = (hm * hm * (ep - E[i]) + hp * hp * (E[i] - em)) / (hm * hp * (hm + hp));
     double kr = kappa[i] * rho[i];
     double R = fabs(d) / (kr * E[i]);
-    double lam = p->limiter == ORA_LIM_THIRD ? 1.0 / 3.0 : ora_lambda(R);
+    double lam = ora_limiter(p->limiter, R);
     D_cell[i] = p->c * lam / kr;
   }
   return 0;

@@ -15,7 +15,7 @@ extern "C" {
 #endif
 
 enum { ORA_BC_PERIODIC = 0, ORA_BC_NEUMANN = 1, ORA_BC_DIRICHLET = 2, ORA_BC_CONTINUOUS = 3 };
-enum { ORA_LIM_LP = 0, ORA_LIM_THIRD = 1 };
+enum { ORA_LIM_LP = 0, ORA_LIM_THIRD = 1, ORA_LIM_MINERBO = 2 };
 enum { ORA_OPA_CONST = 0, ORA_OPA_KRAMERS = 1, ORA_OPA_TABLE = 2 };
 enum { ORA_GEOM_CARTESIAN = 0, ORA_GEOM_SPHERICAL = 1 };
 
@@ -38,6 +38,8 @@ typedef struct {
 } ora_phys;
 
 double ora_lambda(double R);
+double ora_lambda_minerbo(double R);
+double ora_limiter(int limiter, double R);
 double ora_temperature(const ora_phys* p, double rho, double eps);
 double ora_kappa(const ora_phys* p, double rho, double T);
 void ora_opacity(size_t n, const ora_phys* p, const double* rho, const double* eps, double* kappa);

@@ -91,7 +91,7 @@ fld_status check_params(fld_ctx* ctx, const fld_params* p, bool solver) {
   if (!p) return fail(ctx, FLD_ERR_INVALID_ARG, "params is NULL");
   if (!(p->c > 0) || !(p->a_rad > 0) || !(p->gamma > 1) || !(p->gas_R > 0))
     return fail(ctx, FLD_ERR_INVALID_ARG, "c, a_rad, gas_R must be > 0 and gamma > 1");
-  if (p->limiter != FLD_LIMITER_LP && p->limiter != FLD_LIMITER_THIRD)
+  if (p->limiter < FLD_LIMITER_LP || p->limiter > FLD_LIMITER_MINERBO)
     return fail(ctx, FLD_ERR_INVALID_ARG, "unknown limiter %d", p->limiter);
   if (p->opacity < FLD_OPACITY_CONST || p->opacity > FLD_OPACITY_TABLE)
     return fail(ctx, FLD_ERR_INVALID_ARG, "unknown opacity model %d", p->opacity);

@@ -93,17 +93,8 @@ __device__ __forceinline__ bool coeffs_cell(const GridDev& g, const CoeffPhys& p
     double d = (em2 - ep2) * (1.0 / 12.0) + (ep1 - em1) * (2.0 / 3.0);
     g2 = fma(d * d, g.inv_dx2[a], g2);
   }
-  double q_ = kap * rh;  // kappa rho, the inverse mean free path
-  double D;
-  if (ph.limiter == FLD_LIMITER_THIRD) {
-    D = ph.c * (1.0 / (3.0 * q_));
-  } else {
-    // c lambda/(kappa rho) with lambda = (2+R)/(6+3R+R^2), R = |grad E|/(kappa rho E),
-    // multiplied through by (kappa rho E)^2 so that one reciprocal remains
-    double gm = sqrt(g2);
-    double qe = q_ * e;
-    D = ph.c * e * (2.0 * qe + gm) * (1.0 / (qe * (6.0 * qe + 3.0 * gm) + g2));
-  }
+  const double q_ = kap * rh;  // kappa rho, the inverse mean free path
+  const double D = limited_D(ph.limiter, ph.c, q_, e, g2, ph.limiter == FLD_LIMITER_THIRD ? 0.0 : sqrt(g2));
   D_out = D;
   return true;
 }

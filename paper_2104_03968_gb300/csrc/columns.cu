@@ -274,14 +274,7 @@ __global__ void k_columns(ColArgs A) {
       else if (A.bc_hi == FLD_BC_NEUMANN) ep = e + vhi * hr;
       else ep = e + (e - sx[n - 2]) * fhi;
       double gm = fabs(cp[i] * (ep - e) + cm[i] * (e - em));
-      double q = k * rh;
-      double D;
-      if (A.limiter == FLD_LIMITER_THIRD) {
-        D = A.c / (3.0 * q);
-      } else {
-        double qe = q * e;
-        D = A.c * e * (2.0 * qe + gm) / (qe * (6.0 * qe + 3.0 * gm) + gm * gm);
-      }
+      const double D = limited_D(A.limiter, A.c, k * rh, e, gm * gm, gm);
       sD[i] = D;
     }
     __syncthreads();
@@ -633,7 +626,7 @@ cudaError_t static_scratch(double** out) {
 
 bool static_params_ok(const fld_params* p) {
   if (!p || !(p->c > 0) || !(p->a_rad > 0) || !(p->gamma > 1) || !(p->gas_R > 0)) return false;
-  if (p->limiter != FLD_LIMITER_LP && p->limiter != FLD_LIMITER_THIRD) return false;
+  if (p->limiter < FLD_LIMITER_LP || p->limiter > FLD_LIMITER_MINERBO) return false;
   if (p->opacity < FLD_OPACITY_CONST || p->opacity > FLD_OPACITY_TABLE) return false;
   if (p->opacity != FLD_OPACITY_TABLE && !(p->kappa0 > 0)) return false;
   if (p->opacity == FLD_OPACITY_TABLE &&

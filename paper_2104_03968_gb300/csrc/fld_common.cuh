@@ -115,4 +115,22 @@ __device__ inline double opacity(const Opacity& o, double rho, double T) {
   return exp10(l);
 }
 
+// Cell diffusion coefficient D = c lambda(R) / (kappa rho) with R = |grad E| / (kappa rho E)
+// (Sect. 2.2, Eqs. fld_lambda and fld_F).  q = kappa rho, g2 = |grad E|^2, gm = |grad E|.  Each
+// limiter is multiplied through by powers of q E so that one reciprocal and at most one square
+// root remain:
+//   LP       lambda = (2+R)/(6+3R+R^2)                 D = c E (2qE + g) / (qE (6qE + 3g) + g^2)
+//   Minerbo  lambda = 2/(3+sqrt(9+12R^2)), R <= 3/2     D = 2 c E / (3qE + sqrt(9 (qE)^2 + 12 g^2))
+//            lambda = 1/(1+R+sqrt(1+2R)),  R > 3/2      D = c E / (qE + g + sqrt(qE (qE + 2g)))
+//   third    lambda = 1/3                              D = c / (3q)
+__device__ __forceinline__ double limited_D(int limiter, double c, double q, double e, double g2, double gm) {
+  const double qe = q * e;
+  if (limiter == FLD_LIMITER_THIRD) return c * (1.0 / (3.0 * q));
+  if (limiter == FLD_LIMITER_MINERBO) {
+    if (gm <= 1.5 * qe) return 2.0 * c * e * (1.0 / (3.0 * qe + sqrt(fma(9.0 * qe, qe, 12.0 * g2))));
+    return c * e * (1.0 / (qe + gm + sqrt(qe * (qe + 2.0 * gm))));
+  }
+  return c * e * (2.0 * qe + gm) * (1.0 / (qe * (6.0 * qe + 3.0 * gm) + g2));
+}
+
 }  // namespace fld

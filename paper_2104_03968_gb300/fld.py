@@ -23,7 +23,7 @@ import torch
 from . import build as _build
 
 BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3}
-LIMITER = {"lp": 0, "third": 1}
+LIMITER = {"lp": 0, "third": 1, "minerbo": 2}
 OPACITY = {"const": 0, "kramers": 1, "table": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 ORDER = {"diffuse_then_exchange": 0, "exchange_then_diffuse": 1}

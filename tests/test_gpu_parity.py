@@ -55,7 +55,7 @@ BCS = {
 
 @pytest.mark.parametrize("shape", [(70, 45), (24, 20, 18), (300,)])
 @pytest.mark.parametrize("bcname", ["periodic", "neumann", "dirichlet", "mixed", "continuous"])
-@pytest.mark.parametrize("limiter", ["lp", "third"])
+@pytest.mark.parametrize("limiter", ["lp", "third", "minerbo"])
 def test_coeffs_parity(ctx, shape, bcname, limiter):
     from paper_2104_03968_gb300 import fld
     case = inputs.random_small(shape, seed=len(shape) * 7 + len(bcname), bc=BCS[bcname], limiter=limiter)
@@ -294,6 +294,19 @@ def _column_case(ncol, ncell, seed=0):
     return case
 
 
+def test_step_parity_minerbo(ctx):
+    """The Minerbo limiter through a full 3-D step (both branches of the limiter are met)."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.lognormal_3d(n=32, seed=12)
+    g, p = case["grid"], dict(case["phys"], limiter="minerbo")
+    e_o, E_o, _ = oracle.step(g, p, case["dt"], case["rho"], case["eps"], case["E"], rtol=1e-14)
+    eps, E = dev(case["eps"]), dev(case["E"])
+    info = fld.step(ctx, g, solver(p, precision="mixed", rtol=1e-13), case["dt"], dev(case["rho"]), eps, E)
+    assert info["status"] == 0
+    assert relerr(host(E), E_o) < TOL
+    assert relerr(host(eps), e_o) < TOL
+
+
 @pytest.mark.parametrize("ncell", [64, 100, 2048])
 @pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -303,7 +316,9 @@ def test_columns_step_parity(ctx, ncell, order, precision):
     from paper_2104_03968_gb300 import fld
     ncol = 6
     case = _column_case(ncol, ncell)
-    p = solver(case["phys"], order=order, precision=precision)
+    # the Minerbo limiter rides along on one configuration
+    lim = "minerbo" if (ncell, order, precision) == (100, "exchange_then_diffuse", "mixed") else "lp"
+    p = solver(case["phys"], order=order, precision=precision, limiter=lim)
     col = {"r_faces": case["r_faces"], "geometry": "spherical", "bc": case["bc"]}
     eps, E = dev(case["eps"]), dev(case["E"])
     info = fld.columns_step(ctx, case["r_faces"], "spherical", tuple(case["bc"]), case["bc_lo"], case["bc_hi"], p,

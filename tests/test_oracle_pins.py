@@ -35,6 +35,41 @@ def test_lambda_limits():
     assert np.all(lams * Rs <= 1.0 + 1e-15)
 
 
+def test_minerbo_limits():
+    """The Minerbo limiter (the alternative Sect. 2.2 names): the same diffusion and
+    free-streaming limits as Eq. (fld_lambda), a different O(R^2) term (1/3 - R^2/9), and its
+    two branches meet at R = 3/2 with the common value 2/9."""
+    lm = oracle.lam_minerbo
+    assert lm(0.0) == 1.0 / 3.0
+    for R in (1e-2, 1e-3):
+        assert abs(lm(R) - (1 / 3 - R * R / 9)) < 0.2 * R ** 3
+    for R in (1e6, 1e8):
+        assert abs(R * lm(R) - 1.0) < 3.0 / R ** 0.5
+    h = 1e-9
+    assert lm(1.5) == pytest.approx(2.0 / 9.0, rel=1e-15)
+    assert lm(1.5 - h) == pytest.approx(2.0 / 9.0, rel=1e-8)
+    assert lm(1.5 + h) == pytest.approx(2.0 / 9.0, rel=1e-8)
+    Rs = np.logspace(-6, 6, 200)
+    lams = np.array([lm(r) for r in Rs])
+    assert np.all(np.diff(lams) < 0)
+    assert np.all(lams * Rs <= 1.0 + 1e-15)
+    # it differs from Levermore-Pomraning between the limits (a wrong dispatch would not)
+    assert abs(lm(1.0) - oracle.lam(1.0)) > 0.02
+    # through the coefficients: the same thick-limit D and a causal flux
+    n = 32
+    g = _line_grid(n)
+    x = (np.arange(n) + 0.5) * 0.5
+    phys = dict(inputs.code_units(), c=3.0, limiter="minerbo")
+    E = np.exp(0.3 * x)
+    rho = np.full(n, 2.0)
+    D = oracle.coeffs(g, phys, E, rho, np.full(n, 1e7))
+    assert np.allclose(D, phys["c"] / (3 * 1e7 * 2.0), rtol=1e-10)
+    D, gm = oracle.coeffs(g, phys, E, rho, np.full(n, 1e-9), with_grad=True)
+    assert np.all(D * gm <= phys["c"] * E * (1 + 1e-14))
+    # R = 0.3 / (1e-9 * 2) = 1.5e8 and R lambda = 1 - sqrt(2/R) + O(1/R) on the upper branch
+    assert np.allclose((D * gm)[2:-2], phys["c"] * E[2:-2], rtol=3 * (2 / 1.5e8) ** 0.5)
+
+
 def test_golden_paper_values():
     """Numbers the paper prints for its limiter and test setups."""
     with open(os.path.join(GOLDEN, "paper_values.json")) as f:
