@@ -38,6 +38,12 @@ KERNEL_MODEL = {
     # colour's x, the 3 face arrays (the FP32 sweep rebuilds 1/diag from them; FP64 reads 1/diag)
     "smooth_L0": {"bound": "hbm", "bytes_f32": 3 * 0.5 * 4 + 3 * 4, "bytes_f64": 4 * 0.5 * 8 + 3 * 8},
     "smooth_L0_zero": {"bound": "hbm", "bytes_f32": 3 * 0.5 * 4, "bytes_f64": 3 * 0.5 * 8},
+    # one full red-black sweep in one pass (wavefront): r, 3 faces, x in, x out (the FP64 sweep
+    # also reads 1/diag); from x = 0 the first colour reads 1/diag instead of x; the last sweep of a
+    # cycle also updates the FP64 iterate (read + write 16 B)
+    "wave_L0": {"bound": "hbm", "bytes_f32": 4 + 12 + 4 + 4, "bytes_f64": 8 + 24 + 8 + 8 + 8},
+    "wave_L0_zero": {"bound": "hbm", "bytes_f32": 4 + 12 + 2 + 4, "bytes_f64": 8 + 24 + 8 + 8},
+    "wave_L0_update": {"bound": "hbm", "bytes_f32": 4 + 12 + 4 + 4 + 16, "bytes_f64": 8 + 24 + 8 + 8 + 8 + 16},
     "restrict_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 3 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 3 * 8 + 8 / 8},
     "prolong_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
     # FP64 outer residual r = b - d x + sum_6 w x_nb, and r^2: 7 FMA + 1 FMA

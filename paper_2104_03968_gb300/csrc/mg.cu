@@ -13,6 +13,8 @@
 // restriction and prolongation run in FP32 while the residual, update and norm stay FP64.
 #include <array>
 #include <cstdio>
+#include <cstdlib>
+#include <vector>
 
 #include "kernels.h"
 #include "mg.h"
@@ -149,6 +151,173 @@ __global__ void __launch_bounds__(512) k_coarse_solve(LevelDev<T> L, long long n
   coarse_solve_block<T>(L, ncell, invd, r, x, tmp, sweeps, use_rb);
 }
 
+
+// ----------------------------------------------------------------------------- wavefront sweeps
+//
+// One launch performs a full red-black sweep (colour c0, then the other colour) on a large 3-D
+// level in one pass over HBM.  The work is cut into items (half-sweep h in {0, 1}, z-plane k,
+// chunk of rows); blocks take items in ticket order from an atomic counter.  Item (1, k) may start
+// once (0, k-1), (0, k) and (0, k+1) are finished -- the values it reads are final and the values
+// it overwrites have been read.  The host orders the tickets so that half-sweep 1 trails
+// half-sweep 0 by `skew` planes: the planes it revisits are still in L2, and its dependencies were
+// handed out long before, so blocks rarely wait.  A block only ever waits for smaller tickets,
+// which running blocks hold, so the scheme cannot deadlock; every wait is bounded all the same
+// and sets the error word when it runs out.  Ordering: the compute warps' stores, a barrier among
+// them, then one of them increments the plane's counter with release semantics; a dependent
+// block's scheduling thread observes the counters and fences (acquire), and the block barrier
+// orders its compute warps' reads after that.
+// The arithmetic per cell is the one of k_smooth, so the result equals two k_smooth launches.
+constexpr int kWaveThreads = 256;
+constexpr int kWaveCompute = kWaveThreads - 32;  // warps 1..7 compute, warp 0 schedules
+constexpr int kWaveUnroll = 4;
+constexpr int kWaveItem = 2 * kWaveCompute * kWaveUnroll;  // colour cells per item (rows of a plane)
+constexpr long long kWaveSpinLimit = 1LL << 21;  // with up to 1 us sleeps: about two seconds
+
+struct WaveDev {
+  const int* order;
+  unsigned* ctl;
+  int nchunk, rows;
+  unsigned total;
+};
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait until the previous half-sweep has finished planes k-1, k and k+1 (on a bounded z
+// axis the missing neighbour is replaced by k itself), then fence: the relaxed reads and the fence
+// form an acquire, and the block barrier that follows extends it to the other threads.
+__device__ __forceinline__ bool wave_wait(unsigned* ctl, const unsigned* done_prev, int k, int nz, bool periodic, unsigned target) {
+  const int km = k > 0 ? k - 1 : (periodic ? nz - 1 : k);
+  const int kp = k < nz - 1 ? k + 1 : (periodic ? 0 : k);
+  unsigned ns = 32;
+  for (long long it = 0;; ++it) {
+    const unsigned a = ld_relaxed_gpu(done_prev + km), b = ld_relaxed_gpu(done_prev + k),
+                   c = ld_relaxed_gpu(done_prev + kp);
+    if (a >= target && b >= target && c >= target) break;
+    if (it > kWaveSpinLimit || *(volatile unsigned*)ctl != 0u) {
+      atomicOr(ctl, 1u);
+      return false;
+    }
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  return true;
+}
+
+// One face of a cell, branch-free: the cell across it (the cell itself where the face has none, so
+// that the load stays valid), cv multiplying w x_nb in the sum and cd multiplying w in the diagonal:
+// interior or periodic (+1, +1), Dirichlet ghost (0, +1), Neumann (0, 0), linear extrapolation
+// (-1, -1) -- the same terms, in the same order and rounding, as for_each_face in k_smooth.
+template <class T>
+__device__ __forceinline__ void wave_face(bool inside, int bc, int idx, int across, int wrap, int mirror, T w, const T* x,
+                                          T& a, T& d) {
+  const bool per = bc == FLD_BC_PERIODIC, cont = bc == FLD_BC_CONTINUOUS, dir = bc == FLD_BC_DIRICHLET;
+  const int nb = inside ? across : (per ? wrap : (cont ? mirror : idx));
+  const T cv = (inside || per) ? T(1) : (cont ? T(-1) : T(0));
+  const T cd = (inside || per || dir) ? T(1) : (cont ? T(-1) : T(0));
+  a = fma(cv * w, x[nb], a);
+  d = fma(cd, w, d);
+}
+
+// New value of cell (i, j, k) of a 3-D level (32-bit indices: the level has fewer than 2^31 cells
+// and faces per axis).
+template <class T>
+__device__ __forceinline__ T wave_cell(const LevelDev<T>& L, const T* __restrict__ invd, const T* __restrict__ r,
+                                       const T* x, int i, int j, int k, bool zero) {
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const int sy = nx, sz = nx * ny;
+  const int idx = i + sy * j + sz * k;
+  T a = r[idx];
+  if (zero) return a * invd[idx];
+  T d = T(1);
+  const int fx = i + (nx + 1) * (j + ny * k);
+  const int fy = i + nx * (j + (ny + 1) * k);
+  wave_face<T>(i > 0, L.bc[0], idx, idx - 1, idx + (nx - 1), idx + 1, L.w[0][fx], x, a, d);
+  wave_face<T>(i < nx - 1, L.bc[1], idx, idx + 1, idx - (nx - 1), idx - 1, L.w[0][fx + 1], x, a, d);
+  wave_face<T>(j > 0, L.bc[2], idx, idx - sy, idx + (ny - 1) * sy, idx + sy, L.w[1][fy], x, a, d);
+  wave_face<T>(j < ny - 1, L.bc[3], idx, idx + sy, idx - (ny - 1) * sy, idx - sy, L.w[1][fy + nx], x, a, d);
+  wave_face<T>(k > 0, L.bc[4], idx, idx - sz, idx + (nz - 1) * sz, idx + sz, L.w[2][idx], x, a, d);
+  wave_face<T>(k < nz - 1, L.bc[5], idx, idx + sz, idx - (nz - 1) * sz, idx - sz, L.w[2][idx + sz], x, a, d);
+  if constexpr (sizeof(T) == sizeof(float)) return __fdividef(a, d);
+  else return a * invd[idx];
+}
+
+template <class T, bool ZERO, bool UPDATE>
+__global__ void __launch_bounds__(kWaveThreads, 4) k_wave_sweep(LevelDev<T> L, const T* __restrict__ invd,
+                                                                const T* __restrict__ r, T* x, int c0,
+                                                                double* __restrict__ x64, WaveDev W) {
+  // Warp 0 is the control warp: its thread 0 takes the next ticket and waits for that item's
+  // dependencies while warps 1..7 compute the current item; the ticket is handed over at the block
+  // barrier.  The compute warps publish their own item's completion (a barrier among themselves,
+  // then a release increment), so a completion never waits on a control warp.
+  __shared__ unsigned s_ticket[2];
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const int nxh = (nx + 1) >> 1;
+  const bool zper = L.bc[4] == FLD_BC_PERIODIC;
+  unsigned* done = W.ctl + 2;
+  const int ct = (int)threadIdx.x - 32;  // compute thread, 0 .. kWaveCompute - 1
+  auto take = [&]() -> unsigned {
+    unsigned t = atomicAdd(W.ctl + 1, 1u);
+    if (t < W.total) {
+      const int g = (int)(t / (unsigned)W.nchunk);
+      const int h = W.order[2 * g], k = W.order[2 * g + 1];
+      if (h > 0 && !wave_wait(W.ctl, done + (h - 1) * nz, k, nz, zper, (unsigned)W.nchunk)) t = W.total;
+    }
+    return t;
+  };
+  if (threadIdx.x == 0) s_ticket[0] = take();
+  for (int cur = 0;; cur ^= 1) {
+    __syncthreads();
+    const unsigned t = s_ticket[cur];
+    if (t >= W.total) return;
+    if (ct < 0) {
+      if (threadIdx.x == 0) s_ticket[cur ^ 1] = take();
+      continue;
+    }
+    const int g = (int)(t / (unsigned)W.nchunk);
+    const int h = W.order[2 * g], k = W.order[2 * g + 1];
+    const int colour = c0 ^ h;
+    const int j0 = (int)(t % (unsigned)W.nchunk) * W.rows;
+    const int cells = (min(ny, j0 + W.rows) - j0) * nxh;
+    const bool zero = ZERO && h == 0;
+    constexpr int U = sizeof(T) == sizeof(float) ? kWaveUnroll : kWaveUnroll / 2;  // FP64: registers
+    for (int base = 0; base < cells; base += kWaveCompute * U) {
+      T v[U];
+      int id[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        // branch-free, so that the loads of all U cells are in flight together; a slot
+        // past the end of the item computes a valid cell and skips the store
+        const int q = base + u * kWaveCompute + ct;
+        const int qq = min(q, cells - 1);
+        const int j = j0 + qq / nxh;
+        int i = 2 * (qq % nxh) + ((colour + j + k) & 1);
+        ok[u] = q < cells && i < nx;
+        i = min(i, nx - 1);
+        v[u] = wave_cell<T>(L, invd, r, x, i, j, k, zero);
+        id[u] = i + nx * (j + ny * k);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+        x[id[u]] = v[u];
+        if (UPDATE) x64[id[u]] += (double)v[u];
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kWaveCompute) : "memory");
+    if (ct == 0) red_release_gpu_add(done + h * nz + k, 1u);
+  }
+}
+
 // ----------------------------------------------------------------------------- host side
 
 static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -159,10 +328,109 @@ Multigrid::~Multigrid() {
 
 static inline long long cells3(const std::array<int, 3>& n) { return (long long)n[0] * n[1] * n[2]; }
 
+template <class T>
+static LevelDev<T> level_dev(const GridDev& g, const std::array<int, 3>& n, void* const w[3]) {
+  LevelDev<T> L;
+  for (int a = 0; a < 3; ++a) L.n[a] = n[a];
+  L.ndim = g.ndim;
+  for (int f = 0; f < 6; ++f) L.bc[f] = g.bc[f];
+  for (int a = 0; a < 3; ++a) L.w[a] = (const T*)w[a];
+  return L;
+}
+
 static inline long long faces3(const std::array<int, 3>& n, int a) {
   long long c = 1;
   for (int b = 0; b < 3; ++b) c *= (b == a) ? n[b] + 1 : n[b];
   return c;
+}
+
+// Levels that take the wavefront sweep: 3-D and too large to stay in L2 between two passes
+// (4 Mi cells; FLD_WAVE_MIN_CELLS overrides the threshold).
+static long long wave_min_cells() {
+  const char* v = getenv("FLD_WAVE_MIN_CELLS");
+  return v ? std::max(1LL, atoll(v)) : (1LL << 22);
+}
+
+static bool wave_eligible(const GridDev& g, const std::array<int, 3>& n) {
+  const long long faces_x = (long long)(n[0] + 1) * n[1] * n[2];
+  return g.ndim == 3 && cells3(n) >= wave_min_cells() && n[2] >= 4 && faces_x < (1LL << 31) &&
+         (long long)n[0] * (n[1] + 1) * n[2] < (1LL << 31) && (long long)n[0] * n[1] * (n[2] + 1) < (1LL << 31);
+}
+
+// Ticket order of the (half-sweep, plane) groups.  Half-sweep 1 trails half-sweep 0 by `skew`
+// positions.  On a periodic z axis the planes are visited folded (0, nz-1, 1, nz-2, ...), which
+// puts every pair of ring neighbours, the wrap-around pair included, within two positions.
+static std::vector<int> wave_order(int nz, bool periodic, int skew) {
+  const int sk = std::max(skew, periodic ? 2 : 1);
+  auto plane = [&](int p) { return periodic ? ((p & 1) ? nz - 1 - (p >> 1) : (p >> 1)) : p; };
+  std::vector<int> o;
+  o.reserve(4 * (size_t)nz);
+  for (int t = 0; t < nz + sk; ++t)
+    for (int h = 0; h < 2; ++h) {
+      const int p = t - sk * h;
+      if (p >= 0 && p < nz) {
+        o.push_back(h);
+        o.push_back(plane(p));
+      }
+    }
+  return o;
+}
+
+cudaError_t Multigrid::configure_wave() {
+  wave_.assign(dims_.size(), WaveLevel{});
+  wave_ctl_ = (unsigned*)arena_.take((2 + 2 * (size_t)dims_[0][2]) * sizeof(unsigned));
+  if (!wave_ctl_) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemset(wave_ctl_, 0, (2 + 2 * (size_t)dims_[0][2]) * sizeof(unsigned));
+  if (e != cudaSuccess) return e;
+  const char* skew_env = getenv("FLD_WAVE_SKEW");
+  for (size_t l = 0; l < dims_.size(); ++l) {
+    const std::array<int, 3>& n = dims_[l];
+    if (!wave_eligible(g_, n)) continue;
+    WaveLevel& W = wave_[l];
+    const int nxh = (n[0] + 1) / 2;
+    W.rows = std::max(1, kWaveItem / nxh);
+    W.nchunk = (n[1] + W.rows - 1) / W.rows;
+    // half-sweep 1 trails by about 2 Mi cells' worth of planes: far enough (in tickets) that its
+    // dependencies are done when it starts, near enough that those planes are still in L2
+    const long long plane = (long long)n[0] * n[1];
+    const int skew = skew_env ? std::max(1, atoi(skew_env)) : (int)std::max(2LL, ((1LL << 21) + plane - 1) / plane);
+    std::vector<int> o = wave_order(n[2], g_.bc[4] == FLD_BC_PERIODIC, skew);
+    W.order = (int*)arena_.take(o.size() * sizeof(int));
+    if (!W.order) return cudaErrorMemoryAllocation;
+    e = cudaMemcpy(W.order, o.data(), o.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  if (!wave_blocks_[0]) {
+    int dev = 0, sms = 0, bf = 0, bd = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_wave_sweep<float, false, true>, kWaveThreads, 0);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_wave_sweep<double, false, true>, kWaveThreads, 0);
+    if (e != cudaSuccess) return e;
+    wave_blocks_[0] = std::max(1, bf) * sms;
+    wave_blocks_[1] = std::max(1, bd) * sms;
+  }
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t Multigrid::wave_sweep(int l, bool zero, int c0, double* x64, cudaStream_t s) {
+  const std::array<int, 3>& n = dims_[l];
+  const WaveLevel& W = wave_[l];
+  cudaError_t e = cudaMemsetAsync(wave_ctl_ + 1, 0, (1 + 2 * (size_t)n[2]) * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  WaveDev d{W.order, wave_ctl_, W.nchunk, W.rows, (unsigned)(2LL * n[2] * W.nchunk)};
+  LevelDev<T> L = level_dev<T>(g_, n, lv_[l].w);
+  const unsigned grid = std::min<unsigned>(d.total, (unsigned)wave_blocks_[sizeof(T) == sizeof(float) ? 0 : 1]);
+  const T* invd = (const T*)lv_[l].invd;
+  const T* r = (const T*)lv_[l].r;
+  T* x = (T*)lv_[l].x;
+  if (zero) k_wave_sweep<T, true, false><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, nullptr, d);
+  else if (x64) k_wave_sweep<T, false, true><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, x64, d);
+  else k_wave_sweep<T, false, false><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, nullptr, d);
+  return cudaGetLastError();
 }
 
 cudaError_t Multigrid::configure(const GridDev& g, int precision) {
@@ -197,7 +465,9 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
     if (l > 0 || precision == FLD_PREC_MIXED)
       for (int a = 0; a < g.ndim; ++a) add(faces3(dims_[l], a) * es);
     for (int k = 0; k < 4; ++k) add(n * es);  // invd, x, r, tmp
+    if (wave_eligible(g, dims_[l])) add(4 * (size_t)dims_[l][2] * sizeof(int));
   }
+  add((2 + 2 * (size_t)dims_[0][2]) * sizeof(unsigned));
   cudaError_t e = arena_.reserve(bytes + 4096);
   if (e != cudaSuccess) return e;
   for (int a = 0; a < 3; ++a) w64_[a] = a < g.ndim ? (double*)arena_.take(faces3(dims_[0], a) * sizeof(double)) : nullptr;
@@ -226,19 +496,12 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
       if (!lv_[l].w[a]) return cudaErrorMemoryAllocation;
   }
   if (!b64_ || !diag64_ || !partials_ || !scal_) return cudaErrorMemoryAllocation;
+  e = configure_wave();
+  if (e != cudaSuccess) return e;
   configured_ = true;
   return cudaSuccess;
 }
 
-template <class T>
-static LevelDev<T> level_dev(const GridDev& g, const std::array<int, 3>& n, void* const w[3]) {
-  LevelDev<T> L;
-  for (int a = 0; a < 3; ++a) L.n[a] = n[a];
-  L.ndim = g.ndim;
-  for (int f = 0; f < 6; ++f) L.bc[f] = g.bc[f];
-  for (int a = 0; a < 3; ++a) L.w[a] = (const T*)w[a];
-  return L;
-}
 
 template <class T>
 cudaError_t Multigrid::setup_t(double dt, const double* D_cell, const double* E_old, cudaStream_t s) {
@@ -295,9 +558,16 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
   }
   long long nhalf = (long long)((n[0] + 1) / 2) * n[1] * n[2];
   unsigned gb = nblk(nhalf);
+  const bool wave = wave_[l].order != nullptr;
   // pre-smoothing from a zero initial guess: red, black, ...
   const char* sm_name = l == 0 ? "smooth_L0" : "smooth_Lc";
   for (int it = 0; it < nu1; ++it) {
+    if (wave) {
+      TraceScope ts(l == 0 ? (it == 0 ? "wave_L0_zero" : "wave_L0") : "wave_Lc", s);
+      cudaError_t e = wave_sweep<T>(l, it == 0, 0, nullptr, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     {
       TraceScope ts(it == 0 ? (l == 0 ? "smooth_L0_zero" : "smooth_Lc") : sm_name, s);
       if (it == 0) k_smooth<T, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
@@ -321,6 +591,12 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
   // final correction to the FP64 iterate
   for (int it = 0; it < nu2; ++it) {
     bool last = x64 && it == nu2 - 1;
+    if (wave) {
+      TraceScope ts(l == 0 ? (last ? "wave_L0_update" : "wave_L0") : "wave_Lc", s);
+      cudaError_t e = wave_sweep<T>(l, false, 1, last ? x64 : nullptr, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     {
       TraceScope ts(sm_name, s);
       if (last) k_smooth<T, false, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1, x64);
@@ -349,6 +625,12 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
   int cycles = 0;
   double rel = 0.0;
   int status = FLD_ERR_NOT_CONVERGED;
+  unsigned* wave_err = reinterpret_cast<unsigned*>(host_scal_ + 3);
+  *wave_err = 0u;
+  {
+    cudaError_t e = cudaMemsetAsync(wave_ctl_, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+  }
   for (;;) {
     {
       TraceScope ts("residual", s);
@@ -361,8 +643,14 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
     x_in = x;
     cudaError_t e = cudaMemcpyAsync(host_scal_, scal_, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
+    if (cycles > 0) e = cudaMemcpyAsync(wave_err, wave_ctl_, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
+    if (*wave_err) {
+      status = FLD_ERR_DEVICE_TIMEOUT;
+      break;
+    }
     bb = host_scal_[1];
     double rr = host_scal_[0];
     rel = bb > 0 ? sqrt(rr / bb) : sqrt(rr);

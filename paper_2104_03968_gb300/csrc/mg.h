@@ -82,7 +82,20 @@ class Multigrid {
   double* diag64_ = nullptr;
   double* partials_ = nullptr;
   double* scal_ = nullptr;      // [0] = ||r||^2, [1] = ||b||^2
-  double* host_scal_ = nullptr; // pinned mirror
+  double* host_scal_ = nullptr; // pinned mirror ([3] holds the wavefront error word)
+  // Wavefront smoothing (large 3-D levels): per level, the (half-sweep, plane) of each group of
+  // `nchunk` tickets in ticket order; control words [0] error, [1] ticket, [2..] finished chunks
+  // per (half-sweep, plane).
+  struct WaveLevel {
+    int* order = nullptr;  // 2 ints (h, plane) per group
+    int nchunk = 0, rows = 0;
+  };
+  std::vector<WaveLevel> wave_;
+  unsigned* wave_ctl_ = nullptr;
+  int wave_blocks_[2] = {0, 0};  // resident blocks of the sweep kernel (float, double)
+  cudaError_t configure_wave();
+  template <class T>
+  cudaError_t wave_sweep(int l, bool zero, int c0, double* x64, cudaStream_t s);
   int nparts_ = 0;
   // inner levels (type-erased; cast to T per precision)
   struct LevelBuf {

@@ -187,10 +187,10 @@ __device__ __forceinline__ void smooth_colour_cell(const LevelDev<T>& L, const T
     T d = T(1);
     for_each_face(L, i, j, k, idx, [&](T w, int kind, long long nb) {
       if (kind == kInterior) {
-        v += w * x[nb];
+        v = fma(w, x[nb], v);
         if (kOwnDiag) d += w;
       } else if (kind == kContinuous) {
-        v -= w * x[nb];
+        v = fma(-w, x[nb], v);
         if (kOwnDiag) d -= w;
       } else if (kind == kDirichlet) {
         if (kOwnDiag) d += w;
