@@ -2,6 +2,7 @@
 // 2104.03968: Sect. 2.2 Eqs. fld_lambda and fld_F; Sect. 3.2 Eq. ileyk_flux; Sect. 3.4 faces).
 #pragma once
 
+#include "df.cuh"
 #include "fld_common.cuh"
 
 namespace fld {
@@ -104,10 +105,14 @@ __device__ __forceinline__ bool coeffs_cell(const GridDev& g, const CoeffPhys& p
 // q_a = n_a - 1 otherwise (boundary face: ghost D = interior D).  The three harmonic means
 // 2 D_c D_nb / (D_c + D_nb) share one reciprocal: 1/(s0 s1 s2), then 1/s_a is the product of the
 // other two sums times it.
+// With lo arrays (l0..l2 non-null, TW = float) the FP32 copy is the truncated leading part of the
+// FP64 weight and lo receives the remainder, so that t + l carries the weight to ~2^-47.
 template <class TW>
 __device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const double* __restrict__ D, long long idx,
                                            double* __restrict__ w0, double* __restrict__ w1, double* __restrict__ w2,
-                                           TW* __restrict__ t0, TW* __restrict__ t1, TW* __restrict__ t2) {
+                                           TW* __restrict__ t0, TW* __restrict__ t1, TW* __restrict__ t2,
+                                           float* __restrict__ l0 = nullptr, float* __restrict__ l1 = nullptr,
+                                           float* __restrict__ l2 = nullptr) {
   int q[3];
   q[0] = (int)(idx % g.n[0]);
   long long r = idx / g.n[0];
@@ -136,20 +141,28 @@ __device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const do
   const double rd[3] = {den[1] * den[2] * inv, den[0] * den[2] * inv, den[0] * den[1] * inv};
   double* W[3] = {w0, w1, w2};
   TW* Tt[3] = {t0, t1, t2};
+  float* Lo[3] = {l0, l1, l2};
+  auto put = [&](int a, long long f, double w) {
+    W[a][f] = w;
+    if (Lo[a]) {
+      float h, l;
+      split_f64(w, h, l);
+      Tt[a][f] = (TW)h;
+      Lo[a][f] = l;
+    } else if (Tt[a]) {
+      Tt[a][f] = (TW)w;
+    }
+  };
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a >= g.ndim) break;
     const double s = dt * g.inv_dx2[a];
     const double w = s * (pair[a] ? num[a] * rd[a] : num[a]);
-    const long long f = face_index(g.n, a, q[0], q[1], q[2], q[a]);
-    W[a][f] = w;
-    if (Tt[a]) Tt[a][f] = (TW)w;
+    put(a, face_index(g.n, a, q[0], q[1], q[2], q[a]), w);
     const bool periodic = g.bc[2 * a + 1] == FLD_BC_PERIODIC;
     if ((periodic && q[a] == 0) || (!periodic && q[a] == g.n[a] - 1)) {
       const double wu = periodic ? w : s * Dc;
-      const long long fu = face_index(g.n, a, q[0], q[1], q[2], g.n[a]);
-      W[a][fu] = wu;
-      if (Tt[a]) Tt[a][fu] = (TW)wu;
+      put(a, face_index(g.n, a, q[0], q[1], q[2], g.n[a]), wu);
     }
   }
 }

@@ -11,9 +11,10 @@ cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double 
                           int limiter, const double* E, const double* rho, const double* eps,
                           double* kappa_out, double* D_out, unsigned* status, cudaStream_t s);
 
-// w64[a] (and w32[a] when non-null) receive the face weights of axis a (layout of fld_common.cuh)
+// w64[a] (and w32[a] when non-null) receive the face weights of axis a (layout of fld_common.cuh);
+// with w32lo, w32 holds the truncated leading 24 bits of each weight and w32lo the remainder
 cudaError_t launch_faces(const GridDev& g, double dt, const double* D, double* const w64[3], float* const w32[3],
-                         cudaStream_t s);
+                         float* const w32lo[3], cudaStream_t s);
 
 cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity& op, const double* rho,
                             const double* kappa, double* eps, double* E, int* info_iters, int* info_bisect,

@@ -11,13 +11,16 @@
 //                       they cover / 4 (rediscretisation), one-block coarsest solve.
 // T = double is the plain FP64 solver; T = float gives the mixed form whose smoother,
 // restriction and prolongation run in FP32 while the residual, update and norm stay FP64.
+#include <algorithm>
 #include <array>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "kernels.h"
 #include "mg.h"
+#include "df.cuh"
 #include "mg_device.cuh"
 #include "trace.h"
 
@@ -73,12 +76,15 @@ __global__ void k_sumsq(const double* __restrict__ x, long long n, double* __res
 // ----------------------------------------------------------------------------- setup kernels
 // (the per-cell bodies are in mg_device.cuh, shared with the batched solver)
 
+// With dhi/dlo (mixed solver): also the diagonal as a double-float for the residual updates.
 template <class T>
 __global__ void k_fine_setup(LevelDev<double> L, GridDev g, const double* __restrict__ E_old, double* __restrict__ b,
-                             double* __restrict__ diag, T* __restrict__ invd) {
+                             double* __restrict__ diag, T* __restrict__ invd, float* __restrict__ dhi,
+                             float* __restrict__ dlo) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.ncell) return;
   fine_setup_cell<T>(L, g, E_old, idx, b, diag, invd);
+  if (dhi) split_f64(diag[idx], dhi[idx], dlo[idx]);
 }
 
 template <class T>
@@ -112,6 +118,116 @@ __global__ void __launch_bounds__(256, 4) k_residual64(LevelDev<double> L, long 
     acc = fma_residual_cell<T>(L, x_in, x_out, b, diag, r_out, idx, acc);
   acc = block_sum(acc);
   if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+}
+
+// Both mixed-solver residual kernels walk whole x rows (one row per block iteration), so the
+// division of a cell index into (i, j, k) happens once per row rather than once per cell.
+
+// Mixed solver, exact outer residual: r = b - A x in FP64, stored as the double-float (rhi, rlo);
+// rhi is the FP32 right-hand side of the next V-cycle.  parts: per-block sum of r^2.
+__global__ void __launch_bounds__(256, 4) k_residual64_df(LevelDev<double> L, const double* x_in, double* x_out,
+                                                          const double* __restrict__ b, const double* __restrict__ diag,
+                                                          float* __restrict__ rhi, float* __restrict__ rlo,
+                                                          double* __restrict__ parts) {
+  const int nx = L.n[0], ny = L.n[1];
+  const long long rows = (long long)ny * L.n[2];
+  double acc = 0.0;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = (int)(row % ny), k = (int)(row / ny);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const long long idx = (long long)i + (long long)nx * row;
+      const double xc = x_in[idx];
+      double s = fma(-diag[idx], xc, b[idx]);
+      for_each_face(L, i, j, k, idx, [&](double w, int kind, long long nb) {
+        if (kind == kInterior) s = fma(w, x_in[nb], s);
+        else if (kind == kContinuous) s = fma(-w, x_in[nb], s);
+      });
+      if (x_out != x_in) x_out[idx] = xc;
+      split_f64(s, rhi[idx], rlo[idx]);
+      acc = fma(s, s, acc);
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+}
+
+// Mixed solver, updated outer residual after a V-cycle that added the correction d to x:
+//   r_new = r_old - A d,
+// in double-float arithmetic: A's weights and diagonal as hi + lo floats, d exact in FP32, every
+// product exact (two_prod) and the sum carried as s + e.  The error per cell is a small multiple
+// of 2^-48 m, m = |r_old| + diag |d| + sum |w d_nb|.  parts[blk] = sum (scale r_new)^2,
+// parts[nparts + blk] = sum (scale m)^2, summed in FP32 per thread (they steer the iteration and
+// bound its error; neither needs more digits).
+// One face term of the update, branch-free (as wave_face): the neighbour (the cell itself where the
+// face has none, with coefficient 0) and the sign (+1 interior or periodic, -1 extrapolated).
+__device__ __forceinline__ void df_face(bool inside, int bc, int idx, int across, int wrap, int mirror, float whi,
+                                        float wlo, const float* __restrict__ d, float& s, float& e, float& m) {
+  const bool per = bc == FLD_BC_PERIODIC, cont = bc == FLD_BC_CONTINUOUS;
+  const int nb = inside ? across : (per ? wrap : (cont ? mirror : idx));
+  const float sg = (inside || per) ? 1.f : (cont ? -1.f : 0.f);
+  const float xn = sg * d[nb];
+  float t, te, s2, e2;
+  two_prod(whi, xn, t, te);
+  te = fmaf(wlo, xn, te);
+  two_sum(s, t, s2, e2);
+  s = s2;
+  e += e2 + te;
+  m += fabsf(t);
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) k_residual_update(LevelDev<float> L, LevelDev<float> Llo,
+                                                         const float* __restrict__ dhi, const float* __restrict__ dlo,
+                                                         const float* __restrict__ d, float* __restrict__ rhi,
+                                                         float* __restrict__ rlo, float scale, int nparts,
+                                                         double* __restrict__ parts) {
+  // 32-bit indices: the caller guarantees fewer than 2^31 cells and faces per axis
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const int rows = ny * nz, sy = nx, sz = nx * ny;
+  float ss = 0.f, mm = 0.f;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % ny, k = row / ny;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const int idx = i + nx * row;
+      const float dc = d[idx];
+      const float ro = rhi[idx];
+      // s + e = r_old - diag * dc
+      float p, pe, s, e;
+      two_prod(dhi[idx], dc, p, pe);
+      pe = fmaf(dlo[idx], dc, pe);
+      two_sum(ro, -p, s, e);
+      e += rlo[idx] - pe;
+      float m = fabsf(ro) + fabsf(p);
+      const int fx = i + (nx + 1) * row;
+      df_face(i > 0, L.bc[0], idx, idx - 1, idx + (nx - 1), idx + 1, L.w[0][fx], Llo.w[0][fx], d, s, e, m);
+      df_face(i < nx - 1, L.bc[1], idx, idx + 1, idx - (nx - 1), idx - 1, L.w[0][fx + 1], Llo.w[0][fx + 1], d, s, e, m);
+      if (NDIM >= 2) {
+        const int fy = i + nx * (j + (ny + 1) * k);
+        df_face(j > 0, L.bc[2], idx, idx - sy, idx + (ny - 1) * sy, idx + sy, L.w[1][fy], Llo.w[1][fy], d, s, e, m);
+        df_face(j < ny - 1, L.bc[3], idx, idx + sy, idx - (ny - 1) * sy, idx - sy, L.w[1][fy + nx], Llo.w[1][fy + nx],
+                d, s, e, m);
+      }
+      if (NDIM == 3) {
+        df_face(k > 0, L.bc[4], idx, idx - sz, idx + (nz - 1) * sz, idx + sz, L.w[2][idx], Llo.w[2][idx], d, s, e, m);
+        df_face(k < nz - 1, L.bc[5], idx, idx + sz, idx - (nz - 1) * sz, idx - sz, L.w[2][idx + sz],
+                Llo.w[2][idx + sz], d, s, e, m);
+      }
+      float rh, rl;
+      quick_two_sum(s, e, rh, rl);
+      rhi[idx] = rh;
+      rlo[idx] = rl;
+      const float rs = rh * scale, ms = m * scale;
+      ss = fmaf(rs, rs, ss);
+      mm = fmaf(ms, ms, mm);
+    }
+  }
+  const double bs = block_sum((double)ss);
+  __syncthreads();  // block_sum's shared scratch is reused
+  const double bm = block_sum((double)mm);
+  if (threadIdx.x == 0) {
+    parts[blockIdx.x] = bs;
+    parts[nparts + blockIdx.x] = bm;
+  }
 }
 
 // x64 += d (used only when no post-smoothing sweep carries the update)
@@ -458,8 +574,13 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   auto add = [&](size_t b) { bytes += (b + 511) & ~(size_t)255; };
   for (int a = 0; a < g.ndim; ++a) add(faces3(dims_[0], a) * sizeof(double));
   for (int k = 0; k < 2; ++k) add(N * sizeof(double));  // b, diag
-  add(nparts_ * sizeof(double));
-  add(4 * sizeof(double));
+  add(2 * nparts_ * sizeof(double));
+  add(8 * sizeof(double));
+  const bool df = precision == FLD_PREC_MIXED;  // double-float residual updates
+  if (df) {
+    for (int a = 0; a < g.ndim; ++a) add(faces3(dims_[0], a) * sizeof(float));  // weights, low parts
+    for (int k = 0; k < 3; ++k) add(N * sizeof(float));                           // diag hi, lo; r lo
+  }
   for (size_t l = 0; l < dims_.size(); ++l) {
     long long n = cells3(dims_[l]);
     if (l > 0 || precision == FLD_PREC_MIXED)
@@ -473,11 +594,21 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   for (int a = 0; a < 3; ++a) w64_[a] = a < g.ndim ? (double*)arena_.take(faces3(dims_[0], a) * sizeof(double)) : nullptr;
   b64_ = (double*)arena_.take(N * sizeof(double));
   diag64_ = (double*)arena_.take(N * sizeof(double));
-  partials_ = (double*)arena_.take(nparts_ * sizeof(double));
-  scal_ = (double*)arena_.take(4 * sizeof(double));
+  partials_ = (double*)arena_.take(2 * nparts_ * sizeof(double));
+  scal_ = (double*)arena_.take(8 * sizeof(double));
   if (!host_scal_) {
-    e = cudaMallocHost(&host_scal_, 4 * sizeof(double));
+    e = cudaMallocHost(&host_scal_, 8 * sizeof(double));
     if (e != cudaSuccess) return e;
+  }
+  for (int a = 0; a < 3; ++a) w32lo_[a] = nullptr;
+  dhi_ = dlo_ = rlo_ = nullptr;
+  if (df) {
+    for (int a = 0; a < g.ndim; ++a)
+      if (!(w32lo_[a] = (float*)arena_.take(faces3(dims_[0], a) * sizeof(float)))) return cudaErrorMemoryAllocation;
+    dhi_ = (float*)arena_.take(N * sizeof(float));
+    dlo_ = (float*)arena_.take(N * sizeof(float));
+    rlo_ = (float*)arena_.take(N * sizeof(float));
+    if (!dhi_ || !dlo_ || !rlo_) return cudaErrorMemoryAllocation;
   }
   lv_.assign(dims_.size(), LevelBuf{});
   for (size_t l = 0; l < dims_.size(); ++l) {
@@ -508,13 +639,13 @@ cudaError_t Multigrid::setup_t(double dt, const double* D_cell, const double* E_
   float* w32[3] = {nullptr, nullptr, nullptr};
   if (precision_ == FLD_PREC_MIXED)
     for (int a = 0; a < g_.ndim; ++a) w32[a] = (float*)lv_[0].w[a];
-  cudaError_t e = launch_faces(g_, dt, D_cell, w64_, w32, s);
+  cudaError_t e = launch_faces(g_, dt, D_cell, w64_, w32, dhi_ ? w32lo_ : nullptr, s);
   if (e != cudaSuccess) return e;
   void* w64v[3] = {w64_[0], w64_[1], w64_[2]};
   LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
   {
     TraceScope ts("fine_setup", s);
-    k_fine_setup<T><<<nblk(g_.ncell), kBlock, 0, s>>>(L64, g_, E_old, b64_, diag64_, (T*)lv_[0].invd);
+    k_fine_setup<T><<<nblk(g_.ncell), kBlock, 0, s>>>(L64, g_, E_old, b64_, diag64_, (T*)lv_[0].invd, dhi_, dlo_);
   }
   for (size_t l = 1; l < dims_.size(); ++l) {
     TraceScope ts("coarse_setup", s);
@@ -613,11 +744,27 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
   return cudaGetLastError();
 }
 
+// Outer loop.  FP64 solver: every iteration computes the exact residual b - A x in FP64.  Mixed
+// solver: after a V-cycle the residual is updated, r <- r - A d, in double-float arithmetic (the
+// correction d is exact in FP32; see k_residual_update) instead of being recomputed in FP64.  The
+// update's rounding error is bounded per iteration by kDrift ||m|| (m per cell = |r_old| +
+// diag |d| + sum |w d_nb|, relative to ||b||), summed over the updates since the last exact
+// residual; convergence is accepted when the updated residual plus that bound is within rtol, else
+// an exact FP64 residual decides.
 template <class T>
 cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                                SolveStats* st, cudaStream_t s) {
+  constexpr double kDrift = 0x1p-43;  // 32 x 2^-48: a generous multiple of the per-cell error / m
   void* w64v[3] = {w64_[0], w64_[1], w64_[2]};
   LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
+  const bool mixed = sizeof(T) == sizeof(float) && dhi_ != nullptr;
+  LevelDev<float> L32{}, L32lo{};
+  if (mixed) {
+    void* wlo[3] = {w32lo_[0], w32lo_[1], w32lo_[2]};
+    L32 = level_dev<float>(g_, dims_[0], lv_[0].w);
+    L32lo = level_dev<float>(g_, dims_[0], wlo);
+  }
+  const double N = (double)g_.ncell;
   // the FP64 iterate lives in E_new; the first residual copies E_old into it
   const double* x_in = E_old;
   double* x = E_new;
@@ -625,23 +772,40 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
   int cycles = 0;
   double rel = 0.0;
   int status = FLD_ERR_NOT_CONVERGED;
-  unsigned* wave_err = reinterpret_cast<unsigned*>(host_scal_ + 3);
+  unsigned* wave_err = reinterpret_cast<unsigned*>(host_scal_ + 7);
   *wave_err = 0u;
   {
     cudaError_t e = cudaMemsetAsync(wave_ctl_, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
   }
+  bool updates = false;   // residual updates allowed (decided at the first exact residual)
+  bool exact = true;      // next residual: exact FP64 (else an update)
+  double drift = 0.0;
+  float scale = 0.f;
   for (;;) {
-    {
+    const bool upd = !exact;
+    if (upd) {
+      TraceScope ts("residual_update", s);
+      const float* dv = (const float*)lv_[0].x;
+      float* rv = (float*)lv_[0].r;
+      if (g_.ndim == 3)
+        k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, scale, nparts_, partials_);
+      else if (g_.ndim == 2)
+        k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, scale, nparts_, partials_);
+      else
+        k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, scale, nparts_, partials_);
+      k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
+      k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
+    } else {
       TraceScope ts("residual", s);
-      k_residual64<T><<<nparts_, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r, partials_);
-    }
-    {
-      TraceScope ts("reduce", s);
+      if (mixed)
+        k_residual64_df<<<nparts_, kBlock, 0, s>>>(L64, x_in, x, b64_, diag64_, (float*)lv_[0].r, rlo_, partials_);
+      else
+        k_residual64<T><<<nparts_, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r, partials_);
       k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
     }
     x_in = x;
-    cudaError_t e = cudaMemcpyAsync(host_scal_, scal_, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(host_scal_, scal_, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     if (cycles > 0) e = cudaMemcpyAsync(wave_err, wave_ctl_, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
@@ -652,21 +816,42 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       break;
     }
     bb = host_scal_[1];
-    double rr = host_scal_[0];
-    rel = bb > 0 ? sqrt(rr / bb) : sqrt(rr);
+    if (upd) {
+      // scaled sums: sum (r / rms(b))^2 = N ||r||^2 / ||b||^2
+      rel = sqrt(host_scal_[0] / N);
+      drift += kDrift * sqrt(host_scal_[2] / N);
+    } else {
+      const double rr = host_scal_[0];
+      rel = bb > 0 ? sqrt(rr / bb) : sqrt(rr);
+      drift = 0.0;
+      if (cycles == 0 && mixed && bb > 0) {
+        // updates need the residuals (down to ~1e-3 rtol rms(b)) and their error terms in the
+        // normal FP32 range
+        const double rms = sqrt(bb / N);
+        long long maxf = g_.ncell;
+        for (int a = 0; a < g_.ndim; ++a) maxf = std::max(maxf, faces3(dims_[0], a));
+        updates = rms * std::max(rtol, 1e-16) * 1e-3 >= 0x1p-76 && rms <= 0x1p90 && maxf < (1LL << 31);
+        scale = (float)(1.0 / rms);
+      }
+    }
     if (!(rel == rel) || rel > 1e300) {
       status = FLD_ERR_NONFINITE;
       break;
     }
-    if (rel <= rtol) {
+    if (rel + drift <= rtol) {
       status = FLD_OK;
       break;
+    }
+    if (upd && rel <= rtol) {
+      exact = true;  // the estimate is converged but the bound does not certify it
+      continue;
     }
     if (cycles >= max_cycles) break;
     // one V-cycle on A d = r; its last finest-level sweep adds d to x
     e = vcycle<T>(0, nu1, nu2, x, s);
     if (e != cudaSuccess) return e;
     ++cycles;
+    exact = !updates;
   }
   st->cycles = cycles;
   st->relres = rel;

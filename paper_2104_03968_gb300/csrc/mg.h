@@ -81,8 +81,14 @@ class Multigrid {
   double* b64_ = nullptr;
   double* diag64_ = nullptr;
   double* partials_ = nullptr;
-  double* scal_ = nullptr;      // [0] = ||r||^2, [1] = ||b||^2
-  double* host_scal_ = nullptr; // pinned mirror ([3] holds the wavefront error word)
+  double* scal_ = nullptr;      // [0] = ||r||^2, [1] = ||b||^2, [2] = update error measure (scaled)
+  double* host_scal_ = nullptr; // pinned mirror ([7] holds the wavefront error word)
+  // mixed solver: low parts of the finest FP32 weights, the diagonal as hi + lo, and the low part
+  // of the outer residual (its high part is the V-cycle's right-hand side)
+  float* w32lo_[3] = {nullptr, nullptr, nullptr};
+  float* dhi_ = nullptr;
+  float* dlo_ = nullptr;
+  float* rlo_ = nullptr;
   // Wavefront smoothing (large 3-D levels): per level, the (half-sweep, plane) of each group of
   // `nchunk` tickets in ticket order; control words [0] error, [1] ticket, [2..] finished chunks
   // per (half-sweep, plane).

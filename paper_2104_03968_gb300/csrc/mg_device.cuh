@@ -84,17 +84,19 @@ __device__ __forceinline__ double block_sum(double v) {
 // b = E_old + boundary constants (Dirichlet ghost value, Neumann gradient); the FP64 diagonal
 // of the outer operator and its inverse in T for the finest inner level.
 template <class T>
-__device__ __forceinline__ void fine_setup_cell(const LevelDev<double>& L, const GridDev& g,
-                                                const double* __restrict__ E_old, long long idx, double* __restrict__ b,
-                                                double* __restrict__ diag, T* __restrict__ invd) {
+__device__ __forceinline__ double fine_setup_cell(const LevelDev<double>& L, const GridDev& g,
+                                                  const double* __restrict__ E_old, long long idx,
+                                                  double* __restrict__ b, double* __restrict__ diag,
+                                                  T* __restrict__ invd) {
   int i, j, k;
   unflatten(g.n, idx, i, j, k);
-  double d = 1.0, cst = 0.0;
+  double d = 1.0, cst = 0.0, wsum = 0.0;
   int face = 0;
   // boundary constants need to know which side each boundary face is on
   for_each_face(L, i, j, k, idx, [&](double w, int kind, long long) {
     int a = face >> 1, side = face & 1;
     ++face;
+    wsum += w;
     if (kind == kInterior) d += w;
     else if (kind == kDirichlet) {
       d += w;
@@ -110,6 +112,7 @@ __device__ __forceinline__ void fine_setup_cell(const LevelDev<double>& L, const
   diag[idx] = d;
   if (sizeof(T) == sizeof(float)) invd[idx] = (T)(1.0f / (float)d);  // the FP32 smoother's 1/diag
   else invd[idx] = (T)(1.0 / d);
+  return fma(2.0, wsum, 1.0);  // bound on the row's absolute sum: |diag| + sum |off-diagonal|
 }
 
 // Coarse face `idx` of axis a (coarse face layout m = coarse dims with m[a] + 1): the mean of the
