@@ -48,9 +48,9 @@ KERNEL_MODEL = {
     "prolong_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
     # FP64 outer residual r = b - d x + sum_6 w x_nb, and r^2: 7 FMA + 1 FMA
     "residual": {"bound": "alu", "flops": 16},
-    # mixed solver's double-float residual update r -= A d: d (4, neighbours from cache), r hi/lo
-    # in and out (16), weights hi and lo (24), diagonal hi and lo (8)
-    "residual_update": {"bound": "hbm", "bytes_f32": 4 + 16 + 24 + 8, "bytes_f64": 4 + 16 + 24 + 8},
+    # mixed solver's double-float residual update r -= A d and x += d: d (4, neighbours from cache), r hi/lo
+    # in and out (16), weights hi and lo (24), diagonal hi and lo (8), the FP64 iterate (16)
+    "residual_update": {"bound": "hbm", "bytes_f32": 4 + 16 + 24 + 8 + 16, "bytes_f64": 4 + 16 + 24 + 8 + 16},
     # opacity (10), 5-point gradient in 3 axes (21), limiter and D (14)
     "coeffs": {"bound": "alu", "flops": 45},
     # three harmonic means sharing one reciprocal, times dt/dx^2

@@ -151,8 +151,8 @@ __global__ void __launch_bounds__(256, 4) k_residual64_df(LevelDev<double> L, co
   if (threadIdx.x == 0) parts[blockIdx.x] = acc;
 }
 
-// Mixed solver, updated outer residual after a V-cycle that added the correction d to x:
-//   r_new = r_old - A d,
+// Mixed solver, updated outer residual after a V-cycle that computed the correction d:
+//   x += d (FP64),  r_new = r_old - A d,
 // in double-float arithmetic: A's weights and diagonal as hi + lo floats, d exact in FP32, every
 // product exact (two_prod) and the sum carried as s + e.  The error per cell is a small multiple
 // of 2^-48 m, m = |r_old| + diag |d| + sum |w d_nb|.  parts[blk] = sum (scale r_new)^2,
@@ -179,8 +179,8 @@ template <int NDIM>
 __global__ void __launch_bounds__(256) k_residual_update(LevelDev<float> L, LevelDev<float> Llo,
                                                          const float* __restrict__ dhi, const float* __restrict__ dlo,
                                                          const float* __restrict__ d, float* __restrict__ rhi,
-                                                         float* __restrict__ rlo, float scale, int nparts,
-                                                         double* __restrict__ parts) {
+                                                         float* __restrict__ rlo, double* __restrict__ x64, float scale,
+                                                         int nparts, double* __restrict__ parts) {
   // 32-bit indices: the caller guarantees fewer than 2^31 cells and faces per axis
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
   const int rows = ny * nz, sy = nx, sz = nx * ny;
@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(256) k_residual_update(LevelDev<float> L, Leve
       const int idx = i + nx * row;
       const float dc = d[idx];
       const float ro = rhi[idx];
+      x64[idx] += (double)dc;  // the V-cycle's correction joins the FP64 iterate here
       // s + e = r_old - diag * dc
       float p, pe, s, e;
       two_prod(dhi[idx], dc, p, pe);
@@ -251,6 +252,73 @@ __global__ void k_residual_restrict(LevelDev<T> F, const T* __restrict__ rf, con
   if (idx >= (long long)nc[0] * nc[1] * nc[2]) return;
   rc[idx] = restrict_value<T>(F, rf, xf, nc.data(), idx);
   if (xc_zero) xc_zero[idx] = T(0);
+}
+
+// Row-wise restriction and prolongation for levels with long x rows (32-bit indices).  A block
+// takes one coarse row (J, K); each thread owns fine x positions i and sums the residuals r - A x
+// of its 2^(d-1) fine rows; lanes i and i^1 then add their sums (one shuffle) and the even lane
+// writes the coarse cell.  The face terms are branch-free (selects), as in the wavefront sweep.
+template <class T>
+__device__ __forceinline__ void restrict_face(bool inside, int bc, int idx, int across, int wrap, int mirror, T w, T xv,
+                                              const T* __restrict__ x, T& ax) {
+  const bool per = bc == FLD_BC_PERIODIC, cont = bc == FLD_BC_CONTINUOUS, dir = bc == FLD_BC_DIRICHLET;
+  const int nb = inside ? across : (per ? wrap : (cont ? mirror : idx));
+  const T cx = (inside || per || dir) ? T(1) : (cont ? T(-1) : T(0));
+  const T cn = (inside || per) ? T(1) : (cont ? T(-1) : T(0));
+  ax = fma(w, cx * xv - cn * x[nb], ax);
+}
+
+template <class T, int NDIM>
+__global__ void __launch_bounds__(256) k_restrict_rows(LevelDev<T> F, const T* __restrict__ rf, const T* __restrict__ xf,
+                                                       int ncy, int crows, T* __restrict__ rc) {
+  const int nx = F.n[0], ny = F.n[1], nz = F.n[2];
+  const int sy = nx, sz = nx * ny, ncx = nx >> 1;
+  const int iters = (nx + blockDim.x - 1) / blockDim.x;
+  for (int crow = blockIdx.x; crow < crows; crow += gridDim.x) {
+    const int J = NDIM > 1 ? crow % ncy : 0, K = NDIM > 2 ? crow / ncy : 0;
+    for (int it = 0; it < iters; ++it) {
+      const int i0 = it * blockDim.x + threadIdx.x;
+      const int i = min(i0, nx - 1);
+      T acc = T(0);
+#pragma unroll
+      for (int o = 0; o < (1 << (NDIM - 1)); ++o) {
+        const int j = NDIM > 1 ? 2 * J + (o & 1) : 0;
+        const int k = NDIM > 2 ? 2 * K + (o >> 1) : 0;
+        const int idx = i + sy * j + sz * k;
+        const T xv = xf[idx];
+        T ax = xv;
+        const int fx = i + (nx + 1) * (j + ny * k);
+        restrict_face<T>(i > 0, F.bc[0], idx, idx - 1, idx + (nx - 1), idx + 1, F.w[0][fx], xv, xf, ax);
+        restrict_face<T>(i < nx - 1, F.bc[1], idx, idx + 1, idx - (nx - 1), idx - 1, F.w[0][fx + 1], xv, xf, ax);
+        if (NDIM >= 2) {
+          const int fy = i + nx * (j + (ny + 1) * k);
+          restrict_face<T>(j > 0, F.bc[2], idx, idx - sy, idx + (ny - 1) * sy, idx + sy, F.w[1][fy], xv, xf, ax);
+          restrict_face<T>(j < ny - 1, F.bc[3], idx, idx + sy, idx - (ny - 1) * sy, idx - sy, F.w[1][fy + nx], xv, xf,
+                           ax);
+        }
+        if (NDIM == 3) {
+          restrict_face<T>(k > 0, F.bc[4], idx, idx - sz, idx + (nz - 1) * sz, idx + sz, F.w[2][idx], xv, xf, ax);
+          restrict_face<T>(k < nz - 1, F.bc[5], idx, idx + sz, idx - (nz - 1) * sz, idx - sz, F.w[2][idx + sz], xv, xf,
+                           ax);
+        }
+        acc += rf[idx] - ax;
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (!(i0 & 1) && i0 < nx) rc[(i0 >> 1) + ncx * crow] = acc * T(1.0 / (1 << NDIM));
+    }
+  }
+}
+
+// xf += P xc (piecewise constant), one fine row per block iteration
+template <class T, int NDIM>
+__global__ void __launch_bounds__(256) k_prolong_rows(int nx, int ny, int rows, const T* __restrict__ xc, int ncy,
+                                                      T* __restrict__ xf) {
+  const int ncx = nx >> 1;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % ny, k = row / ny;
+    const int crow = NDIM == 3 ? (j >> 1) + ncy * (k >> 1) : (NDIM == 2 ? (j >> 1) : 0);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) xf[i + nx * row] += xc[(i >> 1) + ncx * crow];
+  }
 }
 
 template <class T>
@@ -669,6 +737,15 @@ cudaError_t Multigrid::setup(double dt, const double* D_cell, const double* E_ol
   return precision_ == FLD_PREC_MIXED ? setup_t<float>(dt, D_cell, E_old, s) : setup_t<double>(dt, D_cell, E_old, s);
 }
 
+// Levels that take the row-wise transfer kernels: 2-D or 3-D, rows of at least 128 cells (the
+// kernels work on whole rows), 32-bit indices.
+bool Multigrid::rows_ok(int l) const {
+  const std::array<int, 3>& n = dims_[l];
+  long long mf = cells3(n);
+  for (int a = 0; a < g_.ndim; ++a) mf = std::max(mf, faces3(n, a));
+  return g_.ndim >= 2 && n[0] >= 128 && mf < (1LL << 31);
+}
+
 template <class T>
 cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s) {
   const std::array<int, 3>& n = dims_[l];
@@ -710,13 +787,27 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
   const std::array<int, 3>& nc = dims_[l + 1];
   {
     TraceScope ts(l == 0 ? "restrict_L0" : "restrict_Lc", s);
-    k_residual_restrict<T><<<nblk(cells3(nc)), kBlock, 0, s>>>(L, r, x, nc, (T*)lv_[l + 1].r, nullptr);
+    if (rows_ok(l)) {
+      const int crows = nc[1] * nc[2];
+      const unsigned gr = (unsigned)std::min(crows, 152 * 16);
+      if (g_.ndim == 3) k_restrict_rows<T, 3><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
+      else k_restrict_rows<T, 2><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
+    } else {
+      k_residual_restrict<T><<<nblk(cells3(nc)), kBlock, 0, s>>>(L, r, x, nc, (T*)lv_[l + 1].r, nullptr);
+    }
   }
   cudaError_t e = vcycle<T>(l + 1, nu1, nu2, nullptr, s);
   if (e != cudaSuccess) return e;
   {
     TraceScope ts(l == 0 ? "prolong_L0" : "prolong_Lc", s);
-    k_prolong<T><<<nblk(ncell), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
+    if (rows_ok(l)) {
+      const int rows = n[1] * n[2];
+      const unsigned gr = (unsigned)std::min(rows, 152 * 16);
+      if (g_.ndim == 3) k_prolong_rows<T, 3><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+      else k_prolong_rows<T, 2><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+    } else {
+      k_prolong<T><<<nblk(ncell), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
+    }
   }
   // post-smoothing, colours reversed; on the finest level the last sweep also adds each colour's
   // final correction to the FP64 iterate
@@ -789,11 +880,14 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       const float* dv = (const float*)lv_[0].x;
       float* rv = (float*)lv_[0].r;
       if (g_.ndim == 3)
-        k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, scale, nparts_, partials_);
+        k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
+                                                          partials_);
       else if (g_.ndim == 2)
-        k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, scale, nparts_, partials_);
+        k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
+                                                          partials_);
       else
-        k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, scale, nparts_, partials_);
+        k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
+                                                          partials_);
       k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
       k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
     } else {
@@ -847,8 +941,9 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       continue;
     }
     if (cycles >= max_cycles) break;
-    // one V-cycle on A d = r; its last finest-level sweep adds d to x
-    e = vcycle<T>(0, nu1, nu2, x, s);
+    // one V-cycle on A d = r; d joins x in its last finest-level sweep, or in the residual update
+    // that follows
+    e = vcycle<T>(0, nu1, nu2, updates ? nullptr : x, s);
     if (e != cudaSuccess) return e;
     ++cycles;
     exact = !updates;

@@ -100,6 +100,7 @@ class Multigrid {
   unsigned* wave_ctl_ = nullptr;
   int wave_blocks_[2] = {0, 0};  // resident blocks of the sweep kernel (float, double)
   cudaError_t configure_wave();
+  bool rows_ok(int l) const;
   template <class T>
   cudaError_t wave_sweep(int l, bool zero, int c0, double* x64, cudaStream_t s);
   int nparts_ = 0;
