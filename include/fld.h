@@ -68,6 +68,8 @@ enum { FLD_LIMITER_LP = 0, FLD_LIMITER_THIRD = 1, FLD_LIMITER_MINERBO = 2 };
 enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_KRAMERS = 1, FLD_OPACITY_TABLE = 2 };
 enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 };
 enum { FLD_ORDER_DIFFUSE_THEN_EXCHANGE = 0, FLD_ORDER_EXCHANGE_THEN_DIFFUSE = 1 };
+/* first cycle of the multigrid solve: full multigrid (Sect. 3.4: FMG, then V-cycles) or a V-cycle */
+enum { FLD_START_FMG = 0, FLD_START_VCYCLE = 1 };
 enum { FLD_GEOM_CARTESIAN = 0, FLD_GEOM_SPHERICAL = 1 };
 
 /* Uniform Cartesian grid.  ndim in {1,2,3}; unused axes have n = 1.  bc[2a] / bc[2a+1] are the
@@ -104,6 +106,8 @@ typedef struct {
   int nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after coarse correction; 0 = 2 */
   int exch_maxit;  /* Halley iterations before bisection in the exchange; 0 = 100 */
   int order;       /* FLD_ORDER_* used by fld_step */
+  int start;       /* FLD_START_*: first cycle of fld_diffuse / fld_step (fld_step_batched always
+                      starts with a V-cycle) */
 } fld_params;
 
 typedef struct {

@@ -91,6 +91,8 @@ fld_status check_params(fld_ctx* ctx, const fld_params* p, bool solver) {
   if (!p) return fail(ctx, FLD_ERR_INVALID_ARG, "params is NULL");
   if (!(p->c > 0) || !(p->a_rad > 0) || !(p->gamma > 1) || !(p->gas_R > 0))
     return fail(ctx, FLD_ERR_INVALID_ARG, "c, a_rad, gas_R must be > 0 and gamma > 1");
+  if (p->start != FLD_START_FMG && p->start != FLD_START_VCYCLE)
+    return fail(ctx, FLD_ERR_INVALID_ARG, "unknown start %d", p->start);
   if (p->limiter < FLD_LIMITER_LP || p->limiter > FLD_LIMITER_MINERBO)
     return fail(ctx, FLD_ERR_INVALID_ARG, "unknown limiter %d", p->limiter);
   if (p->opacity < FLD_OPACITY_CONST || p->opacity > FLD_OPACITY_TABLE)
@@ -190,7 +192,7 @@ fld_status run_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, 
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid setup");
   int maxc = p->max_cycles > 0 ? p->max_cycles : 100;
   int nu1 = p->nu1 > 0 ? p->nu1 : 2, nu2 = p->nu2 > 0 ? p->nu2 : 2;
-  e = ctx->mg.solve(E_old, E_new, p->rtol, maxc, nu1, nu2, st, s);
+  e = ctx->mg.solve(E_old, E_new, p->rtol, maxc, nu1, nu2, p->start == FLD_START_FMG, st, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid solve");
   return FLD_OK;
 }

@@ -254,6 +254,26 @@ __global__ void k_residual_restrict(LevelDev<T> F, const T* __restrict__ rf, con
   if (xc_zero) xc_zero[idx] = T(0);
 }
 
+// rc = mean of the 2^d children of each coarse cell (the full-multigrid start restricts the
+// right-hand side itself down the hierarchy)
+template <class T>
+__global__ void k_restrict_avg(std::array<int, 3> nf, int ndim, const T* __restrict__ rf, std::array<int, 3> nc,
+                               T* __restrict__ rc) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nc[0] * nc[1] * nc[2]) return;
+  int I, J, K;
+  unflatten(nc.data(), idx, I, J, K);
+  const int o1 = ndim > 1 ? 2 : 1, o2 = ndim > 2 ? 2 : 1;
+  T sum = T(0);
+  for (int b = 0; b < o2; ++b)
+    for (int a = 0; a < o1; ++a)
+      for (int c = 0; c < 2; ++c) {
+        const int i = 2 * I + c, j = ndim > 1 ? 2 * J + a : J, k = ndim > 2 ? 2 * K + b : K;
+        sum += rf[cell_index(nf.data(), i, j, k)];
+      }
+  rc[idx] = sum / T(2 * o1 * o2);
+}
+
 // Row-wise restriction and prolongation for levels with long x rows (32-bit indices).  A block
 // takes one coarse row (J, K); each thread owns fine x positions i and sums the residuals r - A x
 // of its 2^(d-1) fine rows; lanes i and i^1 then add their sums (one shuffle) and the even lane
@@ -747,7 +767,7 @@ bool Multigrid::rows_ok(int l) const {
 }
 
 template <class T>
-cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s) {
+cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s, bool zero_init) {
   const std::array<int, 3>& n = dims_[l];
   long long ncell = cells3(n);
   LevelDev<T> L = level_dev<T>(g_, n, lv_[l].w);
@@ -767,18 +787,19 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
   long long nhalf = (long long)((n[0] + 1) / 2) * n[1] * n[2];
   unsigned gb = nblk(nhalf);
   const bool wave = wave_[l].order != nullptr;
-  // pre-smoothing from a zero initial guess: red, black, ...
+  // pre-smoothing (from a zero initial guess unless the caller set one): red, black, ...
   const char* sm_name = l == 0 ? "smooth_L0" : "smooth_Lc";
   for (int it = 0; it < nu1; ++it) {
+    const bool zero = it == 0 && zero_init;
     if (wave) {
-      TraceScope ts(l == 0 ? (it == 0 ? "wave_L0_zero" : "wave_L0") : "wave_Lc", s);
-      cudaError_t e = wave_sweep<T>(l, it == 0, 0, nullptr, s);
+      TraceScope ts(l == 0 ? (zero ? "wave_L0_zero" : "wave_L0") : "wave_Lc", s);
+      cudaError_t e = wave_sweep<T>(l, zero, 0, nullptr, s);
       if (e != cudaSuccess) return e;
       continue;
     }
     {
-      TraceScope ts(it == 0 ? (l == 0 ? "smooth_L0_zero" : "smooth_Lc") : sm_name, s);
-      if (it == 0) k_smooth<T, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
+      TraceScope ts(zero ? (l == 0 ? "smooth_L0_zero" : "smooth_Lc") : sm_name, s);
+      if (zero) k_smooth<T, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
       else k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
     }
     TraceScope ts(sm_name, s);
@@ -796,7 +817,7 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
       k_residual_restrict<T><<<nblk(cells3(nc)), kBlock, 0, s>>>(L, r, x, nc, (T*)lv_[l + 1].r, nullptr);
     }
   }
-  cudaError_t e = vcycle<T>(l + 1, nu1, nu2, nullptr, s);
+  cudaError_t e = vcycle<T>(l + 1, nu1, nu2, nullptr, s, true);
   if (e != cudaSuccess) return e;
   {
     TraceScope ts(l == 0 ? "prolong_L0" : "prolong_Lc", s);
@@ -835,6 +856,38 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
   return cudaGetLastError();
 }
 
+// Full-multigrid cycle for A d = r (r on the finest level, d from zero): restrict r down the
+// hierarchy, solve on the coarsest level, then on each finer level start from the prolonged
+// coarse solution and run one V-cycle (Sect. 3.4: FMG first, V-cycles after).  The finest
+// V-cycle's last sweep adds d to x64 when x64 is given.
+template <class T>
+cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
+  const int top = (int)dims_.size() - 1;
+  if (top == 0) return vcycle<T>(0, nu1, nu2, x64, s, true);
+  {
+    TraceScope ts("fmg_restrict", s);
+    for (int l = 0; l < top; ++l)
+      k_restrict_avg<T><<<nblk(cells3(dims_[l + 1])), kBlock, 0, s>>>(dims_[l], g_.ndim, (const T*)lv_[l].r,
+                                                                     dims_[l + 1], (T*)lv_[l + 1].r);
+  }
+  cudaError_t e = vcycle<T>(top, nu1, nu2, nullptr, s, true);
+  if (e != cudaSuccess) return e;
+  for (int l = top - 1; l >= 0; --l) {
+    const std::array<int, 3>& n = dims_[l];
+    const std::array<int, 3>& nc = dims_[l + 1];
+    T* x = (T*)lv_[l].x;
+    {
+      TraceScope ts(l == 0 ? "prolong_L0" : "prolong_Lc", s);
+      e = cudaMemsetAsync(x, 0, cells3(n) * sizeof(T), s);
+      if (e != cudaSuccess) return e;
+      k_prolong<T><<<nblk(cells3(n)), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
+    }
+    e = vcycle<T>(l, nu1, nu2, l == 0 ? x64 : nullptr, s, false);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
 // Outer loop.  FP64 solver: every iteration computes the exact residual b - A x in FP64.  Mixed
 // solver: after a V-cycle the residual is updated, r <- r - A d, in double-float arithmetic (the
 // correction d is exact in FP32; see k_residual_update) instead of being recomputed in FP64.  The
@@ -844,7 +897,7 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
 // an exact FP64 residual decides.
 template <class T>
 cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
-                               SolveStats* st, cudaStream_t s) {
+                               bool fmg_start, SolveStats* st, cudaStream_t s) {
   constexpr double kDrift = 0x1p-43;  // 32 x 2^-48: a generous multiple of the per-cell error / m
   void* w64v[3] = {w64_[0], w64_[1], w64_[2]};
   LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
@@ -943,7 +996,8 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
     if (cycles >= max_cycles) break;
     // one V-cycle on A d = r; d joins x in its last finest-level sweep, or in the residual update
     // that follows
-    e = vcycle<T>(0, nu1, nu2, updates ? nullptr : x, s);
+    if (cycles == 0 && fmg_start) e = fmg<T>(nu1, nu2, updates ? nullptr : x, s);
+    else e = vcycle<T>(0, nu1, nu2, updates ? nullptr : x, s, true);
     if (e != cudaSuccess) return e;
     ++cycles;
     exact = !updates;
@@ -955,9 +1009,9 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
 }
 
 cudaError_t Multigrid::solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
-                             SolveStats* st, cudaStream_t s) {
-  return precision_ == FLD_PREC_MIXED ? solve_t<float>(E_old, E_new, rtol, max_cycles, nu1, nu2, st, s)
-                                      : solve_t<double>(E_old, E_new, rtol, max_cycles, nu1, nu2, st, s);
+                             bool fmg_start, SolveStats* st, cudaStream_t s) {
+  return precision_ == FLD_PREC_MIXED ? solve_t<float>(E_old, E_new, rtol, max_cycles, nu1, nu2, fmg_start, st, s)
+                                      : solve_t<double>(E_old, E_new, rtol, max_cycles, nu1, nu2, fmg_start, st, s);
 }
 
 }  // namespace fld

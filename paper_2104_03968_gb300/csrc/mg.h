@@ -55,9 +55,10 @@ class Multigrid {
   cudaError_t configure(const GridDev& g, int precision);
   // Face weights, diagonals and coarse operators from the cell-centred D; rhs from E_old.
   cudaError_t setup(double dt, const double* D_cell, const double* E_old, unsigned* status, cudaStream_t s);
-  // Outer iterations until ||b - A x||/||b|| <= rtol or max_cycles V-cycles; writes E_new.
+  // Outer iterations until ||b - A x||/||b|| <= rtol or max_cycles cycles; writes E_new.  With
+  // fmg_start the first cycle is a full-multigrid cycle, the others V-cycles.
   cudaError_t solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
-                    SolveStats* st, cudaStream_t s);
+                    bool fmg_start, SolveStats* st, cudaStream_t s);
 
   int levels() const { return (int)dims_.size(); }
   const GridDev& grid() const { return g_; }
@@ -67,9 +68,11 @@ class Multigrid {
   cudaError_t setup_t(double dt, const double* D_cell, const double* E_old, cudaStream_t s);
   template <class T>
   cudaError_t solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
-                      SolveStats* st, cudaStream_t s);
+                      bool fmg_start, SolveStats* st, cudaStream_t s);
   template <class T>
-  cudaError_t vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s);
+  cudaError_t vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s, bool zero_init);
+  template <class T>
+  cudaError_t fmg(int nu1, int nu2, double* x64, cudaStream_t s);
 
   GridDev g_{};
   int precision_ = -1;

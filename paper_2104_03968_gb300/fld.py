@@ -9,7 +9,7 @@ which then copy them to the device and back around the call.
 Parameter dictionaries follow the plain-data schema of ``inputs``: a grid dict
 (ndim, n, dx, bc names, bc_val) and a physics dict (c, a_rad, gamma, gas_R, limiter,
 opacity, kappa0, kr_a, kr_b, table, tlo, thi) extended by solver keys (precision
-"fp64" | "mixed", rtol, max_cycles, nu1, nu2, exch_maxit, order).
+"fp64" | "mixed", rtol, max_cycles, nu1, nu2, exch_maxit, order, start "fmg" | "vcycle").
 """
 from __future__ import annotations
 
@@ -28,6 +28,7 @@ OPACITY = {"const": 0, "kramers": 1, "table": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 ORDER = {"diffuse_then_exchange": 0, "exchange_then_diffuse": 1}
 GEOMETRY = {"cartesian": 0, "spherical": 1}
+START = {"fmg": 0, "vcycle": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "non-positive input", 3: "non-finite residual",
           4: "not converged", 5: "CUDA error", 6: "device timeout", 7: "unsupported"}
 
@@ -49,7 +50,7 @@ class Params(ct.Structure):
                 ("kr_b", ct.c_double), ("table", ct.c_void_p), ("tn", ct.c_int * 2), ("tlo", ct.c_double * 2),
                 ("thi", ct.c_double * 2), ("precision", ct.c_int), ("rtol", ct.c_double),
                 ("max_cycles", ct.c_int), ("nu1", ct.c_int), ("nu2", ct.c_int), ("exch_maxit", ct.c_int),
-                ("order", ct.c_int)]
+                ("order", ct.c_int), ("start", ct.c_int)]
 
 
 class Info(ct.Structure):
@@ -185,6 +186,7 @@ def params_struct(p: dict, keep: list, device) -> Params:
     s.nu2 = int(p.get("nu2", 0))
     s.exch_maxit = int(p.get("exch_maxit", 0))
     s.order = ORDER[p.get("order", "diffuse_then_exchange")]
+    s.start = START[p.get("start", "fmg")]
     return s
 
 

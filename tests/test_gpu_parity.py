@@ -197,6 +197,28 @@ def test_wavefront_sweep_equals_two_pass(shape, bcname, precision, monkeypatch):
     assert relerr(x1, ref) < TOL
 
 
+@pytest.mark.parametrize("shape,bcname", [((64, 64, 64), "periodic"), ((96, 64), "mixed"), ((128,), "dirichlet")])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fmg_start(ctx, shape, bcname, precision):
+    """Full-multigrid first cycle (Sect. 3.4) and plain V-cycle start reach the same discrete
+    solution; the FMG start needs no more cycles."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=60 + len(shape), bc=BCS[bcname], dt_factor=100.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    ref = oracle.diffuse(g, case["dt"], D, case["E"], rtol=1e-14)
+    rtol = 1e-13 if precision == "fp64" else 1e-12
+    cyc = {}
+    for start in ("vcycle", "fmg"):
+        out, info = fld.diffuse(ctx, g, solver(p, precision=precision, rtol=rtol, start=start), case["dt"], dev(D),
+                                dev(case["E"]))
+        assert info["status"] == 0, (start, info)
+        assert relerr(host(out).reshape(ref.shape), ref) < TOL
+        cyc[start] = info["cycles"]
+    assert cyc["fmg"] <= cyc["vcycle"]
+
+
 def test_diffuse_continuous_boundary(ctx):
     from paper_2104_03968_gb300 import fld
     case = inputs.random_small((32, 16), seed=5, bc=BCS["continuous"], dt_factor=2.0)
