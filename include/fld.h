@@ -67,7 +67,10 @@ enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2, FLD_BC_CON
 enum { FLD_LIMITER_LP = 0, FLD_LIMITER_THIRD = 1, FLD_LIMITER_MINERBO = 2 };
 enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_KRAMERS = 1, FLD_OPACITY_TABLE = 2 };
 enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 };
-enum { FLD_ORDER_DIFFUSE_THEN_EXCHANGE = 0, FLD_ORDER_EXCHANGE_THEN_DIFFUSE = 1 };
+/* step order: diffusion then exchange; exchange then diffusion; or the paper's midpoint IMEX scheme
+   (Sect. 3.1): exchange over dt/2 from the old state, diffusion over dt/2, then the exchange over
+   dt from the old state plus twice the half-step diffusion increment */
+enum { FLD_ORDER_DIFFUSE_THEN_EXCHANGE = 0, FLD_ORDER_EXCHANGE_THEN_DIFFUSE = 1, FLD_ORDER_IMEX_MIDPOINT = 2 };
 /* first cycle of the multigrid solve: full multigrid (Sect. 3.4: FMG, then V-cycles) or a V-cycle */
 enum { FLD_START_FMG = 0, FLD_START_VCYCLE = 1 };
 enum { FLD_GEOM_CARTESIAN = 0, FLD_GEOM_SPHERICAL = 1 };

@@ -305,26 +305,44 @@ def step(grid: dict, phys: dict, dt: float, rho, eps, E, order: str = "diffuse_t
     E = _f64(E)
     info = {}
 
-    def diffusion(eps_, E_):
+    def diffusion(eps_, E_, h=dt):
         kap = opacity(phys, rho, eps_)
         D = coeffs(grid, phys, E_, rho, kap)
-        En = diffuse(grid, dt, D, E_, rtol=rtol, method=method)
-        info["relres"] = relres(grid, dt, D, E_, En)
+        En = diffuse(grid, h, D, E_, rtol=rtol, method=method)
+        info["relres"] = relres(grid, h, D, E_, En)
         return En
 
-    def exch(eps_, E_):
+    def exch(eps_, E_, h=dt):
         kap = opacity(phys, rho, eps_)
-        e2, E2, inf = exchange(phys, dt, rho, kap, eps_, E_, maxit=exch_maxit)
+        e2, E2, inf = exchange(phys, h, rho, kap, eps_, E_, maxit=exch_maxit)
         info.update(inf)
         return e2, E2
 
     if order == "diffuse_then_exchange":
         E = diffusion(eps, E)
         eps, E = exch(eps, E)
-    else:
+    elif order == "exchange_then_diffuse":
         eps, E = exch(eps, E)
         E = diffusion(eps, E)
+    elif order == "imex_midpoint":
+        eps, E = imex_midpoint(eps, E, dt, exch, diffusion)
+    else:
+        raise ValueError(f"unknown order {order}")
     return eps, E, info
+
+
+def imex_midpoint(eps, E, dt, exch, diffusion):
+    """Sect. 3.1, the midpoint IMEX scheme for the radiation-energy subsystem of a static
+    medium.  The explicit operator is the local implicit exchange (no advection, no explicit
+    sources here), the implicit operator the diffusion:
+      u+      = u^n advanced by the explicit operator over dt/2,
+      u^{1/2} = u+ advanced by the implicit diffusion over dt/2,
+      u^{n+1} = u^n + dt G_im(u^{1/2}) (the half-step diffusion increment, doubled), then the
+                explicit operator over the full dt from that state."""
+    eps_h, E_h = exch(eps, E, dt / 2)
+    E_mid = diffusion(eps_h, E_h, dt / 2)
+    E_star = E + 2.0 * (E_mid - E_h)
+    return exch(eps, E_star, dt)
 
 
 def column_step(col: dict, phys: dict, dt: float, rho, eps, E, v_lo: float, v_hi: float,
@@ -333,23 +351,27 @@ def column_step(col: dict, phys: dict, dt: float, rho, eps, E, v_lo: float, v_hi
     rho, eps, E = _f64(rho), _f64(eps), _f64(E)
     info = {}
 
-    def diffusion(eps_, E_):
+    def diffusion(eps_, E_, h=dt):
         kap = opacity(phys, rho, eps_)
         D = column_coeffs(col, phys, E_, rho, kap, v_lo, v_hi)
-        En = column_diffuse(col, dt, D, E_, v_lo, v_hi)
-        info["relres"] = column_relres(col, dt, D, E_, En, v_lo, v_hi)
+        En = column_diffuse(col, h, D, E_, v_lo, v_hi)
+        info["relres"] = column_relres(col, h, D, E_, En, v_lo, v_hi)
         return En
 
-    def exch(eps_, E_):
+    def exch(eps_, E_, h=dt):
         kap = opacity(phys, rho, eps_)
-        e2, E2, inf = exchange(phys, dt, rho, kap, eps_, E_, maxit=exch_maxit)
+        e2, E2, inf = exchange(phys, h, rho, kap, eps_, E_, maxit=exch_maxit)
         info.update(inf)
         return e2, E2
 
     if order == "diffuse_then_exchange":
         E = diffusion(eps, E)
         eps, E = exch(eps, E)
-    else:
+    elif order == "exchange_then_diffuse":
         eps, E = exch(eps, E)
         E = diffusion(eps, E)
+    elif order == "imex_midpoint":
+        eps, E = imex_midpoint(eps, E, dt, exch, diffusion)
+    else:
+        raise ValueError(f"unknown order {order}")
     return eps, E, info

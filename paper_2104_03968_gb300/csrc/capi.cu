@@ -31,6 +31,8 @@ struct fld_ctx {
   BatchedSolver* batched = nullptr;
   double* geom = nullptr;  // per-cell geometry of the 1-D column calls
   size_t geom_cap = 0;
+  double* mid = nullptr;   // midpoint IMEX: E^n, eps^n and the half-step E (3 x cells)
+  size_t mid_cap = 0;
 };
 
 namespace {
@@ -108,7 +110,8 @@ fld_status check_params(fld_ctx* ctx, const fld_params* p, bool solver) {
     if (!(p->rtol > 0) || p->rtol >= 1) return fail(ctx, FLD_ERR_INVALID_ARG, "rtol must be in (0, 1)");
     if (p->max_cycles < 0 || p->nu1 < 0 || p->nu2 < 0 || p->nu1 > 16 || p->nu2 > 16)
       return fail(ctx, FLD_ERR_INVALID_ARG, "max_cycles, nu1, nu2 out of range");
-    if (p->order != FLD_ORDER_DIFFUSE_THEN_EXCHANGE && p->order != FLD_ORDER_EXCHANGE_THEN_DIFFUSE)
+    if (p->order != FLD_ORDER_DIFFUSE_THEN_EXCHANGE && p->order != FLD_ORDER_EXCHANGE_THEN_DIFFUSE &&
+        p->order != FLD_ORDER_IMEX_MIDPOINT)
       return fail(ctx, FLD_ERR_INVALID_ARG, "unknown order %d", p->order);
   }
   if (p->exch_maxit < 0) return fail(ctx, FLD_ERR_INVALID_ARG, "exch_maxit must be >= 0");
@@ -161,6 +164,17 @@ fld_status ensure_scratch(fld_ctx* ctx, long long ncell) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->kappa, ncell * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
   ctx->cap = ncell;
+  return FLD_OK;
+}
+
+fld_status ensure_mid(fld_ctx* ctx, long long ncell) {
+  if ((size_t)ncell <= ctx->mid_cap) return FLD_OK;
+  cudaFree(ctx->mid);
+  ctx->mid = nullptr;
+  ctx->mid_cap = 0;
+  cudaError_t e = cudaMalloc(&ctx->mid, 3 * ncell * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint scratch allocation");
+  ctx->mid_cap = ncell;
   return FLD_OK;
 }
 
@@ -260,6 +274,7 @@ fld_status fld_ctx_destroy(fld_ctx* ctx) {
   cudaFree(ctx->D);
   cudaFree(ctx->kappa);
   cudaFree(ctx->geom);
+  cudaFree(ctx->mid);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_info);
   if (ctx->h_info) cudaFreeHost(ctx->h_info);
@@ -357,17 +372,44 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
   ExchangeParams xp = to_exchange(p, dt);
   SolveStats ss;
   cudaError_t e;
-  if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE) {
+  if (p->order == FLD_ORDER_IMEX_MIDPOINT) {
+    // Sect. 3.1, midpoint IMEX for the static-medium subsystem: exchange over dt/2 from u^n,
+    // diffusion over dt/2 (D from that state), then the exchange over dt from u^n plus twice the
+    // half-step diffusion increment
+    if ((st = ensure_mid(ctx, g.ncell)) != FLD_OK) return st;
+    double* E0 = ctx->mid;
+    double* eps0 = ctx->mid + g.ncell;
+    double* Eh = ctx->mid + 2 * g.ncell;
+    const size_t bytes = g.ncell * sizeof(double);
+    e = cudaMemcpyAsync(E0, E, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(eps0, eps, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint copies");
+    ExchangeParams xh = to_exchange(p, 0.5 * dt);
+    e = launch_exchange(g.ncell, xh, op, rho, nullptr, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
+    e = cudaMemcpyAsync(Eh, E, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint copies");
+    e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
+    if ((st = run_diffuse(ctx, grid, p, 0.5 * dt, ctx->D, E, E, &ss, s)) != FLD_OK) return st;
+    e = launch_midpoint_combine(g.ncell, E0, eps0, Eh, E, eps, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint combine launch");
     e = launch_exchange(g.ncell, xp, op, rho, nullptr, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
-  }
-  e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status, s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
-  if ((st = run_diffuse(ctx, grid, p, dt, ctx->D, E, E, &ss, s)) != FLD_OK) return st;
-  if (p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE) {
-    // eps is unchanged by the diffusion, so kappa^n from the coefficient stage is current
-    e = launch_exchange(g.ncell, xp, op, rho, ctx->kappa, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
+  } else {
+    if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE) {
+      e = launch_exchange(g.ncell, xp, op, rho, nullptr, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
+    }
+    e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status,
+                      s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
+    if ((st = run_diffuse(ctx, grid, p, dt, ctx->D, E, E, &ss, s)) != FLD_OK) return st;
+    if (p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE) {
+      // eps is unchanged by the diffusion, so kappa^n from the coefficient stage is current
+      e = launch_exchange(g.ncell, xp, op, rho, ctx->kappa, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
+    }
   }
   unsigned sbits = 0;
   fld_info tmp;
@@ -379,7 +421,7 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
   inf->status = ss.status;
   if (sbits & kStatNonpositive) {
     inf->status = FLD_ERR_NONPOSITIVE;
-    return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input state");
+    return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state");
   }
   if (ss.status != FLD_OK)
     return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",

@@ -23,7 +23,7 @@
 
 namespace fld {
 
-enum { kColStep = 0, kColStepExchangeFirst = 1, kColDiffuse = 2 };
+enum { kColStep = 0, kColStepExchangeFirst = 1, kColDiffuse = 2, kColStepMidpoint = 3 };
 
 // geometry factors shared by all columns: [gl n][gu n][cm n][cp n][hl hr flo fhi]
 __global__ void k_col_geometry(int n, const double* __restrict__ rf, int geometry, double* __restrict__ geom,
@@ -224,12 +224,17 @@ __global__ void k_columns(ColArgs A) {
   double* rb = ra + 2 * P;
   double* rc = rb + 2 * P;
   double* rd = rc + 2 * P;
+  double* sh = rd + 2 * P;  // midpoint IMEX: E after the half-step exchange
   const long long base = (long long)blockIdx.x * n;
   const double dtc = A.dt[blockIdx.x];
+  const double dtd = MODE == kColStepMidpoint ? 0.5 * dtc : dtc;  // the diffusion stage's step
   const double vlo = A.v_lo ? A.v_lo[blockIdx.x] : 0.0, vhi = A.v_hi ? A.v_hi[blockIdx.x] : 0.0;
   const double *gl = A.geom, *gu = A.geom + n, *cm = A.geom + 2 * n, *cp = A.geom + 3 * n;
   const double hl = A.geom[4 * n], hr = A.geom[4 * n + 1], flo = A.geom[4 * n + 2], fhi = A.geom[4 * n + 3];
   const ExchangeParams xp = make_exchange(A.c, 4.0 * A.sigma / A.c, A.gamma, A.gas_R, dtc, A.maxit);
+  const ExchangeParams xp1 = MODE == kColStepMidpoint
+                                 ? make_exchange(A.c, 4.0 * A.sigma / A.c, A.gamma, A.gas_R, 0.5 * dtc, A.maxit)
+                                 : xp;  // the first exchange stage
   int iters = 0, bis = 0;
   bool bad = false;
 
@@ -245,16 +250,17 @@ __global__ void k_columns(ColArgs A) {
   __syncthreads();
   const int s0 = t * M, s1 = min(s0 + M, n);
 
-  if (MODE == kColStepExchangeFirst) {
+  if (MODE == kColStepExchangeFirst || MODE == kColStepMidpoint) {
     for (int i = s0; i < s1; ++i) {
       double e = se[i], E = sx[i];
       double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e));
-      if (exchange_cell(xp, sr[i], k, e, E, iters, bis)) {
+      if (exchange_cell(xp1, sr[i], k, e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
       } else {
         bad = true;
       }
+      if (MODE == kColStepMidpoint) sh[i] = sx[i];
     }
     __syncthreads();
   }
@@ -284,7 +290,7 @@ __global__ void k_columns(ColArgs A) {
   for (int i = s0; i < s1; ++i) {
     double Dl = i > 0 ? harm(sD[i - 1], sD[i]) : sD[0];
     double Du = i < n - 1 ? harm(sD[i], sD[i + 1]) : sD[n - 1];
-    double wl = dtc * Dl * gl[i], wu = dtc * Du * gu[i];
+    double wl = dtd * Dl * gl[i], wu = dtd * Du * gu[i];
     double a = 0.0, b = 1.0, c = 0.0, d = sx[i];
     if (i > 0) {
       a = -wl;
@@ -471,6 +477,23 @@ __global__ void k_columns(ColArgs A) {
       }
     }
   }
+  if (MODE == kColStepMidpoint) {
+    // Sect. 3.1: from u^n plus twice the half-step diffusion increment, the exchange over dt
+    // (u^n is still in global memory: the column is written back at the end)
+    for (int i = s0; i < s1; ++i) {
+      double E = fma(2.0, sx[i] - sh[i], A.Ein[base + i]);
+      double e = A.eps[base + i];
+      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e));
+      if (exchange_cell(xp, sr[i], k, e, E, iters, bis)) {
+        se[i] = e;
+        sx[i] = E;
+      } else {
+        bad = true;
+        se[i] = e;
+        sx[i] = E;
+      }
+    }
+  }
   __syncthreads();
   for (int i = t; i < n; i += P) {
     A.Eout[base + i] = sx[i];
@@ -513,12 +536,14 @@ static int col_threads(int n) {
   return P;
 }
 
-static size_t col_smem(int n, int P) { return (size_t)(9 * n + 8 * P) * sizeof(double); }
+static size_t col_smem(int n, int P, int mode) {
+  return (size_t)((mode == kColStepMidpoint ? 10 : 9) * n + 8 * P) * sizeof(double);
+}
 
 template <int MODE, bool MIXED>
 static cudaError_t launch_kernel(int ncol, int ncell, ColArgs& A, cudaStream_t s) {
   int P = col_threads(ncell);
-  size_t smem = col_smem(ncell, P);
+  size_t smem = col_smem(ncell, P, MODE);
   cudaError_t e = cudaFuncSetAttribute(k_columns<MODE, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_columns<MODE, MIXED><<<ncol, P, smem, s>>>(A);
@@ -578,6 +603,8 @@ cudaError_t launch_columns_step(int ncol, int ncell, const double* r_faces, int 
   A.status = status;
   if (p.order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE)
     return launch_mode<kColStepExchangeFirst>(ncol, ncell, r_faces, geometry, A, status, p.precision, s);
+  if (p.order == FLD_ORDER_IMEX_MIDPOINT)
+    return launch_mode<kColStepMidpoint>(ncol, ncell, r_faces, geometry, A, status, p.precision, s);
   return launch_mode<kColStep>(ncol, ncell, r_faces, geometry, A, status, p.precision, s);
 }
 
@@ -633,7 +660,8 @@ bool static_params_ok(const fld_params* p) {
       (!p->table || p->tn[0] < 2 || p->tn[1] < 2 || !(p->thi[0] > p->tlo[0]) || !(p->thi[1] > p->tlo[1])))
     return false;
   if (p->exch_maxit < 0) return false;
-  return p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE || p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE;
+  return p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE || p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE ||
+         p->order == FLD_ORDER_IMEX_MIDPOINT;
 }
 
 }  // namespace
@@ -675,6 +703,9 @@ extern "C" fld_status fld_columns_step_static(int ncol, int ncell, const double*
   if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE)
     e = mixed ? launch_kernel<kColStepExchangeFirst, true>(ncol, ncell, A, s)
               : launch_kernel<kColStepExchangeFirst, false>(ncol, ncell, A, s);
+  else if (p->order == FLD_ORDER_IMEX_MIDPOINT)
+    e = mixed ? launch_kernel<kColStepMidpoint, true>(ncol, ncell, A, s)
+              : launch_kernel<kColStepMidpoint, false>(ncol, ncell, A, s);
   else
     e = mixed ? launch_kernel<kColStep, true>(ncol, ncell, A, s) : launch_kernel<kColStep, false>(ncol, ncell, A, s);
   if (e != cudaSuccess) return FLD_ERR_CUDA;

@@ -34,4 +34,22 @@ cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity&
   return cudaGetLastError();
 }
 
+// Midpoint IMEX recombination (Sect. 3.1): E = E0 + 2 (E_mid - E_half), eps = eps0 -- the state
+// u^n plus dt times the implicit (diffusion) increment of the half step.
+__global__ void k_midpoint_combine(long long n, const double* __restrict__ E0, const double* __restrict__ eps0,
+                                   const double* __restrict__ Eh, double* __restrict__ E, double* __restrict__ eps) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  E[idx] = fma(2.0, E[idx] - Eh[idx], E0[idx]);
+  eps[idx] = eps0[idx];
+}
+
+cudaError_t launch_midpoint_combine(long long n, const double* E0, const double* eps0, const double* Eh, double* E,
+                                    double* eps, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  TraceScope ts("midpoint_combine", s);
+  k_midpoint_combine<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, E0, eps0, Eh, E, eps);
+  return cudaGetLastError();
+}
+
 }  // namespace fld

@@ -16,6 +16,10 @@ cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double 
 cudaError_t launch_faces(const GridDev& g, double dt, const double* D, double* const w64[3], float* const w32[3],
                          float* const w32lo[3], cudaStream_t s);
 
+// E = E0 + 2 (E - Eh), eps = eps0 (midpoint IMEX recombination)
+cudaError_t launch_midpoint_combine(long long n, const double* E0, const double* eps0, const double* Eh, double* E,
+                                    double* eps, cudaStream_t s);
+
 cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity& op, const double* rho,
                             const double* kappa, double* eps, double* E, int* info_iters, int* info_bisect,
                             unsigned* status, cudaStream_t s);

@@ -26,7 +26,7 @@ BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3}
 LIMITER = {"lp": 0, "third": 1, "minerbo": 2}
 OPACITY = {"const": 0, "kramers": 1, "table": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
-ORDER = {"diffuse_then_exchange": 0, "exchange_then_diffuse": 1}
+ORDER = {"diffuse_then_exchange": 0, "exchange_then_diffuse": 1, "imex_midpoint": 2}
 GEOMETRY = {"cartesian": 0, "spherical": 1}
 START = {"fmg": 0, "vcycle": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "non-positive input", 3: "non-finite residual",

@@ -267,7 +267,7 @@ def test_diffuse_in_place_alias(ctx):
 
 # ----------------------------------------------------------------------------- full step
 
-@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
+@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse", "imex_midpoint"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_step_parity_lognormal(ctx, order, precision):
     from paper_2104_03968_gb300 import fld
@@ -360,7 +360,7 @@ def test_step_parity_minerbo(ctx):
 
 
 @pytest.mark.parametrize("ncell", [64, 100, 2048])
-@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
+@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse", "imex_midpoint"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_columns_step_parity(ctx, ncell, order, precision):
     """The mixed form (FP32 tridiagonal solves inside two FP64 refinement passes) is held to the

@@ -544,3 +544,50 @@ def test_table_opacity_bilinear_reproduces_nodes_and_planes():
     eps_out = inputs.equilibrium_eps(phys, np.array([1e-20]), np.array([1e8]))
     k_out = oracle.opacity(phys, np.array([1e-20]), eps_out)
     assert np.isclose(np.log10(k_out[0]), 0.3 * -16 - 0.8 * 6.5 + 1.0)
+
+
+# ----------------------------------------------------------------------------- IMEX midpoint
+
+def test_imex_midpoint_is_crank_nicolson_without_exchange():
+    """Sect. 3.1: with the gas-radiation coupling negligible (a2 = c kappa rho dt ~ 1e-12), the
+    midpoint scheme's half backward-Euler diffusion plus doubled increment is Crank-Nicolson:
+    each Fourier mode is multiplied by (1 - dt s/2) / (1 + dt s/2) (backward Euler alone gives
+    1 / (1 + dt s))."""
+    n = 64
+    g = inputs.periodic_grid((n,))
+    kap = 5.8e-7
+    phys = dict(inputs.code_units("third"), kappa0=kap)
+    D = phys["c"] / (3 * kap)
+    dt = 1.0 / D
+    x = np.arange(n) + 0.5
+    k = 2 * np.pi * 11 / n
+    E = 1.0 + 0.2 * np.cos(k * x)
+    rho = np.ones(n)
+    eps = inputs.equilibrium_eps(phys, rho, np.ones(n))
+    s = D * 4 * np.sin(k / 2) ** 2
+    e2, E2, _ = oracle.step(g, phys, dt, rho, eps, E, order="imex_midpoint", rtol=1e-14)
+    g_cn = (1 - dt * s / 2) / (1 + dt * s / 2)
+    assert np.abs((E2 - 1.0) / (0.2 * g_cn * np.cos(k * x)) - 1).max() < 1e-8
+    # and it is not backward Euler
+    e3, E3, _ = oracle.step(g, phys, dt, rho, eps, E, order="diffuse_then_exchange", rtol=1e-14)
+    g_be = 1 / (1 + dt * s)
+    assert np.abs((E3 - 1.0) / (0.2 * g_be * np.cos(k * x)) - 1).max() < 1e-8
+    assert abs(g_cn - g_be) > 0.05
+
+
+def test_imex_midpoint_without_diffusion_is_one_full_exchange():
+    """Uniform fields: the implicit (diffusion) increment vanishes, so the scheme's last stage
+    is one exchange step of the full dt from u^n -- the half step only feeds the diffusion."""
+    n = 8
+    g = inputs.periodic_grid((n,))
+    phys = dict(inputs.code_units(), kappa0=3.0)
+    rho = np.full(n, 0.7)
+    eps = inputs.equilibrium_eps(phys, rho, np.full(n, 2.0))
+    E = inputs.rad_energy(phys, np.full(n, 1.0))
+    dt = 0.4
+    e2, E2, _ = oracle.step(g, phys, dt, rho, eps, E, order="imex_midpoint", rtol=1e-14)
+    kapv = oracle.opacity(phys, rho, eps)
+    e1, E1, _ = oracle.exchange(phys, dt, rho, kapv, eps, E)
+    assert np.allclose(E2, E1, rtol=1e-13, atol=0) and np.allclose(e2, e1, rtol=1e-13, atol=0)
+    eh, Eh, _ = oracle.exchange(phys, dt / 2, rho, kapv, eps, E)
+    assert np.abs(Eh / E1 - 1).max() > 1e-3  # the half step is a different state
