@@ -184,6 +184,34 @@ FLD_API fld_status fld_columns_diffuse(fld_ctx* ctx, int ncol, int ncell, const 
                                const double* D_cell, const double* E_old, double* E_new,
                                void* stream);
 
+/* Explicit radiation terms of the current state (Sect. 2.1-2.2 and 3.2), per cell, with every
+   gradient by the 5-point stencil of Sect. 3.2:
+     F     = -D grad E                                  (Eq. fld_F; D as in fld_coeffs)
+     f_r   = rho kappa F / c                            (Eq. rhd_force), work = v . f_r
+     f     = lambda + lambda^2 R^2                      (Eq. fld_Edd_fac, the Eddington factor)
+     P     = E [(1-f)/2 I + (3f-1)/2 n n], n = grad E / |grad E| (n = 0 where grad E = 0)
+                                                         (Eq. fld_Edd)
+     P:grad v = sum_ab P_ab d_b v_a                     (the photon-tiring term)
+   In: E, rho, eps (N cells, device); v = host array of grid->ndim DEVICE pointers to the velocity
+   components, or NULL (then work and tiring are 0).  Velocity ghosts on non-periodic faces are
+   linear extrapolations.  Out (each may be NULL): F and f_r = host arrays of ndim device pointers;
+   P = host array of 6 device pointers (xx, yy, zz, xy, xz, yz); work, fedd, tiring = device arrays.
+   sync == 0: asynchronous, and cells with rho, kappa or E <= 0 (or eps < 0) are left unwritten
+   without an error.  sync != 0: synchronises and returns FLD_ERR_NONPOSITIVE if any cell was. */
+FLD_API fld_status fld_radiation_terms(fld_ctx* ctx, const fld_grid* grid, const fld_params* p,
+                               const double* E, const double* rho, const double* eps,
+                               const double* const* v, double* const* F, double* const* f_r,
+                               double* work, double* fedd, double* const* P, double* tiring,
+                               int sync, void* stream);
+
+/* The explicit radiation-energy source over dt (Sect. 3.1, first stage; Sect. 3.2):
+   E <- E - dt P : grad v, in place (P and the gradients from the state on entry).  v as in
+   fld_radiation_terms (required).  Synchronises; FLD_ERR_NONPOSITIVE when the input is invalid or
+   the update leaves E <= 0 somewhere. */
+FLD_API fld_status fld_photon_tiring_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p,
+                                  double dt, const double* rho, const double* eps,
+                                  const double* const* v, double* E, void* stream);
+
 /* ---- allocation-free column update (no counterpart in the paper; a deployment convenience).
    Some callers cannot allocate device memory when they advance the radiation field: codes whose
    own memory manager has reserved the whole GPU in advance, runtimes that forbid device

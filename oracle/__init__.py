@@ -81,6 +81,7 @@ def _load():
                 "ora_kappa": (ct.c_double, [P, ct.c_double, ct.c_double]),
                 "ora_opacity": (None, [ct.c_size_t, P, _D, _D, _D]),
                 "ora_coeffs": (ct.c_int, [P, P, _D, _D, _D, _D, _D]),
+                "ora_radiation_sources": (ct.c_int, [P, P, _D, _D, _D, P, P, P, _D, _D, P, _D]),
                 "ora_apply": (None, [P, ct.c_double, _D, _D, _D]),
                 "ora_rhs": (None, [P, ct.c_double, _D, _D, _D]),
                 "ora_relres": (ct.c_double, [P, ct.c_double, _D, _D, _D]),
@@ -194,6 +195,36 @@ def coeffs(grid: dict, phys: dict, E, rho, kappa, with_grad: bool = False):
     if st:
         raise ValueError(f"oracle coeffs: status {st}")
     return (D, gm) if with_grad else D
+
+
+def _ptr_array(arrays):
+    """A C array of double pointers (None -> NULL array)."""
+    if arrays is None:
+        return None
+    arr = (_D * len(arrays))(*[_ptr(a) for a in arrays])
+    return ct.cast(arr, ct.c_void_p), arr
+
+
+def radiation_sources(grid: dict, phys: dict, E, rho, kappa, v=None) -> dict:
+    """Sect. 2.1-2.2 and 3.2: per cell the flux F = -D grad E, the force density f_r = rho kappa
+    F / c, its work v . f_r, the Eddington factor f = lambda + lambda^2 R^2, the pressure tensor
+    P = E [(1-f)/2 I + (3f-1)/2 n n] (xx, yy, zz, xy, xz, yz) and the photon-tiring term
+    P : grad v (5-point gradients; velocity ghosts by linear extrapolation)."""
+    E, rho, kappa = _f64(E), _f64(rho), _f64(kappa)
+    nd = int(grid["ndim"])
+    out = {"F": [np.empty_like(E) for _ in range(nd)], "fr": [np.empty_like(E) for _ in range(nd)],
+           "work": np.empty_like(E), "fedd": np.empty_like(E), "P": [np.empty_like(E) for _ in range(6)],
+           "tiring": np.empty_like(E)}
+    vs = None if v is None else [_f64(c) for c in v]
+    keep = []
+    pv = _ptr_array(vs)
+    pF, pfr, pP = _ptr_array(out["F"]), _ptr_array(out["fr"]), _ptr_array(out["P"])
+    st = _load().ora_radiation_sources(_ref(_grid(grid)), _ref(_phys(phys, keep)), _ptr(E), _ptr(rho), _ptr(kappa),
+                                       pv[0] if pv else None, pF[0], pfr[0], _ptr(out["work"]), _ptr(out["fedd"]),
+                                       pP[0], _ptr(out["tiring"]))
+    if st:
+        raise ValueError(f"oracle radiation_sources: status {st}")
+    return out
 
 
 # ----------------------------------------------------------------------------- diffusion

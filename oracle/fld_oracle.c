@@ -8,6 +8,8 @@
  *
  * What each function follows:
  *   ora_lambda            Sect. 2.2, Eq. (fld_lambda): Levermore-Pomraning limiter.
+ *   ora_radiation_sources Sect. 2.1-2.2 and 3.2: flux, radiation force and work, Eddington
+ *                         factor and tensor, photon tiring P : grad v.
  *   ora_lambda_minerbo    the Minerbo limiter that Sect. 2.2 names as the alternative (its
  *                         formula is not printed there; the two-branch form of Minerbo's
  *                         closure, joined at R = 3/2, is restated here).
@@ -169,6 +171,107 @@ int ora_coeffs(const ora_grid* g, const ora_phys* p, const double* E, const doub
     double R = gm / (kr * E[c]);
     double lam = ora_limiter(p->limiter, R);
     D_cell[c] = p->c * lam / kr; /* Sect. 2.2, Eq. (fld_F): F = -c lambda grad E/(kappa rho) */
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ explicit radiation terms */
+
+/* field value at position p along axis a for the velocity components: periodic wrap, else
+   linear extrapolation from the two boundary cells (velocity ghosts; the paper leaves them to
+   the hydro solver) */
+static double sample_extrap(const ora_grid* g, const double* f, const int q[3], int a, int p) {
+  int n = g->n[a];
+  int r[3] = {q[0], q[1], q[2]};
+  if (p >= 0 && p < n) {
+    r[a] = p;
+    return f[lin(g, r)];
+  }
+  int side = p < 0 ? 0 : 1;
+  if (g->bc[2 * a + side] == ORA_BC_PERIODIC) {
+    r[a] = ((p % n) + n) % n;
+    return f[lin(g, r)];
+  }
+  r[a] = side ? n - 1 : 0;
+  double f0 = f[lin(g, r)];
+  r[a] = side ? n - 2 : 1;
+  double f1 = f[lin(g, r)];
+  int d = side ? p - (n - 1) : -p;
+  return f0 + d * (f0 - f1);
+}
+
+/* Sect. 3.2, Eq. (ileyk_flux) along axis a */
+static double grad5(const ora_grid* g, const double* f, const int q[3], int a, int extrap) {
+  double fm2, fm1, fp1, fp2;
+  int i = q[a];
+  if (extrap) {
+    fm2 = sample_extrap(g, f, q, a, i - 2);
+    fm1 = sample_extrap(g, f, q, a, i - 1);
+    fp1 = sample_extrap(g, f, q, a, i + 1);
+    fp2 = sample_extrap(g, f, q, a, i + 2);
+  } else {
+    fm2 = sample(g, f, q, a, i - 2);
+    fm1 = sample(g, f, q, a, i - 1);
+    fp1 = sample(g, f, q, a, i + 1);
+    fp2 = sample(g, f, q, a, i + 2);
+  }
+  return (fm2 / 12.0 - 2.0 / 3.0 * fm1 + 2.0 / 3.0 * fp1 - fp2 / 12.0) / g->dx[a];
+}
+
+int ora_radiation_sources(const ora_grid* g, const ora_phys* p, const double* E, const double* rho,
+                          const double* kappa, const double* const* v, double* const* F, double* const* fr,
+                          double* work, double* fedd, double* const* P, double* tiring) {
+  size_t N = ncells(g);
+  int nd = g->ndim;
+  for (size_t c = 0; c < N; ++c) {
+    if (!(E[c] > 0) || !(rho[c] > 0) || !(kappa[c] > 0)) return 2;
+    int q[3];
+    unlin(g, c, q);
+    double gE[3] = {0, 0, 0}, g2 = 0;
+    for (int a = 0; a < nd; ++a) {
+      gE[a] = grad5(g, E, q, a, 0);
+      g2 += gE[a] * gE[a];
+    }
+    double gm = sqrt(g2);
+    double kr = kappa[c] * rho[c];
+    double R = gm / (kr * E[c]);
+    double lam = ora_limiter(p->limiter, R);
+    double D = p->c * lam / kr;
+    double f = lam + lam * lam * R * R; /* Sect. 2.2, Eq. (fld_Edd_fac) */
+    double nrm[3] = {0, 0, 0};
+    if (gm > 0)
+      for (int a = 0; a < nd; ++a) nrm[a] = gE[a] / gm;
+    double w = 0;
+    for (int a = 0; a < nd; ++a) {
+      double Fa = -D * gE[a];                  /* Sect. 2.2, Eq. (fld_F) */
+      double fa = rho[c] * kappa[c] * Fa / p->c; /* Sect. 2.1, Eq. (rhd_force) */
+      if (F) F[a][c] = Fa;
+      if (fr) fr[a][c] = fa;
+      if (v) w += v[a][c] * fa;
+    }
+    if (work) work[c] = v ? w : 0.0;
+    if (fedd) fedd[c] = f;
+    /* Sect. 2.2, Eq. (fld_Edd): f_ab = (1-f)/2 delta_ab + (3f-1)/2 n_a n_b; P = f_ab E */
+    double Pt[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        Pt[a][b] = E[c] * ((a == b ? 0.5 * (1.0 - f) : 0.0) + 0.5 * (3.0 * f - 1.0) * nrm[a] * nrm[b]);
+    if (P) {
+      P[0][c] = Pt[0][0];
+      P[1][c] = Pt[1][1];
+      P[2][c] = Pt[2][2];
+      P[3][c] = Pt[0][1];
+      P[4][c] = Pt[0][2];
+      P[5][c] = Pt[1][2];
+    }
+    if (tiring) {
+      /* Sect. 3.2: P : grad v = sum_ab P_ab d_b v_a */
+      double t = 0;
+      if (v)
+        for (int a = 0; a < nd; ++a)
+          for (int b = 0; b < nd; ++b) t += Pt[a][b] * grad5(g, v[a], q, b, 1);
+      tiring[c] = t;
+    }
   }
   return 0;
 }

@@ -43,6 +43,11 @@ double ora_limiter(int limiter, double R);
 double ora_temperature(const ora_phys* p, double rho, double eps);
 double ora_kappa(const ora_phys* p, double rho, double T);
 void ora_opacity(size_t n, const ora_phys* p, const double* rho, const double* eps, double* kappa);
+/* explicit radiation quantities: F[ndim], fr[ndim], work, fedd, P[6] (xx yy zz xy xz yz), tiring;
+   any output may be NULL; v (ndim velocity components) may be NULL */
+int ora_radiation_sources(const ora_grid* g, const ora_phys* p, const double* E, const double* rho,
+                          const double* kappa, const double* const* v, double* const* F, double* const* fr,
+                          double* work, double* fedd, double* const* P, double* tiring);
 
 /* 4th-order 5-point gradient, |grad E|, R, lambda and D = c lambda/(kappa rho) per cell. */
 int ora_coeffs(const ora_grid* g, const ora_phys* p, const double* E, const double* rho,

@@ -429,6 +429,73 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
   return FLD_OK;
 }
 
+fld_status fld_radiation_terms(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, const double* E,
+                               const double* rho, const double* eps, const double* const* v, double* const* F,
+                               double* const* f_r, double* work, double* fedd, double* const* P, double* tiring,
+                               int sync, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_grid(ctx, grid);
+  if (st == FLD_OK) st = check_params(ctx, p, false);
+  if (st != FLD_OK) return st;
+  if (!E || !rho || !eps) return fail(ctx, FLD_ERR_INVALID_ARG, "E, rho and eps must be non-NULL");
+  const int nd = grid->ndim;
+  const double* vv[3] = {nullptr, nullptr, nullptr};
+  double* FF[3] = {nullptr, nullptr, nullptr};
+  double* ff[3] = {nullptr, nullptr, nullptr};
+  double* PP[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int a = 0; a < nd; ++a) {
+    if (v) {
+      if (!v[a]) return fail(ctx, FLD_ERR_INVALID_ARG, "velocity component %d is NULL", a);
+      vv[a] = v[a];
+    }
+    if (F) FF[a] = F[a];
+    if (f_r) ff[a] = f_r[a];
+  }
+  if (P)
+    for (int m = 0; m < 6; ++m) PP[m] = P[m];
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  GridDev g = to_dev(grid);
+  if ((st = reset_status(ctx, s)) != FLD_OK) return st;
+  cudaError_t e = launch_radiation_terms(g, to_opacity(p), p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps,
+                                         v ? vv : nullptr, FF, ff, work, fedd, PP, tiring, ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "radiation terms launch");
+  if (sync) {
+    unsigned sbits = 0;
+    int it = 0, bi = 0;
+    if ((st = read_status(ctx, s, &sbits, &it, &bi)) != FLD_OK) return st;
+    if (sbits & kStatNonpositive) return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0)");
+  }
+  return FLD_OK;
+}
+
+fld_status fld_photon_tiring_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                                  const double* rho, const double* eps, const double* const* v, double* E,
+                                  void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!v) return fail(ctx, FLD_ERR_INVALID_ARG, "the velocity components are required");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
+  fld_status st = check_grid(ctx, grid);
+  if (st != FLD_OK) return st;
+  DeviceGuard dg(ctx->device);
+  GridDev g = to_dev(grid);
+  if ((st = ensure_scratch(ctx, g.ncell)) != FLD_OK) return st;
+  // the tiring term into the context's D scratch, then the update (the stencil reads E)
+  st = fld_radiation_terms(ctx, grid, p, E, rho, eps, v, nullptr, nullptr, nullptr, nullptr, nullptr, ctx->D, 0,
+                           stream);
+  if (st != FLD_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_tiring_update(g.ncell, dt, ctx->D, E, ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tiring update launch");
+  unsigned sbits = 0;
+  int it = 0, bi = 0;
+  if ((st = read_status(ctx, s, &sbits, &it, &bi)) != FLD_OK) return st;
+  if (sbits & kStatNonpositive) return fail(ctx, FLD_ERR_NONPOSITIVE, "invalid input or E <= 0 after the update");
+  return FLD_OK;
+}
+
 fld_status fld_step_batched(fld_ctx* ctx, int ngrids, const fld_grid* grids, const fld_params* params, const double* dt,
                             const double* const* rho, double* const* eps, double* const* E, fld_info* infos,
                             void* stream) {

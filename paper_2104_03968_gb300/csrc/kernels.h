@@ -20,6 +20,16 @@ cudaError_t launch_faces(const GridDev& g, double dt, const double* D, double* c
 cudaError_t launch_midpoint_combine(long long n, const double* E0, const double* eps0, const double* Eh, double* E,
                                     double* eps, cudaStream_t s);
 
+// explicit radiation terms (sources.cu); null output pointers are skipped
+cudaError_t launch_radiation_terms(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
+                                   int limiter, const double* E, const double* rho, const double* eps,
+                                   const double* const v[3], double* const F[3], double* const fr[3], double* work,
+                                   double* fedd, double* const P[6], double* tiring, unsigned* status,
+                                   cudaStream_t s);
+// E -= dt * tiring
+cudaError_t launch_tiring_update(long long n, double dt, const double* tiring, double* E, unsigned* status,
+                                 cudaStream_t s);
+
 cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity& op, const double* rho,
                             const double* kappa, double* eps, double* E, int* info_iters, int* info_bisect,
                             unsigned* status, cudaStream_t s);

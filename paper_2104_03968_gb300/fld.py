@@ -74,6 +74,8 @@ _SIGS = {
     "fld_step_batched": [P, ct.c_int, P, P, P, P, P, P, P, P],
     "fld_columns_step": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P, P],
     "fld_columns_diffuse": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P],
+    "fld_radiation_terms": [P, P, P, P, P, P, P, P, P, P, P, P, P, ct.c_int, P],
+    "fld_photon_tiring_step": [P, P, P, ct.c_double, P, P, P, P, P],
 }
 
 
@@ -366,3 +368,45 @@ def columns_step_static(r_faces, geometry: str, bc: tuple, v_lo, v_hi, params: d
         raise FldError(st, "fld_columns_step_static failed" +
                        (f" (ncell {ncell} > {STATIC_MAX_CELLS})" if ncell > STATIC_MAX_CELLS else ""))
     return info.as_dict()
+
+
+def _dev_ptr_array(tensors):
+    """A host array of device pointers (None -> NULL)."""
+    if tensors is None:
+        return None, None
+    arr = (ct.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+    return ct.cast(arr, ct.c_void_p), arr
+
+
+def radiation_terms(ctx: Context, grid: dict, params: dict, E, rho, eps, v=None) -> dict:
+    """Explicit radiation terms (Sect. 2.1-2.2, 3.2) of the state: F, f_r (ndim components each),
+    work, fedd (Eddington factor), P (xx, yy, zz, xy, xz, yz) and tiring (P : grad v).  v: list of
+    ndim velocity tensors or None.  Returns CUDA tensors shaped like E."""
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    nd = int(grid["ndim"])
+    out = {"F": [torch.empty_like(E) for _ in range(nd)], "fr": [torch.empty_like(E) for _ in range(nd)],
+           "work": torch.empty_like(E), "fedd": torch.empty_like(E), "P": [torch.empty_like(E) for _ in range(6)],
+           "tiring": torch.empty_like(E)}
+    if v is not None:
+        for c in v:
+            _dptr(c)
+    pv, kv = _dev_ptr_array(v)
+    pF, kF = _dev_ptr_array(out["F"])
+    pr, kr = _dev_ptr_array(out["fr"])
+    pP, kP = _dev_ptr_array(out["P"])
+    ctx.check(ctx.lib.fld_radiation_terms(ctx.h, ct.byref(g), ct.byref(p), _dptr(E), _dptr(rho), _dptr(eps), pv, pF,
+                                          pr, _dptr(out["work"]), _dptr(out["fedd"]), pP, _dptr(out["tiring"]), 1,
+                                          _stream()))
+    return out
+
+
+def photon_tiring_step(ctx: Context, grid: dict, params: dict, dt: float, rho, eps, v, E) -> None:
+    """E <- E - dt P : grad v in place (the explicit radiation-energy source, Sect. 3.1-3.2)."""
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    for c in v:
+        _dptr(c)
+    pv, kv = _dev_ptr_array(v)
+    ctx.check(ctx.lib.fld_photon_tiring_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(rho), _dptr(eps), pv,
+                                             _dptr(E), _stream()))

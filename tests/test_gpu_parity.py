@@ -339,6 +339,36 @@ def test_step_full_size_128(ctx, precision):
     assert np.abs(host(eps).ravel()[idx] / e_s - 1).max() < tol
 
 
+# ----------------------------------------------------------------------------- explicit terms
+
+@pytest.mark.parametrize("shape,bcname", [((24, 20, 18), "periodic"), ((70, 45), "mixed"), ((40, 24, 16), "dirichlet"),
+                                          ((300,), "neumann")])
+@pytest.mark.parametrize("limiter", ["lp", "minerbo"])
+def test_radiation_terms_parity(ctx, shape, bcname, limiter):
+    """Flux, force, work, Eddington factor and tensor, photon tiring (Sect. 2.1-2.2, 3.2)."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=80 + len(shape), bc=BCS[bcname], limiter=limiter)
+    g, p = case["grid"], case["phys"]
+    rng = np.random.default_rng(81)
+    v = [rng.standard_normal(case["E"].shape) for _ in range(len(shape))]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    ref = oracle.radiation_sources(g, p, case["E"], case["rho"], kap, v=v)
+    out = fld.radiation_terms(ctx, g, p, dev(case["E"]), dev(case["rho"]), dev(case["eps"]), v=[dev(c) for c in v])
+    torch.cuda.synchronize()
+    for key in ("F", "fr", "P"):
+        for a, (o, r) in enumerate(zip(out[key], ref[key])):
+            if key == "P" and len(shape) < 3 and a in (4, 5):
+                continue  # components with a z index are 0 in 2-D / 1-D on both sides
+            assert relerr(host(o).reshape(r.shape), r) < 1e-12, (key, a)
+    for key in ("work", "fedd", "tiring"):
+        assert relerr(host(out[key]).reshape(ref[key].shape), ref[key]) < 1e-12, key
+    # the explicit step E <- E - dt P : grad v
+    dt = 1e-3
+    E = dev(case["E"])
+    fld.photon_tiring_step(ctx, g, p, dt, dev(case["rho"]), dev(case["eps"]), [dev(c) for c in v], E)
+    assert relerr(host(E).reshape(case["E"].shape), case["E"] - dt * ref["tiring"]) < 1e-13
+
+
 # ----------------------------------------------------------------------------- columns
 
 def _column_case(ncol, ncell, seed=0):

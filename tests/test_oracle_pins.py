@@ -591,3 +591,83 @@ def test_imex_midpoint_without_diffusion_is_one_full_exchange():
     assert np.allclose(E2, E1, rtol=1e-13, atol=0) and np.allclose(e2, e1, rtol=1e-13, atol=0)
     eh, Eh, _ = oracle.exchange(phys, dt / 2, rho, kapv, eps, E)
     assert np.abs(Eh / E1 - 1).max() > 1e-3  # the half step is a different state
+
+
+# ----------------------------------------------------------------------------- explicit terms
+
+def _box_grid(nx, ny, bc="continuous", dx=0.5):
+    return {"ndim": 2, "n": [nx, ny, 1], "dx": [dx, dx, 1.0], "bc": [bc] * 4 + ["periodic"] * 2,
+            "bc_val": [0.0] * 6}
+
+
+def test_eddington_tensor_trace_and_limits():
+    """Sect. 2.2, Eqs. (fld_Edd_fac) and (fld_Edd): tr f = 1 for any f and unit n, so tr P = E;
+    f -> 1/3 (isotropic P = E/3 I) when optically thick, f -> 1 (P = E n n) when free streaming."""
+    nx, ny = 20, 14
+    g = _box_grid(nx, ny)
+    x = (np.arange(nx) + 0.5) * 0.5
+    y = (np.arange(ny) + 0.5) * 0.5
+    X, Y = np.meshgrid(x, y)
+    E = np.exp(0.2 * X - 0.1 * Y)
+    rho = np.ones_like(E)
+    phys = inputs.code_units()
+    for kap, f_lim in ((1e8, 1.0 / 3.0), (1e-10, 1.0)):
+        out = oracle.radiation_sources(g, phys, E, rho, np.full_like(E, kap))
+        P = out["P"]
+        assert np.allclose(P[0] + P[1] + P[2], E, rtol=1e-14, atol=0)
+        assert np.allclose(out["fedd"], f_lim, rtol=1e-6)
+        if f_lim == 1.0:
+            # P = E n n with n along grad E = (0.2, -0.1) / |.|
+            n = np.array([0.2, -0.1]) / np.hypot(0.2, -0.1)
+            assert np.allclose(P[0][2:-2, 2:-2], E[2:-2, 2:-2] * n[0] ** 2, rtol=1e-4)
+            assert np.allclose(P[3][2:-2, 2:-2], E[2:-2, 2:-2] * n[0] * n[1], rtol=1e-4)
+            assert np.allclose(P[2], 0.0, atol=1e-4 * E.max())
+            # and |F| -> c E
+            Fm = np.hypot(out["F"][0], out["F"][1])
+            assert np.allclose(Fm[2:-2, 2:-2], phys["c"] * E[2:-2, 2:-2], rtol=1e-4)
+        else:
+            assert np.allclose(P[0], E / 3, rtol=1e-6) and np.allclose(P[3], 0, atol=1e-6 * E.max())
+
+
+def test_radiation_force_thick_limit_is_pressure_gradient():
+    """Eq. (rhd_force) with the thick-limit flux: f_r = rho kappa F / c = -grad(E/3), exact for a
+    cubic E (the 5-point gradient differentiates cubics exactly)."""
+    nx, ny = 16, 10
+    g = _box_grid(nx, ny)
+    x = (np.arange(nx) + 0.5) * 0.5
+    y = (np.arange(ny) + 0.5) * 0.5
+    X, Y = np.meshgrid(x, y)
+    E = 5.0 + 0.3 * X ** 3 - 0.2 * X * Y + 0.1 * Y ** 2
+    dEx = 0.9 * X ** 2 - 0.2 * Y
+    dEy = -0.2 * X + 0.2 * Y
+    phys = inputs.code_units("third")
+    out = oracle.radiation_sources(g, phys, E, np.full_like(E, 2.0), np.full_like(E, 3.0))
+    inner = (slice(2, -2), slice(2, -2))  # the extrapolated ghost cells are linear, E is not
+    assert np.allclose(out["fr"][0][inner], -dEx[inner] / 3, rtol=1e-11, atol=1e-12)
+    assert np.allclose(out["fr"][1][inner], -dEy[inner] / 3, rtol=1e-11, atol=1e-12)
+    # work with a uniform velocity u is u . f_r
+    u = (0.7, -1.3)
+    v = [np.full_like(E, u[0]), np.full_like(E, u[1])]
+    out = oracle.radiation_sources(g, phys, E, np.full_like(E, 2.0), np.full_like(E, 3.0), v=v)
+    assert np.allclose(out["work"][inner], -(u[0] * dEx + u[1] * dEy)[inner] / 3, rtol=1e-11, atol=1e-12)
+
+
+def test_photon_tiring_expansion_and_rotation():
+    """Sect. 3.2: P : grad v.  A uniform expansion v = a x in 3-D gives grad v = a I, so
+    P : grad v = a tr P = a E exactly; a rigid rotation has an antisymmetric grad v, which the
+    symmetric P annihilates."""
+    nx, ny, nz = 12, 10, 8
+    g = {"ndim": 3, "n": [nx, ny, nz], "dx": [0.5, 0.5, 0.5], "bc": ["continuous"] * 6, "bc_val": [0.0] * 6}
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) * 0.5, (np.arange(ny) + 0.5) * 0.5, (np.arange(nx) + 0.5) * 0.5,
+                          indexing="ij")
+    E = np.exp(0.3 * x + 0.15 * y - 0.1 * z)
+    rho = np.ones_like(E)
+    phys = inputs.code_units()
+    for kap in (1e-3, 1.0, 1e3):
+        kappa = np.full_like(E, kap)
+        a = 0.37
+        out = oracle.radiation_sources(g, phys, E, rho, kappa, v=[a * x, a * y, a * z])
+        assert np.allclose(out["tiring"], a * E, rtol=1e-12)
+        w = 1.9
+        out = oracle.radiation_sources(g, phys, E, rho, kappa, v=[-w * y, w * x, np.zeros_like(E)])
+        assert np.abs(out["tiring"]).max() < 1e-12 * E.max()
