@@ -144,6 +144,14 @@ FLD_API fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_par
                        const double* D_cell, const double* E_old, double* E_new, fld_info* info,
                        void* stream);
 
+/* fld_diffuse with a diagonal-tensor D (the anisotropic variant Sect. 6 mentions: one diffusion
+   coefficient per grid direction).  D_axis: host array of grid->ndim DEVICE pointers; D_axis[a]
+   is the cell-centred D of axis a, and the faces of axis a take its harmonic mean.  Otherwise as
+   fld_diffuse (synchronises). */
+FLD_API fld_status fld_diffuse_aniso(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                             const double* const* D_axis, const double* E_old, double* E_new,
+                             fld_info* info, void* stream);
+
 /* Point-implicit exchange (Sect. 3.3) on n independent cells, in place on eps and E.  kappa may
    be NULL, in which case it is evaluated from rho and eps with the opacity model of p.
    Asynchronous; `info` (may be NULL) is filled after a stream synchronisation. */

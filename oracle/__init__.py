@@ -88,6 +88,10 @@ def _load():
                 "ora_diffuse_cg": (ct.c_int, [P, ct.c_double, _D, _D, _D, ct.c_double, ct.c_int,
                                               _D, ct.POINTER(ct.c_int)]),
                 "ora_diffuse_dense": (ct.c_int, [P, ct.c_double, _D, _D, _D]),
+                "ora_apply_aniso": (None, [P, ct.c_double, P, _D, _D]),
+                "ora_relres_aniso": (ct.c_double, [P, ct.c_double, P, _D, _D]),
+                "ora_diffuse_cg_aniso": (ct.c_int, [P, ct.c_double, P, _D, _D, ct.c_double, ct.c_int,
+                                                    _D, ct.POINTER(ct.c_int)]),
                 "ora_column_coeffs": (ct.c_int, [ct.c_int, _D, ct.c_int, ct.c_int, ct.c_double,
                                                  ct.c_double, P, _D, _D, _D, _D]),
                 "ora_column_diffuse": (ct.c_int, [ct.c_int, _D, ct.c_int, ct.c_int, ct.c_int,
@@ -243,19 +247,49 @@ def rhs(grid: dict, dt: float, D, E_old) -> np.ndarray:
     return out
 
 
+def _axes(grid: dict, D):
+    """A list of per-axis D arrays (a diagonal tensor), or None for one scalar D field."""
+    if isinstance(D, (list, tuple)):
+        if len(D) != int(grid["ndim"]):
+            raise ValueError("a diagonal-tensor D needs one array per axis")
+        arrs = [_f64(d) for d in D]
+        return arrs + [arrs[0]] * (3 - len(arrs))
+    return None
+
+
 def relres(grid: dict, dt: float, D, E_old, x) -> float:
-    """||b - A x||_2 / ||b||_2 of the backward-Euler system of Sect. 3.4."""
-    D, E_old, x = _f64(D), _f64(E_old), _f64(x)
+    """||b - A x||_2 / ||b||_2 of the backward-Euler system of Sect. 3.4 (D: one array, or one
+    per axis for a diagonal-tensor D)."""
+    E_old, x = _f64(E_old), _f64(x)
+    ax = _axes(grid, D)
+    if ax is not None:
+        pa = _ptr_array(ax)
+        return _load().ora_relres_aniso(_ref(_grid(grid)), float(dt), pa[0], _ptr(E_old), _ptr(x))
+    D = _f64(D)
     return _load().ora_relres(_ref(_grid(grid)), float(dt), _ptr(D), _ptr(E_old), _ptr(x))
 
 
 def diffuse(grid: dict, dt: float, D, E_old, rtol: float = 1e-13, maxit: int = 100000,
             method: str = "cg") -> np.ndarray:
-    """E^{n+1} solving Eq. (discdiff) (times dt) by Jacobi-CG or dense LU."""
-    D, E_old = _f64(D), _f64(E_old)
+    """E^{n+1} solving Eq. (discdiff) (times dt) by Jacobi-CG or dense LU.  D: one array, or one
+    per axis (a diagonal-tensor D, Jacobi-CG only)."""
+    E_old = _f64(E_old)
     x = np.empty_like(E_old)
     lib = _load()
     g = _ref(_grid(grid))
+    ax = _axes(grid, D)
+    if ax is not None:
+        pa = _ptr_array(ax)
+        rr = ct.c_double()
+        it = ct.c_int()
+        st = lib.ora_diffuse_cg_aniso(g, float(dt), pa[0], _ptr(E_old), _ptr(x), float(rtol), int(maxit),
+                                      ct.byref(rr), ct.byref(it))
+        if st not in (0, 4):
+            raise ValueError(f"oracle CG: status {st}")
+        diffuse.last_relres = rr.value
+        diffuse.last_iters = it.value
+        return x
+    D = _f64(D)
     if method == "dense":
         st = lib.ora_diffuse_dense(g, float(dt), _ptr(D), _ptr(E_old), _ptr(x))
         if st:

@@ -282,12 +282,13 @@ static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
 /* Contribution of one face of cell q (axis a, side 0 = lower, 1 = upper) to the row of
    the dt-scaled operator:  self*x_q + cnb*x_nb  on the left, cconst on the right. */
-static void face_term(const ora_grid* g, double dt, const double* D, const int q[3], int a, int side,
+static void face_term(const ora_grid* g, double dt, const double* const* Dax, const int q[3], int a, int side,
                       double* cself, long* nb, double* cnb, double* cconst) {
   int n = g->n[a];
   int i = q[a];
   int j = side ? i + 1 : i - 1;
   int r[3] = {q[0], q[1], q[2]};
+  const double* D = Dax[a]; /* the diffusion coefficient of axis a (a diagonal tensor D) */
   double Di = D[lin(g, q)];
   double h2 = g->dx[a] * g->dx[a];
   *nb = -1;
@@ -326,7 +327,7 @@ static void face_term(const ora_grid* g, double dt, const double* D, const int q
   }
 }
 
-void ora_apply(const ora_grid* g, double dt, const double* D, const double* x, double* Ax) {
+static void apply_ax(const ora_grid* g, double dt, const double* const* Dax, const double* x, double* Ax) {
   size_t N = ncells(g);
   for (size_t c = 0; c < N; ++c) {
     int q[3];
@@ -336,7 +337,7 @@ void ora_apply(const ora_grid* g, double dt, const double* D, const double* x, d
       for (int side = 0; side < 2; ++side) {
         double cs, cn, cc;
         long nb;
-        face_term(g, dt, D, q, a, side, &cs, &nb, &cn, &cc);
+        face_term(g, dt, Dax, q, a, side, &cs, &nb, &cn, &cc);
         s += cs * x[c];
         if (nb >= 0) s += cn * x[nb];
       }
@@ -344,7 +345,7 @@ void ora_apply(const ora_grid* g, double dt, const double* D, const double* x, d
   }
 }
 
-void ora_rhs(const ora_grid* g, double dt, const double* D, const double* E_old, double* b) {
+static void rhs_ax(const ora_grid* g, double dt, const double* const* Dax, const double* E_old, double* b) {
   size_t N = ncells(g);
   for (size_t c = 0; c < N; ++c) {
     int q[3];
@@ -354,7 +355,7 @@ void ora_rhs(const ora_grid* g, double dt, const double* D, const double* E_old,
       for (int side = 0; side < 2; ++side) {
         double cs, cn, cc;
         long nb;
-        face_term(g, dt, D, q, a, side, &cs, &nb, &cn, &cc);
+        face_term(g, dt, Dax, q, a, side, &cs, &nb, &cn, &cc);
         s += cc;
       }
     b[c] = s;
@@ -367,12 +368,13 @@ static double dot(size_t n, const double* a, const double* b) {
   return s;
 }
 
-double ora_relres(const ora_grid* g, double dt, const double* D, const double* E_old, const double* x) {
+static double relres_ax(const ora_grid* g, double dt, const double* const* Dax, const double* E_old,
+                        const double* x) {
   size_t N = ncells(g);
   double* b = malloc(N * sizeof(double));
   double* Ax = malloc(N * sizeof(double));
-  ora_rhs(g, dt, D, E_old, b);
-  ora_apply(g, dt, D, x, Ax);
+  rhs_ax(g, dt, Dax, E_old, b);
+  apply_ax(g, dt, Dax, x, Ax);
   double rr = 0;
   for (size_t c = 0; c < N; ++c) rr += (b[c] - Ax[c]) * (b[c] - Ax[c]);
   double bb = dot(N, b, b);
@@ -381,8 +383,8 @@ double ora_relres(const ora_grid* g, double dt, const double* D, const double* E
   return sqrt(rr / bb);
 }
 
-int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* E_old, double* x,
-                   double rtol, int maxit, double* relres, int* iters) {
+static int diffuse_cg_ax(const ora_grid* g, double dt, const double* const* Dax, const double* E_old, double* x,
+                         double rtol, int maxit, double* relres, int* iters) {
   for (int f = 0; f < 2 * g->ndim; ++f)
     if (g->bc[f] == ORA_BC_CONTINUOUS) return 1; /* not symmetric */
   size_t N = ncells(g);
@@ -392,7 +394,7 @@ int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* 
   double* pv = malloc(N * sizeof(double));
   double* Ap = malloc(N * sizeof(double));
   double* dinv = malloc(N * sizeof(double));
-  ora_rhs(g, dt, D, E_old, b);
+  rhs_ax(g, dt, Dax, E_old, b);
   for (size_t c = 0; c < N; ++c) {
     int q[3];
     unlin(g, c, q);
@@ -401,14 +403,14 @@ int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* 
       for (int side = 0; side < 2; ++side) {
         double cs, cn, cc;
         long nb;
-        face_term(g, dt, D, q, a, side, &cs, &nb, &cn, &cc);
+        face_term(g, dt, Dax, q, a, side, &cs, &nb, &cn, &cc);
         d += cs;
       }
     dinv[c] = 1.0 / d;
     x[c] = E_old[c];
   }
   double bnorm = sqrt(dot(N, b, b));
-  ora_apply(g, dt, D, x, Ap);
+  apply_ax(g, dt, Dax, x, Ap);
   for (size_t c = 0; c < N; ++c) r[c] = b[c] - Ap[c];
   for (size_t c = 0; c < N; ++c) z[c] = dinv[c] * r[c];
   memcpy(pv, z, N * sizeof(double));
@@ -417,7 +419,7 @@ int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* 
   double best = sqrt(dot(N, r, r)) / bnorm;
   int since_check = 0;
   while (it < maxit && best > rtol) {
-    ora_apply(g, dt, D, pv, Ap);
+    apply_ax(g, dt, Dax, pv, Ap);
     double alpha = rz / dot(N, pv, Ap);
     for (size_t c = 0; c < N; ++c) {
       x[c] += alpha * pv[c];
@@ -428,7 +430,7 @@ int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* 
     double rn = sqrt(dot(N, r, r)) / bnorm;
     if (rn <= rtol || since_check >= 50) {
       /* replace the recursive residual by the true one */
-      ora_apply(g, dt, D, x, Ap);
+      apply_ax(g, dt, Dax, x, Ap);
       for (size_t c = 0; c < N; ++c) r[c] = b[c] - Ap[c];
       double tn = sqrt(dot(N, r, r)) / bnorm;
       since_check = 0;
@@ -452,7 +454,7 @@ int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* 
     rz = rz2;
     for (size_t c = 0; c < N; ++c) pv[c] = z[c] + beta * pv[c];
   }
-  double rel = ora_relres(g, dt, D, E_old, x);
+  double rel = relres_ax(g, dt, Dax, E_old, x);
   if (relres) *relres = rel;
   if (iters) *iters = it;
   free(b);
@@ -462,6 +464,37 @@ int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* 
   free(Ap);
   free(dinv);
   return rel <= rtol ? 0 : 4;
+}
+
+
+/* public forms: one D for all axes, or one per axis (the diagonal-tensor D of Sect. 6) */
+void ora_apply(const ora_grid* g, double dt, const double* D, const double* x, double* Ax) {
+  const double* Dax[3] = {D, D, D};
+  apply_ax(g, dt, Dax, x, Ax);
+}
+void ora_rhs(const ora_grid* g, double dt, const double* D, const double* E_old, double* b) {
+  const double* Dax[3] = {D, D, D};
+  rhs_ax(g, dt, Dax, E_old, b);
+}
+double ora_relres(const ora_grid* g, double dt, const double* D, const double* E_old, const double* x) {
+  const double* Dax[3] = {D, D, D};
+  return relres_ax(g, dt, Dax, E_old, x);
+}
+int ora_diffuse_cg(const ora_grid* g, double dt, const double* D, const double* E_old, double* x, double rtol,
+                   int maxit, double* relres, int* iters) {
+  const double* Dax[3] = {D, D, D};
+  return diffuse_cg_ax(g, dt, Dax, E_old, x, rtol, maxit, relres, iters);
+}
+void ora_apply_aniso(const ora_grid* g, double dt, const double* const* Dax, const double* x, double* Ax) {
+  apply_ax(g, dt, Dax, x, Ax);
+}
+double ora_relres_aniso(const ora_grid* g, double dt, const double* const* Dax, const double* E_old,
+                        const double* x) {
+  return relres_ax(g, dt, Dax, E_old, x);
+}
+int ora_diffuse_cg_aniso(const ora_grid* g, double dt, const double* const* Dax, const double* E_old, double* x,
+                         double rtol, int maxit, double* relres, int* iters) {
+  return diffuse_cg_ax(g, dt, Dax, E_old, x, rtol, maxit, relres, iters);
 }
 
 /* Gaussian elimination with partial pivoting on a dense row-major n x n matrix. */
@@ -497,6 +530,7 @@ static int dense_solve(int n, double* M, double* rhs) {
 }
 
 int ora_diffuse_dense(const ora_grid* g, double dt, const double* D, const double* E_old, double* x) {
+  const double* Dax[3] = {D, D, D};
   size_t N = ncells(g);
   if (N > 8192) return 1;
   double* M = calloc(N * N, sizeof(double));
@@ -508,7 +542,7 @@ int ora_diffuse_dense(const ora_grid* g, double dt, const double* D, const doubl
       for (int side = 0; side < 2; ++side) {
         double cs, cn, cc;
         long nb;
-        face_term(g, dt, D, q, a, side, &cs, &nb, &cn, &cc);
+        face_term(g, dt, Dax, q, a, side, &cs, &nb, &cn, &cc);
         M[c * N + c] += cs;
         if (nb >= 0) M[c * N + nb] += cn;
       }

@@ -62,6 +62,12 @@ double ora_relres(const ora_grid* g, double dt, const double* D_cell, const doub
 /* Jacobi-preconditioned conjugate gradients (symmetric boundary conditions only). */
 int ora_diffuse_cg(const ora_grid* g, double dt, const double* D_cell, const double* E_old, double* E_new,
                    double rtol, int maxit, double* relres, int* iters);
+/* the same with a diagonal-tensor D: Dax[a] is the cell-centred D of axis a */
+void ora_apply_aniso(const ora_grid* g, double dt, const double* const* Dax, const double* x, double* Ax);
+double ora_relres_aniso(const ora_grid* g, double dt, const double* const* Dax, const double* E_old,
+                        const double* x);
+int ora_diffuse_cg_aniso(const ora_grid* g, double dt, const double* const* Dax, const double* E_old, double* x,
+                         double rtol, int maxit, double* relres, int* iters);
 /* Dense LU with partial pivoting on the assembled matrix (small grids; any boundary). */
 int ora_diffuse_dense(const ora_grid* g, double dt, const double* D_cell, const double* E_old, double* E_new);
 

@@ -160,13 +160,14 @@ __global__ void kb_faces(const Tile* __restrict__ tiles, const BFine* __restrict
   const BFine& f = fine[tl.grid];
   const BLev<T>& L0 = lev[tl.grid * kMaxLev];
   const bool copy = sizeof(T) == sizeof(float);
+  const double* const Dax[3] = {f.D, f.D, f.D};
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
     long long idx = tl.start + c;
     if (copy)
-      faces_cell<float>(f.g, f.dt, f.D, idx, f.w64[0], f.w64[1], f.w64[2], (float*)L0.L.w[0], (float*)L0.L.w[1],
+      faces_cell<float>(f.g, f.dt, Dax, idx, f.w64[0], f.w64[1], f.w64[2], (float*)L0.L.w[0], (float*)L0.L.w[1],
                         (float*)L0.L.w[2]);
     else
-      faces_cell<double>(f.g, f.dt, f.D, idx, f.w64[0], f.w64[1], f.w64[2], nullptr, nullptr, nullptr);
+      faces_cell<double>(f.g, f.dt, Dax, idx, f.w64[0], f.w64[1], f.w64[2], nullptr, nullptr, nullptr);
   }
 }
 

@@ -197,7 +197,7 @@ fld_status read_status(fld_ctx* ctx, cudaStream_t s, unsigned* status, int* iter
   return FLD_OK;
 }
 
-fld_status run_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* D,
+fld_status run_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* const D[3],
                        const double* E_old, double* E_new, SolveStats* st, cudaStream_t s) {
   GridDev g = to_dev(grid);
   cudaError_t e = ctx->mg.configure(g, p->precision);
@@ -302,20 +302,15 @@ fld_status fld_coeffs(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, c
   return FLD_OK;
 }
 
-fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* D_cell,
-                       const double* E_old, double* E_new, fld_info* info, void* stream) {
-  if (!ctx) return FLD_ERR_INVALID_ARG;
-  ctx->err.clear();
-  fld_status st = check_grid(ctx, grid);
-  if (st == FLD_OK) st = check_params(ctx, p, true);
-  if (st == FLD_OK) st = check_coarsest(ctx, grid);
-  if (st != FLD_OK) return st;
-  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
-  if (!D_cell || !E_old || !E_new) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell, E_old and E_new must be non-NULL");
+namespace {
+
+fld_status diffuse_common(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                          const double* const Dax[3], const double* E_old, double* E_new, fld_info* info,
+                          void* stream) {
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   SolveStats ss;
-  st = run_diffuse(ctx, grid, p, dt, D_cell, E_old, E_new, &ss, s);
+  fld_status st = run_diffuse(ctx, grid, p, dt, Dax, E_old, E_new, &ss, s);
   if (st != FLD_OK) return st;
   if (info) {
     memset(info, 0, sizeof(*info));
@@ -327,6 +322,46 @@ fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, 
     return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
                 ss.relres, ss.cycles);
   return FLD_OK;
+}
+
+fld_status diffuse_checks(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* E_old,
+                          double* E_new) {
+  fld_status st = check_grid(ctx, grid);
+  if (st == FLD_OK) st = check_params(ctx, p, true);
+  if (st == FLD_OK) st = check_coarsest(ctx, grid);
+  if (st != FLD_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
+  if (!E_old || !E_new) return fail(ctx, FLD_ERR_INVALID_ARG, "E_old and E_new must be non-NULL");
+  return FLD_OK;
+}
+
+}  // namespace
+
+fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* D_cell,
+                       const double* E_old, double* E_new, fld_info* info, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = diffuse_checks(ctx, grid, p, dt, E_old, E_new);
+  if (st != FLD_OK) return st;
+  if (!D_cell) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell must be non-NULL");
+  const double* const Dax[3] = {D_cell, D_cell, D_cell};
+  return diffuse_common(ctx, grid, p, dt, Dax, E_old, E_new, info, stream);
+}
+
+fld_status fld_diffuse_aniso(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                             const double* const* D_axis, const double* E_old, double* E_new, fld_info* info,
+                             void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = diffuse_checks(ctx, grid, p, dt, E_old, E_new);
+  if (st != FLD_OK) return st;
+  if (!D_axis) return fail(ctx, FLD_ERR_INVALID_ARG, "D_axis must be non-NULL");
+  const double* Dax[3] = {nullptr, nullptr, nullptr};
+  for (int a = 0; a < 3; ++a) {
+    Dax[a] = a < grid->ndim ? D_axis[a] : D_axis[0];
+    if (!Dax[a]) return fail(ctx, FLD_ERR_INVALID_ARG, "D_axis[%d] is NULL", a);
+  }
+  return diffuse_common(ctx, grid, p, dt, Dax, E_old, E_new, info, stream);
 }
 
 fld_status fld_exchange(fld_ctx* ctx, size_t n, const fld_params* p, double dt, const double* rho, const double* kappa,
@@ -391,7 +426,8 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
     if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint copies");
     e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
-    if ((st = run_diffuse(ctx, grid, p, 0.5 * dt, ctx->D, E, E, &ss, s)) != FLD_OK) return st;
+    const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
+    if ((st = run_diffuse(ctx, grid, p, 0.5 * dt, Dax, E, E, &ss, s)) != FLD_OK) return st;
     e = launch_midpoint_combine(g.ncell, E0, eps0, Eh, E, eps, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint combine launch");
     e = launch_exchange(g.ncell, xp, op, rho, nullptr, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
@@ -404,7 +440,8 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
     e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status,
                       s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
-    if ((st = run_diffuse(ctx, grid, p, dt, ctx->D, E, E, &ss, s)) != FLD_OK) return st;
+    const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
+    if ((st = run_diffuse(ctx, grid, p, dt, Dax, E, E, &ss, s)) != FLD_OK) return st;
     if (p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE) {
       // eps is unchanged by the diffusion, so kappa^n from the coefficient stage is current
       e = launch_exchange(g.ncell, xp, op, rho, ctx->kappa, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);

@@ -22,13 +22,17 @@ __global__ void k_coeffs(GridDev g, CoeffPhys ph, const double* __restrict__ E, 
   D_out[idx] = D;
 }
 
+struct DAxes {
+  const double* d[3];
+};
+
 template <class TW>
-__global__ void k_faces(GridDev g, double dt, const double* __restrict__ D, double* __restrict__ w0,
+__global__ void k_faces(GridDev g, double dt, DAxes D, double* __restrict__ w0,
                         double* __restrict__ w1, double* __restrict__ w2, TW* __restrict__ t0, TW* __restrict__ t1,
                         TW* __restrict__ t2, float* __restrict__ l0, float* __restrict__ l1, float* __restrict__ l2) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.ncell) return;
-  faces_cell<TW>(g, dt, D, idx, w0, w1, w2, t0, t1, t2, l0, l1, l2);
+  faces_cell<TW>(g, dt, D.d, idx, w0, w1, w2, t0, t1, t2, l0, l1, l2);
 }
 
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -43,9 +47,10 @@ cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double 
   return cudaGetLastError();
 }
 
-cudaError_t launch_faces(const GridDev& g, double dt, const double* D, double* const w64[3], float* const w32[3],
-                         float* const w32lo[3], cudaStream_t s) {
+cudaError_t launch_faces(const GridDev& g, double dt, const double* const Dax[3], double* const w64[3],
+                         float* const w32[3], float* const w32lo[3], cudaStream_t s) {
   TraceScope ts("faces", s);
+  const DAxes D{{Dax[0], Dax[1], Dax[2]}};
   if (w32 && w32[0])
     k_faces<float><<<blocks_for(g.ncell), kBlock, 0, s>>>(g, dt, D, w64[0], w64[1], w64[2], w32[0], w32[1], w32[2],
                                                            w32lo ? w32lo[0] : nullptr, w32lo ? w32lo[1] : nullptr,

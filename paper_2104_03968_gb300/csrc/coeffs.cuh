@@ -107,8 +107,10 @@ __device__ __forceinline__ bool coeffs_cell(const GridDev& g, const CoeffPhys& p
 // other two sums times it.
 // With lo arrays (l0..l2 non-null, TW = float) the FP32 copy is the truncated leading part of the
 // FP64 weight and lo receives the remainder, so that t + l carries the weight to ~2^-47.
+// D[a] is the cell-centred diffusion coefficient of axis a: the same array three times for the
+// scalar D of the paper, three arrays for a diagonal-tensor D.
 template <class TW>
-__device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const double* __restrict__ D, long long idx,
+__device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const double* const (&D)[3], long long idx,
                                            double* __restrict__ w0, double* __restrict__ w1, double* __restrict__ w2,
                                            TW* __restrict__ t0, TW* __restrict__ t1, TW* __restrict__ t2,
                                            float* __restrict__ l0 = nullptr, float* __restrict__ l1 = nullptr,
@@ -118,7 +120,7 @@ __device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const do
   long long r = idx / g.n[0];
   q[1] = (int)(r % g.n[1]);
   q[2] = (int)(r / g.n[1]);
-  const double Dc = __ldg(D + idx);
+  double Dc[3] = {0.0, 0.0, 0.0};
   double num[3] = {0, 0, 0}, den[3] = {1, 1, 1};
   bool pair[3] = {false, false, false};
   long long stride = 1;
@@ -126,13 +128,14 @@ __device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const do
   for (int a = 0; a < 3; ++a) {
     if (a < g.ndim) {
       int p = q[a];
+      Dc[a] = (a == 0 || D[a] != D[0]) ? __ldg(D[a] + idx) : Dc[0];
       if (p > 0 || g.bc[2 * a] == FLD_BC_PERIODIC) {
-        double Dn = __ldg(D + (p > 0 ? idx - stride : idx + (long long)(g.n[a] - 1) * stride));
-        num[a] = 2.0 * Dc * Dn;
-        den[a] = Dc + Dn;
+        double Dn = __ldg(D[a] + (p > 0 ? idx - stride : idx + (long long)(g.n[a] - 1) * stride));
+        num[a] = 2.0 * Dc[a] * Dn;
+        den[a] = Dc[a] + Dn;
         pair[a] = true;
       } else {
-        num[a] = Dc;
+        num[a] = Dc[a];
       }
     }
     stride *= g.n[a];
@@ -161,7 +164,7 @@ __device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const do
     put(a, face_index(g.n, a, q[0], q[1], q[2], q[a]), w);
     const bool periodic = g.bc[2 * a + 1] == FLD_BC_PERIODIC;
     if ((periodic && q[a] == 0) || (!periodic && q[a] == g.n[a] - 1)) {
-      const double wu = periodic ? w : s * Dc;
+      const double wu = periodic ? w : s * Dc[a];
       put(a, face_index(g.n, a, q[0], q[1], q[2], g.n[a]), wu);
     }
   }

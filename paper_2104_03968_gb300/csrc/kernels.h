@@ -12,9 +12,10 @@ cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double 
                           double* kappa_out, double* D_out, unsigned* status, cudaStream_t s);
 
 // w64[a] (and w32[a] when non-null) receive the face weights of axis a (layout of fld_common.cuh);
-// with w32lo, w32 holds the truncated leading 24 bits of each weight and w32lo the remainder
-cudaError_t launch_faces(const GridDev& g, double dt, const double* D, double* const w64[3], float* const w32[3],
-                         float* const w32lo[3], cudaStream_t s);
+// with w32lo, w32 holds the truncated leading 24 bits of each weight and w32lo the remainder.
+// Dax[a]: cell-centred D of axis a (the same pointer three times for a scalar D).
+cudaError_t launch_faces(const GridDev& g, double dt, const double* const Dax[3], double* const w64[3],
+                         float* const w32[3], float* const w32lo[3], cudaStream_t s);
 
 // E = E0 + 2 (E - Eh), eps = eps0 (midpoint IMEX recombination)
 cudaError_t launch_midpoint_combine(long long n, const double* E0, const double* eps0, const double* Eh, double* E,

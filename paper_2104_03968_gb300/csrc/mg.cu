@@ -723,7 +723,7 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
 
 
 template <class T>
-cudaError_t Multigrid::setup_t(double dt, const double* D_cell, const double* E_old, cudaStream_t s) {
+cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const double* E_old, cudaStream_t s) {
   float* w32[3] = {nullptr, nullptr, nullptr};
   if (precision_ == FLD_PREC_MIXED)
     for (int a = 0; a < g_.ndim; ++a) w32[a] = (float*)lv_[0].w[a];
@@ -752,7 +752,8 @@ cudaError_t Multigrid::setup_t(double dt, const double* D_cell, const double* E_
   return cudaGetLastError();
 }
 
-cudaError_t Multigrid::setup(double dt, const double* D_cell, const double* E_old, unsigned* status, cudaStream_t s) {
+cudaError_t Multigrid::setup(double dt, const double* const D_cell[3], const double* E_old, unsigned* status,
+                             cudaStream_t s) {
   (void)status;
   return precision_ == FLD_PREC_MIXED ? setup_t<float>(dt, D_cell, E_old, s) : setup_t<double>(dt, D_cell, E_old, s);
 }

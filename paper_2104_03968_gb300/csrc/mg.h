@@ -53,8 +53,9 @@ class Multigrid {
 
   // (Re)build the level hierarchy for grid g and precision; keeps buffers when unchanged.
   cudaError_t configure(const GridDev& g, int precision);
-  // Face weights, diagonals and coarse operators from the cell-centred D; rhs from E_old.
-  cudaError_t setup(double dt, const double* D_cell, const double* E_old, unsigned* status, cudaStream_t s);
+  // Face weights, diagonals and coarse operators from the cell-centred D (D_cell[a] for the faces
+  // of axis a); rhs from E_old.
+  cudaError_t setup(double dt, const double* const D_cell[3], const double* E_old, unsigned* status, cudaStream_t s);
   // Outer iterations until ||b - A x||/||b|| <= rtol or max_cycles cycles; writes E_new.  With
   // fmg_start the first cycle is a full-multigrid cycle, the others V-cycles.
   cudaError_t solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
@@ -65,7 +66,7 @@ class Multigrid {
 
  private:
   template <class T>
-  cudaError_t setup_t(double dt, const double* D_cell, const double* E_old, cudaStream_t s);
+  cudaError_t setup_t(double dt, const double* const D_cell[3], const double* E_old, cudaStream_t s);
   template <class T>
   cudaError_t solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                       bool fmg_start, SolveStats* st, cudaStream_t s);

@@ -75,6 +75,7 @@ _SIGS = {
     "fld_columns_step": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P, P],
     "fld_columns_diffuse": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P],
     "fld_radiation_terms": [P, P, P, P, P, P, P, P, P, P, P, P, P, ct.c_int, P],
+    "fld_diffuse_aniso": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_photon_tiring_step": [P, P, P, ct.c_double, P, P, P, P, P],
 }
 
@@ -223,6 +224,22 @@ def diffuse(ctx: Context, grid: dict, params: dict, dt: float, D, E_old, out=Non
     info = Info()
     st = ctx.lib.fld_diffuse(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(D), _dptr(E_old), _dptr(E_new),
                              ct.byref(info), _stream())
+    if st and st != 4:
+        ctx.check(st)
+    return E_new, info.as_dict()
+
+
+def diffuse_aniso(ctx: Context, grid: dict, params: dict, dt: float, D_axis, E_old, out=None):
+    """Backward-Euler diffusion with a diagonal-tensor D (one CUDA tensor per axis)."""
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    for d in D_axis:
+        _dptr(d)
+    arr = (ct.c_void_p * len(D_axis))(*[d.data_ptr() for d in D_axis])
+    E_new = torch.empty_like(E_old) if out is None else out
+    info = Info()
+    st = ctx.lib.fld_diffuse_aniso(ctx.h, ct.byref(g), ct.byref(p), float(dt), ct.cast(arr, ct.c_void_p),
+                                   _dptr(E_old), _dptr(E_new), ct.byref(info), _stream())
     if st and st != 4:
         ctx.check(st)
     return E_new, info.as_dict()

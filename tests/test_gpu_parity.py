@@ -219,6 +219,27 @@ def test_fmg_start(ctx, shape, bcname, precision):
     assert cyc["fmg"] <= cyc["vcycle"]
 
 
+@pytest.mark.parametrize("shape,bcname", [((32, 24, 16), "periodic"), ((64, 48), "mixed"), ((48, 32, 24), "dirichlet")])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_diffuse_diagonal_tensor(ctx, shape, bcname, precision):
+    """fld_diffuse_aniso: one heterogeneous D per axis, against the oracle's per-axis operator."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=90 + len(shape), bc=BCS[bcname], dt_factor=50.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    rng = np.random.default_rng(91)
+    Dax = [D * np.exp(0.5 * rng.standard_normal(D.shape)) * f for f in (1.0, 0.3, 2.0)[:len(shape)]]
+    ref = oracle.diffuse(g, case["dt"], Dax, case["E"], rtol=1e-14)
+    rtol = 1e-13 if precision == "fp64" else 1e-12
+    out, info = fld.diffuse_aniso(ctx, g, solver(p, precision=precision, rtol=rtol), case["dt"], [dev(d) for d in Dax],
+                                  dev(case["E"]))
+    assert info["status"] == 0, info
+    x = host(out).reshape(ref.shape)
+    assert oracle.relres(g, case["dt"], Dax, case["E"], x) < 3 * rtol
+    assert relerr(x, ref) < TOL
+
+
 def test_diffuse_continuous_boundary(ctx):
     from paper_2104_03968_gb300 import fld
     case = inputs.random_small((32, 16), seed=5, bc=BCS["continuous"], dt_factor=2.0)
