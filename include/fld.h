@@ -60,8 +60,12 @@ typedef enum {
   FLD_ERR_UNSUPPORTED = 7
 } fld_status;
 
-/* boundary conditions (Sect. 3.4): ghost value, fixed gradient, linear extrapolation */
-enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2, FLD_BC_CONTINUOUS = 3 };
+/* boundary conditions (Sect. 3.4): ghost value, fixed gradient, linear extrapolation; and, for the
+   inner face of radial columns only, a fixed luminosity L (Sect. 5.2): the ghost is
+   E_0 + L dr / (4 pi r_0^2 D_0) with r_0 the first cell centre, dr the distance to the ghost centre
+   and D_0 the first cell's D of the state entering the step (whose gradient there uses a linear
+   extrapolation); the boundary value is L */
+enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2, FLD_BC_CONTINUOUS = 3, FLD_BC_LUMINOSITY = 4 };
 /* Eq. fld_lambda; lambda = 1/3 (the diffusion limit); or the Minerbo limiter, the alternative
    Sect. 2.2 names: lambda = 2/(3 + sqrt(9 + 12 R^2)) for R <= 3/2, 1/(1 + R + sqrt(1 + 2R)) above */
 enum { FLD_LIMITER_LP = 0, FLD_LIMITER_THIRD = 1, FLD_LIMITER_MINERBO = 2 };
@@ -87,6 +91,20 @@ typedef struct {
   double bc_val[6];
 } fld_grid;
 
+/* CAK line opacity of radial columns (Sect. 5.1, Eq. kap_cak), added to the opacity model wherever
+   the opacity enters (coefficients and exchange):
+     kappa_CAK = kQ / (1 - alpha) (|dv/dr| / (c kQ rho))^alpha,
+   dv/dr by the central difference of the cell-centre velocities (one-sided at the column ends),
+   alpha(x), x = 1 - r_star / r: alpha_in for x <= x_in, alpha_out for x >= x_out, linear between
+   (the paper: 0.66, 0.5, 0.4, 0.65). */
+typedef struct {
+  const double* v;            /* DEVICE, [column][cell]: radial velocity at the cell centres */
+  double kappa_e_Qbar;        /* kQ, the line opacity when every line is optically thin */
+  double r_star;
+  double alpha_in, alpha_out; /* 0 <= alpha < 1 */
+  double x_in, x_out;         /* x_in <= x_out */
+} fld_cak;
+
 typedef struct {
   /* physics (code units or cgs, consistently) */
   double c;        /* speed of light */
@@ -111,6 +129,7 @@ typedef struct {
   int order;       /* FLD_ORDER_* used by fld_step */
   int start;       /* FLD_START_*: first cycle of fld_diffuse / fld_step (fld_step_batched always
                       starts with a V-cycle) */
+  const fld_cak* cak; /* HOST pointer; column calls only: CAK line opacity, or NULL */
 } fld_params;
 
 typedef struct {

@@ -34,7 +34,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3}
+BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3, "luminosity": 4}
 LIMITER = {"lp": 0, "third": 1, "minerbo": 2}
 OPACITY = {"const": 0, "kramers": 1, "table": 2}
 GEOMETRY = {"cartesian": 0, "spherical": 1}
@@ -92,6 +92,8 @@ def _load():
                 "ora_relres_aniso": (ct.c_double, [P, ct.c_double, P, _D, _D]),
                 "ora_diffuse_cg_aniso": (ct.c_int, [P, ct.c_double, P, _D, _D, ct.c_double, ct.c_int,
                                                     _D, ct.POINTER(ct.c_int)]),
+                "ora_kappa_cak": (None, [ct.c_int, _D, _D, _D, ct.c_double, ct.c_double, ct.c_double,
+                                         ct.c_double, ct.c_double, ct.c_double, ct.c_double, _D]),
                 "ora_column_coeffs": (ct.c_int, [ct.c_int, _D, ct.c_int, ct.c_int, ct.c_double,
                                                  ct.c_double, P, _D, _D, _D, _D]),
                 "ora_column_diffuse": (ct.c_int, [ct.c_int, _D, ct.c_int, ct.c_int, ct.c_int,
@@ -410,21 +412,38 @@ def imex_midpoint(eps, E, dt, exch, diffusion):
     return exch(eps, E_star, dt)
 
 
+def kappa_cak(col: dict, phys: dict, rho, cak: dict) -> np.ndarray:
+    """Sect. 5.1, Eq. (kap_cak): the CAK line opacity of one column.  cak: {"v": radial velocity
+    at the cell centres, "kappa_e_Qbar", "r_star", "alpha_in", "alpha_out", "x_in", "x_out"}."""
+    rf = _f64(col["r_faces"])
+    rho, v = _f64(rho), _f64(cak["v"])
+    out = np.empty_like(rho)
+    _load().ora_kappa_cak(rf.size - 1, _ptr(rf), _ptr(rho), _ptr(v), float(phys["c"]), float(cak["kappa_e_Qbar"]),
+                          float(cak["r_star"]), float(cak["alpha_in"]), float(cak["alpha_out"]), float(cak["x_in"]),
+                          float(cak["x_out"]), _ptr(out))
+    return out
+
+
 def column_step(col: dict, phys: dict, dt: float, rho, eps, E, v_lo: float, v_hi: float,
-                order: str = "diffuse_then_exchange", exch_maxit: int = 100):
-    """One radiation-energy update of a single 1-D column (tridiagonal diffusion)."""
+                order: str = "diffuse_then_exchange", exch_maxit: int = 100, cak: dict = None):
+    """One radiation-energy update of a single 1-D column (tridiagonal diffusion).  With cak, the
+    CAK line opacity (Sect. 5.1) is added to the opacity model everywhere the opacity enters."""
     rho, eps, E = _f64(rho), _f64(eps), _f64(E)
     info = {}
+    k_line = kappa_cak(col, phys, rho, cak) if cak is not None else 0.0
+
+    def kappa_of(eps_):
+        return opacity(phys, rho, eps_) + k_line
 
     def diffusion(eps_, E_, h=dt):
-        kap = opacity(phys, rho, eps_)
+        kap = kappa_of(eps_)
         D = column_coeffs(col, phys, E_, rho, kap, v_lo, v_hi)
         En = column_diffuse(col, h, D, E_, v_lo, v_hi)
         info["relres"] = column_relres(col, h, D, E_, En, v_lo, v_hi)
         return En
 
     def exch(eps_, E_, h=dt):
-        kap = opacity(phys, rho, eps_)
+        kap = kappa_of(eps_)
         e2, E2, inf = exchange(phys, h, rho, kap, eps_, E_, maxit=exch_maxit)
         info.update(inf)
         return e2, E2

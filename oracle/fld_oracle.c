@@ -8,6 +8,7 @@
  *
  * What each function follows:
  *   ora_lambda            Sect. 2.2, Eq. (fld_lambda): Levermore-Pomraning limiter.
+ *   ora_kappa_cak         Sect. 5.1, Eq. (kap_cak): CAK line opacity along a radial column.
  *   ora_radiation_sources Sect. 2.1-2.2 and 3.2: flux, radiation force and work, Eddington
  *                         factor and tensor, photon tiring P : grad v.
  *   ora_lambda_minerbo    the Minerbo limiter that Sect. 2.2 names as the alternative (its
@@ -42,6 +43,8 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+static const double kPi = 3.14159265358979323846;
 
 /* ------------------------------------------------------------------ physics */
 
@@ -563,6 +566,9 @@ static double col_centre(int n, const double* rf, int i) {
 }
 
 static double col_ghost(int n, const double* rf, const double* E, int side, int bc, double v) {
+  /* the luminosity boundary needs D, which needs this gradient: the coefficients see a linear
+     extrapolation there (the operator then imposes the luminosity with that D) */
+  if (bc == ORA_BC_LUMINOSITY) bc = ORA_BC_CONTINUOUS;
   if (side == 0) {
     double h = col_centre(n, rf, 0) - col_centre(n, rf, -1);
     if (bc == ORA_BC_DIRICHLET) return v;
@@ -573,6 +579,19 @@ static double col_ghost(int n, const double* rf, const double* E, int side, int 
   if (bc == ORA_BC_DIRICHLET) return v;
   if (bc == ORA_BC_NEUMANN) return E[n - 1] + v * h;
   return E[n - 1] + (E[n - 1] - E[n - 2]) * h / (col_centre(n, rf, n - 1) - col_centre(n, rf, n - 2));
+}
+
+void ora_kappa_cak(int n, const double* rf, const double* rho, const double* v, double c, double kQ,
+                   double rstar, double a_in, double a_out, double x_in, double x_out, double* out) {
+  for (int i = 0; i < n; ++i) {
+    double r = col_centre(n, rf, i);
+    double x = 1.0 - rstar / r;
+    double alpha = x <= x_in ? a_in : (x >= x_out ? a_out : a_in + (a_out - a_in) * (x - x_in) / (x_out - x_in));
+    /* second-order central difference of v; one-sided at the column ends */
+    int lo = i > 0 ? i - 1 : 0, hi = i < n - 1 ? i + 1 : n - 1;
+    double dvdr = (v[lo] - v[hi]) / (col_centre(n, rf, lo) - col_centre(n, rf, hi));
+    out[i] = kQ / (1.0 - alpha) * pow(fabs(dvdr) / (c * kQ * rho[i]), alpha);
+  }
 }
 
 int ora_column_coeffs(int n, const double* rf, int bc_lo, int bc_hi, double v_lo, double v_hi,
@@ -622,6 +641,10 @@ static void col_row(int n, const double* rf, int geom, int bc_lo, int bc_hi, dou
     *cst += wl * v_lo;
   } else if (bc_lo == ORA_BC_NEUMANN) {
     *cst -= wl * v_lo * hl;
+  } else if (bc_lo == ORA_BC_LUMINOSITY) {
+    /* Sect. 5.2: ghost = E_0 + L dr / (4 pi r_0^2 D_0), D from the state entering the step */
+    double r0 = col_centre(n, rf, 0);
+    *cst += wl * v_lo * hl / (4.0 * kPi * r0 * r0 * D[0]);
   } else { /* continuous: ghost = x0 - (x1-x0)*hl/h01 */
     double f = hl / (col_centre(n, rf, 1) - col_centre(n, rf, 0));
     *diag += wl * (-f);

@@ -14,7 +14,8 @@
 extern "C" {
 #endif
 
-enum { ORA_BC_PERIODIC = 0, ORA_BC_NEUMANN = 1, ORA_BC_DIRICHLET = 2, ORA_BC_CONTINUOUS = 3 };
+enum { ORA_BC_PERIODIC = 0, ORA_BC_NEUMANN = 1, ORA_BC_DIRICHLET = 2, ORA_BC_CONTINUOUS = 3,
+       ORA_BC_LUMINOSITY = 4 /* columns, inner face only: fixed luminosity (Sect. 5.2) */ };
 enum { ORA_LIM_LP = 0, ORA_LIM_THIRD = 1, ORA_LIM_MINERBO = 2 };
 enum { ORA_OPA_CONST = 0, ORA_OPA_KRAMERS = 1, ORA_OPA_TABLE = 2 };
 enum { ORA_GEOM_CARTESIAN = 0, ORA_GEOM_SPHERICAL = 1 };
@@ -73,6 +74,10 @@ int ora_diffuse_dense(const ora_grid* g, double dt, const double* D_cell, const 
 
 /* One 1-D column on a stretched radial grid (r_faces: n+1 values).  Finite-volume operator with
    area r^2 and volume (r+^3-r-^3)/3 (spherical) or 1 and width (Cartesian); Thomas algorithm. */
+/* Sect. 5.1, Eq. (kap_cak): CAK line opacity of one column from the radial velocity v at the cell
+   centres; alpha(x), x = 1 - rstar/r: a_in for x <= x_in, a_out for x >= x_out, linear between */
+void ora_kappa_cak(int n, const double* rf, const double* rho, const double* v, double c, double kQ,
+                   double rstar, double a_in, double a_out, double x_in, double x_out, double* out);
 int ora_column_coeffs(int n, const double* r_faces, int bc_lo, int bc_hi, double v_lo, double v_hi,
                       const ora_phys* p, const double* E, const double* rho, const double* kappa,
                       double* D_cell);

@@ -89,8 +89,11 @@ fld_status check_grid(fld_ctx* ctx, const fld_grid* g) {
   return FLD_OK;
 }
 
-fld_status check_params(fld_ctx* ctx, const fld_params* p, bool solver) {
+fld_status check_params(fld_ctx* ctx, const fld_params* p, bool solver, bool columns = false) {
   if (!p) return fail(ctx, FLD_ERR_INVALID_ARG, "params is NULL");
+  if (p->cak && !columns) return fail(ctx, FLD_ERR_INVALID_ARG, "the CAK line opacity applies to column calls only");
+  if (!cak_valid(p->cak))
+    return fail(ctx, FLD_ERR_INVALID_ARG, "CAK: v, kappa_e_Qbar > 0, r_star > 0, 0 <= alpha < 1, x_in <= x_out");
   if (!(p->c > 0) || !(p->a_rad > 0) || !(p->gamma > 1) || !(p->gas_R > 0))
     return fail(ctx, FLD_ERR_INVALID_ARG, "c, a_rad, gas_R must be > 0 and gamma > 1");
   if (p->start != FLD_START_FMG && p->start != FLD_START_VCYCLE)
@@ -566,8 +569,11 @@ fld_status fld_columns_step(fld_ctx* ctx, int ncol, int ncell, const double* r_f
                             const double* rho, double* eps, double* E, fld_info* info, void* stream) {
   if (!ctx) return FLD_ERR_INVALID_ARG;
   ctx->err.clear();
-  fld_status st = check_params(ctx, p, false);
+  fld_status st = check_params(ctx, p, false, true);
   if (st != FLD_OK) return st;
+  if (p->order != FLD_ORDER_DIFFUSE_THEN_EXCHANGE && p->order != FLD_ORDER_EXCHANGE_THEN_DIFFUSE &&
+      p->order != FLD_ORDER_IMEX_MIDPOINT)
+    return fail(ctx, FLD_ERR_INVALID_ARG, "unknown order %d", p->order);
   std::string err;
   st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);
   if (st != FLD_OK) return fail(ctx, st, "%s", err.c_str());
@@ -595,7 +601,7 @@ fld_status fld_columns_diffuse(fld_ctx* ctx, int ncol, int ncell, const double* 
                                const double* D_cell, const double* E_old, double* E_new, void* stream) {
   if (!ctx) return FLD_ERR_INVALID_ARG;
   ctx->err.clear();
-  fld_status st = check_params(ctx, p, false);
+  fld_status st = check_params(ctx, p, false, true);
   if (st != FLD_OK) return st;
   std::string err;
   st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);

@@ -61,6 +61,10 @@ __global__ void k_col_geometry(int n, const double* __restrict__ rf, int geometr
 struct ColArgs {
   int n;
   int bc_lo, bc_hi;
+  const double* rf;  // r_faces (n + 1)
+  // CAK line opacity (cak_v null: none)
+  const double* cak_v;
+  double cak_kQ, cak_rstar, cak_a_in, cak_a_out, cak_x_in, cak_x_out;
   const double* v_lo;
   const double* v_hi;
   const double* dt;
@@ -225,6 +229,8 @@ __global__ void k_columns(ColArgs A) {
   double* rc = rb + 2 * P;
   double* rd = rc + 2 * P;
   double* sh = rd + 2 * P;  // midpoint IMEX: E after the half-step exchange
+  double* sq = sh + (MODE == kColStepMidpoint ? n : 0);  // CAK line opacity per cell
+  const bool cak = MODE != kColDiffuse && A.cak_v != nullptr;
   const long long base = (long long)blockIdx.x * n;
   const double dtc = A.dt[blockIdx.x];
   const double dtd = MODE == kColStepMidpoint ? 0.5 * dtc : dtc;  // the diffusion stage's step
@@ -248,12 +254,27 @@ __global__ void k_columns(ColArgs A) {
     }
   }
   __syncthreads();
+  if (cak) {
+    // Sect. 5.1, Eq. kap_cak: alpha(1 - R*/r), dv/dr central (one-sided at the ends)
+    for (int i = t; i < n; i += P) {
+      auto rc = [&](int k) { return 0.5 * (A.rf[k] + A.rf[k + 1]); };
+      const double r = rc(i), x = 1.0 - A.cak_rstar / r;
+      const double alpha = x <= A.cak_x_in    ? A.cak_a_in
+                           : x >= A.cak_x_out ? A.cak_a_out
+                                              : A.cak_a_in + (A.cak_a_out - A.cak_a_in) * (x - A.cak_x_in) /
+                                                                 (A.cak_x_out - A.cak_x_in);
+      const int lo = i > 0 ? i - 1 : 0, hi = i < n - 1 ? i + 1 : n - 1;
+      const double dvdr = (A.cak_v[base + lo] - A.cak_v[base + hi]) / (rc(lo) - rc(hi));
+      sq[i] = A.cak_kQ / (1.0 - alpha) * pow(fabs(dvdr) / (A.c * A.cak_kQ * sr[i]), alpha);
+    }
+    __syncthreads();
+  }
   const int s0 = t * M, s1 = min(s0 + M, n);
 
   if (MODE == kColStepExchangeFirst || MODE == kColStepMidpoint) {
     for (int i = s0; i < s1; ++i) {
       double e = se[i], E = sx[i];
-      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e));
+      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
       if (exchange_cell(xp1, sr[i], k, e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
@@ -267,7 +288,7 @@ __global__ void k_columns(ColArgs A) {
   if (MODE != kColDiffuse) {
     for (int i = s0; i < s1; ++i) {
       double e = sx[i], rh = sr[i];
-      double k = opacity(A.op, rh, temperature(A.gamma, A.gas_R, rh, se[i]));
+      double k = opacity(A.op, rh, temperature(A.gamma, A.gas_R, rh, se[i])) + (cak ? sq[i] : 0.0);
       sk[i] = k;
       if (!(e > 0.0) || !(rh > 0.0) || !(k > 0.0) || !(se[i] >= 0.0)) bad = true;
       double em, ep;
@@ -300,6 +321,10 @@ __global__ void k_columns(ColArgs A) {
       d += wl * vlo;
     } else if (A.bc_lo == FLD_BC_NEUMANN) {
       d -= wl * vlo * hl;
+    } else if (A.bc_lo == FLD_BC_LUMINOSITY) {
+      // Sect. 5.2: ghost = E_0 + L hl / (4 pi r_0^2 D_0)
+      const double r0 = 0.5 * (A.rf[0] + A.rf[1]);
+      d += wl * vlo * hl / (4.0 * 3.14159265358979323846 * r0 * r0 * sD[0]);
     } else {
       b -= wl * flo;
       c += wl * flo;
@@ -483,7 +508,7 @@ __global__ void k_columns(ColArgs A) {
     for (int i = s0; i < s1; ++i) {
       double E = fma(2.0, sx[i] - sh[i], A.Ein[base + i]);
       double e = A.eps[base + i];
-      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e));
+      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
       if (exchange_cell(xp, sr[i], k, e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
@@ -505,6 +530,12 @@ __global__ void k_columns(ColArgs A) {
   }
 }
 
+bool cak_valid(const fld_cak* c) {
+  if (!c) return true;
+  return c->v && c->kappa_e_Qbar > 0 && c->r_star > 0 && c->alpha_in >= 0 && c->alpha_in < 1 && c->alpha_out >= 0 &&
+         c->alpha_out < 1 && c->x_in <= c->x_out;
+}
+
 fld_status columns_validate(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo, int bc_hi,
                             const double* v_lo, const double* v_hi, const double* dt, std::string* err) {
   char buf[256];
@@ -521,10 +552,11 @@ fld_status columns_validate(int ncol, int ncell, const double* r_faces, int geom
   if (!r_faces) return bad("r_faces is NULL");
   if (geometry != FLD_GEOM_CARTESIAN && geometry != FLD_GEOM_SPHERICAL) return bad("unknown geometry");
   for (int bc : {bc_lo, bc_hi})
-    if (bc != FLD_BC_DIRICHLET && bc != FLD_BC_NEUMANN && bc != FLD_BC_CONTINUOUS)
-      return bad("column boundaries must be Dirichlet, Neumann or continuous");
+    if (bc != FLD_BC_DIRICHLET && bc != FLD_BC_NEUMANN && bc != FLD_BC_CONTINUOUS && bc != FLD_BC_LUMINOSITY)
+      return bad("column boundaries must be Dirichlet, Neumann, continuous or (inner) luminosity");
+  if (bc_hi == FLD_BC_LUMINOSITY) return bad("the luminosity boundary is for the inner face only");
   if ((bc_lo != FLD_BC_CONTINUOUS && !v_lo) || (bc_hi != FLD_BC_CONTINUOUS && !v_hi))
-    return bad("v_lo / v_hi are required for Dirichlet and Neumann boundaries");
+    return bad("v_lo / v_hi are required for Dirichlet, Neumann and luminosity boundaries");
   if (!dt) return bad("dt is NULL");
   return FLD_OK;
 }
@@ -536,14 +568,14 @@ static int col_threads(int n) {
   return P;
 }
 
-static size_t col_smem(int n, int P, int mode) {
-  return (size_t)((mode == kColStepMidpoint ? 10 : 9) * n + 8 * P) * sizeof(double);
+static size_t col_smem(int n, int P, int mode, bool cak) {
+  return (size_t)((9 + (mode == kColStepMidpoint ? 1 : 0) + (cak ? 1 : 0)) * n + 8 * P) * sizeof(double);
 }
 
 template <int MODE, bool MIXED>
 static cudaError_t launch_kernel(int ncol, int ncell, ColArgs& A, cudaStream_t s) {
   int P = col_threads(ncell);
-  size_t smem = col_smem(ncell, P, MODE);
+  size_t smem = col_smem(ncell, P, MODE, MODE != kColDiffuse && A.cak_v != nullptr);
   cudaError_t e = cudaFuncSetAttribute(k_columns<MODE, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_columns<MODE, MIXED><<<ncol, P, smem, s>>>(A);
@@ -559,12 +591,22 @@ static cudaError_t launch_mode(int ncol, int ncell, const double* r_faces, int g
                                      : launch_kernel<MODE, false>(ncol, ncell, A, s);
 }
 
-static ColArgs col_args(int ncell, int bc_lo, int bc_hi, const double* v_lo, const double* v_hi, const fld_params& p,
-                        const double* dt, double* geom) {
+static ColArgs col_args(int ncell, const double* r_faces, int bc_lo, int bc_hi, const double* v_lo,
+                        const double* v_hi, const fld_params& p, const double* dt, double* geom) {
   ColArgs A{};
   A.n = ncell;
+  A.rf = r_faces;
   A.bc_lo = bc_lo;
   A.bc_hi = bc_hi;
+  if (p.cak) {
+    A.cak_v = p.cak->v;
+    A.cak_kQ = p.cak->kappa_e_Qbar;
+    A.cak_rstar = p.cak->r_star;
+    A.cak_a_in = p.cak->alpha_in;
+    A.cak_a_out = p.cak->alpha_out;
+    A.cak_x_in = p.cak->x_in;
+    A.cak_x_out = p.cak->x_out;
+  }
   A.v_lo = v_lo;
   A.v_hi = v_hi;
   A.dt = dt;
@@ -593,7 +635,7 @@ cudaError_t launch_columns_step(int ncol, int ncell, const double* r_faces, int 
                                 const double* v_lo, const double* v_hi, const fld_params& p, const double* dt,
                                 const double* rho, double* eps, double* E, double* geom, int* info_iters,
                                 int* info_bisect, unsigned* status, cudaStream_t s) {
-  ColArgs A = col_args(ncell, bc_lo, bc_hi, v_lo, v_hi, p, dt, geom);
+  ColArgs A = col_args(ncell, r_faces, bc_lo, bc_hi, v_lo, v_hi, p, dt, geom);
   A.rho = rho;
   A.Ein = E;
   A.Eout = E;
@@ -612,7 +654,7 @@ cudaError_t launch_columns_diffuse(int ncol, int ncell, const double* r_faces, i
                                    const double* v_lo, const double* v_hi, const fld_params& p, const double* dt,
                                    const double* D_cell, const double* E_old, double* E_new, double* geom,
                                    cudaStream_t s) {
-  ColArgs A = col_args(ncell, bc_lo, bc_hi, v_lo, v_hi, p, dt, geom);
+  ColArgs A = col_args(ncell, r_faces, bc_lo, bc_hi, v_lo, v_hi, p, dt, geom);
   A.Din = D_cell;
   A.Ein = E_old;
   A.Eout = E_new;
@@ -659,7 +701,7 @@ bool static_params_ok(const fld_params* p) {
   if (p->opacity == FLD_OPACITY_TABLE &&
       (!p->table || p->tn[0] < 2 || p->tn[1] < 2 || !(p->thi[0] > p->tlo[0]) || !(p->thi[1] > p->tlo[1])))
     return false;
-  if (p->exch_maxit < 0) return false;
+  if (p->exch_maxit < 0 || !cak_valid(p->cak)) return false;
   return p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE || p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE ||
          p->order == FLD_ORDER_IMEX_MIDPOINT;
 }
@@ -689,7 +731,7 @@ extern "C" fld_status fld_columns_step_static(int ncol, int ncell, const double*
   int* bisect = reinterpret_cast<int*>(scratch + kStaticGeom + 2);
   // the counters keep the previous call's values: clear them
   if (cudaMemsetAsync(scratch + kStaticGeom, 0, 3 * sizeof(double), s) != cudaSuccess) return FLD_ERR_CUDA;
-  ColArgs A = col_args(ncell, bc_lo, bc_hi, v_lo, v_hi, *p, dt, geom);
+  ColArgs A = col_args(ncell, r_faces, bc_lo, bc_hi, v_lo, v_hi, *p, dt, geom);
   A.rho = rho;
   A.Ein = E;
   A.Eout = E;

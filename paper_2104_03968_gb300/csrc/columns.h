@@ -11,6 +11,8 @@ namespace fld {
 
 constexpr int kColumnMaxCells = 2048;
 
+// CAK parameters (NULL is valid: no CAK term)
+bool cak_valid(const fld_cak* c);
 fld_status columns_validate(int ncol, int ncell, const double* r_faces, int geometry, int bc_lo, int bc_hi,
                             const double* v_lo, const double* v_hi, const double* dt, std::string* err);
 

@@ -22,7 +22,7 @@ import torch
 
 from . import build as _build
 
-BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3}
+BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3, "luminosity": 4}
 LIMITER = {"lp": 0, "third": 1, "minerbo": 2}
 OPACITY = {"const": 0, "kramers": 1, "table": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
@@ -44,13 +44,18 @@ class Grid(ct.Structure):
                 ("bc_val", ct.c_double * 6)]
 
 
+class Cak(ct.Structure):
+    _fields_ = [("v", ct.c_void_p), ("kappa_e_Qbar", ct.c_double), ("r_star", ct.c_double),
+                ("alpha_in", ct.c_double), ("alpha_out", ct.c_double), ("x_in", ct.c_double), ("x_out", ct.c_double)]
+
+
 class Params(ct.Structure):
     _fields_ = [("c", ct.c_double), ("a_rad", ct.c_double), ("gamma", ct.c_double), ("gas_R", ct.c_double),
                 ("limiter", ct.c_int), ("opacity", ct.c_int), ("kappa0", ct.c_double), ("kr_a", ct.c_double),
                 ("kr_b", ct.c_double), ("table", ct.c_void_p), ("tn", ct.c_int * 2), ("tlo", ct.c_double * 2),
                 ("thi", ct.c_double * 2), ("precision", ct.c_int), ("rtol", ct.c_double),
                 ("max_cycles", ct.c_int), ("nu1", ct.c_int), ("nu2", ct.c_int), ("exch_maxit", ct.c_int),
-                ("order", ct.c_int), ("start", ct.c_int)]
+                ("order", ct.c_int), ("start", ct.c_int), ("cak", ct.c_void_p)]
 
 
 class Info(ct.Structure):
@@ -190,6 +195,16 @@ def params_struct(p: dict, keep: list, device) -> Params:
     s.exch_maxit = int(p.get("exch_maxit", 0))
     s.order = ORDER[p.get("order", "diffuse_then_exchange")]
     s.start = START[p.get("start", "fmg")]
+    cak = p.get("cak")
+    if cak is not None:
+        v = cak["v"]
+        if not isinstance(v, torch.Tensor) or not v.is_cuda:
+            v = torch.as_tensor(np.ascontiguousarray(v, dtype=np.float64), device=device)
+        v = v.contiguous()
+        c = Cak(v.data_ptr(), float(cak["kappa_e_Qbar"]), float(cak["r_star"]), float(cak["alpha_in"]),
+                float(cak["alpha_out"]), float(cak["x_in"]), float(cak["x_out"]))
+        keep.extend([v, c])
+        s.cak = ct.cast(ct.pointer(c), ct.c_void_p)
     return s
 
 

@@ -242,11 +242,13 @@ def wind_columns(ncol: int = 4096, ncell: int = 2048, seed: int = 4, dt_factor: 
     rho = np.empty((ncol, ncell))
     E = np.empty((ncol, ncell))
     Tg = np.empty((ncol, ncell))
+    vel = np.empty((ncol, ncell))
     for j in range(ncol):
         Mdot = Mdot0 * rng.uniform(0.8, 1.2)
         vinf = vinf0 * rng.uniform(0.8, 1.2)
         rs = Rs * rng.uniform(1.02, 1.3)
         v = np.maximum(vinf * np.sqrt(np.maximum(1 - Rs / rc, 0.0)), 1e-3 * vinf)
+        vel[j] = v
         r_wind = Mdot / (4 * np.pi * rc ** 2 * v)
         vs = max(vinf * math.sqrt(1 - Rs / rs), 1e-3 * vinf)
         rho_s = Mdot / (4 * np.pi * rs ** 2 * vs)
@@ -265,7 +267,14 @@ def wind_columns(ncol: int = 4096, ncell: int = 2048, seed: int = 4, dt_factor: 
     return {"name": f"wind_columns_{ncol}x{ncell}", "phys": phys, "r_faces": rf,
             "geometry": "spherical", "bc": ["dirichlet", "dirichlet"], "rho": rho, "eps": eps,
             "E": E, "bc_lo": E[:, 0].copy(), "bc_hi": E[:, -1].copy(), "dt": dt_factor * dt_exp,
-            "dt_exp": dt_exp}
+            "dt_exp": dt_exp, "v": vel, "L": L, "r_star": Rs}
+
+
+def wind_cak(case: dict, Qbar: float = 2000.0) -> dict:
+    """CAK line-opacity parameters of the wind columns (Sect. 5.1): kappa_e Qbar with electron
+    scattering kappa_e = 0.2 cm^2/g, alpha 0.66 -> 0.5 between 1 - R*/r = 0.4 and 0.65."""
+    return {"v": case["v"], "kappa_e_Qbar": 0.2 * Qbar, "r_star": case["r_star"], "alpha_in": 0.66,
+            "alpha_out": 0.5, "x_in": 0.4, "x_out": 0.65}
 
 
 def heating_cooling(e_ratio: float, dt: float, ncell: int = 16) -> dict:

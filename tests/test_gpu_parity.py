@@ -434,6 +434,30 @@ def test_columns_step_parity(ctx, ncell, order, precision):
         assert relerr(host(eps)[j], e_o) < TOL
 
 
+@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse", "imex_midpoint"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_columns_wind_cak_and_luminosity(ctx, order, precision):
+    """Sect. 5.1-5.2: CAK line opacity from the wind velocity added to the table opacity, and the
+    fixed-luminosity inner boundary, through the fused column kernel."""
+    from paper_2104_03968_gb300 import fld
+    ncol, ncell = 4, 512
+    case = _column_case(ncol, ncell, seed=2)
+    cak = inputs.wind_cak(case)
+    p = solver(case["phys"], order=order, precision=precision, cak=cak)
+    L = np.full(ncol, case["L"])
+    eps, E = dev(case["eps"]), dev(case["E"])
+    info = fld.columns_step(ctx, case["r_faces"], "spherical", ("luminosity", "dirichlet"), L, case["bc_hi"], p,
+                            case["dt"], dev(case["rho"]), eps, E)
+    assert info["status"] == 0
+    col = {"r_faces": case["r_faces"], "geometry": "spherical", "bc": ("luminosity", "dirichlet")}
+    for j in range(ncol):
+        cj = dict(cak, v=case["v"][j])
+        e_o, E_o, _ = oracle.column_step(col, case["phys"], case["dt"][j], case["rho"][j], case["eps"][j],
+                                         case["E"][j], L[j], case["bc_hi"][j], order=order, cak=cj)
+        assert relerr(host(E)[j], E_o) < TOL
+        assert relerr(host(eps)[j], e_o) < TOL
+
+
 @pytest.mark.parametrize("geometry", ["spherical", "cartesian"])
 @pytest.mark.parametrize("bc", [("dirichlet", "dirichlet"), ("neumann", "dirichlet"), ("continuous", "neumann")])
 def test_columns_diffuse_parity(ctx, geometry, bc):

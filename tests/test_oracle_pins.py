@@ -698,3 +698,58 @@ def test_diagonal_tensor_diffusion_fourier():
     # the relative residual routine agrees on the per-axis operator
     assert oracle.relres(g, dt, [np.full_like(E, d) for d in Ds], E, ref) < 1e-13
     assert oracle.relres(g, dt, [np.full_like(E, d) for d in Ds[::-1]], E, ref) > 1e-3
+
+
+# ----------------------------------------------------------------------------- wind columns
+
+def _cak_case(n=200, a=1e-3):
+    rf = np.geomspace(1.0, 10.0, n + 1)
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    cak = {"v": a * rc, "kappa_e_Qbar": 2000.0, "r_star": 1.0, "alpha_in": 0.66, "alpha_out": 0.5,
+           "x_in": 0.4, "x_out": 0.65}
+    return {"r_faces": rf, "geometry": "spherical", "bc": ("dirichlet", "dirichlet")}, rc, cak
+
+
+def test_cak_opacity_power_law_and_alpha_profile():
+    """Sect. 5.1, Eq. (kap_cak): for a linear velocity law dv/dr = a exactly (central and one-sided
+    differences alike), so kappa_CAK ~ a^alpha and rho^-alpha: doubling a multiplies it by 2^alpha(r)
+    and doubling rho by 2^-alpha(r), which recovers alpha(r) = 0.66 for 1 - R*/r <= 0.4, 0.5 beyond
+    0.65 and the straight line between; where a = c kappa_e Qbar rho the bracket is 1 and
+    kappa_CAK = kappa_e Qbar / (1 - alpha)."""
+    col, rc, cak = _cak_case()
+    phys = inputs.code_units()
+    rho = np.full(rc.size, 0.5)
+    k1 = oracle.kappa_cak(col, phys, rho, cak)
+    k2 = oracle.kappa_cak(col, phys, rho, dict(cak, v=2 * cak["v"]))
+    k3 = oracle.kappa_cak(col, phys, 2 * rho, cak)
+    alpha = np.log2(k2 / k1)
+    x = 1 - 1.0 / rc
+    want = np.where(x <= 0.4, 0.66, np.where(x >= 0.65, 0.5, 0.66 + (0.5 - 0.66) * (x - 0.4) / 0.25))
+    assert np.allclose(alpha, want, atol=1e-12)
+    assert np.allclose(np.log2(k3 / k1), -want, atol=1e-12)
+    a = phys["c"] * cak["kappa_e_Qbar"] * rho[0]
+    k4 = oracle.kappa_cak(col, phys, rho, dict(cak, v=a * rc))
+    assert np.allclose(k4, cak["kappa_e_Qbar"] / (1 - want), rtol=1e-12)
+
+
+def test_luminosity_boundary_steady_state():
+    """Sect. 5.2: the inner ghost E_{-1} = E_0 + L dr / (4 pi r_0^2 D_0).  At steady state (uniform
+    D, spherical volumes, Dirichlet outside) every face then carries the same luminosity
+    4 pi r_f^2 D (E_i - E_{i+1}) / h = L (r_{1/2} / r_0)^2 (the boundary flux the ghost implies), and
+    E approaches E_out + L / (4 pi D) (1/r - 1/r_out) as the grid is refined."""
+    phys = dict(inputs.code_units("third"), kappa0=2.0)
+    L, E_out = 5.0, 1.0
+    errs = []
+    for n in (100, 200, 400):
+        rf = np.linspace(1.0, 3.0, n + 1)
+        rc = 0.5 * (rf[1:] + rf[:-1])
+        col = {"r_faces": rf, "geometry": "spherical", "bc": ("luminosity", "dirichlet")}
+        rho = np.ones(n)
+        D = np.full(n, phys["c"] / (3 * 2.0))
+        x = oracle.column_diffuse(col, 1e30, D, np.full(n, E_out), L, E_out)
+        h = np.diff(rc)
+        lum = 4 * np.pi * rf[1:-1] ** 2 * D[0] * (x[:-1] - x[1:]) / h
+        assert np.allclose(lum, L * (rf[0] / rc[0]) ** 2, rtol=1e-9)
+        exact = E_out + L / (4 * np.pi * D[0]) * (1 / rc - 1 / 3.0)
+        errs.append(np.abs(x / exact - 1).max())
+    assert errs[0] < 2e-2 and errs[1] < errs[0] * 0.7 and errs[2] < errs[1] * 0.7
