@@ -205,7 +205,7 @@ fld_status run_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, 
   GridDev g = to_dev(grid);
   cudaError_t e = ctx->mg.configure(g, p->precision);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid allocation");
-  e = ctx->mg.setup(dt, D, E_old, ctx->d_status, s);
+  e = ctx->mg.setup(dt, D, E_old, p->rtol, ctx->d_status, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid setup");
   int maxc = p->max_cycles > 0 ? p->max_cycles : 100;
   int nu1 = p->nu1 > 0 ? p->nu1 : 2, nu2 = p->nu2 > 0 ? p->nu2 : 2;

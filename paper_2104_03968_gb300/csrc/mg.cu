@@ -21,6 +21,7 @@
 #include "kernels.h"
 #include "mg.h"
 #include "df.cuh"
+#include "mg_df.h"
 #include "mg_device.cuh"
 #include "trace.h"
 
@@ -667,7 +668,8 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   const bool df = precision == FLD_PREC_MIXED;  // double-float residual updates
   if (df) {
     for (int a = 0; a < g.ndim; ++a) add(faces3(dims_[0], a) * sizeof(float));  // weights, low parts
-    for (int k = 0; k < 3; ++k) add(N * sizeof(float));                           // diag hi, lo; r lo
+    for (int k = 0; k < 5; ++k) add(N * sizeof(float));                           // diag hi, lo; r lo; b hi, lo
+    add(sizeof(unsigned));
   }
   for (size_t l = 0; l < dims_.size(); ++l) {
     long long n = cells3(dims_[l]);
@@ -689,14 +691,18 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
     if (e != cudaSuccess) return e;
   }
   for (int a = 0; a < 3; ++a) w32lo_[a] = nullptr;
-  dhi_ = dlo_ = rlo_ = nullptr;
+  dhi_ = dlo_ = rlo_ = bhi_ = blo_ = nullptr;
+  df_flag_ = nullptr;
   if (df) {
     for (int a = 0; a < g.ndim; ++a)
       if (!(w32lo_[a] = (float*)arena_.take(faces3(dims_[0], a) * sizeof(float)))) return cudaErrorMemoryAllocation;
     dhi_ = (float*)arena_.take(N * sizeof(float));
     dlo_ = (float*)arena_.take(N * sizeof(float));
     rlo_ = (float*)arena_.take(N * sizeof(float));
-    if (!dhi_ || !dlo_ || !rlo_) return cudaErrorMemoryAllocation;
+    bhi_ = (float*)arena_.take(N * sizeof(float));
+    blo_ = (float*)arena_.take(N * sizeof(float));
+    df_flag_ = (unsigned*)arena_.take(sizeof(unsigned));
+    if (!dhi_ || !dlo_ || !rlo_ || !bhi_ || !blo_ || !df_flag_) return cudaErrorMemoryAllocation;
   }
   lv_.assign(dims_.size(), LevelBuf{});
   for (size_t l = 0; l < dims_.size(); ++l) {
@@ -723,17 +729,57 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
 
 
 template <class T>
-cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const double* E_old, cudaStream_t s) {
+cudaError_t Multigrid::fp64_operator(cudaStream_t s) {
   float* w32[3] = {nullptr, nullptr, nullptr};
   if (precision_ == FLD_PREC_MIXED)
     for (int a = 0; a < g_.ndim; ++a) w32[a] = (float*)lv_[0].w[a];
-  cudaError_t e = launch_faces(g_, dt, D_cell, w64_, w32, dhi_ ? w32lo_ : nullptr, s);
+  cudaError_t e = launch_faces(g_, dt_, D_ax_, w64_, w32, dhi_ ? w32lo_ : nullptr, s);
   if (e != cudaSuccess) return e;
   void* w64v[3] = {w64_[0], w64_[1], w64_[2]};
   LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
   {
     TraceScope ts("fine_setup", s);
-    k_fine_setup<T><<<nblk(g_.ncell), kBlock, 0, s>>>(L64, g_, E_old, b64_, diag64_, (T*)lv_[0].invd, dhi_, dlo_);
+    k_fine_setup<T><<<nblk(g_.ncell), kBlock, 0, s>>>(L64, g_, E_old_, b64_, diag64_, (T*)lv_[0].invd, dhi_, dlo_);
+  }
+  {
+    TraceScope ts("norm_b", s);
+    k_sumsq<<<nparts_, kBlock, 0, s>>>(b64_, g_.ncell, partials_);
+    k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_ + 1);
+  }
+  fp64_op_ = true;
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const double* E_old, double rtol,
+                               cudaStream_t s) {
+  dt_ = dt;
+  for (int a = 0; a < 3; ++a) D_ax_[a] = D_cell[a];
+  E_old_ = E_old;
+  fp64_op_ = false;
+  // double-float setup: mixed solver, a tolerance the certified updates reach, one scalar D,
+  // 32-bit indices
+  long long maxf = g_.ncell;
+  for (int a = 0; a < g_.ndim; ++a) maxf = std::max(maxf, faces3(dims_[0], a));
+  df_mode_ = sizeof(T) == sizeof(float) && dhi_ != nullptr && rtol >= 1e-10 && D_cell[1] == D_cell[0] &&
+             D_cell[2] == D_cell[0] && maxf < (1LL << 31);
+  cudaError_t e;
+  if (df_mode_) {
+    e = cudaMemsetAsync(df_flag_, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const DfConst K = make_df_const(g_, dt);
+    float* w32[3] = {nullptr, nullptr, nullptr};
+    for (int a = 0; a < g_.ndim; ++a) w32[a] = (float*)lv_[0].w[a];
+    e = launch_faces_df(g_, K, D_cell[0], w32, w32lo_, df_flag_, s);
+    if (e != cudaSuccess) return e;
+    void* wlo[3] = {w32lo_[0], w32lo_[1], w32lo_[2]};
+    e = launch_fine_setup_df(g_, K, level_dev<float>(g_, dims_[0], lv_[0].w), level_dev<float>(g_, dims_[0], wlo),
+                             E_old, dhi_, dlo_, (float*)lv_[0].invd, bhi_, blo_, partials_, nparts_, scal_, df_flag_,
+                             s);
+    if (e != cudaSuccess) return e;
+  } else {
+    e = fp64_operator<T>(s);
+    if (e != cudaSuccess) return e;
   }
   for (size_t l = 1; l < dims_.size(); ++l) {
     TraceScope ts("coarse_setup", s);
@@ -743,19 +789,14 @@ cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const d
     LevelDev<T> L = level_dev<T>(g_, dims_[l], lv_[l].w);
     k_invd<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, cells3(dims_[l]), (T*)lv_[l].invd);
   }
-  // ||b||^2
-  {
-    TraceScope ts("norm_b", s);
-    k_sumsq<<<nparts_, kBlock, 0, s>>>(b64_, g_.ncell, partials_);
-    k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_ + 1);
-  }
   return cudaGetLastError();
 }
 
-cudaError_t Multigrid::setup(double dt, const double* const D_cell[3], const double* E_old, unsigned* status,
-                             cudaStream_t s) {
+cudaError_t Multigrid::setup(double dt, const double* const D_cell[3], const double* E_old, double rtol,
+                             unsigned* status, cudaStream_t s) {
   (void)status;
-  return precision_ == FLD_PREC_MIXED ? setup_t<float>(dt, D_cell, E_old, s) : setup_t<double>(dt, D_cell, E_old, s);
+  return precision_ == FLD_PREC_MIXED ? setup_t<float>(dt, D_cell, E_old, rtol, s)
+                                      : setup_t<double>(dt, D_cell, E_old, rtol, s);
 }
 
 // Levels that take the row-wise transfer kernels: 2-D or 3-D, rows of at least 128 cells (the
@@ -899,7 +940,9 @@ cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
 template <class T>
 cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                                bool fmg_start, SolveStats* st, cudaStream_t s) {
-  constexpr double kDrift = 0x1p-43;  // 32 x 2^-48: a generous multiple of the per-cell error / m
+  // per-cell error of a double-float residual over m (|b or r_old| + |diag x| + sum |w x_nb|): the
+  // operations' roundings plus the 2^-45 representation error of the double-float weights
+  constexpr double kDrift = 0x1p-42;
   void* w64v[3] = {w64_[0], w64_[1], w64_[2]};
   LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
   const bool mixed = sizeof(T) == sizeof(float) && dhi_ != nullptr;
@@ -925,6 +968,9 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
   }
   bool updates = false;   // residual updates allowed (decided at the first exact residual)
   bool exact = true;      // next residual: exact FP64 (else an update)
+  bool df_res = false;    // this residual came from the double-float setup
+  unsigned* df_flag = reinterpret_cast<unsigned*>(host_scal_ + 6);
+  *df_flag = 0u;
   double drift = 0.0;
   float scale = 0.f;
   for (;;) {
@@ -946,16 +992,32 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
     } else {
       TraceScope ts("residual", s);
-      if (mixed)
-        k_residual64_df<<<nparts_, kBlock, 0, s>>>(L64, x_in, x, b64_, diag64_, (float*)lv_[0].r, rlo_, partials_);
-      else
-        k_residual64<T><<<nparts_, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r, partials_);
-      k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
+      df_res = mixed && df_mode_ && !fp64_op_ && cycles == 0;
+      if (df_res) {
+        // double-float first residual from the double-float setup (no FP64 operator exists yet)
+        cudaError_t e = launch_residual0_df(g_.ndim, L32, L32lo, dhi_, dlo_, bhi_, blo_, x_in, x, (float*)lv_[0].r,
+                                            rlo_, scal_, nparts_, partials_, s);
+        if (e != cudaSuccess) return e;
+        k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
+        k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
+      } else {
+        if (mixed && !fp64_op_) {
+          cudaError_t e = fp64_operator<T>(s);  // an exact residual after a double-float setup
+          if (e != cudaSuccess) return e;
+        }
+        if (mixed)
+          k_residual64_df<<<nparts_, kBlock, 0, s>>>(L64, x_in, x, b64_, diag64_, (float*)lv_[0].r, rlo_, partials_);
+        else
+          k_residual64<T><<<nparts_, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r,
+                                                     partials_);
+        k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
+      }
     }
-    x_in = x;
     cudaError_t e = cudaMemcpyAsync(host_scal_, scal_, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     if (cycles > 0) e = cudaMemcpyAsync(wave_err, wave_ctl_, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if (df_res) e = cudaMemcpyAsync(df_flag, df_flag_, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
@@ -963,8 +1025,22 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       status = FLD_ERR_DEVICE_TIMEOUT;
       break;
     }
+    if (df_res && *df_flag) {
+      // a value left the double-float window: redo the setup and this residual in FP64
+      e = fp64_operator<T>(s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    x_in = x;
     bb = host_scal_[1];
-    if (upd) {
+    if (df_res) {
+      // scaled sums, as for the updates
+      rel = sqrt(host_scal_[0] / N);
+      drift = kDrift * sqrt(host_scal_[2] / N);
+      const double rms = sqrt(bb / N);
+      updates = rms * std::max(rtol, 1e-16) * 1e-3 >= 0x1p-76 && rms <= 0x1p90;
+      scale = (float)(1.0 / rms);
+    } else if (upd) {
       // scaled sums: sum (r / rms(b))^2 = N ||r||^2 / ||b||^2
       rel = sqrt(host_scal_[0] / N);
       drift += kDrift * sqrt(host_scal_[2] / N);

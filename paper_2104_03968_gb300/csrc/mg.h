@@ -55,7 +55,9 @@ class Multigrid {
   cudaError_t configure(const GridDev& g, int precision);
   // Face weights, diagonals and coarse operators from the cell-centred D (D_cell[a] for the faces
   // of axis a); rhs from E_old.
-  cudaError_t setup(double dt, const double* const D_cell[3], const double* E_old, unsigned* status, cudaStream_t s);
+  // rtol: the solve's tolerance (the mixed solver sets up in double-float when rtol >= 1e-10).
+  cudaError_t setup(double dt, const double* const D_cell[3], const double* E_old, double rtol, unsigned* status,
+                    cudaStream_t s);
   // Outer iterations until ||b - A x||/||b|| <= rtol or max_cycles cycles; writes E_new.  With
   // fmg_start the first cycle is a full-multigrid cycle, the others V-cycles.
   cudaError_t solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
@@ -66,7 +68,10 @@ class Multigrid {
 
  private:
   template <class T>
-  cudaError_t setup_t(double dt, const double* const D_cell[3], const double* E_old, cudaStream_t s);
+  cudaError_t setup_t(double dt, const double* const D_cell[3], const double* E_old, double rtol, cudaStream_t s);
+  // the FP64 finest-level operator (weights, diagonal, rhs, ||b||) for the exact FP64 residual
+  template <class T>
+  cudaError_t fp64_operator(cudaStream_t s);
   template <class T>
   cudaError_t solve_t(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                       bool fmg_start, SolveStats* st, cudaStream_t s);
@@ -93,6 +98,16 @@ class Multigrid {
   float* dhi_ = nullptr;
   float* dlo_ = nullptr;
   float* rlo_ = nullptr;
+  // double-float setup (mixed solver, rtol >= 1e-10): rhs b as hi + lo, the out-of-window flag,
+  // and the setup inputs kept for an FP64 redo
+  float* bhi_ = nullptr;
+  float* blo_ = nullptr;
+  unsigned* df_flag_ = nullptr;
+  bool df_mode_ = false;
+  bool fp64_op_ = false;
+  double dt_ = 0.0;
+  const double* D_ax_[3] = {nullptr, nullptr, nullptr};
+  const double* E_old_ = nullptr;
   // Wavefront smoothing (large 3-D levels): per level, the (half-sweep, plane) of each group of
   // `nchunk` tickets in ticket order; control words [0] error, [1] ticket, [2..] finished chunks
   // per (half-sweep, plane).

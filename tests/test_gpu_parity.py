@@ -240,6 +240,43 @@ def test_diffuse_diagonal_tensor(ctx, shape, bcname, precision):
     assert relerr(x, ref) < TOL
 
 
+@pytest.mark.parametrize("shape,bcname", [((64, 48, 40), "periodic"), ((96, 64), "mixed"), ((48, 40, 32), "neumann"),
+                                          ((40, 32, 24), "dirichlet"), ((80, 48), "continuous"), ((512,), "mixed")])
+@pytest.mark.parametrize("rtol", [1e-8, 1e-10])
+def test_mixed_double_float_setup(ctx, shape, bcname, rtol):
+    """At rtol >= 1e-10 the mixed solver builds its finest level (weights, diagonal, rhs, first
+    residual) in double-float arithmetic; the oracle's FP64 operator applied to the result must
+    meet rtol, whatever the boundary conditions."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=100 + len(shape) + len(bcname), bc=BCS[bcname], dt_factor=100.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    out, info = fld.diffuse(ctx, g, solver(p, precision="mixed", rtol=rtol), case["dt"], dev(D), dev(case["E"]))
+    assert info["status"] == 0, info
+    x = host(out).reshape(case["E"].shape)
+    assert oracle.relres(g, case["dt"], D, case["E"], x) <= 1.01 * rtol
+    if bcname != "continuous":  # the oracle's CG needs a symmetric operator
+        ref = oracle.diffuse(g, case["dt"], D, case["E"], rtol=1e-14)
+        assert relerr(x, ref) < 1e3 * rtol
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1e30])
+def test_mixed_double_float_setup_out_of_window(ctx, scale):
+    """E outside the double-float window [2^-77, 2^90) (|E| ~ 1e-25 or 1e30): the setup falls back to
+    FP64 and the solve still meets rtol (the problem is linear, so the solution scales with E)."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small((48, 40, 32), seed=7, bc=BCS["periodic"], dt_factor=100.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    E = case["E"] * scale
+    out, info = fld.diffuse(ctx, g, solver(p, precision="mixed", rtol=1e-8), case["dt"], dev(D), dev(E))
+    assert info["status"] == 0, info
+    x = host(out).reshape(E.shape)
+    assert oracle.relres(g, case["dt"], D, E, x) <= 1.01e-8
+
+
 def test_diffuse_continuous_boundary(ctx):
     from paper_2104_03968_gb300 import fld
     case = inputs.random_small((32, 16), seed=5, bc=BCS["continuous"], dt_factor=2.0)
