@@ -60,9 +60,9 @@ __device__ __forceinline__ bool coeffs_cell(const GridDev& g, const CoeffPhys& p
   double kap;
   if (ph.op.model == FLD_OPACITY_KRAMERS && ph.op.kr_a == 1.0 && ph.op.kr_b == -3.5) {
     // kappa = kappa0 rho T^-3.5 with 1/T = rho gas_R / ((gamma-1) eps): one reciprocal, one sqrt
-    double it = rh * ph.gas_R * (1.0 / ((ph.gamma - 1.0) * ep));
+    double it = rh * ph.gas_R * rcp_nr((ph.gamma - 1.0) * ep);
     double it2 = it * it;
-    kap = ph.op.kappa0 * rh * it2 * it * sqrt(it);
+    kap = ph.op.kappa0 * rh * it2 * it * sqrt_nr(it);
   } else {
     kap = opacity(ph.op, rh, temperature(ph.gamma, ph.gas_R, rh, ep));
   }
@@ -95,7 +95,7 @@ __device__ __forceinline__ bool coeffs_cell(const GridDev& g, const CoeffPhys& p
     g2 = fma(d * d, g.inv_dx2[a], g2);
   }
   const double q_ = kap * rh;  // kappa rho, the inverse mean free path
-  const double D = limited_D(ph.limiter, ph.c, q_, e, g2, ph.limiter == FLD_LIMITER_THIRD ? 0.0 : sqrt(g2));
+  const double D = limited_D(ph.limiter, ph.c, q_, e, g2, ph.limiter == FLD_LIMITER_THIRD ? 0.0 : sqrt_nr(g2));
   D_out = D;
   return true;
 }
@@ -140,7 +140,7 @@ __device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const do
     }
     stride *= g.n[a];
   }
-  const double inv = 1.0 / (den[0] * den[1] * den[2]);
+  const double inv = rcp_nr(den[0] * den[1] * den[2]);
   const double rd[3] = {den[1] * den[2] * inv, den[0] * den[2] * inv, den[0] * den[1] * inv};
   double* W[3] = {w0, w1, w2};
   TW* Tt[3] = {t0, t1, t2};

@@ -65,7 +65,7 @@ __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k
   const double r3 = r * r * r;
   const double P = r3 * B;
   // one reciprocal gives 1/rho^3, 1/(1+a2) and 1/S
-  const double inv = 1.0 / (P * S);
+  const double inv = rcp_nr(P * S);
   double ir3, u, invS;
   if (pos_finite(inv)) {
     ir3 = B * S * inv;

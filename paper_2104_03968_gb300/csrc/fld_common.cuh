@@ -91,8 +91,42 @@ __device__ __forceinline__ long long cell_index(const int n[3], int i, int j, in
   return (long long)i + (long long)n[0] * ((long long)j + (long long)n[1] * k);
 }
 
+// Reciprocal and reciprocal square root for positive FP64 values, by Newton-Raphson refinement of
+// an FP32 seed: x = m 2^k with m in [1, 2) (or [2, 4) for the square root, k even), the FP32
+// intrinsic on m, one Newton step in FP64, and the power of two put back through the exponent
+// field.  Relative error ~2^-47 (one step squares the seed's ~2^-24); about half the FP64
+// instructions of the correctly rounded operations, which GB300 builds from the same pieces.
+// Zero, subnormal, infinite or NaN input takes the IEEE operation (out of line, so that the
+// compiler does not predicate it into every call).
+static __device__ __noinline__ double rcp_ieee(double x) { return 1.0 / x; }
+static __device__ __noinline__ double rsqrt_ieee(double x) { return 1.0 / sqrt(x); }
+
+__device__ __forceinline__ double rcp_nr(double x) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int ef = (hi >> 20) & 0x7ff;
+  if (ef == 0 || ef == 0x7ff) return rcp_ieee(x);
+  const double m = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, lo);
+  const double r0 = (double)__frcp_rn((float)m);
+  const double r = fma(r0, fma(-m, r0, 1.0), r0);  // 1/m, in (0.5, 1]
+  return __hiloint2double(__double2hiint(r) - ((ef - 1023) << 20), __double2loint(r));
+}
+
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int ef = (hi >> 20) & 0x7ff;
+  if (ef == 0 || ef == 0x7ff || hi < 0) return rsqrt_ieee(x);
+  const int k = ef - 1023, kk = k & ~1;  // x = m 2^kk, m in [1, 4)
+  const double m = __hiloint2double((hi & 0x000fffff) | ((1023 + (k - kk)) << 20), lo);
+  const double y0 = (double)__frsqrt_rn((float)m);
+  const double y = y0 * fma(-0.5 * m * y0, y0, 1.5);  // 1/sqrt(m), in (0.5, 1]
+  return __hiloint2double(__double2hiint(y) - ((kk / 2) << 20), __double2loint(y));
+}
+
+// sqrt(x) = x / sqrt(x) for x > 0, 0 for x == 0
+__device__ __forceinline__ double sqrt_nr(double x) { return x > 0.0 ? x * rsqrt_nr(x) : 0.0; }
+
 __device__ __forceinline__ double temperature(double gamma, double gas_R, double rho, double eps) {
-  return (gamma - 1.0) * eps / (rho * gas_R);
+  return (gamma - 1.0) * eps * rcp_nr(rho * gas_R);
 }
 
 // Opacity per cell: constant, Kramers-like power law, or bilinear table in (log10 rho,
@@ -100,7 +134,10 @@ __device__ __forceinline__ double temperature(double gamma, double gas_R, double
 __device__ inline double opacity(const Opacity& o, double rho, double T) {
   if (o.model == FLD_OPACITY_CONST) return o.kappa0;
   if (o.model == FLD_OPACITY_KRAMERS) {
-    if (o.kr_a == 1.0 && o.kr_b == -3.5) return o.kappa0 * rho / (T * T * T * sqrt(T));
+    if (o.kr_a == 1.0 && o.kr_b == -3.5) {
+      const double it = rcp_nr(T);
+      return o.kappa0 * rho * (it * it * it) * sqrt_nr(it);  // rho T^-3.5
+    }
     return o.kappa0 * pow(rho, o.kr_a) * pow(T, o.kr_b);
   }
   double u = (log10(rho) - o.tlo0) / (o.thi0 - o.tlo0) * (o.tn0 - 1);
@@ -125,12 +162,12 @@ __device__ inline double opacity(const Opacity& o, double rho, double T) {
 //   third    lambda = 1/3                              D = c / (3q)
 __device__ __forceinline__ double limited_D(int limiter, double c, double q, double e, double g2, double gm) {
   const double qe = q * e;
-  if (limiter == FLD_LIMITER_THIRD) return c * (1.0 / (3.0 * q));
+  if (limiter == FLD_LIMITER_THIRD) return c * rcp_nr(3.0 * q);
   if (limiter == FLD_LIMITER_MINERBO) {
-    if (gm <= 1.5 * qe) return 2.0 * c * e * (1.0 / (3.0 * qe + sqrt(fma(9.0 * qe, qe, 12.0 * g2))));
-    return c * e * (1.0 / (qe + gm + sqrt(qe * (qe + 2.0 * gm))));
+    if (gm <= 1.5 * qe) return 2.0 * c * e * rcp_nr(3.0 * qe + sqrt_nr(fma(9.0 * qe, qe, 12.0 * g2)));
+    return c * e * rcp_nr(qe + gm + sqrt_nr(qe * (qe + 2.0 * gm)));
   }
-  return c * e * (2.0 * qe + gm) * (1.0 / (qe * (6.0 * qe + 3.0 * gm) + g2));
+  return c * e * (2.0 * qe + gm) * rcp_nr(qe * (6.0 * qe + 3.0 * gm) + g2);
 }
 
 }  // namespace fld
