@@ -215,7 +215,9 @@ def timed_steps(torch, fld, ctx, g, p, dt, rho, eps, E, steps, trace=False):
     stream = torch.cuda.current_stream()
     infos = []
     if trace:
-        fld.trace_enable(ctx, True)
+        # finest-level and per-step kernels only: the coarse levels' small launches are where the
+        # event records would cost host time inside the timed region
+        fld.trace_enable(ctx, True, major_only=True)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)

@@ -276,7 +276,8 @@ typedef struct {
   double total_ms;
 } fld_trace_entry;
 
-/* on != 0 clears the record and starts tracing; on == 0 stops it (the record is kept). */
+/* on != 0 clears the record and starts tracing (on == 2: only the finest-level and per-step kernels,
+   which costs fewer event records per step); on == 0 stops it (the record is kept). */
 FLD_API fld_status fld_trace_enable(fld_ctx* ctx, int on);
 /* Writes up to `max` entries to `out` and their count to *n.  Synchronises. */
 FLD_API fld_status fld_trace_report(fld_ctx* ctx, fld_trace_entry* out, int max, int* n);

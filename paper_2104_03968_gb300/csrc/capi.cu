@@ -621,6 +621,7 @@ fld_status fld_trace_enable(fld_ctx* ctx, int on) {
   DeviceGuard dg(ctx->device);
   if (on) tracer().clear();
   tracer().on = on != 0;
+  tracer().major_only = on == 2;
   return FLD_OK;
 }
 

@@ -58,4 +58,11 @@ std::vector<Tracer::Entry> Tracer::report() {
   return out;
 }
 
+bool minor_scope(const char* name) {
+  const std::string n(name);
+  const size_t L = n.size();
+  return (L > 3 && n.compare(L - 3, 3, "_Lc") == 0) || n.compare(0, 7, "coarse_") == 0 || n == "reduce" ||
+         n == "fmg_restrict";
+}
+
 }  // namespace fld

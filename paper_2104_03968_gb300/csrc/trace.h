@@ -11,6 +11,7 @@ namespace fld {
 class Tracer {
  public:
   bool on = false;
+  bool major_only = false;  // skip the coarse-level and bookkeeping scopes (cheaper to record)
   void begin(const char* name, cudaStream_t s);
   void end(cudaStream_t s);
   void clear();
@@ -36,11 +37,16 @@ class Tracer {
 
 Tracer& tracer();
 
+// Scopes of the coarse multigrid levels and of small bookkeeping kernels ("..._Lc", "coarse_...",
+// "reduce", "fmg_restrict")
+bool minor_scope(const char* name);
+
 // Records the launches between construction and destruction under `name` when tracing is on.
 struct TraceScope {
   cudaStream_t s;
   bool active;
-  TraceScope(const char* name, cudaStream_t st) : s(st), active(tracer().on) {
+  TraceScope(const char* name, cudaStream_t st)
+      : s(st), active(tracer().on && !(tracer().major_only && minor_scope(name))) {
     if (active) tracer().begin(name, s);
   }
   ~TraceScope() {

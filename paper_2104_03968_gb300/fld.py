@@ -361,10 +361,11 @@ class TraceEntry(ct.Structure):
     _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int), ("total_ms", ct.c_double)]
 
 
-def trace_enable(ctx: Context, on: bool = True):
-    """Start (clearing the record) or stop per-kernel launch timing with CUDA events."""
+def trace_enable(ctx: Context, on: bool = True, major_only: bool = False):
+    """Start (clearing the record) or stop per-kernel launch timing with CUDA events; major_only
+    skips the coarse-level and bookkeeping kernels."""
     ctx.lib.fld_trace_enable.argtypes = [P, ct.c_int]
-    ctx.check(ctx.lib.fld_trace_enable(ctx.h, 1 if on else 0))
+    ctx.check(ctx.lib.fld_trace_enable(ctx.h, (2 if major_only else 1) if on else 0))
 
 
 def trace_report(ctx: Context) -> dict:
