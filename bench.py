@@ -202,11 +202,16 @@ def run_reference(args, world, rank):
     return 0
 
 
-def workload_config(args):
-    return {"workload": f"lognormal-density Kramers-opacity periodic grid {args.n}^3, dt = 100x explicit limit, "
-                        f"full FLD step (coeffs + multigrid diffusion to {args.rtol:g} + exchange)",
-            "grid": [args.n] * 3, "cells": args.n ** 3, "rtol": args.rtol, "precision": args.precision,
-            "nu1": 2, "nu2": 2, "l2_flush": "inputs larger than L2 (1 GiB per field)", "parallelism": "replicas"}
+def workload_config(args, nu=None):
+    """nu: the (nu1, nu2) the library's autotuner chose (reported by the solve), if known."""
+    cfg = {"workload": f"lognormal-density Kramers-opacity periodic grid {args.n}^3, dt = 100x explicit limit, "
+                       f"full FLD step (coeffs + multigrid diffusion to {args.rtol:g} + exchange)",
+           "grid": [args.n] * 3, "cells": args.n ** 3, "rtol": args.rtol, "precision": args.precision,
+           "multigrid": "FMG first cycle, V-cycles after; red-black Gauss-Seidel sweep counts autotuned",
+           "l2_flush": "inputs larger than L2 (1 GiB per field)", "parallelism": "replicas"}
+    if nu is not None:
+        cfg["nu1"], cfg["nu2"] = nu
+    return cfg
 
 
 # ----------------------------------------------------------------------------- GPU leg
@@ -383,7 +388,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64+f32 (FP32 V-cycles, FP64 residual/update/norm/exchange)" if args.precision == "mixed"
                 else "f64",
-                "data": "synthetic", "config": workload_config(args), "roofline": roof, "roofline_hbm": roof_hbm, "cpu_baseline": cpu,
+                "data": "synthetic", "config": workload_config(args, (infos[0]["nu1"], infos[0]["nu2"])), "roofline": roof,
+                "roofline_hbm": roof_hbm, "cpu_baseline": cpu,
                 "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in sorted(rep.items(), key=lambda kv: -kv[1][1])},
                 "cycles_per_step": [i["cycles"] for i in infos],

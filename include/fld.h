@@ -124,7 +124,10 @@ typedef struct {
                       an FP64 defect-correction loop (FP64 residual, update and norm) */
   double rtol;     /* stop when ||b - A E||_2 / ||b||_2 <= rtol */
   int max_cycles;  /* outer iterations (one V-cycle each); 0 = 100 */
-  int nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after coarse correction; 0 = 2 */
+  int nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after coarse correction.  Both 0:
+                      autotuned on the first solve of a grid configuration (per rtol and start:
+                      candidate pairs are timed on a scratch iterate, the fastest converged pair
+                      is kept for later calls); one 0: that one is 2 */
   int exch_maxit;  /* Halley iterations before bisection in the exchange; 0 = 100 */
   int order;       /* FLD_ORDER_* used by fld_step */
   int start;       /* FLD_START_*: first cycle of fld_diffuse / fld_step (fld_step_batched always
@@ -138,6 +141,7 @@ typedef struct {
   int exch_max_iters;      /* largest number of root iterations over the cells */
   int bisection_fallbacks; /* cells that fell back to bisection */
   int status;              /* fld_status of this grid / column set */
+  int nu1, nu2;            /* sweep counts the multigrid solve used (after autotuning) */
 } fld_info;
 
 typedef struct fld_ctx fld_ctx;

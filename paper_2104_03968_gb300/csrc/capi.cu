@@ -208,8 +208,7 @@ fld_status run_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, 
   e = ctx->mg.setup(dt, D, E_old, p->rtol, ctx->d_status, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid setup");
   int maxc = p->max_cycles > 0 ? p->max_cycles : 100;
-  int nu1 = p->nu1 > 0 ? p->nu1 : 2, nu2 = p->nu2 > 0 ? p->nu2 : 2;
-  e = ctx->mg.solve(E_old, E_new, p->rtol, maxc, nu1, nu2, p->start == FLD_START_FMG, st, s);
+  e = ctx->mg.solve(E_old, E_new, p->rtol, maxc, p->nu1, p->nu2, p->start == FLD_START_FMG, st, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid solve");
   return FLD_OK;
 }
@@ -320,6 +319,8 @@ fld_status diffuse_common(fld_ctx* ctx, const fld_grid* grid, const fld_params* 
     info->cycles = ss.cycles;
     info->rel_residual = ss.relres;
     info->status = ss.status;
+    info->nu1 = ss.nu1;
+    info->nu2 = ss.nu2;
   }
   if (ss.status != FLD_OK)
     return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
@@ -459,6 +460,8 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
   inf->cycles = ss.cycles;
   inf->rel_residual = ss.relres;
   inf->status = ss.status;
+  inf->nu1 = ss.nu1;
+  inf->nu2 = ss.nu2;
   if (sbits & kStatNonpositive) {
     inf->status = FLD_ERR_NONPOSITIVE;
     return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state");

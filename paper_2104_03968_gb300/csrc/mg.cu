@@ -529,6 +529,7 @@ static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / 
 
 Multigrid::~Multigrid() {
   if (host_scal_) cudaFreeHost(host_scal_);
+  if (tune_x_) cudaFree(tune_x_);
 }
 
 static inline long long cells3(const std::array<int, 3>& n) { return (long long)n[0] * n[1] * n[2]; }
@@ -645,6 +646,7 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   g_ = g;  // dx and bc values may change freely
   if (same) return cudaSuccess;
   configured_ = false;
+  tuned_.clear();
   precision_ = precision;
   dims_.clear();
   std::array<int, 3> d = {g.n[0], g.n[1], g.n[2]};
@@ -1085,8 +1087,67 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
   return cudaStreamSynchronize(s);
 }
 
+cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int* nu1, int* nu2,
+                                cudaStream_t s) {
+  for (const auto& t : tuned_)
+    if (t[0] == rtol && t[1] == (fmg_start ? 1.0 : 0.0)) {
+      *nu1 = (int)t[2];
+      *nu2 = (int)t[3];
+      return cudaSuccess;
+    }
+  const size_t n = (size_t)g_.ncell;
+  if (tune_cap_ < n) {
+    if (tune_x_) cudaFree(tune_x_);
+    tune_x_ = nullptr;
+    tune_cap_ = 0;
+    cudaError_t e = cudaMalloc(&tune_x_, n * sizeof(double));
+    if (e != cudaSuccess) return e;
+    tune_cap_ = n;
+  }
+  static const int cand[][2] = {{2, 2}, {3, 3}, {2, 1}, {4, 2}, {4, 4}, {5, 3}, {3, 2}, {1, 1}};
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e != cudaSuccess) return e;
+  int best1 = 2, best2 = 2;
+  float best = 1e30f;
+  for (const auto& c : cand) {
+    SolveStats cs;
+    e = cudaEventRecord(a, s);
+    if (e == cudaSuccess)
+      e = precision_ == FLD_PREC_MIXED
+              ? solve_t<float>(E_old, tune_x_, rtol, max_cycles, c[0], c[1], fmg_start, &cs, s)
+              : solve_t<double>(E_old, tune_x_, rtol, max_cycles, c[0], c[1], fmg_start, &cs, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) break;
+    if (cs.status == FLD_OK && ms < best) {
+      best = ms;
+      best1 = c[0];
+      best2 = c[1];
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return e;
+  tuned_.push_back({rtol, fmg_start ? 1.0 : 0.0, (double)best1, (double)best2});
+  *nu1 = best1;
+  *nu2 = best2;
+  return cudaSuccess;
+}
+
 cudaError_t Multigrid::solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                              bool fmg_start, SolveStats* st, cudaStream_t s) {
+  if (nu1 == 0 && nu2 == 0) {
+    cudaError_t e = autotune(E_old, rtol, max_cycles, fmg_start, &nu1, &nu2, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (nu1 == 0) nu1 = 2;
+  if (nu2 == 0) nu2 = 2;
+  st->nu1 = nu1;
+  st->nu2 = nu2;
   return precision_ == FLD_PREC_MIXED ? solve_t<float>(E_old, E_new, rtol, max_cycles, nu1, nu2, fmg_start, st, s)
                                       : solve_t<double>(E_old, E_new, rtol, max_cycles, nu1, nu2, fmg_start, st, s);
 }

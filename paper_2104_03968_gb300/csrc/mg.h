@@ -40,6 +40,7 @@ struct SolveStats {
   int cycles = 0;
   double relres = 0.0;
   int status = FLD_OK;
+  int nu1 = 0, nu2 = 0;
 };
 
 // Operator A = I + dt * (-div D grad) on one grid, solved by an outer FP64 defect-correction
@@ -59,7 +60,9 @@ class Multigrid {
   cudaError_t setup(double dt, const double* const D_cell[3], const double* E_old, double rtol, unsigned* status,
                     cudaStream_t s);
   // Outer iterations until ||b - A x||/||b|| <= rtol or max_cycles cycles; writes E_new.  With
-  // fmg_start the first cycle is a full-multigrid cycle, the others V-cycles.
+  // fmg_start the first cycle is a full-multigrid cycle, the others V-cycles.  nu1 = nu2 = 0: the
+  // sweep counts are autotuned on the first solve of this configuration (per rtol and start; the
+  // candidates run on a scratch iterate, the fastest converged pair is kept).
   cudaError_t solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                     bool fmg_start, SolveStats* st, cudaStream_t s);
 
@@ -80,8 +83,14 @@ class Multigrid {
   template <class T>
   cudaError_t fmg(int nu1, int nu2, double* x64, cudaStream_t s);
 
+  cudaError_t autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int* nu1, int* nu2,
+                       cudaStream_t s);
+
   GridDev g_{};
   int precision_ = -1;
+  std::vector<std::array<double, 4>> tuned_;  // (rtol, fmg_start, nu1, nu2)
+  double* tune_x_ = nullptr;                  // scratch iterate of the autotuning solves
+  size_t tune_cap_ = 0;
   bool configured_ = false;
   std::vector<std::array<int, 3>> dims_;
   DeviceArena arena_;
