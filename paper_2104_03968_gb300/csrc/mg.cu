@@ -528,8 +528,15 @@ __global__ void __launch_bounds__(kWaveThreads, 4) k_wave_sweep(LevelDev<T> L, c
 static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 Multigrid::~Multigrid() {
+  drop_graphs();
+  if (cap_stream_) cudaStreamDestroy(cap_stream_);
   if (host_scal_) cudaFreeHost(host_scal_);
   if (tune_x_) cudaFree(tune_x_);
+}
+
+void Multigrid::drop_graphs() {
+  for (auto& g : graphs_) cudaGraphExecDestroy(g.exec);
+  graphs_.clear();
 }
 
 static inline long long cells3(const std::array<int, 3>& n) { return (long long)n[0] * n[1] * n[2]; }
@@ -647,6 +654,7 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   if (same) return cudaSuccess;
   configured_ = false;
   tuned_.clear();
+  drop_graphs();
   precision_ = precision;
   dims_.clear();
   std::array<int, 3> d = {g.n[0], g.n[1], g.n[2]};
@@ -812,6 +820,49 @@ bool Multigrid::rows_ok(int l) const {
 
 template <class T>
 cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s, bool zero_init) {
+  // graphs: the levels without a wavefront sweep, below the finest, when no FP64 iterate is
+  // updated and the per-launch trace is off (its events are host-side bookkeeping)
+  const bool graph = graphs_ok_ && !capturing_ && l > 0 && wave_[l].order == nullptr && x64 == nullptr &&
+                     !(tracer().on && !tracer().major_only);
+  if (graph) {
+    cudaError_t e = vcycle_graph<T>(l, nu1, nu2, s, zero_init);
+    if (e == cudaSuccess) return e;
+    cudaGetLastError();  // capture unavailable here: run the launches directly from now on
+    graphs_ok_ = false;
+  }
+  return vcycle_direct<T>(l, nu1, nu2, x64, s, zero_init);
+}
+
+template <class T>
+cudaError_t Multigrid::vcycle_graph(int l, int nu1, int nu2, cudaStream_t s, bool zero_init) {
+  for (const auto& g : graphs_)
+    if (g.l == l && g.nu1 == nu1 && g.nu2 == nu2 && g.zero == (int)zero_init) return cudaGraphLaunch(g.exec, s);
+  cudaError_t e = cudaSuccess;
+  if (!cap_stream_) e = cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  // the captured work reads what earlier launches on s wrote: capture is only recording, the
+  // replay below is ordered on s
+  e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  capturing_ = true;
+  cudaError_t ec = vcycle_direct<T>(l, nu1, nu2, nullptr, cap_stream_, zero_init);
+  capturing_ = false;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cap_stream_, &graph);
+  if (ec != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return ec != cudaSuccess ? ec : e;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  graphs_.push_back({l, nu1, nu2, (int)zero_init, exec});
+  return cudaGraphLaunch(exec, s);
+}
+
+template <class T>
+cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaStream_t s, bool zero_init) {
   const std::array<int, 3>& n = dims_[l];
   long long ncell = cells3(n);
   LevelDev<T> L = level_dev<T>(g_, n, lv_[l].w);

@@ -81,6 +81,13 @@ class Multigrid {
   template <class T>
   cudaError_t vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t s, bool zero_init);
   template <class T>
+  cudaError_t vcycle_direct(int l, int nu1, int nu2, double* x64, cudaStream_t s, bool zero_init);
+  // V-cycles of the levels below the wavefront ones replay as CUDA graphs (captured once per
+  // (level, nu1, nu2, zero start) on a private stream): they are many small launches
+  template <class T>
+  cudaError_t vcycle_graph(int l, int nu1, int nu2, cudaStream_t s, bool zero_init);
+  void drop_graphs();
+  template <class T>
   cudaError_t fmg(int nu1, int nu2, double* x64, cudaStream_t s);
 
   cudaError_t autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int* nu1, int* nu2,
@@ -89,6 +96,14 @@ class Multigrid {
   GridDev g_{};
   int precision_ = -1;
   std::vector<std::array<double, 4>> tuned_;  // (rtol, fmg_start, nu1, nu2)
+  struct GraphEntry {
+    int l, nu1, nu2, zero;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs_;
+  cudaStream_t cap_stream_ = nullptr;
+  bool capturing_ = false;
+  bool graphs_ok_ = true;
   double* tune_x_ = nullptr;                  // scratch iterate of the autotuning solves
   size_t tune_cap_ = 0;
   bool configured_ = false;
