@@ -12,6 +12,7 @@
 // back to bisection after `maxit` iterations.
 #pragma once
 
+#include "df.cuh"
 #include "fld_common.cuh"
 
 namespace fld {
@@ -54,6 +55,19 @@ __device__ inline double halley64(double a, double cc, int maxit, int* iters, in
 }
 
 // Updates (e, E) of one cell in place.  Returns false (and leaves them) on invalid input.
+// two FP64 Newton steps from the FP32 root (tiny or huge coefficients); d: the last step
+static __device__ __noinline__ double polish64(double a, double cc, float y32, float r1f, float* d) {
+  const double r1 = (double)r1f;
+  double y = (double)y32, dd = 0.0;
+  for (int it = 0; it < 2; ++it) {
+    const double y2 = y * y;
+    dd = fma(a * y2, y2, y - cc) * r1;
+    y -= dd;
+  }
+  *d = (float)dd;
+  return y;
+}
+
 __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k, double& e, double& E, int& iters,
                                      int& bis) {
   const double e0 = e, E0 = E;
@@ -108,21 +122,34 @@ __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k
       if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
       z = zn;
     }
-    // FP64 Newton polish with the FP64 residual and the FP32 root's reciprocal slope
-    // 1/f'(y) = 1/(4 a y^3 + 1): each step multiplies the error by about 1e-7, so two steps take
-    // the FP32 root (~1e-7) below FP64 rounding.
+    // Newton polish of the FP32 root, two steps with the FP32 root's reciprocal slope
+    // 1/f'(y) = 1/(4 a y^3 + 1) as the step factor (each step multiplies the error by ~1e-7, so two
+    // take the FP32 root to the rounding of the arithmetic): in double-float arithmetic (df.cuh)
+    // while a, cc and y keep their low parts normal floats, else in FP64 (out of line).
     const float y32 = ys * z;
-    const double r1 = (double)__frcp_rn(fmaf(4.0f * af * y32 * y32, y32, 1.0f));
-    y = (double)y32;
-    double d = 0.0;
+    const float r1 = __frcp_rn(fmaf(4.0f * af * y32 * y32, y32, 1.0f));
+    float d = 0.0f, yh = 0.0f;
+    if (cf >= 0x1p-60f && af <= 0x1p60f) {
+      float ah, al, ch, cl;
+      split_f64(a, ah, al);
+      split_f64(cc, ch, cl);
+      const dfl A{ah, al}, C{-ch, -cl};
+      dfl Y{y32, 0.0f};
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      double y2 = y * y;
-      d = fma(a * y2, y2, y - cc) * r1;
-      y -= d;
+      for (int it = 0; it < 2; ++it) {
+        const dfl Y2 = df_mul(Y, Y);
+        const dfl F = df_add(df_add(df_mul(A, df_mul(Y2, Y2)), Y), C);
+        d = F.hi * r1;
+        Y = df_add(Y, {-d, 0.0f});
+      }
+      y = (double)Y.hi + (double)Y.lo;
+      yh = Y.hi;
+    } else {
+      y = polish64(a, cc, y32, r1, &d);
+      yh = (float)y;
     }
     iters += 2;
-    if (!(fabsf((float)d) <= 1e-12f * (float)y) || !(y > 0.0)) {
+    if (!(fabsf(d) <= 1e-12f * yh) || !(yh > 0.0f)) {
       int it2 = 0;
       y = halley64(a, cc, p.maxit, &it2, &bis);
       iters += it2;
