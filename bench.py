@@ -210,7 +210,7 @@ def workload_config(args, nu=None):
            "multigrid": "FMG first cycle, V-cycles after; red-black Gauss-Seidel sweep counts autotuned",
            "l2_flush": "inputs larger than L2 (1 GiB per field)", "parallelism": "replicas"}
     if nu is not None:
-        cfg["nu1"], cfg["nu2"] = nu
+        cfg["nu1"], cfg["nu2"], cfg["nu1_coarse"], cfg["nu2_coarse"] = nu
     return cfg
 
 
@@ -388,7 +388,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64+f32 (FP32 V-cycles, FP64 residual/update/norm/exchange)" if args.precision == "mixed"
                 else "f64",
-                "data": "synthetic", "config": workload_config(args, (infos[0]["nu1"], infos[0]["nu2"])), "roofline": roof,
+                "data": "synthetic", "config": workload_config(args, (infos[0]["nu1"], infos[0]["nu2"], infos[0]["nu1_coarse"],
+                                                                 infos[0]["nu2_coarse"])), "roofline": roof,
                 "roofline_hbm": roof_hbm, "cpu_baseline": cpu,
                 "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in sorted(rep.items(), key=lambda kv: -kv[1][1])},

@@ -126,8 +126,9 @@ typedef struct {
   int max_cycles;  /* outer iterations (one V-cycle each); 0 = 100 */
   int nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after coarse correction.  Both 0:
                       autotuned on the first solve of a grid configuration (per rtol and start:
-                      candidate pairs are timed on a scratch iterate, the fastest converged pair
-                      is kept for later calls); one 0: that one is 2 */
+                      candidate sets -- a pair for the finest level, a pair for the coarser
+                      ones -- are timed on a scratch iterate, the fastest converged set is kept
+                      for later calls); otherwise every level uses them (0 = 2) */
   int exch_maxit;  /* Halley iterations before bisection in the exchange; 0 = 100 */
   int order;       /* FLD_ORDER_* used by fld_step */
   int start;       /* FLD_START_*: first cycle of fld_diffuse / fld_step (fld_step_batched always
@@ -141,7 +142,8 @@ typedef struct {
   int exch_max_iters;      /* largest number of root iterations over the cells */
   int bisection_fallbacks; /* cells that fell back to bisection */
   int status;              /* fld_status of this grid / column set */
-  int nu1, nu2;            /* sweep counts the multigrid solve used (after autotuning) */
+  int nu1, nu2;            /* sweep counts the multigrid solve used on the finest level */
+  int nu1_coarse, nu2_coarse; /* and on the coarser levels (differ only when autotuned) */
 } fld_info;
 
 typedef struct fld_ctx fld_ctx;

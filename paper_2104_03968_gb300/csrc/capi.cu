@@ -321,6 +321,8 @@ fld_status diffuse_common(fld_ctx* ctx, const fld_grid* grid, const fld_params* 
     info->status = ss.status;
     info->nu1 = ss.nu1;
     info->nu2 = ss.nu2;
+    info->nu1_coarse = ss.nu1_coarse;
+    info->nu2_coarse = ss.nu2_coarse;
   }
   if (ss.status != FLD_OK)
     return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
@@ -462,6 +464,8 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
   inf->status = ss.status;
   inf->nu1 = ss.nu1;
   inf->nu2 = ss.nu2;
+  inf->nu1_coarse = ss.nu1_coarse;
+  inf->nu2_coarse = ss.nu2_coarse;
   if (sbits & kStatNonpositive) {
     inf->status = FLD_ERR_NONPOSITIVE;
     return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state");

@@ -350,10 +350,22 @@ __global__ void k_prolong(std::array<int, 3> nf, int ndim, const T* __restrict__
   prolong_cell<T>(nf.data(), ndim, xc, nc.data(), xf, idx);
 }
 
+// The coarsest level, one block.  With in_smem the iterate (and the Jacobi scratch) live in shared
+// memory: the sweeps are a chain of block barriers, and each round trip through global memory
+// would otherwise set their pace.
 template <class T>
-__global__ void __launch_bounds__(512) k_coarse_solve(LevelDev<T> L, long long ncell, const T* __restrict__ invd, const T* __restrict__ r,
-                               T* __restrict__ x, T* __restrict__ tmp, int sweeps, int use_rb) {
-  coarse_solve_block<T>(L, ncell, invd, r, x, tmp, sweeps, use_rb);
+__global__ void __launch_bounds__(512) k_coarse_solve(LevelDev<T> L, long long ncell, const T* __restrict__ invd,
+                                                      const T* __restrict__ r, T* __restrict__ x, T* __restrict__ tmp,
+                                                      int sweeps, int use_rb, int in_smem) {
+  extern __shared__ __align__(16) unsigned char coarse_smem[];
+  if (in_smem) {
+    T* xs = reinterpret_cast<T*>(coarse_smem);
+    coarse_solve_block<T>(L, ncell, invd, r, xs, xs + ncell, sweeps, use_rb);
+    __syncthreads();
+    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) x[c] = xs[c];
+  } else {
+    coarse_solve_block<T>(L, ncell, invd, r, x, tmp, sweeps, use_rb);
+  }
 }
 
 
@@ -875,7 +887,10 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
       if ((n[a] & 1) && (g_.bc[2 * a] == FLD_BC_PERIODIC)) rb = false;
     int sweeps = rb ? 40 : 80;
     TraceScope ts("coarse_solve", s);
-    k_coarse_solve<T><<<1, 512, 0, s>>>(L, ncell, invd, r, x, (T*)lv_[l].tmp, sweeps, rb ? 1 : 0);
+    const size_t smem = 2 * (size_t)ncell * sizeof(T);
+    const int in_smem = smem <= 48 * 1024 ? 1 : 0;
+    k_coarse_solve<T><<<1, 512, in_smem ? smem : 0, s>>>(L, ncell, invd, r, x, (T*)lv_[l].tmp, sweeps, rb ? 1 : 0,
+                                                         in_smem);
     if (x64) k_add_correction<T><<<nblk(ncell), kBlock, 0, s>>>(ncell, x, x64);
     return cudaGetLastError();
   }
@@ -912,7 +927,7 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
       k_residual_restrict<T><<<nblk(cells3(nc)), kBlock, 0, s>>>(L, r, x, nc, (T*)lv_[l + 1].r, nullptr);
     }
   }
-  cudaError_t e = vcycle<T>(l + 1, nu1, nu2, nullptr, s, true);
+  cudaError_t e = vcycle<T>(l + 1, nuc1_, nuc2_, nullptr, s, true);  // coarser levels: their own counts
   if (e != cudaSuccess) return e;
   {
     TraceScope ts(l == 0 ? "prolong_L0" : "prolong_Lc", s);
@@ -959,13 +974,14 @@ template <class T>
 cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
   const int top = (int)dims_.size() - 1;
   if (top == 0) return vcycle<T>(0, nu1, nu2, x64, s, true);
+  // nu1, nu2: the finest level's counts; the coarser levels use nuc1_, nuc2_
   {
     TraceScope ts("fmg_restrict", s);
     for (int l = 0; l < top; ++l)
       k_restrict_avg<T><<<nblk(cells3(dims_[l + 1])), kBlock, 0, s>>>(dims_[l], g_.ndim, (const T*)lv_[l].r,
                                                                      dims_[l + 1], (T*)lv_[l + 1].r);
   }
-  cudaError_t e = vcycle<T>(top, nu1, nu2, nullptr, s, true);
+  cudaError_t e = vcycle<T>(top, nuc1_, nuc2_, nullptr, s, true);
   if (e != cudaSuccess) return e;
   for (int l = top - 1; l >= 0; --l) {
     const std::array<int, 3>& n = dims_[l];
@@ -977,7 +993,7 @@ cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
       if (e != cudaSuccess) return e;
       k_prolong<T><<<nblk(cells3(n)), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
     }
-    e = vcycle<T>(l, nu1, nu2, l == 0 ? x64 : nullptr, s, false);
+    e = vcycle<T>(l, l == 0 ? nu1 : nuc1_, l == 0 ? nu2 : nuc2_, l == 0 ? x64 : nullptr, s, false);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
@@ -1138,12 +1154,11 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
   return cudaStreamSynchronize(s);
 }
 
-cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int* nu1, int* nu2,
+cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int nu[4],
                                 cudaStream_t s) {
   for (const auto& t : tuned_)
     if (t[0] == rtol && t[1] == (fmg_start ? 1.0 : 0.0)) {
-      *nu1 = (int)t[2];
-      *nu2 = (int)t[3];
+      for (int k = 0; k < 4; ++k) nu[k] = (int)t[2 + k];
       return cudaSuccess;
     }
   const size_t n = (size_t)g_.ncell;
@@ -1155,14 +1170,19 @@ cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles
     if (e != cudaSuccess) return e;
     tune_cap_ = n;
   }
-  static const int cand[][2] = {{2, 2}, {3, 3}, {2, 1}, {4, 2}, {4, 4}, {5, 3}, {3, 2}, {1, 1}};
+  // (finest pre, finest post, coarser pre, coarser post)
+  static const int cand[][4] = {{2, 2, 2, 2}, {3, 3, 3, 3}, {4, 4, 2, 1}, {5, 3, 2, 1}, {4, 4, 2, 2}, {3, 3, 2, 1},
+                                {4, 2, 2, 1}, {6, 4, 2, 1}, {2, 1, 2, 1}, {1, 1, 1, 1}};
   cudaEvent_t a, b;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   if (e != cudaSuccess) return e;
-  int best1 = 2, best2 = 2;
+  int best_k = 0;
   float best = 1e30f;
-  for (const auto& c : cand) {
+  for (int k = 0; k < (int)(sizeof(cand) / sizeof(cand[0])); ++k) {
+    const int* c = cand[k];
+    nuc1_ = c[2];
+    nuc2_ = c[3];
     SolveStats cs;
     e = cudaEventRecord(a, s);
     if (e == cudaSuccess)
@@ -1176,31 +1196,33 @@ cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles
     if (e != cudaSuccess) break;
     if (cs.status == FLD_OK && ms < best) {
       best = ms;
-      best1 = c[0];
-      best2 = c[1];
+      best_k = k;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e != cudaSuccess) return e;
-  tuned_.push_back({rtol, fmg_start ? 1.0 : 0.0, (double)best1, (double)best2});
-  *nu1 = best1;
-  *nu2 = best2;
+  const int* c = cand[best_k];
+  tuned_.push_back({rtol, fmg_start ? 1.0 : 0.0, (double)c[0], (double)c[1], (double)c[2], (double)c[3]});
+  for (int k = 0; k < 4; ++k) nu[k] = c[k];
   return cudaSuccess;
 }
 
 cudaError_t Multigrid::solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                              bool fmg_start, SolveStats* st, cudaStream_t s) {
+  int nu[4] = {nu1 ? nu1 : 2, nu2 ? nu2 : 2, nu1 ? nu1 : 2, nu2 ? nu2 : 2};
   if (nu1 == 0 && nu2 == 0) {
-    cudaError_t e = autotune(E_old, rtol, max_cycles, fmg_start, &nu1, &nu2, s);
+    cudaError_t e = autotune(E_old, rtol, max_cycles, fmg_start, nu, s);
     if (e != cudaSuccess) return e;
   }
-  if (nu1 == 0) nu1 = 2;
-  if (nu2 == 0) nu2 = 2;
-  st->nu1 = nu1;
-  st->nu2 = nu2;
-  return precision_ == FLD_PREC_MIXED ? solve_t<float>(E_old, E_new, rtol, max_cycles, nu1, nu2, fmg_start, st, s)
-                                      : solve_t<double>(E_old, E_new, rtol, max_cycles, nu1, nu2, fmg_start, st, s);
+  nuc1_ = nu[2];
+  nuc2_ = nu[3];
+  st->nu1 = nu[0];
+  st->nu2 = nu[1];
+  st->nu1_coarse = nu[2];
+  st->nu2_coarse = nu[3];
+  return precision_ == FLD_PREC_MIXED ? solve_t<float>(E_old, E_new, rtol, max_cycles, nu[0], nu[1], fmg_start, st, s)
+                                      : solve_t<double>(E_old, E_new, rtol, max_cycles, nu[0], nu[1], fmg_start, st, s);
 }
 
 }  // namespace fld

@@ -40,7 +40,7 @@ struct SolveStats {
   int cycles = 0;
   double relres = 0.0;
   int status = FLD_OK;
-  int nu1 = 0, nu2 = 0;
+  int nu1 = 0, nu2 = 0, nu1_coarse = 0, nu2_coarse = 0;
 };
 
 // Operator A = I + dt * (-div D grad) on one grid, solved by an outer FP64 defect-correction
@@ -61,8 +61,9 @@ class Multigrid {
                     cudaStream_t s);
   // Outer iterations until ||b - A x||/||b|| <= rtol or max_cycles cycles; writes E_new.  With
   // fmg_start the first cycle is a full-multigrid cycle, the others V-cycles.  nu1 = nu2 = 0: the
-  // sweep counts are autotuned on the first solve of this configuration (per rtol and start; the
-  // candidates run on a scratch iterate, the fastest converged pair is kept).
+  // sweep counts -- one pair for the finest level, one for the coarser levels -- are autotuned on
+  // the first solve of this configuration (per rtol and start; the candidates run on a scratch
+  // iterate, the fastest converged set is kept); otherwise every level uses (nu1, nu2).
   cudaError_t solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                     bool fmg_start, SolveStats* st, cudaStream_t s);
 
@@ -90,12 +91,13 @@ class Multigrid {
   template <class T>
   cudaError_t fmg(int nu1, int nu2, double* x64, cudaStream_t s);
 
-  cudaError_t autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int* nu1, int* nu2,
-                       cudaStream_t s);
+  // nu = (finest pre, finest post, coarser pre, coarser post)
+  cudaError_t autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int nu[4], cudaStream_t s);
 
   GridDev g_{};
   int precision_ = -1;
-  std::vector<std::array<double, 4>> tuned_;  // (rtol, fmg_start, nu1, nu2)
+  std::vector<std::array<double, 6>> tuned_;  // (rtol, fmg_start, nu1, nu2, coarser nu1, nu2)
+  int nuc1_ = 2, nuc2_ = 2;                   // sweep counts of the levels below the finest
   struct GraphEntry {
     int l, nu1, nu2, zero;
     cudaGraphExec_t exec;

@@ -60,7 +60,8 @@ class Params(ct.Structure):
 
 class Info(ct.Structure):
     _fields_ = [("cycles", ct.c_int), ("rel_residual", ct.c_double), ("exch_max_iters", ct.c_int),
-                ("bisection_fallbacks", ct.c_int), ("status", ct.c_int), ("nu1", ct.c_int), ("nu2", ct.c_int)]
+                ("bisection_fallbacks", ct.c_int), ("status", ct.c_int), ("nu1", ct.c_int), ("nu2", ct.c_int),
+                ("nu1_coarse", ct.c_int), ("nu2_coarse", ct.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
