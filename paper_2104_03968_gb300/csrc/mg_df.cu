@@ -8,6 +8,8 @@
 // the weight is scaled back.  A cell whose values leave the window where the double-float parts
 // stay normal floats (|value| outside [2^-77, 2^90)) sets a flag; the solver then redoes the
 // setup in FP64.
+#include <algorithm>
+
 #include "df.cuh"
 #include "kernels.h"
 #include "mg_df.h"
@@ -58,37 +60,69 @@ __device__ __forceinline__ dfl face_weight_df(double Dc, double Dn, bool pair, d
 
 }  // namespace
 
-__global__ void k_faces_df(GridDev g, DfConst K, const double* __restrict__ D, float* __restrict__ w0,
-                           float* __restrict__ w1, float* __restrict__ w2, float* __restrict__ l0,
-                           float* __restrict__ l1, float* __restrict__ l2, unsigned* __restrict__ flag) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.ncell) return;
-  int q[3];
-  unflatten(g.n, idx, q[0], q[1], q[2]);
-  float* W[3] = {w0, w1, w2};
-  float* Lo[3] = {l0, l1, l2};
-  const double Dc = D[idx];
+// Whole x rows per block iteration, 32-bit indices (the caller guarantees < 2^31 cells and faces
+// per axis).
+__global__ void __launch_bounds__(256) k_faces_df(GridDev g, DfConst K, const double* __restrict__ D,
+                                                  float* __restrict__ w0, float* __restrict__ w1,
+                                                  float* __restrict__ w2, float* __restrict__ l0,
+                                                  float* __restrict__ l1, float* __restrict__ l2,
+                                                  unsigned* __restrict__ flag) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int rows = ny * nz;
+  const bool per[3] = {g.bc[0] == FLD_BC_PERIODIC, g.bc[2] == FLD_BC_PERIODIC, g.bc[4] == FLD_BC_PERIODIC};
+  const bool perh[3] = {g.bc[1] == FLD_BC_PERIODIC, g.bc[3] == FLD_BC_PERIODIC, g.bc[5] == FLD_BC_PERIODIC};
   unsigned bad = 0u;
-  long long stride = 1;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a >= g.ndim) break;
-    const int p = q[a];
-    const dfl s{K.s_hi[a], K.s_lo[a]};
-    const bool pair = p > 0 || g.bc[2 * a] == FLD_BC_PERIODIC;
-    const double Dn = pair ? D[p > 0 ? idx - stride : idx + (long long)(g.n[a] - 1) * stride] : Dc;
-    const dfl w = face_weight_df(Dc, Dn, pair, s, bad);
-    const long long f = face_index(g.n, a, q[0], q[1], q[2], p);
-    W[a][f] = w.hi;
-    Lo[a][f] = w.lo;
-    const bool periodic = g.bc[2 * a + 1] == FLD_BC_PERIODIC;
-    if ((periodic && p == 0) || (!periodic && p == g.n[a] - 1)) {
-      const dfl wu = periodic ? w : face_weight_df(Dc, Dc, false, s, bad);
-      const long long fu = face_index(g.n, a, q[0], q[1], q[2], g.n[a]);
-      W[a][fu] = wu.hi;
-      Lo[a][fu] = wu.lo;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % ny, k = row / ny;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const int idx = i + nx * row;
+      const double Dc = D[idx];
+      // x faces: lower face i of row (j, k), and face nx when this cell owns it
+      {
+        const dfl s{K.s_hi[0], K.s_lo[0]};
+        const bool pair = i > 0 || per[0];
+        const double Dn = pair ? D[i > 0 ? idx - 1 : idx + (nx - 1)] : Dc;
+        const dfl w = face_weight_df(Dc, Dn, pair, s, bad);
+        const int f = i + (nx + 1) * row;
+        w0[f] = w.hi;
+        l0[f] = w.lo;
+        if ((perh[0] && i == 0) || (!perh[0] && i == nx - 1)) {
+          const dfl wu = perh[0] ? w : face_weight_df(Dc, Dc, false, s, bad);
+          w0[f - i + nx] = wu.hi;
+          l0[f - i + nx] = wu.lo;
+        }
+      }
+      if (g.ndim >= 2) {
+        const dfl s{K.s_hi[1], K.s_lo[1]};
+        const bool pair = j > 0 || per[1];
+        const double Dn = pair ? D[j > 0 ? idx - nx : idx + (ny - 1) * nx] : Dc;
+        const dfl w = face_weight_df(Dc, Dn, pair, s, bad);
+        const int f = i + nx * (j + (ny + 1) * k);
+        w1[f] = w.hi;
+        l1[f] = w.lo;
+        if ((perh[1] && j == 0) || (!perh[1] && j == ny - 1)) {
+          const dfl wu = perh[1] ? w : face_weight_df(Dc, Dc, false, s, bad);
+          const int fu = i + nx * (ny + (ny + 1) * k);
+          w1[fu] = wu.hi;
+          l1[fu] = wu.lo;
+        }
+      }
+      if (g.ndim == 3) {
+        const int sz = nx * ny;
+        const dfl s{K.s_hi[2], K.s_lo[2]};
+        const bool pair = k > 0 || per[2];
+        const double Dn = pair ? D[k > 0 ? idx - sz : idx + (nz - 1) * sz] : Dc;
+        const dfl w = face_weight_df(Dc, Dn, pair, s, bad);
+        w2[idx] = w.hi;
+        l2[idx] = w.lo;
+        if ((perh[2] && k == 0) || (!perh[2] && k == nz - 1)) {
+          const dfl wu = perh[2] ? w : face_weight_df(Dc, Dc, false, s, bad);
+          const int fu = i + nx * (j + ny * nz);
+          w2[fu] = wu.hi;
+          l2[fu] = wu.lo;
+        }
+      }
     }
-    stride *= g.n[a];
   }
   if (bad) atomicOr(flag, 1u);
 }
@@ -270,8 +304,8 @@ DfConst make_df_const(const GridDev& g, double dt) {
 cudaError_t launch_faces_df(const GridDev& g, const DfConst& K, const double* D, float* const w[3],
                             float* const wlo[3], unsigned* flag, cudaStream_t s) {
   TraceScope ts("faces", s);
-  k_faces_df<<<(unsigned)((g.ncell + kBlock - 1) / kBlock), kBlock, 0, s>>>(g, K, D, w[0], w[1], w[2], wlo[0], wlo[1],
-                                                                            wlo[2], flag);
+  const int rows = g.n[1] * g.n[2];
+  k_faces_df<<<(unsigned)std::min(rows, 152 * 16), 256, 0, s>>>(g, K, D, w[0], w[1], w[2], wlo[0], wlo[1], wlo[2], flag);
   return cudaGetLastError();
 }
 
