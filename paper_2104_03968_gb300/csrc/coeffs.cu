@@ -11,13 +11,13 @@
 
 namespace fld {
 
-__global__ void k_coeffs(GridDev g, CoeffPhys ph, const double* __restrict__ E, const double* __restrict__ rho,
-                         const double* __restrict__ eps, double* __restrict__ kappa_out, double* __restrict__ D_out,
-                         unsigned* __restrict__ status) {
+__global__ void k_coeffs(GridDev g, CoeffPhys ph, CoeffDf K, const double* __restrict__ E,
+                         const double* __restrict__ rho, const double* __restrict__ eps,
+                         double* __restrict__ kappa_out, double* __restrict__ D_out, unsigned* __restrict__ status) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.ncell) return;
   double kap, D;
-  if (!coeffs_cell(g, ph, E, rho, eps, idx, kap, D)) atomicOr(status, kStatNonpositive);
+  if (!coeffs_cell_fast(g, ph, K, E, rho, eps, idx, kap, D)) atomicOr(status, kStatNonpositive);
   if (kappa_out) kappa_out[idx] = kap;
   D_out[idx] = D;
 }
@@ -43,7 +43,8 @@ cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double 
   if (g.ncell == 0) return cudaSuccess;
   TraceScope ts("coeffs", s);
   CoeffPhys ph{op, c, gamma, gas_R, limiter};
-  k_coeffs<<<blocks_for(g.ncell), kBlock, 0, s>>>(g, ph, E, rho, eps, kappa_out, D_out, status);
+  k_coeffs<<<blocks_for(g.ncell), kBlock, 0, s>>>(g, ph, make_coeff_df(ph, g), E, rho, eps, kappa_out, D_out,
+                                                   status);
   return cudaGetLastError();
 }
 

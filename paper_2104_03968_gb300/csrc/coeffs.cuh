@@ -2,6 +2,8 @@
 // 2104.03968: Sect. 2.2 Eqs. fld_lambda and fld_F; Sect. 3.2 Eq. ileyk_flux; Sect. 3.4 faces).
 #pragma once
 
+#include <cmath>
+
 #include "df.cuh"
 #include "fld_common.cuh"
 
@@ -47,7 +49,29 @@ __device__ __forceinline__ double sample_E(const double* __restrict__ E, const G
   return e0 + d * (e0 - e1);
 }
 
-// Opacity and cell-centred D of one cell: kappa(rho, T), the 5-point gradient of E, R,
+// The two FP64 differences of the 5-point stencil of Eq. ileyk_flux along axis a at cell (i,j,k):
+// d1 = E[p-2] - E[p+2] and d2 = E[p+1] - E[p-1], so that dE/dx = (d1 + 8 d2) / (12 dx).
+__device__ __forceinline__ void grad_diffs(const GridDev& g, const double* __restrict__ E, long long idx, int i, int j,
+                                           int k, int a, double& d1, double& d2) {
+  const int p = a == 0 ? i : (a == 1 ? j : k);
+  double em2, em1, ep1, ep2;
+  if (p >= 2 && p < g.n[a] - 2) {
+    const long long s = a == 0 ? 1 : (a == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
+    em2 = __ldg(E + idx - 2 * s);
+    em1 = __ldg(E + idx - s);
+    ep1 = __ldg(E + idx + s);
+    ep2 = __ldg(E + idx + 2 * s);
+  } else {
+    em2 = sample_E(E, g, i, j, k, a, p - 2);
+    em1 = sample_E(E, g, i, j, k, a, p - 1);
+    ep1 = sample_E(E, g, i, j, k, a, p + 1);
+    ep2 = sample_E(E, g, i, j, k, a, p + 2);
+  }
+  d1 = em2 - ep2;
+  d2 = ep1 - em1;
+}
+
+// Opacity and cell-centred D of one cell in FP64: kappa(rho, T), the 5-point gradient of E, R,
 // lambda(R) and D = c lambda/(kappa rho).  Returns false (D = 0) for rho, kappa, E <= 0 or eps < 0.
 __device__ __forceinline__ bool coeffs_cell(const GridDev& g, const CoeffPhys& ph, const double* __restrict__ E,
                                             const double* __restrict__ rho, const double* __restrict__ eps,
@@ -72,32 +96,161 @@ __device__ __forceinline__ bool coeffs_cell(const GridDev& g, const CoeffPhys& p
     return false;
   }
   double g2 = 0.0;
-  int q[3] = {i, j, k};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a >= g.ndim) break;
-    int p = q[a];
-    double em2, em1, ep1, ep2;
-    if (p >= 2 && p < g.n[a] - 2) {
-      long long s = a == 0 ? 1 : (a == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
-      em2 = __ldg(E + idx - 2 * s);
-      em1 = __ldg(E + idx - s);
-      ep1 = __ldg(E + idx + s);
-      ep2 = __ldg(E + idx + 2 * s);
-    } else {
-      em2 = sample_E(E, g, i, j, k, a, p - 2);
-      em1 = sample_E(E, g, i, j, k, a, p - 1);
-      ep1 = sample_E(E, g, i, j, k, a, p + 1);
-      ep2 = sample_E(E, g, i, j, k, a, p + 2);
-    }
+    double d1, d2;
+    grad_diffs(g, E, idx, i, j, k, a, d1, d2);
     // 5-point 4th-order central difference (the 1/dx factor is applied with g2 below)
-    double d = (em2 - ep2) * (1.0 / 12.0) + (ep1 - em1) * (2.0 / 3.0);
+    double d = d1 * (1.0 / 12.0) + d2 * (2.0 / 3.0);
     g2 = fma(d * d, g.inv_dx2[a], g2);
   }
   const double q_ = kap * rh;  // kappa rho, the inverse mean free path
   const double D = limited_D(ph.limiter, ph.c, q_, e, g2, ph.limiter == FLD_LIMITER_THIRD ? 0.0 : sqrt_nr(g2));
   D_out = D;
   return true;
+}
+
+static __device__ __noinline__ bool coeffs_cell_f64(const GridDev& g, const CoeffPhys& ph, const double* E,
+                                                   const double* rho, const double* eps, long long idx, double& kap,
+                                                   double& D) {
+  return coeffs_cell(g, ph, E, rho, eps, idx, kap, D);
+}
+
+// Constants of the double-float coefficient path, split on the host.
+struct CoeffDf {
+  dfl c, gm1, gas_R, kappa0;  // c, gamma - 1, gas_R, kappa0
+  dfl ig[3];                  // 1 / (144 dx_a^2): |grad E|^2 = sum_a (d1 + 8 d2)^2 ig_a
+  int kramers;                // 1: kappa0 rho T^-3.5; 0: constant kappa0
+  int ok;                     // the opacity model is one of the two and every constant is in the window
+};
+
+__host__ inline CoeffDf make_coeff_df(const CoeffPhys& ph, const GridDev& g) {
+  auto split = [](double v) {
+    dfl x;
+    x.hi = (float)v;
+    x.lo = (float)(v - (double)x.hi);
+    return x;
+  };
+  auto in = [](double v) { return v == 0.0 || (std::fabs(v) >= 0x1p-100 && std::fabs(v) < 0x1p125); };
+  CoeffDf K{};
+  K.c = split(ph.c);
+  K.gm1 = split(ph.gamma - 1.0);
+  K.gas_R = split(ph.gas_R);
+  K.kappa0 = split(ph.op.kappa0);
+  K.kramers = ph.op.model == FLD_OPACITY_KRAMERS;
+  bool ok = (ph.op.model == FLD_OPACITY_CONST ||
+             (ph.op.model == FLD_OPACITY_KRAMERS && ph.op.kr_a == 1.0 && ph.op.kr_b == -3.5)) &&
+            ph.c > 0.0 && in(ph.c) && ph.op.kappa0 > 0.0 && in(ph.op.kappa0) &&
+            (ph.op.model == FLD_OPACITY_CONST ||
+             (ph.gamma > 1.0 && in(ph.gamma - 1.0) && ph.gas_R > 0.0 && in(ph.gas_R)));
+  for (int a = 0; a < 3; ++a) {
+    const double v = a < g.ndim ? g.inv_dx2[a] / 144.0 : 0.0;
+    K.ig[a] = split(v);
+    ok = ok && in(v);
+  }
+  K.ok = ok;
+  return K;
+}
+
+// The same cell in double-float arithmetic (df.cuh) on the FP32 pipe, for constant or Kramers
+// (a = 1, b = -3.5) opacity: the FP64 stencil differences are the only FP64 arithmetic besides the
+// two final roundings.  Inputs must already be valid (E, rho, eps > 0).  Every product whose low
+// part could leave the normal floats is checked against the double-float window (df_in); sums of
+// positive terms need no check, since an underflowed term is negligible beside an in-window sum.
+// Returns false, with the outputs unset, when a value leaves the window; the caller then takes the
+// FP64 path.  Relative error a few 2^-47.
+__device__ __forceinline__ bool coeffs_cell_df(const GridDev& g, const CoeffPhys& ph, const CoeffDf& K,
+                                               const double* __restrict__ E, long long idx, int i, int j, int k,
+                                               double e, double rh, double ep, double& kap_out, double& D_out) {
+  bool ok, o2, o3;
+  dfl Ed, R, EP;
+  split_f64_try(e, Ed.hi, Ed.lo, ok);
+  split_f64_try(rh, R.hi, R.lo, o2);
+  split_f64_try(ep, EP.hi, EP.lo, o3);
+  ok = ok && o2 && o3 && df_in(Ed) && df_in(R);
+  dfl kap = K.kappa0;
+  if (K.kramers) {
+    // 1/T = rho gas_R / ((gamma-1) eps); kappa = kappa0 rho (1/T)^3 sqrt(1/T)
+    const dfl den = df_mul(EP, K.gm1);
+    ok = ok && df_in(den);
+    const dfl rg = df_mul(R, K.gas_R);
+    const dfl it = df_div(rg, den);
+    const dfl it3 = df_mul(df_sqr(it), it);  // it^2 lies between it and it^3
+    const dfl kr = df_mul(K.kappa0, R);
+    const dfl krt = df_mul(kr, it3);
+    kap = df_mul(krt, df_sqrt(it));
+    ok = ok && df_in(rg) && df_in(it) && df_in(it3) && df_in(kr) && df_in(krt);
+  }
+  const dfl q = df_mul(kap, R);  // kappa rho
+  ok = ok && df_in(kap) && df_in(q);
+  dfl g2{0.0f, 0.0f};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.ndim) break;
+    double d1, d2;
+    grad_diffs(g, E, idx, i, j, k, a, d1, d2);
+    dfl A, B;
+    split_f64_try(d1, A.hi, A.lo, o2);
+    split_f64_try(d2, B.hi, B.lo, o3);
+    const dfl d = df_add(A, df_scale(B, 8.0f));  // 12 dx dE/dx
+    ok = ok && o2 && o3 && (d.hi == 0.0f || df_in(d));
+    g2 = df_add_pos(g2, df_mul(df_sqr(d), K.ig[a]));
+  }
+  ok = ok && (g2.hi == 0.0f || df_in(g2));
+  const dfl qe = df_mul(q, Ed);
+  ok = ok && df_in(qe);
+  dfl D;
+  if (ph.limiter == FLD_LIMITER_THIRD) {
+    D = df_div(K.c, df_mul_f(q, 3.0f));
+  } else {
+    const dfl gm = g2.hi == 0.0f ? dfl{0.0f, 0.0f} : df_sqrt(g2);
+    const dfl ce = df_mul(K.c, Ed);
+    ok = ok && df_in(ce);
+    if (ph.limiter == FLD_LIMITER_MINERBO) {
+      if (gm.hi <= 1.5f * qe.hi) {
+        // 2 c E / (3 qE + sqrt(9 (qE)^2 + 12 g^2))
+        const dfl t = df_add_pos(df_mul_f(df_sqr(qe), 9.0f), df_mul_f(g2, 12.0f));
+        ok = ok && df_in(t);
+        const dfl s = df_sqrt(t);
+        D = df_div(df_scale(ce, 2.0f), df_add_pos(df_mul_f(qe, 3.0f), s));
+      } else {
+        // c E / (qE + g + sqrt(qE (qE + 2 g)))
+        const dfl t = df_mul(qe, df_add_pos(qe, df_scale(gm, 2.0f)));
+        ok = ok && df_in(t);
+        const dfl s = df_sqrt(t);
+        D = df_div(ce, df_add_pos(df_add_pos(qe, gm), s));
+      }
+    } else {
+      // Levermore-Pomraning: c E (2 qE + g) / (qE (6 qE + 3 g) + g^2)
+      const dfl num = df_mul(ce, df_add_pos(df_scale(qe, 2.0f), gm));
+      const dfl den = df_add_pos(df_mul(qe, df_add_pos(df_mul_f(qe, 6.0f), df_mul_f(gm, 3.0f))), g2);
+      ok = ok && df_in(num) && df_in(den);
+      D = df_div(num, den);
+    }
+  }
+  ok = ok && df_in(D);
+  if (!ok) return false;
+  kap_out = df_to_f64(kap);
+  D_out = df_to_f64(D);
+  return true;
+}
+
+// Either path for one cell: the double-float one when its constants allow, else (or when a value
+// leaves its window) FP64.  Returns false (D = 0) for invalid input, as coeffs_cell.
+__device__ __forceinline__ bool coeffs_cell_fast(const GridDev& g, const CoeffPhys& ph, const CoeffDf& K,
+                                                 const double* __restrict__ E, const double* __restrict__ rho,
+                                                 const double* __restrict__ eps, long long idx, double& kap,
+                                                 double& D) {
+  if (K.ok) {
+    const double e = __ldg(E + idx), rh = __ldg(rho + idx), ep = __ldg(eps + idx);
+    if (gt_zero(e) && gt_zero(rh) && gt_zero(ep)) {
+      const int i = (int)(idx % g.n[0]);
+      const long long r = idx / g.n[0];
+      if (coeffs_cell_df(g, ph, K, E, idx, i, (int)(r % g.n[1]), (int)(r / g.n[1]), e, rh, ep, kap, D)) return true;
+    }
+  }
+  return coeffs_cell_f64(g, ph, E, rho, eps, idx, kap, D);
 }
 
 // One thread per cell writes the lower face of each axis (face q_a), and the face n_a when it

@@ -14,7 +14,7 @@ __global__ void k_exchange(long long n, ExchangeParams p, Opacity op, const doub
   if (idx < n) {
     double r = rho[idx], e = eps[idx], En = E[idx];
     double k = kappa_in ? kappa_in[idx] : opacity(op, r, temperature(p.gamma, p.gas_R, r, e));
-    if (exchange_cell(p, r, k, e, En, iters, bis)) {
+    if (exchange_cell_fast(p, r, k, e, En, iters, bis)) {
       eps[idx] = e;
       E[idx] = En;
     } else {

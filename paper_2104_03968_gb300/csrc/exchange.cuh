@@ -54,7 +54,6 @@ __device__ inline double halley64(double a, double cc, int maxit, int* iters, in
   return 0.5 * (lo + hi);
 }
 
-// Updates (e, E) of one cell in place.  Returns false (and leaves them) on invalid input.
 // two FP64 Newton steps from the FP32 root (tiny or huge coefficients); d: the last step
 static __device__ __noinline__ double polish64(double a, double cc, float y32, float r1f, float* d) {
   const double r1 = (double)r1f;
@@ -68,6 +67,54 @@ static __device__ __noinline__ double polish64(double a, double cc, float y32, f
   return y;
 }
 
+// FP32 root of a y^4 + y - cc = 0 for af in [1e-30, 1e30], cf in [1e-30, 1]: y = ys z with
+// ys = min(cc, (cc/a)^(1/4)) >= root, so that alpha z^4 + beta z = 1 with max(alpha, beta) = 1 and
+// the root z lies in [0.72, 1]; safeguarded Halley on z.  Also returns r1 = 1/f'(y) for the polish.
+__device__ __forceinline__ float halley32(float af, float cf, int& iters, float& r1) {
+  const float ys = fminf(cf, sqrtf(sqrtf(cf / af)));
+  const float ys2 = ys * ys;
+  const float alpha = af * ys2 * ys2 / cf, beta = ys / cf;
+  float z = 1.0f, lo = 0.0f, hi = 1.0f;
+  for (int it = 0; it < 12; ++it) {
+    const float z2 = z * z;
+    const float f = fmaf(alpha * z2, z2, fmaf(beta, z, -1.0f));
+    ++iters;
+    if (f < 0.0f) lo = z;
+    else hi = z;
+    const float f1 = fmaf(4.0f * alpha * z2, z, beta);
+    const float f2 = 12.0f * alpha * z2;
+    float zn = z - 2.0f * f * f1 / (2.0f * f1 * f1 - f * f2);
+    // a converged step may land on the bracket end just set from z: accept it before the
+    // safeguard would replace it by a bisection
+    if (fabsf(zn - z) <= 4e-7f * zn) {
+      z = zn;
+      break;
+    }
+    if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
+    z = zn;
+  }
+  const float y32 = ys * z;
+  r1 = __frcp_rn(fmaf(4.0f * af * y32 * y32, y32, 1.0f));
+  return y32;
+}
+
+// Newton polish of the FP32 root in double-float arithmetic, two steps with the FP32 root's
+// reciprocal slope r1 = 1/(4 a y^3 + 1) as the step factor (each step multiplies the error by
+// ~1e-7, so two take the FP32 root to the rounding of the arithmetic).  d: the last step.
+__device__ __forceinline__ dfl polish_df(dfl A, dfl C, float y32, float r1, float& d) {
+  dfl Y{y32, 0.0f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const dfl Y2 = df_sqr(Y);
+    const dfl F = df_add(df_add(df_mul(A, df_sqr(Y2)), Y), df_neg(C));
+    d = F.hi * r1;
+    Y = df_add(Y, {-d, 0.0f});
+  }
+  return Y;
+}
+
+// Updates (e, E) of one cell in place with FP64 coefficients.  Returns false (and leaves them) on
+// invalid input.
 __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k, double& e, double& E, int& iters,
                                      int& bis) {
   const double e0 = e, E0 = E;
@@ -98,50 +145,16 @@ __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k
   const float af = (float)a, cf = (float)cc;
   double y;
   if (af >= 1e-30f && af <= 1e30f && cf >= 1e-30f) {
-    // y = ys z with ys = min(cc, (cc/a)^(1/4)) >= root: alpha z^4 + beta z = 1 with
-    // max(alpha, beta) = 1, so the root z lies in [0.72, 1]
-    float ys = fminf(cf, sqrtf(sqrtf(cf / af)));
-    float ys2 = ys * ys;
-    float alpha = af * ys2 * ys2 / cf, beta = ys / cf;
-    float z = 1.0f, lo = 0.0f, hi = 1.0f;
-    for (int it = 0; it < 12; ++it) {
-      float z2 = z * z;
-      float f = fmaf(alpha * z2, z2, fmaf(beta, z, -1.0f));
-      ++iters;
-      if (f < 0.0f) lo = z;
-      else hi = z;
-      float f1 = fmaf(4.0f * alpha * z2, z, beta);
-      float f2 = 12.0f * alpha * z2;
-      float zn = z - 2.0f * f * f1 / (2.0f * f1 * f1 - f * f2);
-      // a converged step may land on the bracket end just set from z: accept it before the
-      // safeguard would replace it by a bisection
-      if (fabsf(zn - z) <= 4e-7f * zn) {
-        z = zn;
-        break;
-      }
-      if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
-      z = zn;
-    }
-    // Newton polish of the FP32 root, two steps with the FP32 root's reciprocal slope
-    // 1/f'(y) = 1/(4 a y^3 + 1) as the step factor (each step multiplies the error by ~1e-7, so two
-    // take the FP32 root to the rounding of the arithmetic): in double-float arithmetic (df.cuh)
-    // while a, cc and y keep their low parts normal floats, else in FP64 (out of line).
-    const float y32 = ys * z;
-    const float r1 = __frcp_rn(fmaf(4.0f * af * y32 * y32, y32, 1.0f));
+    float r1;
+    const float y32 = halley32(af, cf, iters, r1);
+    // polish in double-float while a, cc and y keep their low parts normal floats, else in FP64
+    // (out of line)
     float d = 0.0f, yh = 0.0f;
     if (cf >= 0x1p-60f && af <= 0x1p60f) {
       float ah, al, ch, cl;
       split_f64(a, ah, al);
       split_f64(cc, ch, cl);
-      const dfl A{ah, al}, C{-ch, -cl};
-      dfl Y{y32, 0.0f};
-#pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const dfl Y2 = df_mul(Y, Y);
-        const dfl F = df_add(df_add(df_mul(A, df_mul(Y2, Y2)), Y), C);
-        d = F.hi * r1;
-        Y = df_add(Y, {-d, 0.0f});
-      }
+      const dfl Y = polish_df({ah, al}, {ch, cl}, y32, r1, d);
       y = (double)Y.hi + (double)Y.lo;
       yh = Y.hi;
     } else {
@@ -162,6 +175,89 @@ __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k
   e = x;
   E = fma(a1 * x2, x2, E0) * u;
   return true;
+}
+
+static __device__ __noinline__ bool exchange_cell_f64(const ExchangeParams& p, double r, double k, double& e,
+                                                      double& E, int& iters, int& bis) {
+  return exchange_cell(p, r, k, e, E, iters, bis);
+}
+
+// The exchange of one valid cell (S = eps + E > 0) in double-float arithmetic, with no FP64
+// arithmetic but the sum S and the two final roundings.  Each FP64 input is split into a mantissa
+// in [1, 2) and a power of two; the products and quotients that form the dimensionless quartic
+// coefficients
+//     a2 = c dt kappa rho,   a = k4 kappa S^3 / (rho^3 (1 + a2)),   cc = a2 v + eps/S,
+//     v = E / ((1 + a2) S)
+// and the new energies
+//     x = S y,   E^{n+1} = S (a y^4 + v)      (from E^{n+1} = (a1 x^4 + E^n)/(1 + a2))
+// multiply mantissas and add the exponents as integers, so the path holds in any unit system in
+// which a, cc and E^{n+1}/S lie in the double-float window (cgs included), not only near 1.
+// Returns false (outputs unset) where the cell needs the FP64 path: a value outside the window or
+// the FP32 root's range, or a polish that did not converge.
+__device__ __forceinline__ bool exchange_cell_df(const ExchangeParams& p, double r, double k, double e0, double E0,
+                                                 double S, double& e_out, double& E_out, int& iters) {
+  bool ok, o1, o2, o3, o4, o5, o6;
+  dfl rm, km, Sm, em, Em, cm, qm;
+  int re, ke, Se, ee, Ee, ce, qx;
+  xsplit(r, rm, re, ok);
+  xsplit(k, km, ke, o1);
+  xsplit(S, Sm, Se, o2);
+  xsplit(p.cdt, cm, ce, o3);
+  xsplit(p.k4, qm, qx, o4);
+  xsplit0(e0, em, ee, o5);
+  xsplit0(E0, Em, Ee, o6);
+  ok = ok && o1 && o2 && o3 && o4 && o5 && o6;
+  // a2 = c dt kappa rho; B = 1 + a2 as mantissa and exponent (1 is negligible beside a2 > 2^100)
+  const dfl a2m = df_mul(df_mul(cm, km), rm);
+  const int a2e = ce + ke + re;
+  dfl Bm = a2m;
+  int Be = a2e;
+  if (a2e <= 100) {
+    const dfl B = df_add_pos({1.0f, 0.0f}, xval(a2m, a2e, ok));
+    Be = exponent_f32(B.hi);
+    Bm = df_scale(B, pow2f(-Be));
+  }
+  // v = E / (B S), cc = a2 v + eps / S, a = k4 kappa S^3 / (rho^3 B)
+  const dfl vm = df_div(Em, df_mul(Bm, Sm));
+  const int ve = Ee - Be - Se;
+  const dfl C = df_add_pos(xval(df_mul(a2m, vm), a2e + ve, ok), xval(df_div(em, Sm), ee - Se, ok));
+  const dfl am = df_div(df_mul(df_mul(qm, km), df_mul(df_sqr(Sm), Sm)), df_mul(df_mul(df_sqr(rm), rm), Bm));
+  const int ae = qx + ke + 3 * Se - 3 * re - Be;
+  const dfl A = xval(am, ae, ok);
+  const float af = A.hi, cf = C.hi;
+  // the FP32 root's range and the double-float polish's window
+  if (!(ok && df_in(A) && df_in(C) && af >= 1e-30f && af <= 0x1p60f && cf >= 0x1p-60f)) return false;
+  float r1, d = 0.0f;
+  const float y32 = halley32(af, cf, iters, r1);
+  const dfl Y = polish_df(A, C, y32, r1, d);
+  iters += 2;
+  if (!(fabsf(d) <= 1e-12f * Y.hi) || !(Y.hi > 0.0f)) return false;
+  // x = S y and E^{n+1} / S = a y^4 + v (y = Ym 2^Ye)
+  const int Ye = exponent_f32(Y.hi);
+  const dfl Ym = df_scale(Y, pow2f(-Ye));
+  const dfl ES = df_add_pos(xval(df_mul(am, df_sqr(df_sqr(Ym))), ae + 4 * Ye, ok), xval(vm, ve, ok));
+  ok = ok && df_in(ES);
+  e_out = ldexp_f64(df_to_f64(df_mul(Sm, Y)), Se, ok);
+  E_out = ldexp_f64(df_to_f64(df_mul(ES, Sm)), Se, ok);
+  return ok;
+}
+
+// Either path for one cell: double-float, else FP64 (out of line).  Same contract as exchange_cell.
+__device__ __forceinline__ bool exchange_cell_fast(const ExchangeParams& p, double r, double k, double& e, double& E,
+                                                   int& iters, int& bis) {
+  const double e0 = e, E0 = E;
+  if (!(gt_zero(r) && gt_zero(k) && ge_zero(e0) && ge_zero(E0))) return false;
+  const double S = e0 + E0;
+  if (!pos_finite(S)) return true;  // eps = E = 0: nothing to exchange
+  double eo, Eo;
+  int it = 0;
+  if (exchange_cell_df(p, r, k, e0, E0, S, eo, Eo, it)) {
+    e = eo;
+    E = Eo;
+    iters += it;
+    return true;
+  }
+  return exchange_cell_f64(p, r, k, e, E, iters, bis);
 }
 
 // warp-aggregated diagnostics: max iterations and bisection count

@@ -34,22 +34,18 @@ __device__ __forceinline__ bool in_window(float x) {
   return x == 0.0f || (e > -78 && e < 90);
 }
 
-// s * 2 Dc Dn / (Dc + Dn) (pair) or s * Dc (boundary face) as a double-float
-__device__ __forceinline__ dfl face_weight_df(double Dc, double Dn, bool pair, dfl s, unsigned& bad) {
-  const int sh = exponent_f64(Dc);
-  float ch, cl;
-  bool ok;
-  split_f64_scaled(Dc, sh, ch, cl, ok);
-  if (!ok) bad = 1u;
-  const dfl c{ch, cl};
+// s * 2 Dc Dn / (Dc + Dn) (pair) or s * Dc (boundary face) as a double-float.  c = Dc 2^-sh is
+// the cell's own value, split once per cell; Dn is scaled by the same power of two.
+__device__ __forceinline__ dfl face_weight_df(dfl c, int sh, double Dn, bool pair, dfl s, unsigned& bad) {
   dfl w;
   if (pair) {
     float nh, nl;
+    bool ok;
     split_f64_scaled(Dn, sh, nh, nl, ok);
     if (!ok) bad = 1u;
     const dfl n{nh, nl};
-    const dfl h = df_div(df_mul(c, n), df_add(c, n));
-    w = df_mul(df_mul(h, s), {2.0f, 0.0f});
+    const dfl h = df_div(df_mul(c, n), df_add_pos(c, n));
+    w = df_scale(df_mul(h, s), 2.0f);
   } else {
     w = df_mul(c, s);
   }
@@ -77,17 +73,24 @@ __global__ void __launch_bounds__(256) k_faces_df(GridDev g, DfConst K, const do
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const int idx = i + nx * row;
       const double Dc = D[idx];
+      const int sh = exponent_f64(Dc);
+      dfl c;
+      {
+        bool ok;
+        split_f64_scaled(Dc, sh, c.hi, c.lo, ok);
+        if (!ok) bad = 1u;
+      }
       // x faces: lower face i of row (j, k), and face nx when this cell owns it
       {
         const dfl s{K.s_hi[0], K.s_lo[0]};
         const bool pair = i > 0 || per[0];
         const double Dn = pair ? D[i > 0 ? idx - 1 : idx + (nx - 1)] : Dc;
-        const dfl w = face_weight_df(Dc, Dn, pair, s, bad);
+        const dfl w = face_weight_df(c, sh, Dn, pair, s, bad);
         const int f = i + (nx + 1) * row;
         w0[f] = w.hi;
         l0[f] = w.lo;
         if ((perh[0] && i == 0) || (!perh[0] && i == nx - 1)) {
-          const dfl wu = perh[0] ? w : face_weight_df(Dc, Dc, false, s, bad);
+          const dfl wu = perh[0] ? w : face_weight_df(c, sh, Dc, false, s, bad);
           w0[f - i + nx] = wu.hi;
           l0[f - i + nx] = wu.lo;
         }
@@ -96,12 +99,12 @@ __global__ void __launch_bounds__(256) k_faces_df(GridDev g, DfConst K, const do
         const dfl s{K.s_hi[1], K.s_lo[1]};
         const bool pair = j > 0 || per[1];
         const double Dn = pair ? D[j > 0 ? idx - nx : idx + (ny - 1) * nx] : Dc;
-        const dfl w = face_weight_df(Dc, Dn, pair, s, bad);
+        const dfl w = face_weight_df(c, sh, Dn, pair, s, bad);
         const int f = i + nx * (j + (ny + 1) * k);
         w1[f] = w.hi;
         l1[f] = w.lo;
         if ((perh[1] && j == 0) || (!perh[1] && j == ny - 1)) {
-          const dfl wu = perh[1] ? w : face_weight_df(Dc, Dc, false, s, bad);
+          const dfl wu = perh[1] ? w : face_weight_df(c, sh, Dc, false, s, bad);
           const int fu = i + nx * (ny + (ny + 1) * k);
           w1[fu] = wu.hi;
           l1[fu] = wu.lo;
@@ -112,11 +115,11 @@ __global__ void __launch_bounds__(256) k_faces_df(GridDev g, DfConst K, const do
         const dfl s{K.s_hi[2], K.s_lo[2]};
         const bool pair = k > 0 || per[2];
         const double Dn = pair ? D[k > 0 ? idx - sz : idx + (nz - 1) * sz] : Dc;
-        const dfl w = face_weight_df(Dc, Dn, pair, s, bad);
+        const dfl w = face_weight_df(c, sh, Dn, pair, s, bad);
         w2[idx] = w.hi;
         l2[idx] = w.lo;
         if ((perh[2] && k == 0) || (!perh[2] && k == nz - 1)) {
-          const dfl wu = perh[2] ? w : face_weight_df(Dc, Dc, false, s, bad);
+          const dfl wu = perh[2] ? w : face_weight_df(c, sh, Dc, false, s, bad);
           const int fu = i + nx * (j + ny * nz);
           w2[fu] = wu.hi;
           l2[fu] = wu.lo;
