@@ -11,13 +11,36 @@
 
 namespace fld {
 
-__global__ void k_coeffs(GridDev g, CoeffPhys ph, CoeffDf K, const double* __restrict__ E,
-                         const double* __restrict__ rho, const double* __restrict__ eps,
-                         double* __restrict__ kappa_out, double* __restrict__ D_out, unsigned* __restrict__ status) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.ncell) return;
+// One thread per cell; the coordinates come from 32-bit divisions by invariant divisors (the
+// launcher takes the 64-bit kernel beyond 2^32 cells).
+// The structures are __grid_constant__ so that the out-of-line FP64 fallback can take their
+// address without a per-thread local copy; five blocks of 256 per SM (48 registers), as the
+// double-float chains are latency-bound.
+__global__ void __launch_bounds__(kBlock, 5)
+    k_coeffs(const __grid_constant__ GridDev g, const __grid_constant__ CoeffPhys ph, CoeffDf K, FastDiv f0,
+             FastDiv f1, const double* __restrict__ E, const double* __restrict__ rho, const double* __restrict__ eps,
+             double* __restrict__ kappa_out, double* __restrict__ D_out, unsigned* __restrict__ status) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned long long)g.ncell) return;
+  const unsigned r = fast_div(idx, f0), k = fast_div(r, f1);
+  const int i = (int)(idx - r * f0.d), j = (int)(r - k * f1.d);
   double kap, D;
-  if (!coeffs_cell_fast(g, ph, K, E, rho, eps, idx, kap, D)) atomicOr(status, kStatNonpositive);
+  if (!coeffs_cell_fast(g, ph, K, E, rho, eps, idx, i, j, (int)k, kap, D)) atomicOr(status, kStatNonpositive);
+  if (kappa_out) kappa_out[idx] = kap;
+  D_out[idx] = D;
+}
+
+__global__ void k_coeffs64(const __grid_constant__ GridDev g, const __grid_constant__ CoeffPhys ph, CoeffDf K,
+                           const double* __restrict__ E,
+                           const double* __restrict__ rho, const double* __restrict__ eps,
+                           double* __restrict__ kappa_out, double* __restrict__ D_out, unsigned* __restrict__ status) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.ncell) return;
+  const long long r = idx / g.n[0];
+  double kap, D;
+  if (!coeffs_cell_fast(g, ph, K, E, rho, eps, idx, (int)(idx % g.n[0]), (int)(r % g.n[1]), (int)(r / g.n[1]), kap,
+                        D))
+    atomicOr(status, kStatNonpositive);
   if (kappa_out) kappa_out[idx] = kap;
   D_out[idx] = D;
 }
@@ -43,8 +66,13 @@ cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double 
   if (g.ncell == 0) return cudaSuccess;
   TraceScope ts("coeffs", s);
   CoeffPhys ph{op, c, gamma, gas_R, limiter};
-  k_coeffs<<<blocks_for(g.ncell), kBlock, 0, s>>>(g, ph, make_coeff_df(ph, g), E, rho, eps, kappa_out, D_out,
-                                                   status);
+  const CoeffDf K = make_coeff_df(ph, g);
+  if (g.ncell < (1ll << 32) - kBlock)
+    k_coeffs<<<blocks_for(g.ncell), kBlock, 0, s>>>(g, ph, K, make_fastdiv((unsigned)g.n[0]),
+                                                     make_fastdiv((unsigned)g.n[1]), E, rho, eps, kappa_out, D_out,
+                                                     status);
+  else
+    k_coeffs64<<<blocks_for(g.ncell), kBlock, 0, s>>>(g, ph, K, E, rho, eps, kappa_out, D_out, status);
   return cudaGetLastError();
 }
 

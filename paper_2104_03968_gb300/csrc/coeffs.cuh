@@ -154,8 +154,8 @@ __host__ inline CoeffDf make_coeff_df(const CoeffPhys& ph, const GridDev& g) {
 }
 
 // The same cell in double-float arithmetic (df.cuh) on the FP32 pipe, for constant or Kramers
-// (a = 1, b = -3.5) opacity: the FP64 stencil differences are the only FP64 arithmetic besides the
-// two final roundings.  Inputs must already be valid (E, rho, eps > 0).  Every product whose low
+// (a = 1, b = -3.5) opacity: the FP64 stencil differences d1 + 8 d2 are the only FP64 arithmetic
+// besides the two final roundings.  Inputs must already be valid (E, rho, eps > 0).  Every product whose low
 // part could leave the normal floats is checked against the double-float window (df_in); sums of
 // positive terms need no check, since an underflowed term is negligible beside an in-window sum.
 // Returns false, with the outputs unset, when a value leaves the window; the caller then takes the
@@ -190,11 +190,9 @@ __device__ __forceinline__ bool coeffs_cell_df(const GridDev& g, const CoeffPhys
     if (a >= g.ndim) break;
     double d1, d2;
     grad_diffs(g, E, idx, i, j, k, a, d1, d2);
-    dfl A, B;
-    split_f64_try(d1, A.hi, A.lo, o2);
-    split_f64_try(d2, B.hi, B.lo, o3);
-    const dfl d = df_add(A, df_scale(B, 8.0f));  // 12 dx dE/dx
-    ok = ok && o2 && o3 && (d.hi == 0.0f || df_in(d));
+    dfl d;
+    split_f64_try(fma(8.0, d2, d1), d.hi, d.lo, o2);  // 12 dx dE/dx
+    ok = ok && o2 && (d.hi == 0.0f || df_in(d));
     g2 = df_add_pos(g2, df_mul(df_sqr(d), K.ig[a]));
   }
   ok = ok && (g2.hi == 0.0f || df_in(g2));
@@ -238,17 +236,15 @@ __device__ __forceinline__ bool coeffs_cell_df(const GridDev& g, const CoeffPhys
 
 // Either path for one cell: the double-float one when its constants allow, else (or when a value
 // leaves its window) FP64.  Returns false (D = 0) for invalid input, as coeffs_cell.
+// (i, j, k) are the cell's coordinates, idx its index.
 __device__ __forceinline__ bool coeffs_cell_fast(const GridDev& g, const CoeffPhys& ph, const CoeffDf& K,
                                                  const double* __restrict__ E, const double* __restrict__ rho,
-                                                 const double* __restrict__ eps, long long idx, double& kap,
-                                                 double& D) {
+                                                 const double* __restrict__ eps, long long idx, int i, int j, int k,
+                                                 double& kap, double& D) {
   if (K.ok) {
     const double e = __ldg(E + idx), rh = __ldg(rho + idx), ep = __ldg(eps + idx);
-    if (gt_zero(e) && gt_zero(rh) && gt_zero(ep)) {
-      const int i = (int)(idx % g.n[0]);
-      const long long r = idx / g.n[0];
-      if (coeffs_cell_df(g, ph, K, E, idx, i, (int)(r % g.n[1]), (int)(r / g.n[1]), e, rh, ep, kap, D)) return true;
-    }
+    if (gt_zero(e) && gt_zero(rh) && gt_zero(ep) && coeffs_cell_df(g, ph, K, E, idx, i, j, k, e, rh, ep, kap, D))
+      return true;
   }
   return coeffs_cell_f64(g, ph, E, rho, eps, idx, kap, D);
 }

@@ -70,10 +70,13 @@ static __device__ __noinline__ double polish64(double a, double cc, float y32, f
 // FP32 root of a y^4 + y - cc = 0 for af in [1e-30, 1e30], cf in [1e-30, 1]: y = ys z with
 // ys = min(cc, (cc/a)^(1/4)) >= root, so that alpha z^4 + beta z = 1 with max(alpha, beta) = 1 and
 // the root z lies in [0.72, 1]; safeguarded Halley on z.  Also returns r1 = 1/f'(y) for the polish.
+// The divisions and roots take the hardware approximations (about one ulp): they only shift the
+// FP32 root by a few ulps, which the polish removes.
 __device__ __forceinline__ float halley32(float af, float cf, int& iters, float& r1) {
-  const float ys = fminf(cf, sqrtf(sqrtf(cf / af)));
+  const float icf = rcp_approx(cf);
+  const float ys = fminf(cf, rsqrt_approx(sqrt_approx(af * icf)));
   const float ys2 = ys * ys;
-  const float alpha = af * ys2 * ys2 / cf, beta = ys / cf;
+  const float alpha = af * ys2 * ys2 * icf, beta = ys * icf;
   float z = 1.0f, lo = 0.0f, hi = 1.0f;
   for (int it = 0; it < 12; ++it) {
     const float z2 = z * z;
@@ -83,7 +86,7 @@ __device__ __forceinline__ float halley32(float af, float cf, int& iters, float&
     else hi = z;
     const float f1 = fmaf(4.0f * alpha * z2, z, beta);
     const float f2 = 12.0f * alpha * z2;
-    float zn = z - 2.0f * f * f1 / (2.0f * f1 * f1 - f * f2);
+    float zn = z - 2.0f * f * f1 * rcp_approx(2.0f * f1 * f1 - f * f2);
     // a converged step may land on the bracket end just set from z: accept it before the
     // safeguard would replace it by a bisection
     if (fabsf(zn - z) <= 4e-7f * zn) {
@@ -94,7 +97,7 @@ __device__ __forceinline__ float halley32(float af, float cf, int& iters, float&
     z = zn;
   }
   const float y32 = ys * z;
-  r1 = __frcp_rn(fmaf(4.0f * af * y32 * y32, y32, 1.0f));
+  r1 = rcp_approx(fmaf(4.0f * af * y32 * y32, y32, 1.0f));
   return y32;
 }
 
@@ -196,17 +199,17 @@ static __device__ __noinline__ bool exchange_cell_f64(const ExchangeParams& p, d
 // the FP32 root's range, or a polish that did not converge.
 __device__ __forceinline__ bool exchange_cell_df(const ExchangeParams& p, double r, double k, double e0, double E0,
                                                  double S, double& e_out, double& E_out, int& iters) {
-  bool ok, o1, o2, o3, o4, o5, o6;
-  dfl rm, km, Sm, em, Em, cm, qm;
-  int re, ke, Se, ee, Ee, ce, qx;
+  bool ok, o1, o2, o5, o6;
+  dfl rm, km, Sm, em, Em;
+  int re, ke, Se, ee, Ee;
   xsplit(r, rm, re, ok);
   xsplit(k, km, ke, o1);
   xsplit(S, Sm, Se, o2);
-  xsplit(p.cdt, cm, ce, o3);
-  xsplit(p.k4, qm, qx, o4);
   xsplit0(e0, em, ee, o5);
   xsplit0(E0, Em, Ee, o6);
-  ok = ok && o1 && o2 && o3 && o4 && o5 && o6;
+  ok = ok && o1 && o2 && o5 && o6 && p.df_ok;
+  const dfl cm{p.cdt_hi, p.cdt_lo}, qm{p.k4_hi, p.k4_lo};
+  const int ce = p.cdt_e, qx = p.k4_e;
   // a2 = c dt kappa rho; B = 1 + a2 as mantissa and exponent (1 is negligible beside a2 > 2^100)
   const dfl a2m = df_mul(df_mul(cm, km), rm);
   const int a2e = ce + ke + re;

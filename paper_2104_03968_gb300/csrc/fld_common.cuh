@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/fld.h"
@@ -30,7 +31,19 @@ struct ExchangeParams {
   int maxit;
   double cdt;  // c dt
   double k4;   // 4 sigma dt ((gamma-1)/gas_R)^4: a1 = k4 kappa / rho^3
+  // cdt and k4 as m 2^e, m in [1, 2) split into two floats (the double-float exchange path);
+  // df_ok is 0 unless both are positive and finite
+  float cdt_hi, cdt_lo, k4_hi, k4_lo;
+  int cdt_e, k4_e, df_ok;
 };
+
+__host__ __device__ inline void mant_split(double v, float& hi, float& lo, int& e) {
+  int ee = 0;
+  const double m = 2.0 * frexp(v, &ee);
+  e = ee - 1;
+  hi = (float)m;
+  lo = (float)(m - (double)hi);
+}
 
 __host__ __device__ inline ExchangeParams make_exchange(double c, double a_rad, double gamma, double gas_R, double dt,
                                                         int maxit) {
@@ -44,6 +57,9 @@ __host__ __device__ inline ExchangeParams make_exchange(double c, double a_rad, 
   p.cdt = c * dt;
   double t = (gamma - 1.0) / gas_R;
   p.k4 = 4.0 * p.sigma * dt * t * t * t * t;
+  mant_split(p.cdt, p.cdt_hi, p.cdt_lo, p.cdt_e);
+  mant_split(p.k4, p.k4_hi, p.k4_lo, p.k4_e);
+  p.df_ok = p.cdt > 0.0 && p.cdt <= 1.7e308 && p.k4 > 0.0 && p.k4 <= 1.7e308 && p.cdt >= 2.3e-308 && p.k4 >= 2.3e-308;
   return p;
 }
 
@@ -85,6 +101,31 @@ __device__ __forceinline__ long long face_index(const int n[3], int a, int i, in
   if (a == 0) return (long long)f + (long long)(n[0] + 1) * ((long long)j + (long long)n[1] * k);
   if (a == 1) return (long long)i + (long long)n[0] * ((long long)f + (long long)(n[1] + 1) * k);
   return (long long)i + (long long)n[0] * ((long long)j + (long long)n[1] * f);
+}
+
+// Division of 32-bit unsigned numerators by a run-time invariant divisor d >= 1 with a multiply
+// and shifts (Granlund and Montgomery, "Division by invariant integers using multiplication",
+// PLDI 1994, Sect. 4): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) where t = umulhi(m, n).
+struct FastDiv {
+  unsigned d, m;
+  int s1, s2;
+};
+
+__host__ inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__device__ __forceinline__ unsigned fast_div(unsigned n, const FastDiv& f) {
+  const unsigned t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
 }
 
 __device__ __forceinline__ long long cell_index(const int n[3], int i, int j, int k) {

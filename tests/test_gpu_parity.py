@@ -68,6 +68,36 @@ def test_coeffs_parity(ctx, shape, bcname, limiter):
     assert np.abs(host(D).reshape(D_o.shape) / D_o - 1).max() < 1e-12
 
 
+@pytest.mark.parametrize("scaling", ["cgs", "per_cell"])
+@pytest.mark.parametrize("limiter", ["lp", "third", "minerbo"])
+def test_coeffs_unit_scales(ctx, scaling, limiter):
+    """Coefficients in cgs units (values from 1e-21 to 1e25: the double-float path throughout) and
+    with per-cell factors over tens of decades (cells whose values leave the double-float window
+    take the FP64 path): every cell matches the oracle."""
+    from paper_2104_03968_gb300 import fld
+    rng = np.random.default_rng(23)
+    shape = (40, 36, 12)
+    arr = tuple(reversed(shape))
+    phys = inputs.cgs_units(0.6, limiter=limiter)
+    phys.update(opacity="kramers", kappa0=4e25, kr_a=1.0, kr_b=-3.5)
+    rho = 1e-9 * np.exp(0.8 * inputs.smooth_field(rng, arr))
+    T = 1e6 * (1 + 0.3 * inputs.smooth_field(rng, arr))
+    E = inputs.rad_energy(phys, T * (1 + 0.1 * inputs.smooth_field(rng, arr)))
+    eps = inputs.equilibrium_eps(phys, rho, T)
+    if scaling == "per_cell":
+        E = E * 10 ** rng.uniform(-12, 12, arr)
+        rho = rho * 10 ** rng.uniform(-4, 4, arr)
+        eps = eps * 10 ** rng.uniform(-4, 4, arr)
+    g = inputs.periodic_grid(shape, dx=1e10)
+    kap_o = oracle.opacity(phys, rho, eps)
+    D_o = oracle.coeffs(g, phys, E, rho, kap_o)
+    assert np.isfinite(D_o).all() and (D_o > 0).all()  # the case stays inside FP64's range
+    kap, D = fld.coeffs(ctx, g, phys, dev(E), dev(rho), dev(eps))
+    torch.cuda.synchronize()
+    assert np.abs(host(kap).reshape(kap_o.shape) / kap_o - 1).max() < 1e-13
+    assert np.abs(host(D).reshape(D_o.shape) / D_o - 1).max() < 1e-12
+
+
 def test_coeffs_table_opacity(ctx):
     from paper_2104_03968_gb300 import fld
     case = inputs.wind_columns(ncol=4, ncell=64)
