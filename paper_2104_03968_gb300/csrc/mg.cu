@@ -685,12 +685,12 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   auto add = [&](size_t b) { bytes += (b + 511) & ~(size_t)255; };
   for (int a = 0; a < g.ndim; ++a) add(faces3(dims_[0], a) * sizeof(double));
   for (int k = 0; k < 2; ++k) add(N * sizeof(double));  // b, diag
-  add(2 * nparts_ * sizeof(double));
+  add(3 * nparts_ * sizeof(double));
   add(8 * sizeof(double));
   const bool df = precision == FLD_PREC_MIXED;  // double-float residual updates
   if (df) {
     for (int a = 0; a < g.ndim; ++a) add(faces3(dims_[0], a) * sizeof(float));  // weights, low parts
-    for (int k = 0; k < 5; ++k) add(N * sizeof(float));                           // diag hi, lo; r lo; b hi, lo
+    for (int k = 0; k < 3; ++k) add(N * sizeof(float));                           // diag hi, lo; r lo
     add(sizeof(unsigned));
   }
   for (size_t l = 0; l < dims_.size(); ++l) {
@@ -706,14 +706,14 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   for (int a = 0; a < 3; ++a) w64_[a] = a < g.ndim ? (double*)arena_.take(faces3(dims_[0], a) * sizeof(double)) : nullptr;
   b64_ = (double*)arena_.take(N * sizeof(double));
   diag64_ = (double*)arena_.take(N * sizeof(double));
-  partials_ = (double*)arena_.take(2 * nparts_ * sizeof(double));
+  partials_ = (double*)arena_.take(3 * nparts_ * sizeof(double));
   scal_ = (double*)arena_.take(8 * sizeof(double));
   if (!host_scal_) {
     e = cudaMallocHost(&host_scal_, 8 * sizeof(double));
     if (e != cudaSuccess) return e;
   }
   for (int a = 0; a < 3; ++a) w32lo_[a] = nullptr;
-  dhi_ = dlo_ = rlo_ = bhi_ = blo_ = nullptr;
+  dhi_ = dlo_ = rlo_ = nullptr;
   df_flag_ = nullptr;
   if (df) {
     for (int a = 0; a < g.ndim; ++a)
@@ -721,10 +721,8 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
     dhi_ = (float*)arena_.take(N * sizeof(float));
     dlo_ = (float*)arena_.take(N * sizeof(float));
     rlo_ = (float*)arena_.take(N * sizeof(float));
-    bhi_ = (float*)arena_.take(N * sizeof(float));
-    blo_ = (float*)arena_.take(N * sizeof(float));
     df_flag_ = (unsigned*)arena_.take(sizeof(unsigned));
-    if (!dhi_ || !dlo_ || !rlo_ || !bhi_ || !blo_ || !df_flag_) return cudaErrorMemoryAllocation;
+    if (!dhi_ || !dlo_ || !rlo_ || !df_flag_) return cudaErrorMemoryAllocation;
   }
   lv_.assign(dims_.size(), LevelBuf{});
   for (size_t l = 0; l < dims_.size(); ++l) {
@@ -792,12 +790,8 @@ cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const d
     const DfConst K = make_df_const(g_, dt);
     float* w32[3] = {nullptr, nullptr, nullptr};
     for (int a = 0; a < g_.ndim; ++a) w32[a] = (float*)lv_[0].w[a];
+    // the diagonal, 1/diag and b follow in the first residual's pass (solve_t)
     e = launch_faces_df(g_, K, D_cell[0], w32, w32lo_, df_flag_, s);
-    if (e != cudaSuccess) return e;
-    void* wlo[3] = {w32lo_[0], w32lo_[1], w32lo_[2]};
-    e = launch_fine_setup_df(g_, K, level_dev<float>(g_, dims_[0], lv_[0].w), level_dev<float>(g_, dims_[0], wlo),
-                             E_old, dhi_, dlo_, (float*)lv_[0].invd, bhi_, blo_, partials_, nparts_, scal_, df_flag_,
-                             s);
     if (e != cudaSuccess) return e;
   } else {
     e = fp64_operator<T>(s);
@@ -1063,12 +1057,12 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       TraceScope ts("residual", s);
       df_res = mixed && df_mode_ && !fp64_op_ && cycles == 0;
       if (df_res) {
-        // double-float first residual from the double-float setup (no FP64 operator exists yet)
-        cudaError_t e = launch_residual0_df(g_.ndim, L32, L32lo, dhi_, dlo_, bhi_, blo_, x_in, x, (float*)lv_[0].r,
-                                            rlo_, scal_, nparts_, partials_, s);
+        // the finest level's diagonal and the double-float first residual in one pass from the
+        // double-float weights (no FP64 operator exists yet)
+        cudaError_t e = launch_setup_res0_df(g_, make_df_const(g_, dt_), L32, L32lo, x_in, x != x_in ? x : nullptr,
+                                             dhi_, dlo_, (float*)lv_[0].invd, (float*)lv_[0].r, rlo_, nparts_,
+                                             partials_, scal_, df_flag_, s);
         if (e != cudaSuccess) return e;
-        k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
-        k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
       } else {
         if (mixed && !fp64_op_) {
           cudaError_t e = fp64_operator<T>(s);  // an exact residual after a double-float setup
@@ -1103,9 +1097,9 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
     x_in = x;
     bb = host_scal_[1];
     if (df_res) {
-      // scaled sums, as for the updates
-      rel = sqrt(host_scal_[0] / N);
-      drift = kDrift * sqrt(host_scal_[2] / N);
+      // unscaled sums: ||r||^2, ||b||^2 and the error measure's ||m||^2
+      rel = bb > 0 ? sqrt(host_scal_[0] / bb) : sqrt(host_scal_[0]);
+      drift = kDrift * (bb > 0 ? sqrt(host_scal_[2] / bb) : sqrt(host_scal_[2]));
       const double rms = sqrt(bb / N);
       updates = rms * std::max(rtol, 1e-16) * 1e-3 >= 0x1p-76 && rms <= 0x1p90;
       scale = (float)(1.0 / rms);

@@ -124,10 +124,8 @@ class Multigrid {
   float* dhi_ = nullptr;
   float* dlo_ = nullptr;
   float* rlo_ = nullptr;
-  // double-float setup (mixed solver, rtol >= 1e-10): rhs b as hi + lo, the out-of-window flag,
-  // and the setup inputs kept for an FP64 redo
-  float* bhi_ = nullptr;
-  float* blo_ = nullptr;
+  // double-float setup (mixed solver, rtol >= 1e-10): the out-of-window flag and the setup inputs
+  // kept for an FP64 redo
   unsigned* df_flag_ = nullptr;
   bool df_mode_ = false;
   bool fp64_op_ = false;

@@ -1,7 +1,8 @@
-// Double-float setup of the mixed solver's finest level: face weights, diagonal, right-hand side
-// and the first outer residual, computed on the FP32 and integer pipes (see df.cuh) instead of in
-// FP64.  The mixed solver only ever consumes these quantities as hi + lo float pairs (the FP32
-// V-cycle takes the hi parts, the residual updates both), so no FP64 copy is made.
+// Double-float setup of the mixed solver's finest level: face weights, then the diagonal,
+// right-hand side and first outer residual in one pass, computed on the FP32 and integer pipes
+// (see df.cuh) instead of in FP64.  The mixed solver only ever consumes these quantities as hi + lo
+// float pairs (the FP32 V-cycle takes the hi parts, the residual updates both), so no FP64 copy is
+// made.
 //
 // The arithmetic is exponent-scaled where the physical values may leave the FP32 range (D in cgs
 // units): each face's D values are scaled by the same power of two before the harmonic mean and
@@ -130,17 +131,17 @@ __global__ void __launch_bounds__(256) k_faces_df(GridDev g, DfConst K, const do
   if (bad) atomicOr(flag, 1u);
 }
 
-// diag = 1 + sum of the face terms, b = E_old + boundary constants, 1/diag for the smoother, and
-// per-block sums of (b_hi 2^-30)^2 (scaled back by 2^60 in FP64 at the block level).  Whole x rows
-// per block iteration, 32-bit indices (the caller guarantees < 2^31 cells and faces per axis).
+// One face's share of the diagonal (diag = 1 + sum of the face terms) and of the boundary
+// constants of b: interior and periodic faces add w; a Dirichlet face adds w and w v to b; a
+// Neumann face (ghost = x -/+ g dx) moves the constant +/- w g dx to b; a continuous face
+// (linear extrapolation) subtracts w.
 __device__ __forceinline__ void setup_face(bool inside, int bc, int side, dfl w, dfl vb, dfl gdx, dfl& d, dfl& cst) {
   if (inside || bc == FLD_BC_PERIODIC) {
-    d = df_add(d, w);
+    d = df_add_pos(d, w);
   } else if (bc == FLD_BC_DIRICHLET) {
-    d = df_add(d, w);
+    d = df_add_pos(d, w);
     cst = df_add(cst, df_mul(w, vb));
   } else if (bc == FLD_BC_NEUMANN) {
-    // ghost = x -/+ g dx: the constant +/- w g dx moves to the right-hand side
     const dfl m = df_mul(w, gdx);
     cst = df_add(cst, side ? m : df_neg(m));
   } else {
@@ -148,61 +149,9 @@ __device__ __forceinline__ void setup_face(bool inside, int bc, int side, dfl w,
   }
 }
 
-__global__ void __launch_bounds__(256) k_fine_setup_df(GridDev g, DfConst K, LevelDev<float> L, LevelDev<float> Llo,
-                                                       const double* __restrict__ E_old, float* __restrict__ dhi,
-                                                       float* __restrict__ dlo, float* __restrict__ invd,
-                                                       float* __restrict__ bhi, float* __restrict__ blo,
-                                                       double* __restrict__ parts, unsigned* __restrict__ flag) {
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int rows = ny * nz;
-  float acc = 0.0f;
-  unsigned bad = 0u;
-  auto V = [&](int f) { return dfl{K.v_hi[f], K.v_lo[f]}; };
-  auto G = [&](int f) { return dfl{K.gdx_hi[f], K.gdx_lo[f]}; };
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int j = row % ny, k = row / ny;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const int idx = i + nx * row;
-      dfl d{1.0f, 0.0f}, cst{0.0f, 0.0f};
-      const int fx = i + (nx + 1) * row;
-      setup_face(i > 0, g.bc[0], 0, {L.w[0][fx], Llo.w[0][fx]}, V(0), G(0), d, cst);
-      setup_face(i < nx - 1, g.bc[1], 1, {L.w[0][fx + 1], Llo.w[0][fx + 1]}, V(1), G(1), d, cst);
-      if (g.ndim >= 2) {
-        const int fy = i + nx * (j + (ny + 1) * k);
-        setup_face(j > 0, g.bc[2], 0, {L.w[1][fy], Llo.w[1][fy]}, V(2), G(2), d, cst);
-        setup_face(j < ny - 1, g.bc[3], 1, {L.w[1][fy + nx], Llo.w[1][fy + nx]}, V(3), G(3), d, cst);
-      }
-      if (g.ndim == 3) {
-        const int fz = idx, sz = nx * ny;
-        setup_face(k > 0, g.bc[4], 0, {L.w[2][fz], Llo.w[2][fz]}, V(4), G(4), d, cst);
-        setup_face(k < nz - 1, g.bc[5], 1, {L.w[2][fz + sz], Llo.w[2][fz + sz]}, V(5), G(5), d, cst);
-      }
-      float eh, el;
-      bool ok;
-      split_f64_scaled(E_old[idx], 0, eh, el, ok);
-      if (!ok || !in_window(eh)) bad = 1u;
-      const dfl b = df_add({eh, el}, cst);
-      dhi[idx] = d.hi;
-      dlo[idx] = d.lo;
-      invd[idx] = __frcp_rn(d.hi);
-      bhi[idx] = b.hi;
-      blo[idx] = b.lo;
-      const float bs = scale2(b.hi, -30);
-      acc = fmaf(bs, bs, acc);
-    }
-  }
-  const double s = block_sum((double)acc);
-  if (threadIdx.x == 0) parts[blockIdx.x] = s * 0x1p60;
-  if (bad) atomicOr(flag, 1u);
-}
-
-// scal[4] = 1 / rms(b) = sqrt(N / ||b||^2), for the residual kernels' scaled sums
-__global__ void k_residual_scale(double* scal, double ncell) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) scal[4] = scal[1] > 0.0 ? sqrt(ncell / scal[1]) : 1.0;
-}
-
-// one face term of the first residual: sign (+1 interior/periodic, -1 extrapolated, 0 none) times
-// w x_nb, with x_nb split from the FP64 state; branch-free like wave_face
+// One face's term of the first residual: sign (+1 interior/periodic, -1 extrapolated, 0 none)
+// times w x_nb, with x_nb split from the FP64 state, summed into s + e (m: the sum of magnitudes);
+// branch-free like wave_face.
 __device__ __forceinline__ void df0_face(bool inside, int bc, int idx, int across, int wrap, int mirror, float whi,
                                          float wlo, const double* __restrict__ x, float& s, float& e, float& m) {
   const bool per = bc == FLD_BC_PERIODIC, cont = bc == FLD_BC_CONTINUOUS;
@@ -222,70 +171,98 @@ __device__ __forceinline__ void df0_face(bool inside, int bc, int idx, int acros
   m += fabsf(t);
 }
 
-// First outer residual of the mixed solver, r = b - A x with x = E_old (copied to the FP64
-// iterate x64), all in double-float; as k_residual_update otherwise (32-bit indices).
+// The finest level's set-up and the first outer residual of the mixed solver in one pass, in
+// double-float arithmetic: diag = 1 + sum of the face terms (hi, lo) and 1/diag for the smoother,
+// b = E_old + boundary constants (not stored), and r = b - A x with x = E_old, which is also copied
+// into the FP64 iterate x64 unless x64 is null.  Per-block sums: parts[0..n) = sum r_hi^2 in FP64,
+// parts[n..2n) = sum m^2 (m: the magnitudes of the residual's terms, for the drift bound of the
+// updates) and parts[2n..3n) = sum b_hi^2, both accumulated as (v 2^-30)^2 in FP32 and scaled
+// back by 2^60.  *flag |= 1 where E_old leaves the double-float window.  Whole x rows per block
+// iteration, 32-bit indices (the caller guarantees < 2^31 cells and faces per axis).
 template <int NDIM>
-__global__ void __launch_bounds__(256) k_residual0_df(LevelDev<float> L, LevelDev<float> Llo,
-                                                      const float* __restrict__ dhi, const float* __restrict__ dlo,
-                                                      const float* __restrict__ bhi, const float* __restrict__ blo,
-                                                      const double* __restrict__ x, double* __restrict__ x64,
-                                                      float* __restrict__ rhi, float* __restrict__ rlo,
-                                                      const double* __restrict__ scal, int nparts,
-                                                      double* __restrict__ parts) {
-  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+__global__ void __launch_bounds__(256) k_setup_res0_df(GridDev g, DfConst K, LevelDev<float> L, LevelDev<float> Llo,
+                                                       const double* __restrict__ x, double* __restrict__ x64,
+                                                       float* __restrict__ dhi, float* __restrict__ dlo,
+                                                       float* __restrict__ invd, float* __restrict__ rhi,
+                                                       float* __restrict__ rlo, int nparts, double* __restrict__ parts,
+                                                       unsigned* __restrict__ flag) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int rows = ny * nz, sy = nx, sz = nx * ny;
-  const float scale = (float)scal[4];
-  float ss = 0.f, mm = 0.f;
+  float acc_b = 0.f, acc_m = 0.f;
+  double acc_r = 0.0;
+  unsigned bad = 0u;
+  auto V = [&](int f) { return dfl{K.v_hi[f], K.v_lo[f]}; };
+  auto G = [&](int f) { return dfl{K.gdx_hi[f], K.gdx_lo[f]}; };
   for (int row = blockIdx.x; row < rows; row += gridDim.x) {
     const int j = row % ny, k = row / ny;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const int idx = i + nx * row;
       const double xc = x[idx];
-      if (x64 != x) x64[idx] = xc;
+      if (x64) x64[idx] = xc;
       float xh, xl;
-      split_f64(xc, xh, xl);
-      const float bh = bhi[idx];
-      // s + e = b - diag x
-      float p, pe, s, e;
-      const float dh = dhi[idx];
-      two_prod(dh, xh, p, pe);
-      pe = fmaf(dh, xl, pe);
-      pe = fmaf(dlo[idx], xh, pe);
-      two_sum(bh, -p, s, e);
-      e += blo[idx] - pe;
-      float m = fabsf(bh) + fabsf(p);
-      const int fx = i + (nx + 1) * row;
-      df0_face(i > 0, L.bc[0], idx, idx - 1, idx + (nx - 1), idx + 1, L.w[0][fx], Llo.w[0][fx], x, s, e, m);
-      df0_face(i < nx - 1, L.bc[1], idx, idx + 1, idx - (nx - 1), idx - 1, L.w[0][fx + 1], Llo.w[0][fx + 1], x, s,
-               e, m);
+      bool ok;
+      split_f64_scaled(xc, 0, xh, xl, ok);
+      if (!ok || !in_window(xh)) bad = 1u;
+      dfl d{1.0f, 0.0f}, cst{0.0f, 0.0f};
+      float s = 0.f, e = 0.f, m = 0.f;
+      {
+        const int fx = i + (nx + 1) * row;
+        const float w0h = L.w[0][fx], w0l = Llo.w[0][fx], w1h = L.w[0][fx + 1], w1l = Llo.w[0][fx + 1];
+        setup_face(i > 0, g.bc[0], 0, {w0h, w0l}, V(0), G(0), d, cst);
+        setup_face(i < nx - 1, g.bc[1], 1, {w1h, w1l}, V(1), G(1), d, cst);
+        df0_face(i > 0, g.bc[0], idx, idx - 1, idx + (nx - 1), idx + 1, w0h, w0l, x, s, e, m);
+        df0_face(i < nx - 1, g.bc[1], idx, idx + 1, idx - (nx - 1), idx - 1, w1h, w1l, x, s, e, m);
+      }
       if (NDIM >= 2) {
         const int fy = i + nx * (j + (ny + 1) * k);
-        df0_face(j > 0, L.bc[2], idx, idx - sy, idx + (ny - 1) * sy, idx + sy, L.w[1][fy], Llo.w[1][fy], x, s, e, m);
-        df0_face(j < ny - 1, L.bc[3], idx, idx + sy, idx - (ny - 1) * sy, idx - sy, L.w[1][fy + nx],
-                 Llo.w[1][fy + nx], x, s, e, m);
+        const float w0h = L.w[1][fy], w0l = Llo.w[1][fy], w1h = L.w[1][fy + nx], w1l = Llo.w[1][fy + nx];
+        setup_face(j > 0, g.bc[2], 0, {w0h, w0l}, V(2), G(2), d, cst);
+        setup_face(j < ny - 1, g.bc[3], 1, {w1h, w1l}, V(3), G(3), d, cst);
+        df0_face(j > 0, g.bc[2], idx, idx - sy, idx + (ny - 1) * sy, idx + sy, w0h, w0l, x, s, e, m);
+        df0_face(j < ny - 1, g.bc[3], idx, idx + sy, idx - (ny - 1) * sy, idx - sy, w1h, w1l, x, s, e, m);
       }
       if (NDIM == 3) {
-        df0_face(k > 0, L.bc[4], idx, idx - sz, idx + (nz - 1) * sz, idx + sz, L.w[2][idx], Llo.w[2][idx], x, s, e,
-                 m);
-        df0_face(k < nz - 1, L.bc[5], idx, idx + sz, idx - (nz - 1) * sz, idx - sz, L.w[2][idx + sz],
-                 Llo.w[2][idx + sz], x, s, e, m);
+        const float w0h = L.w[2][idx], w0l = Llo.w[2][idx], w1h = L.w[2][idx + sz], w1l = Llo.w[2][idx + sz];
+        setup_face(k > 0, g.bc[4], 0, {w0h, w0l}, V(4), G(4), d, cst);
+        setup_face(k < nz - 1, g.bc[5], 1, {w1h, w1l}, V(5), G(5), d, cst);
+        df0_face(k > 0, g.bc[4], idx, idx - sz, idx + (nz - 1) * sz, idx + sz, w0h, w0l, x, s, e, m);
+        df0_face(k < nz - 1, g.bc[5], idx, idx + sz, idx - (nz - 1) * sz, idx - sz, w1h, w1l, x, s, e, m);
       }
+      const dfl b = df_add({xh, xl}, cst);
+      // r = b - diag x + (s + e)
+      float p, pe;
+      two_prod(d.hi, xh, p, pe);
+      pe = fmaf(d.hi, xl, pe);
+      pe = fmaf(d.lo, xh, pe);
+      float s1, e1, s2, e2;
+      two_sum(b.hi, -p, s1, e1);
+      two_sum(s1, s, s2, e2);
       float rh, rl;
-      quick_two_sum(s, e, rh, rl);
+      quick_two_sum(s2, ((e1 + e2) + (e + b.lo)) - pe, rh, rl);
+      m += fabsf(b.hi) + fabsf(p);
+      dhi[idx] = d.hi;
+      dlo[idx] = d.lo;
+      invd[idx] = __frcp_rn(d.hi);
       rhi[idx] = rh;
       rlo[idx] = rl;
-      const float rs = rh * scale, ms = m * scale;
-      ss = fmaf(rs, rs, ss);
-      mm = fmaf(ms, ms, mm);
+      const float bs = scale2(b.hi, -30), ms = scale2(m, -30);
+      acc_b = fmaf(bs, bs, acc_b);
+      acc_m = fmaf(ms, ms, acc_m);
+      const double rd = f32_to_f64(rh);
+      acc_r = fma(rd, rd, acc_r);
     }
   }
-  const double bs = block_sum((double)ss);
+  const double sr = block_sum(acc_r);
   __syncthreads();  // block_sum's shared scratch is reused
-  const double bm = block_sum((double)mm);
+  const double sm = block_sum((double)acc_m);
+  __syncthreads();
+  const double sb = block_sum((double)acc_b);
   if (threadIdx.x == 0) {
-    parts[blockIdx.x] = bs;
-    parts[nparts + blockIdx.x] = bm;
+    parts[blockIdx.x] = sr;
+    parts[nparts + blockIdx.x] = sm * 0x1p60;
+    parts[2 * nparts + blockIdx.x] = sb * 0x1p60;
   }
+  if (bad) atomicOr(flag, 1u);
 }
 
 // ----------------------------------------------------------------------------- launchers
@@ -312,27 +289,19 @@ cudaError_t launch_faces_df(const GridDev& g, const DfConst& K, const double* D,
   return cudaGetLastError();
 }
 
-cudaError_t launch_fine_setup_df(const GridDev& g, const DfConst& K, const LevelDev<float>& L,
-                                 const LevelDev<float>& Llo, const double* E_old, float* dhi, float* dlo, float* invd,
-                                 float* bhi, float* blo, double* parts, int nparts, double* scal, unsigned* flag,
-                                 cudaStream_t s) {
-  TraceScope ts("fine_setup", s);
-  k_fine_setup_df<<<nparts, 256, 0, s>>>(g, K, L, Llo, E_old, dhi, dlo, invd, bhi, blo, parts, flag);
-  k_reduce<<<1, 1024, 0, s>>>(parts, nparts, scal + 1);
-  k_residual_scale<<<1, 32, 0, s>>>(scal, (double)g.ncell);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_residual0_df(int ndim, const LevelDev<float>& L, const LevelDev<float>& Llo, const float* dhi,
-                                const float* dlo, const float* bhi, const float* blo, const double* x, double* x64,
-                                float* rhi, float* rlo, const double* scal, int nparts, double* parts,
-                                cudaStream_t s) {
-  if (ndim == 3)
-    k_residual0_df<3><<<nparts, 256, 0, s>>>(L, Llo, dhi, dlo, bhi, blo, x, x64, rhi, rlo, scal, nparts, parts);
-  else if (ndim == 2)
-    k_residual0_df<2><<<nparts, 256, 0, s>>>(L, Llo, dhi, dlo, bhi, blo, x, x64, rhi, rlo, scal, nparts, parts);
+cudaError_t launch_setup_res0_df(const GridDev& g, const DfConst& K, const LevelDev<float>& L,
+                                 const LevelDev<float>& Llo, const double* x, double* x64, float* dhi, float* dlo,
+                                 float* invd, float* rhi, float* rlo, int nparts, double* parts, double* scal,
+                                 unsigned* flag, cudaStream_t s) {
+  if (g.ndim == 3)
+    k_setup_res0_df<3><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
+  else if (g.ndim == 2)
+    k_setup_res0_df<2><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
   else
-    k_residual0_df<1><<<nparts, 256, 0, s>>>(L, Llo, dhi, dlo, bhi, blo, x, x64, rhi, rlo, scal, nparts, parts);
+    k_setup_res0_df<1><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
+  k_reduce<<<1, 1024, 0, s>>>(parts, nparts, scal);
+  k_reduce<<<1, 1024, 0, s>>>(parts + nparts, nparts, scal + 2);
+  k_reduce<<<1, 1024, 0, s>>>(parts + 2 * nparts, nparts, scal + 1);
   return cudaGetLastError();
 }
 

@@ -23,19 +23,13 @@ DfConst make_df_const(const GridDev& g, double dt);
 cudaError_t launch_faces_df(const GridDev& g, const DfConst& K, const double* D, float* const w[3],
                             float* const wlo[3], unsigned* flag, cudaStream_t s);
 
-// diagonal (hi, lo), 1/diag, right-hand side b (hi, lo) and ||b||^2 into scal[1], 1/rms(b) into
-// scal[4]
-cudaError_t launch_fine_setup_df(const GridDev& g, const DfConst& K, const LevelDev<float>& L,
-                                 const LevelDev<float>& Llo, const double* E_old, float* dhi, float* dlo, float* invd,
-                                 float* bhi, float* blo, double* parts, int nparts, double* scal, unsigned* flag,
-                                 cudaStream_t s);
-
-// r = b - A x (hi, lo) with x = E_old copied into x64; parts[0..nparts) = sum (scal[4] r)^2,
-// parts[nparts..2 nparts) = the error measure's squares
-cudaError_t launch_residual0_df(int ndim, const LevelDev<float>& L, const LevelDev<float>& Llo, const float* dhi,
-                                const float* dlo, const float* bhi, const float* blo, const double* x, double* x64,
-                                float* rhi, float* rlo, const double* scal, int nparts, double* parts,
-                                cudaStream_t s);
+// diagonal (hi, lo) and 1/diag of the finest level, and the first outer residual r = b - A x
+// (hi, lo) with x = E_old, copied into x64 unless it is null; scal[0] = ||r||^2, scal[1] = ||b||^2,
+// scal[2] = the squared error measure of r's terms.  parts holds 3 nparts doubles.
+cudaError_t launch_setup_res0_df(const GridDev& g, const DfConst& K, const LevelDev<float>& L,
+                                 const LevelDev<float>& Llo, const double* x, double* x64, float* dhi, float* dlo,
+                                 float* invd, float* rhi, float* rlo, int nparts, double* parts, double* scal,
+                                 unsigned* flag, cudaStream_t s);
 
 // defined in mg.cu
 __global__ void k_reduce(const double* __restrict__ parts, int n, double* __restrict__ out);
