@@ -46,19 +46,22 @@ KERNEL_MODEL = {
     "wave_L0_update": {"bound": "hbm", "bytes_f32": 4 + 12 + 4 + 4 + 16, "bytes_f64": 8 + 24 + 8 + 8 + 8 + 16},
     "restrict_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 3 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 3 * 8 + 8 / 8},
     "prolong_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
-    # FP64 outer residual r = b - d x + sum_6 w x_nb, and r^2: 7 FMA + 1 FMA
-    "residual": {"bound": "alu", "flops": 16},
+    # first outer residual.  Mixed: one double-float pass that also builds the diagonal: weights hi
+    # and lo (24), E_old (8), the FP64 iterate's copy (8), diagonal hi and lo and 1/diag (12), r hi
+    # and lo (8).  FP64: r = b - d x + sum_6 w x_nb from w (24), x, b, diag (24), r (8)
+    "residual": {"bound": "hbm", "bytes_f32": 24 + 8 + 8 + 12 + 8, "bytes_f64": 24 + 24 + 8},
     # mixed solver's double-float residual update r -= A d and x += d: d (4, neighbours from cache), r hi/lo
     # in and out (16), weights hi and lo (24), diagonal hi and lo (8), the FP64 iterate (16)
     "residual_update": {"bound": "hbm", "bytes_f32": 4 + 16 + 24 + 8 + 16, "bytes_f64": 4 + 16 + 24 + 8 + 16},
-    # opacity (10), 5-point gradient in 3 axes (21), limiter and D (14)
-    "coeffs": {"bound": "alu", "flops": 45},
-    # three harmonic means sharing one reciprocal, times dt/dx^2
-    "faces": {"bound": "alu", "flops": 27},
-    # coefficients of the rescaled quartic (24), two FP64 polish steps (14), E update (6)
-    "exchange": {"bound": "alu", "flops": 44},
-    # diagonal 1 + sum of 6 faces, rhs copy
-    "fine_setup": {"bound": "alu", "flops": 7},
+    # E, rho, eps in; kappa and D out (double-float arithmetic on the FP32 pipe: issue-bound, far
+    # below this bound)
+    "coeffs": {"bound": "hbm", "bytes_f32": 40, "bytes_f64": 40},
+    # D in; weights out (mixed: hi and lo floats; FP64: doubles and their FP32 copies)
+    "faces": {"bound": "hbm", "bytes_f32": 8 + 24, "bytes_f64": 8 + 24 + 12},
+    # rho, kappa, eps, E in; eps, E out (double-float, issue-bound like coeffs)
+    "exchange": {"bound": "hbm", "bytes_f32": 48, "bytes_f64": 48},
+    # FP64 operator set-up: weights (24) and E_old (8) in; b, diag (16), 1/diag and diag hi/lo (12) out
+    "fine_setup": {"bound": "hbm", "bytes_f32": 24 + 8 + 16 + 12, "bytes_f64": 24 + 8 + 16 + 16},
 }
 # launches per traced scope (some scopes hold several kernels)
 SCOPE_KERNELS = {"faces": 3, "coarse_setup": 4, "norm_b": 2}
@@ -386,7 +389,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64+f32 (FP32 V-cycles, FP64 residual/update/norm/exchange)" if args.precision == "mixed"
+                "dtype": "f64+f32 (FP32 V-cycles; coefficients, weights, residuals and exchange in double-float "
+                         "f32 pairs; FP64 iterate and norms)" if args.precision == "mixed"
                 else "f64",
                 "data": "synthetic", "config": workload_config(args, (infos[0]["nu1"], infos[0]["nu2"], infos[0]["nu1_coarse"],
                                                                  infos[0]["nu2_coarse"])), "roofline": roof,
