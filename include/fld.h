@@ -192,7 +192,7 @@ FLD_API fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params
 /* fld_step on `ngrids` independent grids with their own sizes, parameters and time steps.
    grids, params and dt are HOST arrays of length ngrids; rho/eps/E are HOST arrays of DEVICE
    pointers; infos (may be NULL) receives one fld_info per grid.  Every grid must have ndim 2
-   or 3.  Synchronises. */
+   or 3 and fewer than 2^31 cells (FLD_ERR_INVALID_ARG otherwise).  Synchronises. */
 FLD_API fld_status fld_step_batched(fld_ctx* ctx, int ngrids, const fld_grid* grids,
                             const fld_params* params, const double* dt, const double* const* rho,
                             double* const* eps, double* const* E, fld_info* infos, void* stream);

@@ -47,6 +47,7 @@ struct Tile {
 struct BFine {
   GridDev g;
   CoeffPhys ph;
+  CoeffDf cdf;  // constants of the double-float coefficient path
   ExchangeParams xp;
   double dt;
   int order;
@@ -127,7 +128,7 @@ __global__ void kb_exchange(const Tile* __restrict__ tiles, const BFine* __restr
     double r = f.rho[idx], e = f.eps[idx], En = f.E[idx];
     double k = phase == 0 ? opacity(f.ph.op, r, temperature(f.ph.gamma, f.ph.gas_R, r, e)) : f.kappa[idx];
     int it = 0, bi = 0;
-    if (exchange_cell(f.xp, r, k, e, En, it, bi)) {
+    if (exchange_cell_fast(f.xp, r, k, e, En, it, bi)) {
       f.eps[idx] = e;
       f.E[idx] = En;
     } else {
@@ -147,7 +148,10 @@ __global__ void kb_coeffs(const Tile* __restrict__ tiles, const BFine* __restric
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
     long long idx = tl.start + c;
     double kap, D;
-    if (!coeffs_cell(f.g, f.ph, f.E, f.rho, f.eps, idx, kap, D)) bad = true;
+    const int ic = (int)idx, r = ic / f.g.n[0];  // a grid of the batch has fewer than 2^31 cells
+    if (!coeffs_cell_fast(f.g, f.ph, f.cdf, f.E, f.rho, f.eps, idx, ic - r * f.g.n[0], r % f.g.n[1], r / f.g.n[1], kap,
+                          D))
+      bad = true;
     f.kappa[idx] = kap;
     f.D[idx] = D;
   }
@@ -757,6 +761,7 @@ cudaError_t BatchedSolver::Impl::upload(const fld_params* params, const double* 
     f.ph.gamma = p.gamma;
     f.ph.gas_R = p.gas_R;
     f.ph.limiter = p.limiter;
+    f.cdf = make_coeff_df(f.ph, f.g);
     f.xp = make_exchange(p.c, p.a_rad, p.gamma, p.gas_R, dt[g], p.exch_maxit > 0 ? p.exch_maxit : 100);
     f.dt = dt[g];
     f.order = p.order;

@@ -556,6 +556,8 @@ fld_status fld_step_batched(fld_ctx* ctx, int ngrids, const fld_grid* grids, con
     if (st == FLD_OK) st = check_coarsest(ctx, &grids[i]);
     if (st != FLD_OK) return fail(ctx, st, "grid %d: %s", i, std::string(ctx->err).c_str());
     if (grids[i].ndim < 2) return fail(ctx, FLD_ERR_INVALID_ARG, "grid %d: batched grids need ndim 2 or 3", i);
+    if ((long long)grids[i].n[0] * grids[i].n[1] * grids[i].n[2] >= (1LL << 31))
+      return fail(ctx, FLD_ERR_INVALID_ARG, "grid %d: batched grids hold fewer than 2^31 cells", i);
     if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(ctx, FLD_ERR_INVALID_ARG, "grid %d: dt must be > 0", i);
     if (!rho[i] || !eps[i] || !E[i]) return fail(ctx, FLD_ERR_INVALID_ARG, "grid %d: NULL device array", i);
   }

@@ -275,7 +275,7 @@ __global__ void k_columns(ColArgs A) {
     for (int i = s0; i < s1; ++i) {
       double e = se[i], E = sx[i];
       double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
-      if (exchange_cell(xp1, sr[i], k, e, E, iters, bis)) {
+      if (exchange_cell_fast(xp1, sr[i], k, e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
       } else {
@@ -494,7 +494,7 @@ __global__ void k_columns(ColArgs A) {
   if (MODE == kColStep) {
     for (int i = s0; i < s1; ++i) {
       double e = se[i], E = sx[i];
-      if (exchange_cell(xp, sr[i], sk[i], e, E, iters, bis)) {
+      if (exchange_cell_fast(xp, sr[i], sk[i], e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
       } else {
@@ -509,7 +509,7 @@ __global__ void k_columns(ColArgs A) {
       double E = fma(2.0, sx[i] - sh[i], A.Ein[base + i]);
       double e = A.eps[base + i];
       double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
-      if (exchange_cell(xp, sr[i], k, e, E, iters, bis)) {
+      if (exchange_cell_fast(xp, sr[i], k, e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
       } else {

@@ -354,13 +354,14 @@ __global__ void k_prolong(std::array<int, 3> nf, int ndim, const T* __restrict__
 // memory: the sweeps are a chain of block barriers, and each round trip through global memory
 // would otherwise set their pace.
 template <class T>
-__global__ void __launch_bounds__(512) k_coarse_solve(LevelDev<T> L, long long ncell, const T* __restrict__ invd,
+__global__ void __launch_bounds__(512, 1) k_coarse_solve(LevelDev<T> L, long long ncell, const T* __restrict__ invd,
                                                       const T* __restrict__ r, T* __restrict__ x, T* __restrict__ tmp,
                                                       int sweeps, int use_rb, int in_smem) {
   extern __shared__ __align__(16) unsigned char coarse_smem[];
   if (in_smem) {
     T* xs = reinterpret_cast<T*>(coarse_smem);
-    coarse_solve_block<T>(L, ncell, invd, r, xs, xs + ncell, sweeps, use_rb);
+    if (ncell <= (long long)blockDim.x) coarse_solve_small<T>(L, (int)ncell, invd, r, xs, xs + ncell, sweeps, use_rb);
+    else coarse_solve_block<T>(L, ncell, invd, r, xs, xs + ncell, sweeps, use_rb);
     __syncthreads();
     for (long long c = threadIdx.x; c < ncell; c += blockDim.x) x[c] = xs[c];
   } else {

@@ -289,4 +289,88 @@ __device__ __forceinline__ void coarse_solve_block(const LevelDev<T>& L, long lo
   }
 }
 
+// coarse_solve_block for a level of at most one cell per thread (xs and ts in shared memory):
+// each thread gathers its cell's stencil once -- right-hand side, 1/diag, and for each face the
+// signed weight (+w across interior and periodic faces, -w for the extrapolated neighbour of a
+// continuous face, 0 otherwise) and the neighbour's index -- so that a sweep is six shared-memory
+// reads and FMAs per cell between barriers.  The terms and their order are those of
+// for_each_face, so the iterates equal coarse_solve_block's.
+template <class T>
+__device__ __forceinline__ void coarse_solve_small(const LevelDev<T>& L, int ncell, const T* __restrict__ invd,
+                                                   const T* __restrict__ r, T* xs, T* ts, int sweeps, int use_rb) {
+  const int c = threadIdx.x;
+  const bool act = c < ncell;
+  T cw[6], rv = T(0), id = T(0);
+  int nb[6], par = 0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    cw[f] = T(0);
+    nb[f] = act ? c : 0;
+  }
+  if (act) {
+    int i, j, k;
+    unflatten(L.n, c, i, j, k);
+    par = (i + j + k) & 1;
+    rv = r[c];
+    id = invd[c];
+    const int q[3] = {i, j, k};
+    int stride = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < L.ndim) {
+        const int n = L.n[a], p = q[a];
+        const T wl = L.w[a][face_index(L.n, a, i, j, k, p)];
+        const T wu = L.w[a][face_index(L.n, a, i, j, k, p + 1)];
+        const int bl = L.bc[2 * a], bu = L.bc[2 * a + 1];
+        if (p > 0) {
+          cw[2 * a] = wl;
+          nb[2 * a] = c - stride;
+        } else if (bl == FLD_BC_PERIODIC) {
+          cw[2 * a] = wl;
+          nb[2 * a] = c + (n - 1) * stride;
+        } else if (bl == FLD_BC_CONTINUOUS) {
+          cw[2 * a] = -wl;
+          nb[2 * a] = c + stride;
+        }
+        if (p < n - 1) {
+          cw[2 * a + 1] = wu;
+          nb[2 * a + 1] = c + stride;
+        } else if (bu == FLD_BC_PERIODIC) {
+          cw[2 * a + 1] = wu;
+          nb[2 * a + 1] = c - (n - 1) * stride;
+        } else if (bu == FLD_BC_CONTINUOUS) {
+          cw[2 * a + 1] = -wu;
+          nb[2 * a + 1] = c - stride;
+        }
+        stride *= n;
+      }
+    }
+    xs[c] = T(0);
+  }
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s) {
+    if (use_rb) {
+      for (int color = 0; color < 2; ++color) {
+        if (act && par == color) {
+          T v = rv;
+#pragma unroll
+          for (int f = 0; f < 6; ++f) v += cw[f] * xs[nb[f]];
+          xs[c] = v * id;
+        }
+        __syncthreads();
+      }
+    } else {
+      if (act) {
+        T v = rv;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) v += cw[f] * xs[nb[f]];
+        ts[c] = T(0.2) * xs[c] + T(0.8) * v * id;
+      }
+      __syncthreads();
+      if (act) xs[c] = ts[c];
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace fld
