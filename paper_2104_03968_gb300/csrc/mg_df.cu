@@ -58,8 +58,8 @@ __device__ __forceinline__ dfl face_weight_df(dfl c, int sh, double Dn, bool pai
 }  // namespace
 
 // Whole x rows per block iteration, 32-bit indices (the caller guarantees < 2^31 cells and faces
-// per axis).
-__global__ void __launch_bounds__(256) k_faces_df(GridDev g, DfConst K, const double* __restrict__ D,
+// per axis); eight blocks of 256 per SM (32 registers).
+__global__ void __launch_bounds__(256, 8) k_faces_df(GridDev g, DfConst K, const double* __restrict__ D,
                                                   float* __restrict__ w0, float* __restrict__ w1,
                                                   float* __restrict__ w2, float* __restrict__ l0,
                                                   float* __restrict__ l1, float* __restrict__ l2,
