@@ -107,6 +107,39 @@ __global__ void k_coarse_faces(int a, int ndim, std::array<int, 3> nf, std::arra
   wc[idx] = coarse_face_value<T>(a, ndim, nf.data(), m, idx, wf);
 }
 
+// The same two kernels with 32-bit indices, the coordinates from divisions by invariant divisors
+// (levels whose faces number fewer than 2^31 per axis); the face sum is taken in the same order.
+template <class T>
+__global__ void k_coarse_faces32(int a, int ndim, std::array<int, 3> nf, FastDiv d0, FastDiv d1, unsigned nfaces,
+                                 const T* __restrict__ wf, T* __restrict__ wc) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nfaces) return;
+  const unsigned r = fast_div(idx, d0), q2 = fast_div(r, d1);
+  const int q[3] = {(int)(idx - r * d0.d), (int)(r - q2 * d1.d), (int)q2};
+  int mf[3] = {nf[0], nf[1], nf[2]};
+  mf[a] += 1;
+  const int o1max = (ndim > 1) ? 2 : 1, o2max = (ndim > 2) ? 2 : 1;
+  const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;  // the transverse axes
+  T sum = T(0);
+  for (int o2 = 0; o2 < o2max; ++o2)
+    for (int o1 = 0; o1 < o1max; ++o1) {
+      int f[3];
+      f[a] = 2 * q[a];
+      f[t1] = (t1 < ndim) ? 2 * q[t1] + o1 : q[t1];
+      f[t2] = (t2 < ndim) ? 2 * q[t2] + o2 : q[t2];
+      sum += wf[f[0] + mf[0] * (f[1] + mf[1] * f[2])];
+    }
+  wc[idx] = sum / (T)(4 * o1max * o2max);
+}
+
+template <class T>
+__global__ void k_invd32(LevelDev<T> L, FastDiv d0, FastDiv d1, unsigned ncell, T* __restrict__ invd) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ncell) return;
+  const unsigned r = fast_div(idx, d0), k = fast_div(r, d1);
+  invd[idx] = T(1) / diag_of(L, (int)(idx - r * d0.d), (int)(r - k * d1.d), (int)k, idx);
+}
+
 // ----------------------------------------------------------------------------- cycle kernels
 
 template <class T>
@@ -330,15 +363,19 @@ __global__ void __launch_bounds__(256) k_restrict_rows(LevelDev<T> F, const T* _
   }
 }
 
-// xf += P xc (piecewise constant), one fine row per block iteration
-template <class T, int NDIM>
+// xf += P xc (piecewise constant), or xf = P xc with ASSIGN (the FMG's start on a finer level),
+// one fine row per block iteration
+template <class T, int NDIM, bool ASSIGN = false>
 __global__ void __launch_bounds__(256) k_prolong_rows(int nx, int ny, int rows, const T* __restrict__ xc, int ncy,
                                                       T* __restrict__ xf) {
   const int ncx = nx >> 1;
   for (int row = blockIdx.x; row < rows; row += gridDim.x) {
     const int j = row % ny, k = row / ny;
     const int crow = NDIM == 3 ? (j >> 1) + ncy * (k >> 1) : (NDIM == 2 ? (j >> 1) : 0);
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) xf[i + nx * row] += xc[(i >> 1) + ncx * crow];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      if (ASSIGN) xf[i + nx * row] = xc[(i >> 1) + ncx * crow];
+      else xf[i + nx * row] += xc[(i >> 1) + ncx * crow];
+    }
   }
 }
 
@@ -800,11 +837,24 @@ cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const d
   }
   for (size_t l = 1; l < dims_.size(); ++l) {
     TraceScope ts("coarse_setup", s);
-    for (int a = 0; a < g_.ndim; ++a)
-      k_coarse_faces<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(a, g_.ndim, dims_[l - 1], dims_[l],
-                                                                      (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
+    for (int a = 0; a < g_.ndim; ++a) {
+      std::array<int, 3> m = dims_[l];
+      m[a] += 1;
+      if (faces3(dims_[l - 1], a) < (1LL << 31))
+        k_coarse_faces32<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(
+            a, g_.ndim, dims_[l - 1], make_fastdiv((unsigned)m[0]), make_fastdiv((unsigned)m[1]),
+            (unsigned)faces3(dims_[l], a), (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
+      else
+        k_coarse_faces<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(a, g_.ndim, dims_[l - 1], dims_[l],
+                                                                        (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
+    }
     LevelDev<T> L = level_dev<T>(g_, dims_[l], lv_[l].w);
-    k_invd<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, cells3(dims_[l]), (T*)lv_[l].invd);
+    if (cells3(dims_[l]) < (1LL << 31))
+      k_invd32<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, make_fastdiv((unsigned)dims_[l][0]),
+                                                             make_fastdiv((unsigned)dims_[l][1]),
+                                                             (unsigned)cells3(dims_[l]), (T*)lv_[l].invd);
+    else
+      k_invd<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, cells3(dims_[l]), (T*)lv_[l].invd);
   }
   return cudaGetLastError();
 }
@@ -984,9 +1034,18 @@ cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
     T* x = (T*)lv_[l].x;
     {
       TraceScope ts(l == 0 ? "prolong_L0" : "prolong_Lc", s);
-      e = cudaMemsetAsync(x, 0, cells3(n) * sizeof(T), s);
-      if (e != cudaSuccess) return e;
-      k_prolong<T><<<nblk(cells3(n)), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
+      if (rows_ok(l)) {
+        const int rows = n[1] * n[2];
+        const unsigned gr = (unsigned)std::min(rows, 152 * 16);
+        if (g_.ndim == 3)
+          k_prolong_rows<T, 3, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+        else
+          k_prolong_rows<T, 2, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+      } else {
+        e = cudaMemsetAsync(x, 0, cells3(n) * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+        k_prolong<T><<<nblk(cells3(n)), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
+      }
     }
     e = vcycle<T>(l, l == 0 ? nu1 : nuc1_, l == 0 ? nu2 : nuc2_, l == 0 ? x64 : nullptr, s, false);
     if (e != cudaSuccess) return e;
