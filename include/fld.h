@@ -121,7 +121,11 @@ typedef struct {
   double tlo[2], thi[2];
   /* solver */
   int precision;   /* FLD_PREC_FP64: FP64 multigrid.  FLD_PREC_MIXED: FP32 V-cycles inside
-                      an FP64 defect-correction loop (FP64 residual, update and norm) */
+                      a defect-correction loop whose residuals, updates and norms are FP64-grade:
+                      double-float (pairs of floats, ~2^-46 relative) with a certified error
+                      bound, FP64 where values leave the double-float range or rtol < 1e-10.
+                      Both precisions compute the coefficients and the exchange in double-float
+                      with FP64 fallback per cell. */
   double rtol;     /* stop when ||b - A E||_2 / ||b||_2 <= rtol */
   int max_cycles;  /* outer iterations (one V-cycle each); 0 = 100 */
   int nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after coarse correction.  Both 0:
