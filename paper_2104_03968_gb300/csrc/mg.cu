@@ -381,6 +381,40 @@ __global__ void __launch_bounds__(256) k_prolong_rows(int nx, int ny, int rows, 
   }
 }
 
+// The same for FP32 levels with nx a multiple of 4: each thread takes four fine cells (one float4
+// of xf from one float2 of xc) and four such quads per iteration, loads first, so that the memory
+// accesses are wide and several are in flight.  32-bit indices (rows * nx < 2^31).
+template <int NDIM, bool ASSIGN>
+__global__ void __launch_bounds__(256) k_prolong_rows4(int nx, int ny, int rows, const float* __restrict__ xc,
+                                                       int ncy, float* __restrict__ xf) {
+  constexpr int U = 4;
+  const int nq = nx >> 2, ncx = nx >> 1;
+  const int total = rows * nq;
+  const int stride = (int)(gridDim.x * blockDim.x);
+  for (int q0 = (int)(blockIdx.x * blockDim.x + threadIdx.x); q0 < total; q0 += U * stride) {
+    float2 c[U];
+    float4 f[U];
+    int row[U], iq[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = min(q0 + u * stride, total - 1);
+      row[u] = q / nq;
+      iq[u] = q - row[u] * nq;
+      const int j = row[u] % ny, k = row[u] / ny;
+      const int crow = NDIM == 3 ? (j >> 1) + ncy * (k >> 1) : (j >> 1);
+      c[u] = reinterpret_cast<const float2*>(xc + ncx * crow)[iq[u]];
+      if (!ASSIGN) f[u] = reinterpret_cast<const float4*>(xf + nx * row[u])[iq[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (q0 + u * stride >= total) continue;
+      float4 v = make_float4(c[u].x, c[u].x, c[u].y, c[u].y);
+      if (!ASSIGN) v = make_float4(f[u].x + v.x, f[u].y + v.y, f[u].z + v.z, f[u].w + v.w);
+      reinterpret_cast<float4*>(xf + nx * row[u])[iq[u]] = v;
+    }
+  }
+}
+
 template <class T>
 __global__ void k_prolong(std::array<int, 3> nf, int ndim, const T* __restrict__ xc, std::array<int, 3> nc,
                           T* __restrict__ xf) {
@@ -981,8 +1015,15 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     if (rows_ok(l)) {
       const int rows = n[1] * n[2];
       const unsigned gr = (unsigned)std::min(rows, 152 * 16);
-      if (g_.ndim == 3) k_prolong_rows<T, 3><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
-      else k_prolong_rows<T, 2><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+      if (sizeof(T) == sizeof(float) && n[0] % 4 == 0) {
+        const float* xc = (const float*)lv_[l + 1].x;
+        if (g_.ndim == 3) k_prolong_rows4<3, false><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+        else k_prolong_rows4<2, false><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+      } else if (g_.ndim == 3) {
+        k_prolong_rows<T, 3><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+      } else {
+        k_prolong_rows<T, 2><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+      }
     } else {
       k_prolong<T><<<nblk(ncell), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
     }
@@ -1039,10 +1080,15 @@ cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
       if (rows_ok(l)) {
         const int rows = n[1] * n[2];
         const unsigned gr = (unsigned)std::min(rows, 152 * 16);
-        if (g_.ndim == 3)
+        if (sizeof(T) == sizeof(float) && n[0] % 4 == 0) {
+          const float* xc = (const float*)lv_[l + 1].x;
+          if (g_.ndim == 3) k_prolong_rows4<3, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+          else k_prolong_rows4<2, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+        } else if (g_.ndim == 3) {
           k_prolong_rows<T, 3, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
-        else
+        } else {
           k_prolong_rows<T, 2, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+        }
       } else {
         e = cudaMemsetAsync(x, 0, cells3(n) * sizeof(T), s);
         if (e != cudaSuccess) return e;
