@@ -132,6 +132,38 @@ __global__ void k_coarse_faces32(int a, int ndim, std::array<int, 3> nf, FastDiv
   wc[idx] = sum / (T)(4 * o1max * o2max);
 }
 
+// Faces of a transverse axis a (1 or 2) for FP32 levels with the fine nx a multiple of 4: each
+// thread averages two adjacent coarse faces (I, I+1) from one float4 of fine faces per fine row
+// (2 rows in 2-D, 4 in 3-D); coarse faces of axis a are rows of ncx values, fine ones rows of nx.
+// d1 divides the coarse face row index by the coarse rows per plane of the axis's face layout.
+template <int NDIM>
+__global__ void k_coarse_faces_t4(int a, std::array<int, 3> nf, int ncx, FastDiv d1, unsigned npairs,
+                                  const float* __restrict__ wf, float* __restrict__ wc) {
+  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const int nph = ncx >> 1;                     // pairs per coarse row
+  const unsigned crow = p / (unsigned)nph;      // coarse face row: J + m1 * K in the face layout
+  const int I2 = 2 * (int)(p - crow * (unsigned)nph);  // first of the two coarse faces
+  const unsigned K = fast_div(crow, d1), J = crow - K * d1.d;
+  // fine face layout of axis a: x fastest, then the axis-1 index (ny + 1 faces for a = 1), then z
+  const int m1 = a == 1 ? nf[1] + 1 : nf[1];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int o1n = a == 1 ? 1 : 2, o2n = (NDIM == 3 && a == 1) ? 2 : 1;
+  for (int o2 = 0; o2 < o2n; ++o2)
+    for (int o1 = 0; o1 < o1n; ++o1) {
+      // a = 1: fine (2I.., 2J, 2K + o2); a = 2: fine (2I.., 2J + o1, 2K)
+      const int fj = a == 1 ? 2 * (int)J : 2 * (int)J + o1;
+      const int fk = a == 1 ? (NDIM == 3 ? 2 * (int)K + o2 : 0) : 2 * (int)K;
+      const float4 v = *reinterpret_cast<const float4*>(wf + 2 * I2 + nf[0] * (fj + m1 * fk));
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+  const float inv = 1.0f / (float)(4 * 2 * o1n * o2n);
+  *reinterpret_cast<float2*>(wc + I2 + ncx * crow) = make_float2((acc.x + acc.y) * inv, (acc.z + acc.w) * inv);
+}
+
 template <class T>
 __global__ void k_invd32(LevelDev<T> L, FastDiv d0, FastDiv d1, unsigned ncell, T* __restrict__ invd) {
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -876,7 +908,18 @@ cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const d
     for (int a = 0; a < g_.ndim; ++a) {
       std::array<int, 3> m = dims_[l];
       m[a] += 1;
-      if (faces3(dims_[l - 1], a) < (1LL << 31))
+      const bool small = faces3(dims_[l - 1], a) < (1LL << 31);
+      if (sizeof(T) == sizeof(float) && a > 0 && dims_[l - 1][0] % 4 == 0 && small) {
+        const unsigned npairs = (unsigned)(faces3(dims_[l], a) / 2);
+        if (g_.ndim == 3)
+          k_coarse_faces_t4<3><<<nblk(npairs), kBlock, 0, s>>>(a, dims_[l - 1], m[0], make_fastdiv((unsigned)m[1]),
+                                                               npairs, (const float*)lv_[l - 1].w[a],
+                                                               (float*)lv_[l].w[a]);
+        else
+          k_coarse_faces_t4<2><<<nblk(npairs), kBlock, 0, s>>>(a, dims_[l - 1], m[0], make_fastdiv((unsigned)m[1]),
+                                                               npairs, (const float*)lv_[l - 1].w[a],
+                                                               (float*)lv_[l].w[a]);
+      } else if (small)
         k_coarse_faces32<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(
             a, g_.ndim, dims_[l - 1], make_fastdiv((unsigned)m[0]), make_fastdiv((unsigned)m[1]),
             (unsigned)faces3(dims_[l], a), (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
