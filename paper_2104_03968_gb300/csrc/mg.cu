@@ -1190,6 +1190,7 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
   for (;;) {
     const bool upd = !exact;
     if (upd) {
+      df_res = false;  // an update's sums are scaled by 1/rms(b), and its drift adds to the bound
       TraceScope ts("residual_update", s);
       const float* dv = (const float*)lv_[0].x;
       float* rv = (float*)lv_[0].r;

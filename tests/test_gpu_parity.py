@@ -272,6 +272,27 @@ def test_diffuse_diagonal_tensor(ctx, shape, bcname, precision):
     assert relerr(x, ref) < TOL
 
 
+@pytest.mark.parametrize("shape,bcname", [((64, 48, 40), "periodic"), ((48, 40, 32), "neumann"), ((96, 64), "mixed")])
+@pytest.mark.parametrize("start", ["fmg", "vcycle"])
+def test_mixed_reported_residual_is_the_true_one(ctx, shape, bcname, start):
+    """The relative residual the mixed solver reports after its double-float residual updates is
+    the oracle's ||b - A x|| / ||b|| of the returned x (E of order 1, so that a wrong scaling by
+    rms(b) would show), for several stopping points."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=100 + len(shape) + len(bcname), bc=BCS[bcname], dt_factor=100.0)
+    g, p = case["grid"], case["phys"]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+    for rtol in (1e-3, 1e-6, 1e-8):
+        out, info = fld.diffuse(ctx, g, solver(p, precision="mixed", rtol=rtol, nu1=2, nu2=2, start=start), case["dt"],
+                                dev(D), dev(case["E"]))
+        assert info["status"] == 0 and info["cycles"] >= 1, info
+        x = host(out).reshape(case["E"].shape)
+        true = oracle.relres(g, case["dt"], D, case["E"], x)
+        assert abs(true / info["rel_residual"] - 1) < 1e-3, (rtol, true, info)
+        assert true <= rtol
+
+
 @pytest.mark.parametrize("shape,bcname", [((64, 48, 40), "periodic"), ((96, 64), "mixed"), ((48, 40, 32), "neumann"),
                                           ((40, 32, 24), "dirichlet"), ((80, 48), "continuous"), ((512,), "mixed")])
 @pytest.mark.parametrize("rtol", [1e-8, 1e-10])
