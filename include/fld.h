@@ -193,6 +193,19 @@ FLD_API fld_status fld_exchange(fld_ctx* ctx, size_t n, const fld_params* p, dou
 FLD_API fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
                     const double* rho, double* eps, double* E, fld_info* info, void* stream);
 
+/* The update of fld_step (Sects. 3.1-3.4) on HOST arrays, for callers whose fields live in host
+   memory.  rho, eps, E: HOST arrays of cells, x fastest; eps and E are updated in place.
+   The library copies them into device buffers it owns (allocated on first use, kept in the
+   context), runs the step on `stream`, and copies eps and E back; it returns once they are back.
+   With the default order (diffusion, then exchange) the copies are pipelined in 8 equal cell
+   ranges on a second stream: E first, then rho and eps range by range while the
+   coefficient kernel runs on the ranges already in, and eps and E range by range while the
+   exchange runs on the later ranges.  Page-locked (pinned) host memory is needed for the copies
+   to overlap; pageable memory works, serialised.  Results equal fld_step's on the same data.
+   Errors as fld_step; on a CUDA error the host arrays may hold a partial update. */
+FLD_API fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                         const double* rho, double* eps, double* E, fld_info* info, void* stream);
+
 /* fld_step on `ngrids` independent grids with their own sizes, parameters and time steps.
    grids, params and dt are HOST arrays of length ngrids; rho/eps/E are HOST arrays of DEVICE
    pointers; infos (may be NULL) receives one fld_info per grid.  Every grid must have ndim 2

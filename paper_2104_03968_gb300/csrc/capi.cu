@@ -2,6 +2,7 @@
 // composition of the kernels into the calls declared in include/fld.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -18,6 +19,10 @@
 
 using namespace fld;
 
+// slabs (equal cell ranges) of the host-buffer step: the copies of slab i overlap the coefficient or
+// exchange kernel of the slabs before it
+constexpr int kHostSlabs = 8;
+
 struct fld_ctx {
   int device = 0;
   std::string err;
@@ -33,6 +38,11 @@ struct fld_ctx {
   size_t geom_cap = 0;
   double* mid = nullptr;   // midpoint IMEX: E^n, eps^n and the half-step E (3 x cells)
   size_t mid_cap = 0;
+  // fld_step_host: device copies of rho, eps and E (3 x cells), the copy stream and its events
+  double* stage = nullptr;
+  size_t stage_cap = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev[2 * kHostSlabs + 3] = {};
 };
 
 namespace {
@@ -181,6 +191,23 @@ fld_status ensure_mid(fld_ctx* ctx, long long ncell) {
   return FLD_OK;
 }
 
+fld_status ensure_stage(fld_ctx* ctx, long long ncell) {
+  if (!ctx->copy_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 * kHostSlabs + 3 && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream creation");
+  }
+  if ((size_t)ncell <= ctx->stage_cap) return FLD_OK;
+  cudaFree(ctx->stage);
+  ctx->stage = nullptr;
+  ctx->stage_cap = 0;
+  cudaError_t e = cudaMalloc(&ctx->stage, 3 * ncell * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host-step staging allocation");
+  ctx->stage_cap = ncell;
+  return FLD_OK;
+}
+
 fld_status reset_status(fld_ctx* ctx, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_info, 0, 2 * sizeof(int), s);
@@ -277,6 +304,10 @@ fld_status fld_ctx_destroy(fld_ctx* ctx) {
   cudaFree(ctx->kappa);
   cudaFree(ctx->geom);
   cudaFree(ctx->mid);
+  cudaFree(ctx->stage);
+  for (cudaEvent_t ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_info);
   if (ctx->h_info) cudaFreeHost(ctx->h_info);
@@ -459,6 +490,115 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
   fld_info* inf = info ? info : &tmp;
   memset(inf, 0, sizeof(*inf));
   if ((st = read_status(ctx, s, &sbits, &inf->exch_max_iters, &inf->bisection_fallbacks)) != FLD_OK) return st;
+  inf->cycles = ss.cycles;
+  inf->rel_residual = ss.relres;
+  inf->status = ss.status;
+  inf->nu1 = ss.nu1;
+  inf->nu2 = ss.nu2;
+  inf->nu1_coarse = ss.nu1_coarse;
+  inf->nu2_coarse = ss.nu2_coarse;
+  if (sbits & kStatNonpositive) {
+    inf->status = FLD_ERR_NONPOSITIVE;
+    return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state");
+  }
+  if (ss.status != FLD_OK)
+    return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
+                ss.relres, ss.cycles);
+  return FLD_OK;
+}
+
+fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* rho,
+                         double* eps, double* E, fld_info* info, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_grid(ctx, grid);
+  if (st == FLD_OK) st = check_params(ctx, p, true);
+  if (st == FLD_OK) st = check_coarsest(ctx, grid);
+  if (st != FLD_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
+  if (!rho || !eps || !E) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and E must be non-NULL");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const GridDev g = to_dev(grid);
+  const long long n = g.ncell;
+  if ((st = ensure_stage(ctx, n)) != FLD_OK) return st;
+  double* dr = ctx->stage;
+  double* de = ctx->stage + n;
+  double* dE = ctx->stage + 2 * n;
+  const size_t cell = sizeof(double);
+  cudaStream_t cs = ctx->copy_stream;
+  cudaError_t e;
+  if (p->order != FLD_ORDER_DIFFUSE_THEN_EXCHANGE) {
+    // whole arrays in, fld_step, whole arrays out
+    e = cudaMemcpyAsync(dr, rho, n * cell, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(de, eps, n * cell, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dE, E, n * cell, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copies");
+    st = fld_step(ctx, grid, p, dt, dr, de, dE, info, stream);
+    if (st == FLD_ERR_CUDA) return st;
+    const std::string msg = ctx->err;
+    e = cudaMemcpyAsync(eps, de, n * cell, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E, dE, n * cell, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copies");
+    ctx->err = msg;
+    return st;
+  }
+  if ((st = ensure_scratch(ctx, n)) != FLD_OK) return st;
+  if ((st = reset_status(ctx, s)) != FLD_OK) return st;
+  const Opacity op = to_opacity(p);
+  const ExchangeParams xp = to_exchange(p, dt);
+  cudaEvent_t* ev = ctx->ev;  // [0] s before the copies, [1] E in, [2 + i] slab i in, [2 + S + i] slab i out
+  const int S = (int)std::min<long long>(kHostSlabs, std::max<long long>(1, n / 4096));
+  auto first = [&](int i) { return n * i / S; };
+  // any host copy still queued must finish before an error return, since the caller may then free
+  // the host arrays
+  auto drain = [&](fld_status r) {
+    cudaStreamSynchronize(cs);
+    return r;
+  };
+  // the copies start after the work already queued on the caller's stream (it may use the staging)
+  e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dE, E, n * cell, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], cs);
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    const long long f = first(i), c = first(i + 1) - f;
+    e = cudaMemcpyAsync(dr + f, rho + f, c * cell, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(de + f, eps + f, c * cell, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + i], cs);
+  }
+  if (e != cudaSuccess) return drain(cuda_fail(ctx, e, "host-to-device copies"));
+  // coefficients slab by slab as rho and eps arrive (E, which the stencil reads across slabs, first)
+  e = cudaStreamWaitEvent(s, ev[1], 0);
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    e = cudaStreamWaitEvent(s, ev[2 + i], 0);
+    if (e == cudaSuccess)
+      e = launch_coeffs_range(g, op, p->c, p->gamma, p->gas_R, p->limiter, dE, dr, de, ctx->kappa, ctx->D,
+                              ctx->d_status, first(i), first(i + 1) - first(i), s);
+  }
+  if (e != cudaSuccess) return drain(cuda_fail(ctx, e, "coeffs launch"));
+  SolveStats ss;
+  const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
+  if ((st = run_diffuse(ctx, grid, p, dt, Dax, dE, dE, &ss, s)) != FLD_OK) return drain(st);
+  // exchange slab by slab, each slab's eps and E copied back while the next ones are computed
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    const long long f = first(i), c = first(i + 1) - f;
+    e = launch_exchange(c, xp, op, dr + f, ctx->kappa + f, de + f, dE + f, ctx->d_info, ctx->d_info + 1,
+                        ctx->d_status, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + S + i], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[2 + S + i], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(eps + f, de + f, c * cell, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E + f, dE + f, c * cell, cudaMemcpyDeviceToHost, cs);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+  if (e != cudaSuccess) return drain(cuda_fail(ctx, e, "exchange and device-to-host copies"));
+  unsigned sbits = 0;
+  fld_info tmp;
+  fld_info* inf = info ? info : &tmp;
+  memset(inf, 0, sizeof(*inf));
+  if ((st = read_status(ctx, s, &sbits, &inf->exch_max_iters, &inf->bisection_fallbacks)) != FLD_OK) return drain(st);
   inf->cycles = ss.cycles;
   inf->rel_residual = ss.relres;
   inf->status = ss.status;

@@ -18,10 +18,11 @@ namespace fld {
 // double-float chains are latency-bound (measured 7 % faster than five).
 __global__ void __launch_bounds__(kBlock, 6)
     k_coeffs(const __grid_constant__ GridDev g, const __grid_constant__ CoeffPhys ph, CoeffDf K, FastDiv f0,
-             FastDiv f1, const double* __restrict__ E, const double* __restrict__ rho, const double* __restrict__ eps,
-             double* __restrict__ kappa_out, double* __restrict__ D_out, unsigned* __restrict__ status) {
-  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (unsigned long long)g.ncell) return;
+             FastDiv f1, unsigned first, unsigned end, const double* __restrict__ E, const double* __restrict__ rho,
+             const double* __restrict__ eps, double* __restrict__ kappa_out, double* __restrict__ D_out,
+             unsigned* __restrict__ status) {
+  const unsigned idx = first + blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= end) return;
   const unsigned r = fast_div(idx, f0), k = fast_div(r, f1);
   const int i = (int)(idx - r * f0.d), j = (int)(r - k * f1.d);
   double kap, D;
@@ -31,11 +32,11 @@ __global__ void __launch_bounds__(kBlock, 6)
 }
 
 __global__ void k_coeffs64(const __grid_constant__ GridDev g, const __grid_constant__ CoeffPhys ph, CoeffDf K,
-                           const double* __restrict__ E,
+                           long long first, long long end, const double* __restrict__ E,
                            const double* __restrict__ rho, const double* __restrict__ eps,
                            double* __restrict__ kappa_out, double* __restrict__ D_out, unsigned* __restrict__ status) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.ncell) return;
+  const long long idx = first + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= end) return;
   const long long r = idx / g.n[0];
   double kap, D;
   if (!coeffs_cell_fast(g, ph, K, E, rho, eps, idx, (int)(idx % g.n[0]), (int)(r % g.n[1]), (int)(r / g.n[1]), kap,
@@ -60,20 +61,28 @@ __global__ void k_faces(GridDev g, double dt, DAxes D, double* __restrict__ w0,
 
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
-                          int limiter, const double* E, const double* rho, const double* eps,
-                          double* kappa_out, double* D_out, unsigned* status, cudaStream_t s) {
-  if (g.ncell == 0) return cudaSuccess;
+cudaError_t launch_coeffs_range(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
+                                int limiter, const double* E, const double* rho, const double* eps, double* kappa_out,
+                                double* D_out, unsigned* status, long long first, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
   TraceScope ts("coeffs", s);
   CoeffPhys ph{op, c, gamma, gas_R, limiter};
   const CoeffDf K = make_coeff_df(ph, g);
   if (g.ncell < (1ll << 32) - kBlock)
-    k_coeffs<<<blocks_for(g.ncell), kBlock, 0, s>>>(g, ph, K, make_fastdiv((unsigned)g.n[0]),
-                                                     make_fastdiv((unsigned)g.n[1]), E, rho, eps, kappa_out, D_out,
-                                                     status);
+    k_coeffs<<<blocks_for(count), kBlock, 0, s>>>(g, ph, K, make_fastdiv((unsigned)g.n[0]),
+                                                   make_fastdiv((unsigned)g.n[1]), (unsigned)first,
+                                                   (unsigned)(first + count), E, rho, eps, kappa_out, D_out, status);
   else
-    k_coeffs64<<<blocks_for(g.ncell), kBlock, 0, s>>>(g, ph, K, E, rho, eps, kappa_out, D_out, status);
+    k_coeffs64<<<blocks_for(count), kBlock, 0, s>>>(g, ph, K, first, first + count, E, rho, eps, kappa_out, D_out,
+                                                     status);
   return cudaGetLastError();
+}
+
+cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
+                          int limiter, const double* E, const double* rho, const double* eps,
+                          double* kappa_out, double* D_out, unsigned* status, cudaStream_t s) {
+  if (g.ncell == 0) return cudaSuccess;
+  return launch_coeffs_range(g, op, c, gamma, gas_R, limiter, E, rho, eps, kappa_out, D_out, status, 0, g.ncell, s);
 }
 
 cudaError_t launch_faces(const GridDev& g, double dt, const double* const Dax[3], double* const w64[3],

@@ -77,6 +77,7 @@ _SIGS = {
     "fld_diffuse": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_exchange": [P, ct.c_size_t, P, ct.c_double, P, P, P, P, P, P],
     "fld_step": [P, P, P, ct.c_double, P, P, P, P, P],
+    "fld_step_host": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_step_batched": [P, ct.c_int, P, P, P, P, P, P, P, P],
     "fld_columns_step": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P, P],
     "fld_columns_diffuse": [P, ct.c_int, ct.c_int, P, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P, P, P],
@@ -271,23 +272,53 @@ def exchange(ctx: Context, params: dict, dt: float, rho, eps, E, kappa=None) -> 
     return info.as_dict()
 
 
+def _host_buffer(a, writable: bool):
+    """(pointer, temporary) for a host array: the array's own float64 C-contiguous memory, or a
+    contiguous float64 copy (temporary, to be copied back when writable)."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise TypeError("mixed CUDA and host arrays")
+        if a.dtype == torch.float64 and a.is_contiguous():
+            return ct.c_void_p(a.data_ptr()), None
+        t = a.to(torch.float64).contiguous()
+        return ct.c_void_p(t.data_ptr()), t
+    arr = np.asarray(a)
+    if arr.dtype == np.float64 and arr.flags.c_contiguous and (arr.flags.writeable or not writable):
+        return ct.c_void_p(arr.ctypes.data), None
+    tmp = np.ascontiguousarray(arr, dtype=np.float64)
+    return ct.c_void_p(tmp.ctypes.data), tmp
+
+
+def _assign_back(host, tmp):
+    if isinstance(host, torch.Tensor):
+        host.copy_(tmp.reshape(host.shape))
+    else:
+        host[...] = np.asarray(tmp).reshape(np.shape(host))
+
+
 def step(ctx: Context, grid: dict, params: dict, dt: float, rho, eps, E, allow_unconverged: bool = False) -> dict:
-    """One full update in place on eps and E.  CUDA tensors are updated in place; host arrays
-    are copied to the device, updated, and copied back into the same host buffers."""
+    """One full update in place on eps and E.  CUDA tensors are updated in place on the device;
+    host arrays (numpy, or CPU tensors -- pinned ones let the copies overlap the kernels) go through
+    fld_step_host, which copies them in, steps and copies eps and E back into the same buffers."""
     host = not (isinstance(E, torch.Tensor) and E.is_cuda)
-    if host:
-        hr, he, hE = rho, eps, E
-        rho, eps, E = to_device(rho, ctx), to_device(eps, ctx), to_device(E, ctx)
     keep = []
     g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
     info = Info()
-    st = ctx.lib.fld_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(rho), _dptr(eps), _dptr(E),
-                          ct.byref(info), _stream())
+    if host:
+        pr, _tr = _host_buffer(rho, False)
+        pe, te = _host_buffer(eps, True)
+        pE, tE = _host_buffer(E, True)
+        st = ctx.lib.fld_step_host(ctx.h, ct.byref(g), ct.byref(p), float(dt), pr, pe, pE, ct.byref(info),
+                                   _stream())
+        if te is not None:
+            _assign_back(eps, te)
+        if tE is not None:
+            _assign_back(E, tE)
+    else:
+        st = ctx.lib.fld_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(rho), _dptr(eps), _dptr(E),
+                              ct.byref(info), _stream())
     if st and not (allow_unconverged and st == 4):
         ctx.check(st)
-    if host:
-        _copy_back(he, eps)
-        _copy_back(hE, E)
     return info.as_dict()
 
 

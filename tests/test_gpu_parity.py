@@ -272,6 +272,30 @@ def test_diffuse_diagonal_tensor(ctx, shape, bcname, precision):
     assert relerr(x, ref) < TOL
 
 
+@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
+@pytest.mark.parametrize("kind", ["numpy", "pinned"])
+def test_step_on_host_arrays_equals_device_step(ctx, order, kind):
+    """fld_step_host (host arrays, copies pipelined with the coefficient and exchange kernels over
+    8 cell ranges) gives bit for bit the result of fld_step on device arrays."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small((48, 40, 32), seed=5, bc=BCS["mixed"], dt_factor=30.0)
+    g = case["grid"]
+    p = solver(case["phys"], rtol=1e-10, nu1=2, nu2=2, order=order)
+    eps_d, E_d = dev(case["eps"]), dev(case["E"])
+    info_d = fld.step(ctx, g, p, case["dt"], dev(case["rho"]), eps_d, E_d)
+    if kind == "numpy":
+        rho_h, eps_h, E_h = case["rho"].copy(), case["eps"].copy(), case["E"].copy()
+    else:
+        rho_h, eps_h, E_h = (torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+                             for a in (case["rho"], case["eps"], case["E"]))
+    info_h = fld.step(ctx, g, p, case["dt"], rho_h, eps_h, E_h)
+    assert info_h["status"] == info_d["status"] == 0
+    assert info_h["cycles"] == info_d["cycles"]
+    assert np.array_equal(np.asarray(eps_h).ravel(), host(eps_d).ravel())
+    assert np.array_equal(np.asarray(E_h).ravel(), host(E_d).ravel())
+    assert np.array_equal(np.asarray(rho_h).ravel(), np.asarray(case["rho"]).ravel())  # rho is read only
+
+
 @pytest.mark.parametrize("shape,bcname", [((64, 48, 40), "periodic"), ((48, 40, 32), "neumann"), ((96, 64), "mixed")])
 @pytest.mark.parametrize("start", ["fmg", "vcycle"])
 def test_mixed_reported_residual_is_the_true_one(ctx, shape, bcname, start):
