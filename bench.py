@@ -63,8 +63,6 @@ KERNEL_MODEL = {
     # FP64 operator set-up: weights (24) and E_old (8) in; b, diag (16), 1/diag and diag hi/lo (12) out
     "fine_setup": {"bound": "hbm", "bytes_f32": 24 + 8 + 16 + 12, "bytes_f64": 24 + 8 + 16 + 16},
 }
-# launches per traced scope (some scopes hold several kernels)
-SCOPE_KERNELS = {"faces": 3, "coarse_setup": 4, "norm_b": 2}
 
 
 def load_peaks():
@@ -321,11 +319,13 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
+    n_before = fld.launch_count()
     ms, infos, rep = timed_steps(torch, fld, ctx, g, p, dt, rho0, eps, E, args.steps, trace=True)
+    n_after = fld.launch_count()
     clk = clocks.stop()
     barrier(world)
     ms, value = replica_throughput(world, ncell, args.steps, ms)
-    launches = sum(v[0] * SCOPE_KERNELS.get(k, 1) for k, v in rep.items())
+    launches = (n_after - n_before) * world
     traffic = {}
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tpath):
@@ -453,12 +453,14 @@ def run_batched_workload(args):
     fld.trace_enable(ctx, True)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    n_before = fld.launch_count()
     t0.record()
     infos = []
     for _ in range(args.steps):
         infos = step()
     t1.record()
     torch.cuda.synchronize()
+    n_after = fld.launch_count()
     fld.trace_enable(ctx, False)
     rep = fld.trace_report(ctx)
     ms = t0.elapsed_time(t1)
@@ -468,6 +470,7 @@ def run_batched_workload(args):
             "dtype": "f64" if args.workload == "columns" or args.precision == "fp64" else "f64+f32",
             "data": "synthetic", "config": {"workload": desc, "cells": int(ncell)},
             "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in rep.items()},
+            "gpu_launches": n_after - n_before,
             "status": sorted({i["status"] for i in infos}),
             "max_cycles": max(i["cycles"] for i in infos)}
     print(json.dumps(line), flush=True)

@@ -158,6 +158,12 @@ FLD_API fld_status fld_ctx_destroy(fld_ctx* ctx);
 /* Message of the last error raised on `ctx` (never NULL; empty when none). */
 FLD_API const char* fld_last_error(const fld_ctx* ctx);
 
+/* Kernels this library has launched in the calling process so far, every launch site and the
+   kernels of each CUDA-graph replay included (a graph counts the kernels captured in it; the
+   batched solver's WHILE node counts its body once per pass).  A diagnostic for benchmarks, with
+   no counterpart in the paper; read it before and after the work to count. */
+FLD_API unsigned long long fld_launch_count(void);
+
 /* Per-cell opacity and diffusion coefficient (Sect. 2.2, Eqs. fld_lambda and fld_F, with the
    5-point gradient of Sect. 3.2).  In: E, rho, eps (N cells).  Out: kappa_out (N, may be NULL),
    D_out (N).  Asynchronous. */

@@ -427,6 +427,14 @@ struct BatchedSolver::Impl {
   int maxlev = 0;
   // graph
   cudaGraphExec_t exec = nullptr;
+  // kernels of one graph replay: those outside the WHILE node, and those of one pass of its body
+  unsigned long long k_outer = 0, k_body = 0;
+  // after a replay has finished: count its kernels (the body ran once per pass, ctl_d[1] passes)
+  void count_replay() {
+    int passes = 0;
+    if (cudaMemcpy(&passes, ctl_d + 1, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+      note_launch(k_outer + k_body * (unsigned long long)(passes > 0 ? passes : 0));
+  }
   cudaStream_t cap = nullptr, body = nullptr;
   int nu1 = 2, nu2 = 2;
   bool tuned = false;
@@ -667,19 +675,21 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
     return e;
   }
   cudaStream_t s = cap;
-  kb_reset<<<blocks(ng, 256), 256, 0, s>>>(ng, st_d, ctl_d);
-  kb_exchange<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, st_d, 0);
-  kb_coeffs<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, st_d);
-  kb_faces<T><<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, lev);
-  kb_fine_setup<T><<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, lev);
+  const unsigned long long c0 = launch_count();
+  note_launch(), kb_reset<<<blocks(ng, 256), 256, 0, s>>>(ng, st_d, ctl_d);
+  note_launch(), kb_exchange<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, st_d, 0);
+  note_launch(), kb_coeffs<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, st_d);
+  note_launch(), kb_faces<T><<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, lev);
+  note_launch(), kb_fine_setup<T><<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, lev);
   for (int l = 1; l < maxlev; ++l) {
     if (!cell_r[l].n) continue;
-    kb_coarse_faces<T><<<cell_r[l].n, B, 0, s>>>(tl + cell_r[l].off, lev);
-    kb_invd<T><<<cell_r[l].n, B, 0, s>>>(tl + cell_r[l].off, lev);
+    note_launch(), kb_coarse_faces<T><<<cell_r[l].n, B, 0, s>>>(tl + cell_r[l].off, lev);
+    note_launch(), kb_invd<T><<<cell_r[l].n, B, 0, s>>>(tl + cell_r[l].off, lev);
   }
-  kb_sumsq_b<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, parts_d);
-  kb_bnorm<<<blocks(ng, 256), 256, 0, s>>>(ng, parts_d, st_d);
+  note_launch(), kb_sumsq_b<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, parts_d);
+  note_launch(), kb_bnorm<<<blocks(ng, 256), 256, 0, s>>>(ng, parts_d, st_d);
 
+  const unsigned long long c1 = launch_count();
   // the WHILE node over the cycles
   cudaGraphConditionalHandle handle;
   cudaStreamCaptureStatus cs;
@@ -703,42 +713,48 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(body, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
     cudaStream_t b = body;
-    kb_residual<T><<<fine_r.n, B, 0, b>>>(tl + fine_r.off, fine_d, lev, st_d, parts_d);
-    kb_check<<<1, kCheckThreads, 0, b>>>(ng, parts_d, st_d, ctl_d, iter_cap, handle);
+    note_launch(), kb_residual<T><<<fine_r.n, B, 0, b>>>(tl + fine_r.off, fine_d, lev, st_d, parts_d);
+    note_launch(), kb_check<<<1, kCheckThreads, 0, b>>>(ng, parts_d, st_d, ctl_d, iter_cap, handle);
     // V-cycle: levels down
     for (int l = 0; l + 1 < maxlev; ++l) {
       const Range& sr = smooth_r[l];
       if (!sr.n) continue;
       for (int it = 0; it < nu1_; ++it) {
-        if (it == 0) kb_smooth<T, true, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
-        else kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
-        kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
+        if (it == 0) note_launch(), kb_smooth<T, true, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+        else note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+        note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
       }
-      kb_restrict<T><<<restrict_r[l].n, B, 0, b>>>(tl + restrict_r[l].off, lev, st_d);
+      note_launch(), kb_restrict<T><<<restrict_r[l].n, B, 0, b>>>(tl + restrict_r[l].off, lev, st_d);
     }
-    kb_coarse<T><<<coarse_r.n, 512, 0, b>>>(tl + coarse_r.off, lev, st_d, fine_d);
+    note_launch(), kb_coarse<T><<<coarse_r.n, 512, 0, b>>>(tl + coarse_r.off, lev, st_d, fine_d);
     // levels up
     for (int l = maxlev - 2; l >= 0; --l) {
       const Range& sr = smooth_r[l];
       if (!sr.n) continue;
-      kb_prolong<T><<<prolong_r[l].n, B, 0, b>>>(tl + prolong_r[l].off, lev, st_d);
+      note_launch(), kb_prolong<T><<<prolong_r[l].n, B, 0, b>>>(tl + prolong_r[l].off, lev, st_d);
       for (int it = 0; it < nu2_; ++it) {
         bool last = (l == 0) && it == nu2_ - 1;
         if (last) {
-          kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
-          kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+          note_launch(), kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
+          note_launch(), kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
         } else {
-          kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
-          kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+          note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
+          note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
         }
       }
     }
     cudaGraph_t tmp = nullptr;
     e = cudaStreamEndCapture(b, &tmp);
   }
+  const unsigned long long c2 = launch_count();
   if (e == cudaSuccess) {
-    kb_exchange<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, st_d, 1);
+    note_launch(), kb_exchange<<<fine_r.n, B, 0, s>>>(tl + fine_r.off, fine_d, st_d, 1);
   }
+  // captured, not run: the replays count them (count_replay)
+  const unsigned long long c3 = launch_count();
+  k_outer = (c1 - c0) + (c3 - c2);
+  k_body = c2 - c1;
+  unnote_launches(c3 - c0);
   cudaGraph_t done = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s, &done);
   if (e == cudaSuccess) e = e2;
@@ -844,6 +860,7 @@ fld_status BatchedSolver::run(int ngrids, const fld_grid* grids, const fld_param
         cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) break;
+        I.count_replay();
         cudaEventElapsedTime(&ms, e0, e1);
       }
       if (e != cudaSuccess) break;
@@ -870,6 +887,7 @@ fld_status BatchedSolver::run(int ngrids, const fld_grid* grids, const fld_param
   e = cudaMemcpyAsync(I.st_pinned, I.st_d, ngrids * sizeof(BState), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_err(e, "result read-back");
+  I.count_replay();
   fld_status worst = FLD_OK;
   for (int g = 0; g < ngrids; ++g) {
     const BState& st = I.st_pinned[g];

@@ -318,6 +318,8 @@ fld_status fld_ctx_destroy(fld_ctx* ctx) {
 
 const char* fld_last_error(const fld_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+unsigned long long fld_launch_count(void) { return fld::launch_count(); }
+
 fld_status fld_coeffs(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, const double* E, const double* rho,
                       const double* eps, double* kappa_out, double* D_out, void* stream) {
   if (!ctx) return FLD_ERR_INVALID_ARG;

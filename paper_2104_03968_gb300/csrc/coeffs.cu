@@ -69,12 +69,14 @@ cudaError_t launch_coeffs_range(const GridDev& g, const Opacity& op, double c, d
   CoeffPhys ph{op, c, gamma, gas_R, limiter};
   const CoeffDf K = make_coeff_df(ph, g);
   if (g.ncell < (1ll << 32) - kBlock)
-    k_coeffs<<<blocks_for(count), kBlock, 0, s>>>(g, ph, K, make_fastdiv((unsigned)g.n[0]),
-                                                   make_fastdiv((unsigned)g.n[1]), (unsigned)first,
-                                                   (unsigned)(first + count), E, rho, eps, kappa_out, D_out, status);
+    note_launch(),
+        k_coeffs<<<blocks_for(count), kBlock, 0, s>>>(g, ph, K, make_fastdiv((unsigned)g.n[0]),
+                                                       make_fastdiv((unsigned)g.n[1]), (unsigned)first,
+                                                       (unsigned)(first + count), E, rho, eps, kappa_out, D_out, status);
   else
-    k_coeffs64<<<blocks_for(count), kBlock, 0, s>>>(g, ph, K, first, first + count, E, rho, eps, kappa_out, D_out,
-                                                     status);
+    note_launch(),
+        k_coeffs64<<<blocks_for(count), kBlock, 0, s>>>(g, ph, K, first, first + count, E, rho, eps, kappa_out, D_out,
+                                                         status);
   return cudaGetLastError();
 }
 
@@ -90,12 +92,14 @@ cudaError_t launch_faces(const GridDev& g, double dt, const double* const Dax[3]
   TraceScope ts("faces", s);
   const DAxes D{{Dax[0], Dax[1], Dax[2]}};
   if (w32 && w32[0])
-    k_faces<float><<<blocks_for(g.ncell), kBlock, 0, s>>>(g, dt, D, w64[0], w64[1], w64[2], w32[0], w32[1], w32[2],
-                                                           w32lo ? w32lo[0] : nullptr, w32lo ? w32lo[1] : nullptr,
-                                                           w32lo ? w32lo[2] : nullptr);
+    note_launch(),
+        k_faces<float><<<blocks_for(g.ncell), kBlock, 0, s>>>(g, dt, D, w64[0], w64[1], w64[2], w32[0], w32[1], w32[2],
+                                                               w32lo ? w32lo[0] : nullptr, w32lo ? w32lo[1] : nullptr,
+                                                               w32lo ? w32lo[2] : nullptr);
   else
-    k_faces<double><<<blocks_for(g.ncell), kBlock, 0, s>>>(g, dt, D, w64[0], w64[1], w64[2], nullptr, nullptr,
-                                                            nullptr, nullptr, nullptr, nullptr);
+    note_launch(),
+        k_faces<double><<<blocks_for(g.ncell), kBlock, 0, s>>>(g, dt, D, w64[0], w64[1], w64[2], nullptr, nullptr,
+                                                                nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -578,14 +578,15 @@ static cudaError_t launch_kernel(int ncol, int ncell, ColArgs& A, cudaStream_t s
   size_t smem = col_smem(ncell, P, MODE, MODE != kColDiffuse && A.cak_v != nullptr);
   cudaError_t e = cudaFuncSetAttribute(k_columns<MODE, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_columns<MODE, MIXED><<<ncol, P, smem, s>>>(A);
+  note_launch(), k_columns<MODE, MIXED><<<ncol, P, smem, s>>>(A);
   return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_mode(int ncol, int ncell, const double* r_faces, int geometry, ColArgs& A, unsigned* status,
                                int precision, cudaStream_t s) {
-  k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, const_cast<double*>(A.geom), status);
+  note_launch(),
+      k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, const_cast<double*>(A.geom), status);
   TraceScope ts(precision == FLD_PREC_MIXED ? "columns_mixed" : "columns", s);
   return precision == FLD_PREC_MIXED ? launch_kernel<MODE, true>(ncol, ncell, A, s)
                                      : launch_kernel<MODE, false>(ncol, ncell, A, s);
@@ -739,7 +740,7 @@ extern "C" fld_status fld_columns_step_static(int ncol, int ncell, const double*
   A.info_iters = iters;
   A.info_bisect = bisect;
   A.status = status;
-  k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, geom, status);
+  note_launch(), k_col_geometry<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, r_faces, geometry, geom, status);
   const bool mixed = p->precision == FLD_PREC_MIXED;
   cudaError_t e;
   if (p->order == FLD_ORDER_EXCHANGE_THEN_DIFFUSE)

@@ -34,7 +34,7 @@ cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity&
   if (n == 0) return cudaSuccess;
   unsigned blocks = (unsigned)((n + kBlock - 1) / kBlock);
   TraceScope ts("exchange", s);
-  k_exchange<<<blocks, kBlock, 0, s>>>(n, p, op, rho, kappa, eps, E, info_iters, info_bisect, status);
+  note_launch(), k_exchange<<<blocks, kBlock, 0, s>>>(n, p, op, rho, kappa, eps, E, info_iters, info_bisect, status);
   return cudaGetLastError();
 }
 
@@ -52,7 +52,7 @@ cudaError_t launch_midpoint_combine(long long n, const double* E0, const double*
                                     double* eps, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   TraceScope ts("midpoint_combine", s);
-  k_midpoint_combine<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, E0, eps0, Eh, E, eps);
+  note_launch(), k_midpoint_combine<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, E0, eps0, Eh, E, eps);
   return cudaGetLastError();
 }
 

@@ -10,11 +10,23 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/fld.h"
 
 namespace fld {
 
 constexpr int kBlock = 256;
+
+// Kernels this library has launched in the process, for fld_launch_count: every launch site calls
+// note_launch; a captured CUDA graph counts its kernels at capture (its first launch follows) and
+// again at each later replay.
+extern std::atomic<unsigned long long> g_kernel_launches;
+__host__ inline void note_launch(unsigned long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+__host__ inline void unnote_launches(unsigned long long n) {
+  g_kernel_launches.fetch_sub(n, std::memory_order_relaxed);
+}
+__host__ inline unsigned long long launch_count() { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 struct GridDev {
   int n[3];

@@ -758,9 +758,9 @@ cudaError_t Multigrid::wave_sweep(int l, bool zero, int c0, double* x64, cudaStr
   const T* invd = (const T*)lv_[l].invd;
   const T* r = (const T*)lv_[l].r;
   T* x = (T*)lv_[l].x;
-  if (zero) k_wave_sweep<T, true, false><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, nullptr, d);
-  else if (x64) k_wave_sweep<T, false, true><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, x64, d);
-  else k_wave_sweep<T, false, false><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, nullptr, d);
+  if (zero) note_launch(), k_wave_sweep<T, true, false><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, nullptr, d);
+  else if (x64) note_launch(), k_wave_sweep<T, false, true><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, x64, d);
+  else note_launch(), k_wave_sweep<T, false, false><<<grid, kWaveThreads, 0, s>>>(L, invd, r, x, c0, nullptr, d);
   return cudaGetLastError();
 }
 
@@ -865,12 +865,13 @@ cudaError_t Multigrid::fp64_operator(cudaStream_t s) {
   LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
   {
     TraceScope ts("fine_setup", s);
-    k_fine_setup<T><<<nblk(g_.ncell), kBlock, 0, s>>>(L64, g_, E_old_, b64_, diag64_, (T*)lv_[0].invd, dhi_, dlo_);
+    note_launch(),
+        k_fine_setup<T><<<nblk(g_.ncell), kBlock, 0, s>>>(L64, g_, E_old_, b64_, diag64_, (T*)lv_[0].invd, dhi_, dlo_);
   }
   {
     TraceScope ts("norm_b", s);
-    k_sumsq<<<nparts_, kBlock, 0, s>>>(b64_, g_.ncell, partials_);
-    k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_ + 1);
+    note_launch(), k_sumsq<<<nparts_, kBlock, 0, s>>>(b64_, g_.ncell, partials_);
+    note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_ + 1);
   }
   fp64_op_ = true;
   return cudaGetLastError();
@@ -912,28 +913,32 @@ cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const d
       if (sizeof(T) == sizeof(float) && a > 0 && dims_[l - 1][0] % 4 == 0 && small) {
         const unsigned npairs = (unsigned)(faces3(dims_[l], a) / 2);
         if (g_.ndim == 3)
-          k_coarse_faces_t4<3><<<nblk(npairs), kBlock, 0, s>>>(a, dims_[l - 1], m[0], make_fastdiv((unsigned)m[1]),
-                                                               npairs, (const float*)lv_[l - 1].w[a],
-                                                               (float*)lv_[l].w[a]);
+          note_launch(),
+              k_coarse_faces_t4<3><<<nblk(npairs), kBlock, 0, s>>>(a, dims_[l - 1], m[0], make_fastdiv((unsigned)m[1]),
+                                                                   npairs, (const float*)lv_[l - 1].w[a],
+                                                                   (float*)lv_[l].w[a]);
         else
-          k_coarse_faces_t4<2><<<nblk(npairs), kBlock, 0, s>>>(a, dims_[l - 1], m[0], make_fastdiv((unsigned)m[1]),
-                                                               npairs, (const float*)lv_[l - 1].w[a],
-                                                               (float*)lv_[l].w[a]);
+          note_launch(),
+              k_coarse_faces_t4<2><<<nblk(npairs), kBlock, 0, s>>>(a, dims_[l - 1], m[0], make_fastdiv((unsigned)m[1]),
+                                                                   npairs, (const float*)lv_[l - 1].w[a],
+                                                                   (float*)lv_[l].w[a]);
       } else if (small)
-        k_coarse_faces32<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(
-            a, g_.ndim, dims_[l - 1], make_fastdiv((unsigned)m[0]), make_fastdiv((unsigned)m[1]),
-            (unsigned)faces3(dims_[l], a), (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
+        note_launch(), k_coarse_faces32<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(
+                           a, g_.ndim, dims_[l - 1], make_fastdiv((unsigned)m[0]), make_fastdiv((unsigned)m[1]),
+                           (unsigned)faces3(dims_[l], a), (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
       else
-        k_coarse_faces<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(a, g_.ndim, dims_[l - 1], dims_[l],
-                                                                        (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
+        note_launch(),
+            k_coarse_faces<T><<<nblk(faces3(dims_[l], a)), kBlock, 0, s>>>(a, g_.ndim, dims_[l - 1], dims_[l],
+                                                                            (const T*)lv_[l - 1].w[a], (T*)lv_[l].w[a]);
     }
     LevelDev<T> L = level_dev<T>(g_, dims_[l], lv_[l].w);
     if (cells3(dims_[l]) < (1LL << 31))
-      k_invd32<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, make_fastdiv((unsigned)dims_[l][0]),
-                                                             make_fastdiv((unsigned)dims_[l][1]),
-                                                             (unsigned)cells3(dims_[l]), (T*)lv_[l].invd);
+      note_launch(),
+          k_invd32<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, make_fastdiv((unsigned)dims_[l][0]),
+                                                                 make_fastdiv((unsigned)dims_[l][1]),
+                                                                 (unsigned)cells3(dims_[l]), (T*)lv_[l].invd);
     else
-      k_invd<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, cells3(dims_[l]), (T*)lv_[l].invd);
+      note_launch(), k_invd<T><<<nblk(cells3(dims_[l])), kBlock, 0, s>>>(L, cells3(dims_[l]), (T*)lv_[l].invd);
   }
   return cudaGetLastError();
 }
@@ -972,7 +977,10 @@ cudaError_t Multigrid::vcycle(int l, int nu1, int nu2, double* x64, cudaStream_t
 template <class T>
 cudaError_t Multigrid::vcycle_graph(int l, int nu1, int nu2, cudaStream_t s, bool zero_init) {
   for (const auto& g : graphs_)
-    if (g.l == l && g.nu1 == nu1 && g.nu2 == nu2 && g.zero == (int)zero_init) return cudaGraphLaunch(g.exec, s);
+    if (g.l == l && g.nu1 == nu1 && g.nu2 == nu2 && g.zero == (int)zero_init) {
+      note_launch(g.kernels);
+      return cudaGraphLaunch(g.exec, s);
+    }
   cudaError_t e = cudaSuccess;
   if (!cap_stream_) e = cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking);
   if (e != cudaSuccess) return e;
@@ -980,20 +988,26 @@ cudaError_t Multigrid::vcycle_graph(int l, int nu1, int nu2, cudaStream_t s, boo
   // replay below is ordered on s
   e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
+  const unsigned long long c0 = launch_count();
   capturing_ = true;
   cudaError_t ec = vcycle_direct<T>(l, nu1, nu2, nullptr, cap_stream_, zero_init);
   capturing_ = false;
+  const unsigned long long kernels = launch_count() - c0;  // counted now, for the launch below
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(cap_stream_, &graph);
   if (ec != cudaSuccess || e != cudaSuccess) {
+    unnote_launches(kernels);
     if (graph) cudaGraphDestroy(graph);
     return ec != cudaSuccess ? ec : e;
   }
   cudaGraphExec_t exec = nullptr;
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return e;
-  graphs_.push_back({l, nu1, nu2, (int)zero_init, exec});
+  if (e != cudaSuccess) {
+    unnote_launches(kernels);
+    return e;
+  }
+  graphs_.push_back({l, nu1, nu2, (int)zero_init, exec, kernels});
   return cudaGraphLaunch(exec, s);
 }
 
@@ -1013,9 +1027,10 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     TraceScope ts("coarse_solve", s);
     const size_t smem = 2 * (size_t)ncell * sizeof(T);
     const int in_smem = smem <= 48 * 1024 ? 1 : 0;
-    k_coarse_solve<T><<<1, 512, in_smem ? smem : 0, s>>>(L, ncell, invd, r, x, (T*)lv_[l].tmp, sweeps, rb ? 1 : 0,
-                                                         in_smem);
-    if (x64) k_add_correction<T><<<nblk(ncell), kBlock, 0, s>>>(ncell, x, x64);
+    note_launch(),
+        k_coarse_solve<T><<<1, 512, in_smem ? smem : 0, s>>>(L, ncell, invd, r, x, (T*)lv_[l].tmp, sweeps, rb ? 1 : 0,
+                                                             in_smem);
+    if (x64) note_launch(), k_add_correction<T><<<nblk(ncell), kBlock, 0, s>>>(ncell, x, x64);
     return cudaGetLastError();
   }
   long long nhalf = (long long)((n[0] + 1) / 2) * n[1] * n[2];
@@ -1033,11 +1048,11 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     }
     {
       TraceScope ts(zero ? (l == 0 ? "smooth_L0_zero" : "smooth_Lc") : sm_name, s);
-      if (zero) k_smooth<T, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
-      else k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
+      if (zero) note_launch(), k_smooth<T, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
+      else note_launch(), k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
     }
     TraceScope ts(sm_name, s);
-    k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1);
+    note_launch(), k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1);
   }
   const std::array<int, 3>& nc = dims_[l + 1];
   {
@@ -1045,10 +1060,11 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     if (rows_ok(l)) {
       const int crows = nc[1] * nc[2];
       const unsigned gr = (unsigned)std::min(crows, 152 * 16);
-      if (g_.ndim == 3) k_restrict_rows<T, 3><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
-      else k_restrict_rows<T, 2><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
+      if (g_.ndim == 3) note_launch(),
+          k_restrict_rows<T, 3><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
+      else note_launch(), k_restrict_rows<T, 2><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
     } else {
-      k_residual_restrict<T><<<nblk(cells3(nc)), kBlock, 0, s>>>(L, r, x, nc, (T*)lv_[l + 1].r, nullptr);
+      note_launch(), k_residual_restrict<T><<<nblk(cells3(nc)), kBlock, 0, s>>>(L, r, x, nc, (T*)lv_[l + 1].r, nullptr);
     }
   }
   cudaError_t e = vcycle<T>(l + 1, nuc1_, nuc2_, nullptr, s, true);  // coarser levels: their own counts
@@ -1060,15 +1076,16 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
       const unsigned gr = (unsigned)std::min(rows, 152 * 16);
       if (sizeof(T) == sizeof(float) && n[0] % 4 == 0) {
         const float* xc = (const float*)lv_[l + 1].x;
-        if (g_.ndim == 3) k_prolong_rows4<3, false><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
-        else k_prolong_rows4<2, false><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+        if (g_.ndim == 3) note_launch(),
+            k_prolong_rows4<3, false><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+        else note_launch(), k_prolong_rows4<2, false><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
       } else if (g_.ndim == 3) {
-        k_prolong_rows<T, 3><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+        note_launch(), k_prolong_rows<T, 3><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
       } else {
-        k_prolong_rows<T, 2><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+        note_launch(), k_prolong_rows<T, 2><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
       }
     } else {
-      k_prolong<T><<<nblk(ncell), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
+      note_launch(), k_prolong<T><<<nblk(ncell), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
     }
   }
   // post-smoothing, colours reversed; on the finest level the last sweep also adds each colour's
@@ -1083,16 +1100,16 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     }
     {
       TraceScope ts(sm_name, s);
-      if (last) k_smooth<T, false, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1, x64);
-      else k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1);
+      if (last) note_launch(), k_smooth<T, false, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1, x64);
+      else note_launch(), k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1);
     }
     TraceScope ts(sm_name, s);
-    if (last) k_smooth<T, false, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0, x64);
-    else k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
+    if (last) note_launch(), k_smooth<T, false, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0, x64);
+    else note_launch(), k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
   }
   if (x64 && nu2 == 0) {
     TraceScope ts("add_correction", s);
-    k_add_correction<T><<<nblk(ncell), kBlock, 0, s>>>(ncell, x, x64);
+    note_launch(), k_add_correction<T><<<nblk(ncell), kBlock, 0, s>>>(ncell, x, x64);
   }
   return cudaGetLastError();
 }
@@ -1109,8 +1126,9 @@ cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
   {
     TraceScope ts("fmg_restrict", s);
     for (int l = 0; l < top; ++l)
-      k_restrict_avg<T><<<nblk(cells3(dims_[l + 1])), kBlock, 0, s>>>(dims_[l], g_.ndim, (const T*)lv_[l].r,
-                                                                     dims_[l + 1], (T*)lv_[l + 1].r);
+      note_launch(),
+          k_restrict_avg<T><<<nblk(cells3(dims_[l + 1])), kBlock, 0, s>>>(dims_[l], g_.ndim, (const T*)lv_[l].r,
+                                                                         dims_[l + 1], (T*)lv_[l + 1].r);
   }
   cudaError_t e = vcycle<T>(top, nuc1_, nuc2_, nullptr, s, true);
   if (e != cudaSuccess) return e;
@@ -1125,17 +1143,20 @@ cudaError_t Multigrid::fmg(int nu1, int nu2, double* x64, cudaStream_t s) {
         const unsigned gr = (unsigned)std::min(rows, 152 * 16);
         if (sizeof(T) == sizeof(float) && n[0] % 4 == 0) {
           const float* xc = (const float*)lv_[l + 1].x;
-          if (g_.ndim == 3) k_prolong_rows4<3, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
-          else k_prolong_rows4<2, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+          if (g_.ndim == 3) note_launch(),
+              k_prolong_rows4<3, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
+          else note_launch(), k_prolong_rows4<2, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, xc, nc[1], (float*)x);
         } else if (g_.ndim == 3) {
-          k_prolong_rows<T, 3, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+          note_launch(),
+              k_prolong_rows<T, 3, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
         } else {
-          k_prolong_rows<T, 2, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
+          note_launch(),
+              k_prolong_rows<T, 2, true><<<gr, kBlock, 0, s>>>(n[0], n[1], rows, (const T*)lv_[l + 1].x, nc[1], x);
         }
       } else {
         e = cudaMemsetAsync(x, 0, cells3(n) * sizeof(T), s);
         if (e != cudaSuccess) return e;
-        k_prolong<T><<<nblk(cells3(n)), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
+        note_launch(), k_prolong<T><<<nblk(cells3(n)), kBlock, 0, s>>>(n, g_.ndim, (const T*)lv_[l + 1].x, nc, x);
       }
     }
     e = vcycle<T>(l, l == 0 ? nu1 : nuc1_, l == 0 ? nu2 : nuc2_, l == 0 ? x64 : nullptr, s, false);
@@ -1195,16 +1216,19 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       const float* dv = (const float*)lv_[0].x;
       float* rv = (float*)lv_[0].r;
       if (g_.ndim == 3)
-        k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
-                                                          partials_);
+        note_launch(),
+            k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
+                                                              partials_);
       else if (g_.ndim == 2)
-        k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
-                                                          partials_);
+        note_launch(),
+            k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
+                                                              partials_);
       else
-        k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
-                                                          partials_);
-      k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
-      k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
+        note_launch(),
+            k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
+                                                              partials_);
+      note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
+      note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
     } else {
       TraceScope ts("residual", s);
       df_res = mixed && df_mode_ && !fp64_op_ && cycles == 0;
@@ -1221,11 +1245,12 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
           if (e != cudaSuccess) return e;
         }
         if (mixed)
-          k_residual64_df<<<nparts_, kBlock, 0, s>>>(L64, x_in, x, b64_, diag64_, (float*)lv_[0].r, rlo_, partials_);
+          note_launch(),
+              k_residual64_df<<<nparts_, kBlock, 0, s>>>(L64, x_in, x, b64_, diag64_, (float*)lv_[0].r, rlo_, partials_);
         else
-          k_residual64<T><<<nparts_, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r,
-                                                     partials_);
-        k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
+          note_launch(), k_residual64<T><<<nparts_, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r,
+                                                                    partials_);
+        note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
       }
     }
     cudaError_t e = cudaMemcpyAsync(host_scal_, scal_, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);

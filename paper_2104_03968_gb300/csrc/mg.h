@@ -101,6 +101,7 @@ class Multigrid {
   struct GraphEntry {
     int l, nu1, nu2, zero;
     cudaGraphExec_t exec;
+    unsigned long long kernels;  // kernel launches captured in the graph
   };
   std::vector<GraphEntry> graphs_;
   cudaStream_t cap_stream_ = nullptr;

@@ -287,7 +287,8 @@ cudaError_t launch_faces_df(const GridDev& g, const DfConst& K, const double* D,
                             float* const wlo[3], unsigned* flag, cudaStream_t s) {
   TraceScope ts("faces", s);
   const int rows = g.n[1] * g.n[2];
-  k_faces_df<<<(unsigned)std::min(rows, 152 * 16), 256, 0, s>>>(g, K, D, w[0], w[1], w[2], wlo[0], wlo[1], wlo[2], flag);
+  note_launch(),
+      k_faces_df<<<(unsigned)std::min(rows, 152 * 16), 256, 0, s>>>(g, K, D, w[0], w[1], w[2], wlo[0], wlo[1], wlo[2], flag);
   return cudaGetLastError();
 }
 
@@ -296,14 +297,17 @@ cudaError_t launch_setup_res0_df(const GridDev& g, const DfConst& K, const Level
                                  float* invd, float* rhi, float* rlo, int nparts, double* parts, double* scal,
                                  unsigned* flag, cudaStream_t s) {
   if (g.ndim == 3)
-    k_setup_res0_df<3><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
+    note_launch(),
+        k_setup_res0_df<3><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
   else if (g.ndim == 2)
-    k_setup_res0_df<2><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
+    note_launch(),
+        k_setup_res0_df<2><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
   else
-    k_setup_res0_df<1><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
-  k_reduce<<<1, 1024, 0, s>>>(parts, nparts, scal);
-  k_reduce<<<1, 1024, 0, s>>>(parts + nparts, nparts, scal + 2);
-  k_reduce<<<1, 1024, 0, s>>>(parts + 2 * nparts, nparts, scal + 1);
+    note_launch(),
+        k_setup_res0_df<1><<<nparts, 256, 0, s>>>(g, K, L, Llo, x, x64, dhi, dlo, invd, rhi, rlo, nparts, parts, flag);
+  note_launch(), k_reduce<<<1, 1024, 0, s>>>(parts, nparts, scal);
+  note_launch(), k_reduce<<<1, 1024, 0, s>>>(parts + nparts, nparts, scal + 2);
+  note_launch(), k_reduce<<<1, 1024, 0, s>>>(parts + 2 * nparts, nparts, scal + 1);
   return cudaGetLastError();
 }
 

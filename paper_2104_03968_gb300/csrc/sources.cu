@@ -157,7 +157,8 @@ cudaError_t launch_radiation_terms(const GridDev& g, const Opacity& op, double c
   O.work = work;
   O.fedd = fedd;
   O.tiring = tiring;
-  k_radiation_terms<<<(unsigned)((g.ncell + kBlock - 1) / kBlock), kBlock, 0, s>>>(g, ph, E, rho, eps, V, O, status);
+  note_launch(),
+      k_radiation_terms<<<(unsigned)((g.ncell + kBlock - 1) / kBlock), kBlock, 0, s>>>(g, ph, E, rho, eps, V, O, status);
   return cudaGetLastError();
 }
 
@@ -165,7 +166,7 @@ cudaError_t launch_tiring_update(long long n, double dt, const double* tiring, d
                                  cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   TraceScope ts("tiring_update", s);
-  k_tiring_update<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, dt, tiring, E, status);
+  note_launch(), k_tiring_update<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, dt, tiring, E, status);
   return cudaGetLastError();
 }
 

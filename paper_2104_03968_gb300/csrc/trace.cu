@@ -1,9 +1,12 @@
 // Per-kernel launch timing with CUDA events.
 #include <map>
 
+#include "fld_common.cuh"
 #include "trace.h"
 
 namespace fld {
+
+std::atomic<unsigned long long> g_kernel_launches{0};  // declared in fld_common.cuh
 
 Tracer& tracer() {
   static Tracer t;

@@ -107,6 +107,8 @@ def load():
                 f.restype = ct.c_int
             lib.fld_last_error.argtypes = [P]
             lib.fld_last_error.restype = ct.c_char_p
+            lib.fld_launch_count.argtypes = []
+            lib.fld_launch_count.restype = ct.c_ulonglong
             _lib = lib
     return _lib
 
@@ -141,6 +143,11 @@ class Context:
 
 
 # ----------------------------------------------------------------------------- marshalling
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process so far (graph replays included)."""
+    return int(load().fld_launch_count())
+
 
 def _stream():
     return ct.c_void_p(torch.cuda.current_stream().cuda_stream)

@@ -272,6 +272,32 @@ def test_diffuse_diagonal_tensor(ctx, shape, bcname, precision):
     assert relerr(x, ref) < TOL
 
 
+def test_launch_count(ctx):
+    """fld_launch_count counts the kernels of a step, those replayed in CUDA graphs included: two
+    identical steps (same state, same cycles) count the same, and a 3-D multigrid step with
+    several levels launches more kernels than it has levels x sweeps."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small((64, 48, 40), seed=3, dt_factor=30.0)
+    p = solver(case["phys"], rtol=1e-8, nu1=2, nu2=2)
+    counts, cycles = [], []
+    for _ in range(3):
+        eps, E = dev(case["eps"]), dev(case["E"])
+        n0 = fld.launch_count()
+        info = fld.step(ctx, case["grid"], p, case["dt"], dev(case["rho"]), eps, E)
+        torch.cuda.synchronize()
+        counts.append(fld.launch_count() - n0)
+        cycles.append(info["cycles"])
+    assert cycles[1] == cycles[2] and counts[1] == counts[2], (counts, cycles)
+    assert counts[2] > 4 * 2 * 2 * cycles[2]
+    cases = inputs.batched_2d(ngrids=6, seed=9, nmin=64, nmax=128)
+    args = ([c["grid"] for c in cases], [solver(c["phys"], rtol=1e-8) for c in cases], [c["dt"] for c in cases],
+            [dev(c["rho"]) for c in cases])
+    fld.step_batched(ctx, *args, [dev(c["eps"]) for c in cases], [dev(c["E"]) for c in cases])  # builds the graph
+    n0 = fld.launch_count()
+    fld.step_batched(ctx, *args, [dev(c["eps"]) for c in cases], [dev(c["E"]) for c in cases])
+    assert fld.launch_count() - n0 > 10
+
+
 @pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
 @pytest.mark.parametrize("kind", ["numpy", "pinned"])
 def test_step_on_host_arrays_equals_device_step(ctx, order, kind):
