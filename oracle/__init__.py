@@ -82,6 +82,7 @@ def _load():
                 "ora_opacity": (None, [ct.c_size_t, P, _D, _D, _D]),
                 "ora_coeffs": (ct.c_int, [P, P, _D, _D, _D, _D, _D]),
                 "ora_radiation_sources": (ct.c_int, [P, P, _D, _D, _D, P, P, P, _D, _D, P, _D]),
+                "ora_pseudo_planar_source": (ct.c_int, [P, P, ct.c_double, _D, _D, _D, P, _D]),
                 "ora_apply": (None, [P, ct.c_double, _D, _D, _D]),
                 "ora_rhs": (None, [P, ct.c_double, _D, _D, _D]),
                 "ora_relres": (ct.c_double, [P, ct.c_double, _D, _D, _D]),
@@ -231,6 +232,23 @@ def radiation_sources(grid: dict, phys: dict, E, rho, kappa, v=None) -> dict:
     if st:
         raise ValueError(f"oracle radiation_sources: status {st}")
     return out
+
+
+
+def pseudo_planar_source(grid: dict, phys: dict, x0: float, E, rho, kappa, v=None) -> np.ndarray:
+    """Appendix A: the geometric source of the radiation energy on a Cartesian grid whose x axis
+    stands for the radius, S = -2 (E v_x + F_x) / x + 2 v_x P_xx / x, x = x0 + (i + 1/2) dx_x the
+    cell centre's radius; F and P as in radiation_sources; v = None means v = 0."""
+    E, rho, kappa = _f64(E), _f64(rho), _f64(kappa)
+    S = np.empty_like(E)
+    vs = None if v is None else [_f64(c) for c in v]
+    pv = _ptr_array(vs)
+    keep = []
+    st = _load().ora_pseudo_planar_source(_ref(_grid(grid)), _ref(_phys(phys, keep)), float(x0), _ptr(E), _ptr(rho),
+                                          _ptr(kappa), pv[0] if pv else None, _ptr(S))
+    if st:
+        raise ValueError(f"oracle pseudo_planar_source: status {st}")
+    return S
 
 
 # ----------------------------------------------------------------------------- diffusion

@@ -11,6 +11,9 @@
  *   ora_kappa_cak         Sect. 5.1, Eq. (kap_cak): CAK line opacity along a radial column.
  *   ora_radiation_sources Sect. 2.1-2.2 and 3.2: flux, radiation force and work, Eddington
  *                         factor and tensor, photon tiring P : grad v.
+ *   ora_pseudo_planar_source  Appendix A: the geometric source of the radiation energy on a
+ *                         Cartesian grid whose x axis stands for the radius, -2(E v_x + F_x)/x,
+ *                         plus the radiation-work correction 2 v_x P_xx / x as printed there.
  *   ora_lambda_minerbo    the Minerbo limiter that Sect. 2.2 names as the alternative (its
  *                         formula is not printed there; the two-branch form of Minerbo's
  *                         closure, joined at R = 3/2, is restated here).
@@ -277,6 +280,32 @@ int ora_radiation_sources(const ora_grid* g, const ora_phys* p, const double* E,
     }
   }
   return 0;
+}
+
+int ora_pseudo_planar_source(const ora_grid* g, const ora_phys* p, double x0, const double* E,
+                             const double* rho, const double* kappa, const double* const* v, double* S) {
+  /* Appendix A: x ~ r, so the spherical divergence (1/r^2) d_r (r^2 f) is the Cartesian d_x f
+     plus 2 f / x, moved to the right-hand side as a source.  For the radiation energy the
+     divergence carries f = E v + F; the radiation-work term gets its own correction. */
+  size_t N = ncells(g);
+  double* buf = (double*)malloc(9 * N * sizeof(double)); /* F (3 axes), then P (6 components) */
+  if (!buf) return 3;
+  double* F[3];
+  double* P[6];
+  for (int a = 0; a < 3; ++a) F[a] = buf + (size_t)a * N;
+  for (int m = 0; m < 6; ++m) P[m] = buf + (size_t)(3 + m) * N;
+  int st = ora_radiation_sources(g, p, E, rho, kappa, NULL, F, NULL, NULL, NULL, P, NULL);
+  if (st == 0) {
+    for (size_t c = 0; c < N; ++c) {
+      int q[3];
+      unlin(g, c, q);
+      double x = x0 + (q[0] + 0.5) * g->dx[0]; /* the cell centre's radius */
+      double vx = v ? v[0][c] : 0.0;
+      S[c] = -2.0 * (E[c] * vx + F[0][c]) / x + 2.0 * vx * P[0][c] / x;
+    }
+  }
+  free(buf);
+  return st;
 }
 
 /* ------------------------------------------------------------------ operator */

@@ -50,6 +50,10 @@ int ora_radiation_sources(const ora_grid* g, const ora_phys* p, const double* E,
                           const double* kappa, const double* const* v, double* const* F, double* const* fr,
                           double* work, double* fedd, double* const* P, double* tiring);
 
+/* pseudo-planar geometric source of E (x = x0 + (i + 1/2) dx[0]); v may be NULL (v = 0) */
+int ora_pseudo_planar_source(const ora_grid* g, const ora_phys* p, double x0, const double* E,
+                             const double* rho, const double* kappa, const double* const* v, double* S);
+
 /* 4th-order 5-point gradient, |grad E|, R, lambda and D = c lambda/(kappa rho) per cell. */
 int ora_coeffs(const ora_grid* g, const ora_phys* p, const double* E, const double* rho,
                const double* kappa, double* D_cell, double* gradmag);

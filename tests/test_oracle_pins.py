@@ -673,6 +673,60 @@ def test_photon_tiring_expansion_and_rotation():
         assert np.abs(out["tiring"]).max() < 1e-12 * E.max()
 
 
+def test_pseudo_planar_source_completes_the_spherical_divergence():
+    """Appendix A: with x standing for r, the source -2 F_x / x (v = 0) is what the Cartesian
+    divergence d_x F lacks of the spherical one (1/x^2) d_x (x^2 F).  For E = a + b / x and
+    lambda = 1/3 the flux is F = c b / (3 kappa rho x^2), so x^2 F is constant, the spherical
+    divergence vanishes and S must equal d_x F = -2 c b / (3 kappa rho x^3).  Two inner radii x0
+    pin the cell-centre radius x0 + (i + 1/2) dx."""
+    n, dx, b = 200, 0.01, 0.5
+    g = {"ndim": 1, "n": [n, 1, 1], "dx": [dx, 1, 1], "bc": ["continuous"] * 2 + ["periodic"] * 4,
+         "bc_val": [0.0] * 6}
+    phys = inputs.code_units("third")
+    kap, rho = 3.0, 2.0
+    for x0 in (0.5, 1.0):
+        x = x0 + (np.arange(n) + 0.5) * dx
+        E = 2.0 + b / x
+        S = oracle.pseudo_planar_source(g, phys, x0, E, np.full(n, rho), np.full(n, kap))
+        inner = slice(2, -2)
+        dFdx = -2.0 * phys["c"] * b / (3 * kap * rho * x ** 3)
+        assert np.allclose(S[inner], dFdx[inner], rtol=1e-5, atol=0)
+        # the same from the oracle's own flux, differentiated here by 4th-order central
+        # differences (away from the two cells at each end, whose flux sees the extrapolated ghosts)
+        F = oracle.radiation_sources(g, phys, E, np.full(n, rho), np.full(n, kap))["F"][0]
+        dF = (F[:-4] - 8 * F[1:-3] + 8 * F[3:-1] - F[4:]) / (12 * dx)
+        assert np.allclose(S[4:-4], dF[2:-2], rtol=1e-5, atol=0)
+
+
+def test_pseudo_planar_source_advection_and_work_limits():
+    """Appendix A, S = -2 (E v_x + F_x)/x + 2 v_x P_xx / x, in limits where F and P are known:
+    uniform E (F = 0, f = 1/3, P_xx = E/3) gives -(4/3) E v / x; E varying only across x gives
+    F_x = 0 and P_xx = E (1 - f) / 2, so -2 E v / x when free streaming (f = 1) and -(4/3) E v / x
+    when thick; free streaming along x with v = 0 (F_x = c E for E falling with x) gives
+    -2 c E / x."""
+    phys = inputs.code_units()
+    nx, ny, dx, x0 = 24, 16, 0.25, 3.0
+    x = x0 + (np.arange(nx) + 0.5) * dx
+    g1 = {"ndim": 1, "n": [nx, 1, 1], "dx": [dx, 1, 1], "bc": ["continuous"] * 2 + ["periodic"] * 4,
+          "bc_val": [0.0] * 6}
+    v = 0.2 + 0.1 * np.sin(x)
+    E = np.full(nx, 3.0)
+    S = oracle.pseudo_planar_source(g1, phys, x0, E, np.ones(nx), np.ones(nx), v=[v])
+    assert np.allclose(S, -(4.0 / 3.0) * E * v / x, rtol=1e-14, atol=0)
+    g2 = {"ndim": 2, "n": [nx, ny, 1], "dx": [dx, dx, 1], "bc": ["continuous"] * 4 + ["periodic"] * 2,
+          "bc_val": [0.0] * 6}
+    Y, X = np.meshgrid((np.arange(ny) + 0.5) * dx, x, indexing="ij")
+    E2 = np.exp(0.3 * Y)
+    V = 0.2 + 0.1 * np.sin(X)
+    for kap, want in ((1e-10, -2.0), (1e8, -4.0 / 3.0)):
+        S = oracle.pseudo_planar_source(g2, phys, x0, E2, np.ones_like(E2), np.full_like(E2, kap),
+                                        v=[V, np.zeros_like(V)])
+        assert np.allclose(S, want * E2 * V / X, rtol=1e-6, atol=0)
+    E3 = np.exp(-0.4 * x)
+    S = oracle.pseudo_planar_source(g1, phys, x0, E3, np.ones(nx), np.full(nx, 1e-10))
+    assert np.allclose(S[2:-2], (-2.0 * phys["c"] * E3 / x)[2:-2], rtol=1e-6, atol=0)
+
+
 def test_diagonal_tensor_diffusion_fourier():
     """The diagonal-tensor D (Sect. 6: one diffusion coefficient per grid direction): on a periodic
     grid with uniform D_a per axis each Fourier mode of backward Euler is multiplied by
