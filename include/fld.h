@@ -268,6 +268,24 @@ FLD_API fld_status fld_photon_tiring_step(fld_ctx* ctx, const fld_grid* grid, co
                                   double dt, const double* rho, const double* eps,
                                   const double* const* v, double* E, void* stream);
 
+/* Pseudo-planar geometric source of the radiation energy (Appendix A).  The grid is Cartesian and
+   its x axis (axis 0) stands for the radius of a radially extended problem; the spherical
+   divergence differs from the Cartesian one by 2 f_x / x, which becomes a source.  Per cell
+     S = -2 (E v_x + F_x) / x + 2 v_x P_xx / x,   x = x0 + (i + 1/2) dx[0]
+   (the second term corrects the radiation-work term P : grad v, as printed in the appendix), with
+   F and P exactly as in fld_radiation_terms.  x0 >= 0 is the radius of the grid's lower x face.
+   v = host array of grid->ndim DEVICE pointers to the velocity components, or NULL (v = 0, so
+   S = -2 F_x / x).  S: DEVICE array of N cells (out).  sync as in fld_radiation_terms. */
+FLD_API fld_status fld_pseudo_planar_source(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double x0,
+                                    const double* E, const double* rho, const double* eps,
+                                    const double* const* v, double* S, int sync, void* stream);
+
+/* E <- E + dt S with S the pseudo-planar source of the state on entry (context scratch holds
+   S).  Synchronises; FLD_ERR_NONPOSITIVE when the input is invalid or the update leaves E <= 0. */
+FLD_API fld_status fld_pseudo_planar_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
+                                  double x0, const double* rho, const double* eps,
+                                  const double* const* v, double* E, void* stream);
+
 /* ---- allocation-free column update (no counterpart in the paper; a deployment convenience).
    Some callers cannot allocate device memory when they advance the radiation field: codes whose
    own memory manager has reserved the whole GPU in advance, runtimes that forbid device

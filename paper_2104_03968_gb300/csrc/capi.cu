@@ -648,7 +648,8 @@ fld_status fld_radiation_terms(fld_ctx* ctx, const fld_grid* grid, const fld_par
   GridDev g = to_dev(grid);
   if ((st = reset_status(ctx, s)) != FLD_OK) return st;
   cudaError_t e = launch_radiation_terms(g, to_opacity(p), p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps,
-                                         v ? vv : nullptr, FF, ff, work, fedd, PP, tiring, ctx->d_status, s);
+                                         v ? vv : nullptr, FF, ff, work, fedd, PP, tiring, nullptr, 0.0,
+                                         ctx->d_status, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "radiation terms launch");
   if (sync) {
     unsigned sbits = 0;
@@ -676,8 +677,67 @@ fld_status fld_photon_tiring_step(fld_ctx* ctx, const fld_grid* grid, const fld_
                            stream);
   if (st != FLD_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_tiring_update(g.ncell, dt, ctx->D, E, ctx->d_status, s);
+  cudaError_t e = launch_explicit_update(g.ncell, -dt, ctx->D, E, ctx->d_status, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tiring update launch");
+  unsigned sbits = 0;
+  int it = 0, bi = 0;
+  if ((st = read_status(ctx, s, &sbits, &it, &bi)) != FLD_OK) return st;
+  if (sbits & kStatNonpositive) return fail(ctx, FLD_ERR_NONPOSITIVE, "invalid input or E <= 0 after the update");
+  return FLD_OK;
+}
+
+fld_status fld_pseudo_planar_source(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double x0,
+                                    const double* E, const double* rho, const double* eps, const double* const* v,
+                                    double* S, int sync, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_grid(ctx, grid);
+  if (st == FLD_OK) st = check_params(ctx, p, false);
+  if (st != FLD_OK) return st;
+  if (!(x0 >= 0) || !std::isfinite(x0)) return fail(ctx, FLD_ERR_INVALID_ARG, "x0 must be finite and >= 0");
+  if (!E || !rho || !eps || !S) return fail(ctx, FLD_ERR_INVALID_ARG, "E, rho, eps and S must be non-NULL");
+  const double* vv[3] = {nullptr, nullptr, nullptr};
+  if (v)
+    for (int a = 0; a < grid->ndim; ++a) {
+      if (!v[a]) return fail(ctx, FLD_ERR_INVALID_ARG, "velocity component %d is NULL", a);
+      vv[a] = v[a];
+    }
+  double* none3[3] = {nullptr, nullptr, nullptr};
+  double* none6[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  GridDev g = to_dev(grid);
+  if ((st = reset_status(ctx, s)) != FLD_OK) return st;
+  cudaError_t e = launch_radiation_terms(g, to_opacity(p), p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps,
+                                         v ? vv : nullptr, none3, none3, nullptr, nullptr, none6, nullptr, S, x0,
+                                         ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pseudo-planar source launch");
+  if (sync) {
+    unsigned sbits = 0;
+    int it = 0, bi = 0;
+    if ((st = read_status(ctx, s, &sbits, &it, &bi)) != FLD_OK) return st;
+    if (sbits & kStatNonpositive) return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0)");
+  }
+  return FLD_OK;
+}
+
+fld_status fld_pseudo_planar_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, double x0,
+                                  const double* rho, const double* eps, const double* const* v, double* E,
+                                  void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
+  fld_status st = check_grid(ctx, grid);
+  if (st != FLD_OK) return st;
+  DeviceGuard dg(ctx->device);
+  GridDev g = to_dev(grid);
+  if ((st = ensure_scratch(ctx, g.ncell)) != FLD_OK) return st;
+  // the source into the context's D scratch, then the update (the stencil reads E)
+  st = fld_pseudo_planar_source(ctx, grid, p, x0, E, rho, eps, v, ctx->D, 0, stream);
+  if (st != FLD_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_explicit_update(g.ncell, dt, ctx->D, E, ctx->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pseudo-planar update launch");
   unsigned sbits = 0;
   int it = 0, bi = 0;
   if ((st = read_status(ctx, s, &sbits, &it, &bi)) != FLD_OK) return st;

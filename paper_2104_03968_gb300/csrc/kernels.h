@@ -25,15 +25,16 @@ cudaError_t launch_faces(const GridDev& g, double dt, const double* const Dax[3]
 cudaError_t launch_midpoint_combine(long long n, const double* E0, const double* eps0, const double* Eh, double* E,
                                     double* eps, cudaStream_t s);
 
-// explicit radiation terms (sources.cu); null output pointers are skipped
+// explicit radiation terms (sources.cu); null output pointers are skipped; sg = the pseudo-planar
+// source of E with x0 the radius of the grid's lower x face
 cudaError_t launch_radiation_terms(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
                                    int limiter, const double* E, const double* rho, const double* eps,
                                    const double* const v[3], double* const F[3], double* const fr[3], double* work,
-                                   double* fedd, double* const P[6], double* tiring, unsigned* status,
+                                   double* fedd, double* const P[6], double* tiring, double* sg, double x0,
+                                   unsigned* status, cudaStream_t s);
+// E += a * S
+cudaError_t launch_explicit_update(long long n, double a, const double* S, double* E, unsigned* status,
                                    cudaStream_t s);
-// E -= dt * tiring
-cudaError_t launch_tiring_update(long long n, double dt, const double* tiring, double* E, unsigned* status,
-                                 cudaStream_t s);
 
 cudaError_t launch_exchange(long long n, const ExchangeParams& p, const Opacity& op, const double* rho,
                             const double* kappa, double* eps, double* E, int* info_iters, int* info_bisect,

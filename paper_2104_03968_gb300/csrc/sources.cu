@@ -3,8 +3,10 @@
 // rhd_force) and its work v . f_r, the Eddington factor f = lambda + lambda^2 R^2 (Eq.
 // fld_Edd_fac), the pressure tensor P = E [(1-f)/2 I + (3f-1)/2 n n] (Eq. fld_Edd, n = grad E /
 // |grad E|) and the photon-tiring term P : grad v, with every gradient by the 5-point stencil of
-// Eq. ileyk_flux.  Velocity ghosts on non-periodic faces: linear extrapolation.  FP64; one thread
-// per cell (these terms are evaluated once per step and are FP64-pipe bound like k_coeffs).
+// Eq. ileyk_flux.  Velocity ghosts on non-periodic faces: linear extrapolation.  Optionally the
+// pseudo-planar geometric source of E (Appendix A) on a grid whose x axis stands for the radius:
+// -2 (E v_x + F_x) / x + 2 v_x P_xx / x at the cell centre's radius x.  FP64; one thread per cell
+// (these terms are evaluated once per step and are FP64-pipe bound like k_coeffs).
 #include "coeffs.cuh"
 #include "kernels.h"
 #include "trace.h"
@@ -18,6 +20,8 @@ struct SourceOut {
   double* fedd;
   double* P[6];  // xx yy zz xy xz yz
   double* tiring;
+  double* sg;  // pseudo-planar source of E
+  double x0;   // radius of the grid's lower x face (for sg)
 };
 
 struct VelIn {
@@ -107,6 +111,11 @@ __global__ void k_radiation_terms(GridDev g, CoeffPhys ph, const double* __restr
     O.P[4][idx] = P[0][2];
     O.P[5][idx] = P[1][2];
   }
+  if (O.sg) {
+    const double x = O.x0 + (i + 0.5) * g.dx[0];
+    const double vx = V.v[0] ? V.v[0][idx] : 0.0;
+    O.sg[idx] = (-2.0 * fma(e, vx, -D * gE[0]) + 2.0 * vx * P[0][0]) / x;
+  }
   if (O.tiring) {
     double t = 0.0;
     if (V.v[0]) {
@@ -128,12 +137,13 @@ __global__ void k_radiation_terms(GridDev g, CoeffPhys ph, const double* __restr
   }
 }
 
-// E <- E - dt * tiring (Sect. 3.2: the explicit addition of -P : grad v over dt)
-__global__ void k_tiring_update(long long n, double dt, const double* __restrict__ tiring, double* __restrict__ E,
-                                unsigned* __restrict__ status) {
+// E <- E + a * S: the explicit addition of a source over a step (Sect. 3.2: a = -dt with
+// S = P : grad v; Appendix A: a = dt with the pseudo-planar source)
+__global__ void k_explicit_update(long long n, double a, const double* __restrict__ S, double* __restrict__ E,
+                                  unsigned* __restrict__ status) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
-  const double v = fma(-dt, tiring[idx], E[idx]);
+  const double v = fma(a, S[idx], E[idx]);
   if (!(v > 0.0)) atomicOr(status, kStatNonpositive);
   E[idx] = v;
 }
@@ -141,8 +151,8 @@ __global__ void k_tiring_update(long long n, double dt, const double* __restrict
 cudaError_t launch_radiation_terms(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
                                    int limiter, const double* E, const double* rho, const double* eps,
                                    const double* const v[3], double* const F[3], double* const fr[3], double* work,
-                                   double* fedd, double* const P[6], double* tiring, unsigned* status,
-                                   cudaStream_t s) {
+                                   double* fedd, double* const P[6], double* tiring, double* sg, double x0,
+                                   unsigned* status, cudaStream_t s) {
   if (g.ncell == 0) return cudaSuccess;
   TraceScope ts("radiation_terms", s);
   CoeffPhys ph{op, c, gamma, gas_R, limiter};
@@ -157,16 +167,18 @@ cudaError_t launch_radiation_terms(const GridDev& g, const Opacity& op, double c
   O.work = work;
   O.fedd = fedd;
   O.tiring = tiring;
+  O.sg = sg;
+  O.x0 = x0;
   note_launch(),
       k_radiation_terms<<<(unsigned)((g.ncell + kBlock - 1) / kBlock), kBlock, 0, s>>>(g, ph, E, rho, eps, V, O, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tiring_update(long long n, double dt, const double* tiring, double* E, unsigned* status,
-                                 cudaStream_t s) {
+cudaError_t launch_explicit_update(long long n, double a, const double* S, double* E, unsigned* status,
+                                   cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  TraceScope ts("tiring_update", s);
-  note_launch(), k_tiring_update<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, dt, tiring, E, status);
+  TraceScope ts("explicit_update", s);
+  note_launch(), k_explicit_update<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, a, S, E, status);
   return cudaGetLastError();
 }
 

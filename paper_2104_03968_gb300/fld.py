@@ -84,6 +84,8 @@ _SIGS = {
     "fld_radiation_terms": [P, P, P, P, P, P, P, P, P, P, P, P, P, ct.c_int, P],
     "fld_diffuse_aniso": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_photon_tiring_step": [P, P, P, ct.c_double, P, P, P, P, P],
+    "fld_pseudo_planar_source": [P, P, P, ct.c_double, P, P, P, P, P, ct.c_int, P],
+    "fld_pseudo_planar_step": [P, P, P, ct.c_double, ct.c_double, P, P, P, P, P],
 }
 
 
@@ -482,3 +484,31 @@ def photon_tiring_step(ctx: Context, grid: dict, params: dict, dt: float, rho, e
     pv, kv = _dev_ptr_array(v)
     ctx.check(ctx.lib.fld_photon_tiring_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(rho), _dptr(eps), pv,
                                              _dptr(E), _stream()))
+
+
+def pseudo_planar_source(ctx: Context, grid: dict, params: dict, x0: float, E, rho, eps, v=None):
+    """Pseudo-planar geometric source of E (Appendix A) on a grid whose x axis stands for the
+    radius: -2 (E v_x + F_x) / x + 2 v_x P_xx / x, x = x0 + (i + 1/2) dx_x.  v: list of ndim
+    velocity tensors or None.  Returns a CUDA tensor shaped like E."""
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    if v is not None:
+        for c in v:
+            _dptr(c)
+    pv, kv = _dev_ptr_array(v)
+    S = torch.empty_like(E)
+    ctx.check(ctx.lib.fld_pseudo_planar_source(ctx.h, ct.byref(g), ct.byref(p), float(x0), _dptr(E), _dptr(rho),
+                                               _dptr(eps), pv, _dptr(S), 1, _stream()))
+    return S
+
+
+def pseudo_planar_step(ctx: Context, grid: dict, params: dict, dt: float, x0: float, rho, eps, v, E) -> None:
+    """E <- E + dt S in place, S the pseudo-planar source of the state on entry (Appendix A)."""
+    keep = []
+    g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
+    if v is not None:
+        for c in v:
+            _dptr(c)
+    pv, kv = _dev_ptr_array(v)
+    ctx.check(ctx.lib.fld_pseudo_planar_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), float(x0), _dptr(rho),
+                                             _dptr(eps), pv, _dptr(E), _stream()))

@@ -530,6 +530,32 @@ def test_radiation_terms_parity(ctx, shape, bcname, limiter):
     assert relerr(host(E).reshape(case["E"].shape), case["E"] - dt * ref["tiring"]) < 1e-13
 
 
+@pytest.mark.parametrize("shape,bcname", [((24, 20, 18), "periodic"), ((70, 45), "mixed"), ((300,), "neumann"),
+                                          ((1000,), "dirichlet")])
+@pytest.mark.parametrize("x0", [0.0, 7.5])
+def test_pseudo_planar_parity(ctx, shape, bcname, x0):
+    """The pseudo-planar source of E (Appendix A), with and without a velocity field, and the
+    explicit step E <- E + dt S; x0 < 0 is rejected before any launch."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small(shape, seed=90 + len(shape), bc=BCS[bcname])
+    g, p = case["grid"], case["phys"]
+    rng = np.random.default_rng(91)
+    v = [rng.standard_normal(case["E"].shape) for _ in range(len(shape))]
+    kap = oracle.opacity(p, case["rho"], case["eps"])
+    args = (dev(case["E"]), dev(case["rho"]), dev(case["eps"]))
+    for vel in (None, v):
+        ref = oracle.pseudo_planar_source(g, p, x0, case["E"], case["rho"], kap, v=vel)
+        S = fld.pseudo_planar_source(ctx, g, p, x0, *args, v=None if vel is None else [dev(c) for c in vel])
+        torch.cuda.synchronize()
+        assert relerr(host(S).reshape(ref.shape), ref) < 1e-12
+    dt = 1e-4 * float(np.min(case["E"] / np.maximum(np.abs(ref), 1e-300)))
+    E = dev(case["E"])
+    fld.pseudo_planar_step(ctx, g, p, dt, x0, dev(case["rho"]), dev(case["eps"]), [dev(c) for c in v], E)
+    assert relerr(host(E).reshape(case["E"].shape), case["E"] + dt * ref) < 1e-13
+    with pytest.raises(fld.FldError):
+        fld.pseudo_planar_source(ctx, g, p, -1.0, *args)
+
+
 # ----------------------------------------------------------------------------- columns
 
 def _column_case(ncol, ncell, seed=0):
