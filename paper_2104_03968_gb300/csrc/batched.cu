@@ -70,6 +70,7 @@ struct BLev {
   T* r;
   T* tmp;
   long long ncell;
+  FastDiv f0, f1, fh;  // division by n[0], n[1] and (n[0] + 1) / 2: 32-bit index splitting
 };
 
 struct BState {
@@ -166,12 +167,14 @@ __global__ void kb_faces(const Tile* __restrict__ tiles, const BFine* __restrict
   const bool copy = sizeof(T) == sizeof(float);
   const double* const Dax[3] = {f.D, f.D, f.D};
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
-    long long idx = tl.start + c;
+    const unsigned idx = (unsigned)(tl.start + c);
+    int q[3];
+    unflatten32(idx, L0.f0, L0.f1, q[0], q[1], q[2]);
     if (copy)
-      faces_cell<float>(f.g, f.dt, Dax, idx, f.w64[0], f.w64[1], f.w64[2], (float*)L0.L.w[0], (float*)L0.L.w[1],
-                        (float*)L0.L.w[2]);
+      faces_cell_at<float>(f.g, f.dt, Dax, q, idx, f.w64[0], f.w64[1], f.w64[2], (float*)L0.L.w[0],
+                           (float*)L0.L.w[1], (float*)L0.L.w[2]);
     else
-      faces_cell<double>(f.g, f.dt, Dax, idx, f.w64[0], f.w64[1], f.w64[2], nullptr, nullptr, nullptr);
+      faces_cell_at<double>(f.g, f.dt, Dax, q, idx, f.w64[0], f.w64[1], f.w64[2], nullptr, nullptr, nullptr);
   }
 }
 
@@ -181,9 +184,13 @@ __global__ void kb_fine_setup(const Tile* __restrict__ tiles, const BFine* __res
   const Tile tl = tiles[blockIdx.x];
   const BFine& f = fine[tl.grid];
   LevelDev<double> L = fine_level(f);
-  T* invd = lev[tl.grid * kMaxLev].invd;
-  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x)
-    fine_setup_cell<T>(L, f.g, f.E, tl.start + c, f.b, f.diag, invd);
+  const BLev<T>& L0 = lev[tl.grid * kMaxLev];
+  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+    const unsigned idx = (unsigned)(tl.start + c);
+    int i, j, k;
+    unflatten32(idx, L0.f0, L0.f1, i, j, k);
+    fine_setup_at<T>(L, f.g, f.E, i, j, k, idx, f.b, f.diag, L0.invd);
+  }
 }
 
 // coarse level l (tile list over its cells): lower faces of each cell and the faces n_a it owns,
@@ -194,19 +201,19 @@ __global__ void kb_coarse_faces(const Tile* __restrict__ tiles, const BLev<T>* _
   const BLev<T>& C = lev[tl.grid * kMaxLev + tl.level];
   const BLev<T>& F = lev[tl.grid * kMaxLev + tl.level - 1];
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
-    long long idx = tl.start + c;
+    const unsigned idx = (unsigned)(tl.start + c);
     int q[3];
-    unflatten(C.L.n, idx, q[0], q[1], q[2]);
+    unflatten32(idx, C.f0, C.f1, q[0], q[1], q[2]);
     for (int a = 0; a < C.L.ndim; ++a) {
-      int m[3] = {C.L.n[0], C.L.n[1], C.L.n[2]};
-      m[a] += 1;
       long long f0 = face_index(C.L.n, a, q[0], q[1], q[2], q[a]);
       T* wc = const_cast<T*>(C.L.w[a]);
-      wc[f0] = coarse_face_value<T>(a, C.L.ndim, F.L.n, m, f0, F.L.w[a]);
+      wc[f0] = coarse_face_at<T>(a, C.L.ndim, F.L.n, q, F.L.w[a]);
       bool periodic = C.L.bc[2 * a + 1] == FLD_BC_PERIODIC;
       if ((periodic && q[a] == 0) || (!periodic && q[a] == C.L.n[a] - 1)) {
         long long fn = face_index(C.L.n, a, q[0], q[1], q[2], C.L.n[a]);
-        wc[fn] = coarse_face_value<T>(a, C.L.ndim, F.L.n, m, fn, F.L.w[a]);
+        int qn[3] = {q[0], q[1], q[2]};
+        qn[a] = C.L.n[a];
+        wc[fn] = coarse_face_at<T>(a, C.L.ndim, F.L.n, qn, F.L.w[a]);
       }
     }
   }
@@ -217,9 +224,9 @@ __global__ void kb_invd(const Tile* __restrict__ tiles, const BLev<T>* __restric
   const Tile tl = tiles[blockIdx.x];
   const BLev<T>& C = lev[tl.grid * kMaxLev + tl.level];
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
-    long long idx = tl.start + c;
+    const unsigned idx = (unsigned)(tl.start + c);
     int i, j, k;
-    unflatten(C.L.n, idx, i, j, k);
+    unflatten32(idx, C.f0, C.f1, i, j, k);
     C.invd[idx] = T(1) / diag_of(C.L, i, j, k, idx);
   }
 }
@@ -248,10 +255,14 @@ __global__ void kb_residual(const Tile* __restrict__ tiles, const BFine* __restr
   if (!st[tl.grid].active) return;
   const BFine& f = fine[tl.grid];
   LevelDev<double> L = fine_level(f);
-  T* r = lev[tl.grid * kMaxLev].r;
+  const BLev<T>& L0 = lev[tl.grid * kMaxLev];
   double acc = 0.0;
-  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x)
-    acc = fma_residual_cell<T>(L, f.E, f.E, f.b, f.diag, r, tl.start + c, acc);
+  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+    const unsigned idx = (unsigned)(tl.start + c);
+    int i, j, k;
+    unflatten32(idx, L0.f0, L0.f1, i, j, k);
+    acc = fma_residual_at<T>(L, f.E, f.E, f.b, f.diag, L0.r, i, j, k, idx, acc);
+  }
   acc = block_sum(acc);
   if (threadIdx.x == 0) parts[blockIdx.x] = acc;
 }
@@ -300,46 +311,243 @@ __global__ void kb_smooth(const Tile* __restrict__ tiles, const BLev<T>* __restr
   if (!st[tl.grid].active) return;
   const BLev<T>& B = lev[tl.grid * kMaxLev + tl.level];
   double* x64 = UPDATE ? fine[tl.grid].E : nullptr;
-  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x)
-    smooth_colour_cell<T, ZERO, UPDATE>(B.L, B.invd, B.r, B.x, color, tl.start + c, x64);
-}
-
-// tiles over the coarse cells of level l+1 (tile.level = l)
-template <class T>
-__global__ void kb_restrict(const Tile* __restrict__ tiles, const BLev<T>* __restrict__ lev, const BState* __restrict__ st) {
-  const Tile tl = tiles[blockIdx.x];
-  if (!st[tl.grid].active) return;
-  const BLev<T>& F = lev[tl.grid * kMaxLev + tl.level];
-  const BLev<T>& C = lev[tl.grid * kMaxLev + tl.level + 1];
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
-    long long idx = tl.start + c;
-    C.r[idx] = restrict_value<T>(F.L, F.r, F.x, C.L.n, idx);
+    // thread t of the colour: half-row position m, row (j, k); the tile list covers exactly
+    // ((n[0] + 1) / 2) n[1] n[2] threads
+    const unsigned t = (unsigned)(tl.start + c);
+    const unsigned row = fast_div(t, B.fh);
+    const unsigned kk = fast_div(row, B.f1);
+    const int m = (int)(t - row * B.fh.d), j = (int)(row - kk * B.f1.d), k = (int)kk;
+    const int i = 2 * m + ((color + j + k) & 1);
+    if (i >= B.L.n[0]) continue;
+    smooth_at<T, ZERO, UPDATE>(B.L, B.invd, B.r, B.x, i, j, k, (long long)i + (long long)B.L.n[0] * row, x64);
   }
 }
 
-// tiles over the cells of level l (tile.level = l)
+// Where a 2-D level's iterate is: the fused sweeps alternate between x and tmp (a sweep cannot
+// update the array its neighbouring tiles are still reading), the host tracks which one holds it
+// at each point of the V-cycle.  Levels of 3-D grids and coarsest levels keep it in x.
 template <class T>
-__global__ void kb_prolong(const Tile* __restrict__ tiles, const BLev<T>* __restrict__ lev, const BState* __restrict__ st) {
+__device__ __forceinline__ T* iterate_of(const BLev<T>& B, bool in_tmp) {
+  return (in_tmp && B.L.ndim == 2) ? B.tmp : B.x;
+}
+
+// tiles over the coarse cells of level l+1 (tile.level = l); f_tmp: level l's iterate is in tmp
+template <class T>
+__global__ void kb_restrict(const Tile* __restrict__ tiles, const BLev<T>* __restrict__ lev, const BState* __restrict__ st,
+                            int f_tmp) {
   const Tile tl = tiles[blockIdx.x];
   if (!st[tl.grid].active) return;
   const BLev<T>& F = lev[tl.grid * kMaxLev + tl.level];
   const BLev<T>& C = lev[tl.grid * kMaxLev + tl.level + 1];
-  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x)
-    prolong_cell<T>(F.L.n, F.L.ndim, C.x, C.L.n, F.x, tl.start + c);
+  const T* xf = iterate_of(F, f_tmp);
+  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+    const unsigned idx = (unsigned)(tl.start + c);
+    int I, J, K;
+    unflatten32(idx, C.f0, C.f1, I, J, K);
+    C.r[idx] = restrict_at<T>(F.L, F.r, xf, I, J, K);
+  }
+}
+
+// tiles over the cells of level l (tile.level = l); f_tmp / c_tmp: where the iterates of levels l
+// and l+1 are (a grid's coarsest level is always in x)
+template <class T>
+__global__ void kb_prolong(const Tile* __restrict__ tiles, const BLev<T>* __restrict__ lev, const BState* __restrict__ st,
+                           const BFine* __restrict__ fine, int f_tmp, int c_tmp) {
+  const Tile tl = tiles[blockIdx.x];
+  if (!st[tl.grid].active) return;
+  const BLev<T>& F = lev[tl.grid * kMaxLev + tl.level];
+  const BLev<T>& C = lev[tl.grid * kMaxLev + tl.level + 1];
+  T* xf = iterate_of(F, f_tmp);
+  const T* xc = iterate_of(C, c_tmp && tl.level + 1 < fine[tl.grid].nlev - 1);
+  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+    const unsigned idx = (unsigned)(tl.start + c);
+    int i, j, k;
+    unflatten32(idx, F.f0, F.f1, i, j, k);
+    prolong_at<T>(F.L.ndim, xc, C.L.n, xf, i, j, k, idx);
+  }
+}
+
+// ----------------------------------------------------------------------------- fused 2-D sweep
+//
+// One red-black Gauss-Seidel sweep of a 2-D level (colour c0, then 1 - c0) in a single pass over
+// memory.  A block owns a kSwX x kSwY tile of one grid's level and stages the iterate of the tile
+// and two cells around it in shared memory (wrapped across periodic boundaries).  It updates
+// colour c0 on the tile and one cell around it -- the cells around are updated again by the tiles
+// that own them, from the same inputs with the same operations, so the copies agree -- then
+// colour 1 - c0 on the tile, whose neighbours are now all final, and writes the tile.  The
+// per-cell arithmetic is smooth_at's, term for term, so the iterates equal those of two
+// colour launches.  Because neighbouring tiles stage cells this block writes, a sweep reads one
+// array and writes the other (x <-> tmp); the first sweep from zero reads no iterate and writes x.
+
+constexpr int kSwX = 64, kSwY = 32;  // cells of a tile
+constexpr int kSwW = kSwX + 4;       // staged row length (two cells each side)
+
+struct Tile2 {
+  int grid;
+  int level;
+  int i0;
+  int j0;
+};
+
+// grid coordinate of a staged position p in [-2, n + 2): wrapped on a periodic axis (n >= 4 on a
+// smoothed level), false beyond a non-periodic boundary
+__device__ __forceinline__ bool sw_coord(int p, int n, bool periodic, int& out) {
+  if (p >= 0 && p < n) {
+    out = p;
+    return true;
+  }
+  if (!periodic) return false;
+  out = p < 0 ? p + n : p - n;
+  return true;
+}
+
+// contribution of one face, as for_each_face classifies it: across = the neighbour through the
+// face (interior or periodic), inward = the next cell inward (the continuous boundary's ghost)
+template <class T>
+__device__ __forceinline__ void sw_face(T w, bool inner, int bc, T across, T inward, T& v, T& d) {
+  constexpr bool kOwnDiag = sizeof(T) == sizeof(float);
+  if (inner || bc == FLD_BC_PERIODIC) {
+    v = fma(w, across, v);
+    if (kOwnDiag) d += w;
+  } else if (bc == FLD_BC_DIRICHLET) {
+    if (kOwnDiag) d += w;
+  } else if (bc == FLD_BC_CONTINUOUS) {
+    v = fma(-w, inward, v);
+    if (kOwnDiag) d -= w;
+  }
+}
+
+// Asynchronous global -> shared copy of one element (cp.async, sm_80 and later): a thread issues
+// all its copies before waiting on any, so a tile's loads are in flight together.
+template <class T>
+__device__ __forceinline__ void sw_copy(T* smem, const T* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(sizeof(T)));
+}
+__device__ __forceinline__ void sw_copy_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// staged arrays of a tile, each (kSwY + 4) x kSwW: the iterate, the right-hand side, the lower x-
+// and y-faces of each position, and 1/diag (the FP64 smoother, and the first sweep from zero)
+constexpr int kSwS = (kSwY + 4) * kSwW;
+template <class T, bool ZERO>
+__host__ __device__ constexpr int sw_arrays() {
+  return (ZERO || sizeof(T) == sizeof(double)) ? 5 : 4;
+}
+
+// smooth_at for a 2-D cell at staged position e (global gi, gj): the upper faces are the lower
+// faces of the next positions, except on the last row / column, whose own upper face (index n)
+// is read from memory
+template <class T>
+__device__ __forceinline__ T sw_cell(const BLev<T>& B, const T* xs, const T* rs, const T* wxs, const T* wys,
+                                     const T* is, int e, int gi, int gj) {
+  const int n0 = B.L.n[0], n1 = B.L.n[1];
+  T v = rs[e], d = T(1);
+  const T wxu = gi < n0 - 1 ? wxs[e + 1] : B.L.w[0][n0 + (long long)(n0 + 1) * gj];
+  const T wyu = gj < n1 - 1 ? wys[e + kSwW] : B.L.w[1][gi + (long long)n0 * n1];
+  sw_face<T>(wxs[e], gi > 0, B.L.bc[0], xs[e - 1], xs[e + 1], v, d);
+  sw_face<T>(wxu, gi < n0 - 1, B.L.bc[1], xs[e + 1], xs[e - 1], v, d);
+  sw_face<T>(wys[e], gj > 0, B.L.bc[2], xs[e - kSwW], xs[e + kSwW], v, d);
+  sw_face<T>(wyu, gj < n1 - 1, B.L.bc[3], xs[e + kSwW], xs[e - kSwW], v, d);
+  if constexpr (sizeof(T) == sizeof(float)) return __fdividef(v, d);
+  else return v * is[e];
+}
+
+// ZERO: the sweep starts from x = 0 (writes x); otherwise it reads x (from_tmp = 0) or tmp and
+// writes the other.  UPDATE: the finest level's last sweep also adds the result to the FP64 iterate.
+// Dynamic shared memory: sw_arrays<T, ZERO>() * kSwS elements.
+template <class T, bool ZERO, bool UPDATE>
+__global__ void __launch_bounds__(256) kb_sweep2d(const Tile2* __restrict__ tiles, const BLev<T>* __restrict__ lev,
+                                                  const BState* __restrict__ st, const BFine* __restrict__ fine,
+                                                  int c0, int from_tmp) {
+  extern __shared__ __align__(16) unsigned char sw_smem[];
+  T* xs = reinterpret_cast<T*>(sw_smem);
+  T* rs = xs + kSwS;
+  T* wxs = rs + kSwS;
+  T* wys = wxs + kSwS;
+  T* is = wys + kSwS;  // only with sw_arrays() == 5
+  constexpr bool kInvd = sw_arrays<T, ZERO>() == 5;
+  const Tile2 tl = tiles[blockIdx.x];
+  if (!st[tl.grid].active) return;
+  const BLev<T>& B = lev[tl.grid * kMaxLev + tl.level];
+  const int n0 = B.L.n[0], n1 = B.L.n[1];
+  const bool px = B.L.bc[0] == FLD_BC_PERIODIC, py = B.L.bc[2] == FLD_BC_PERIODIC;
+  const int w = min(kSwX, n0 - tl.i0), h = min(kSwY, n1 - tl.j0);
+  const int nst = (h + 4) * kSwW;
+  T* dst = (ZERO || from_tmp) ? B.x : B.tmp;
+  const T* src = from_tmp ? B.tmp : B.x;
+  for (int e = threadIdx.x; e < nst; e += blockDim.x) {
+    const int lj = e / kSwW, li = e - lj * kSwW;
+    int gi, gj;
+    if (li < w + 4 && sw_coord(tl.i0 + li - 2, n0, px, gi) && sw_coord(tl.j0 + lj - 2, n1, py, gj)) {
+      const long long idx = gi + (long long)n0 * gj;
+      if (!ZERO) sw_copy(xs + e, src + idx);
+      sw_copy(rs + e, B.r + idx);
+      sw_copy(wxs + e, B.L.w[0] + gi + (long long)(n0 + 1) * gj);
+      sw_copy(wys + e, B.L.w[1] + idx);
+      if (kInvd) sw_copy(is + e, B.invd + idx);
+    }
+  }
+  sw_copy_wait();
+  __syncthreads();
+  // A smoothed level has even sizes, so wrapping keeps parities and the tile origin is even: in
+  // staged row lj the cells of a colour are the staged columns li with li = colour + j0 + lj (mod 2).
+  // Each half-sweep walks only its colour's cells, kSwW / 2 per staged row.
+  for (int ph = 0; ph < 2; ++ph) {
+    const int colour = ph ? 1 - c0 : c0;
+    const int m = ph ? 2 : 1;  // first staged row / column updated in this half-sweep
+    const int nrow = h + 4 - 2 * m;
+    for (int t = threadIdx.x; t < nrow * (kSwW / 2); t += blockDim.x) {
+      const int q = t / (kSwW / 2), lj = q + m;
+      const int li = 2 * (t - q * (kSwW / 2)) + ((colour + tl.j0 + lj) & 1);
+      if (li < m || li >= w + 4 - m) continue;
+      int gi, gj;
+      if (!sw_coord(tl.i0 + li - 2, n0, px, gi) || !sw_coord(tl.j0 + lj - 2, n1, py, gj)) continue;
+      const int e = lj * kSwW + li;
+      xs[e] = (ZERO && ph == 0) ? rs[e] * is[e] : sw_cell<T>(B, xs, rs, wxs, wys, is, e, gi, gj);
+    }
+    __syncthreads();
+  }
+  double* x64 = UPDATE ? fine[tl.grid].E : nullptr;
+  for (int e = threadIdx.x; e < h * kSwW; e += blockDim.x) {
+    const int lj = e / kSwW, li = e - lj * kSwW;
+    if (li >= w) continue;
+    const long long idx = (tl.i0 + li) + (long long)n0 * (tl.j0 + lj);
+    const T v = xs[e + 2 * kSwW + 2];
+    dst[idx] = v;
+    if (UPDATE) x64[idx] += (double)v;
+  }
+}
+
+template <class T, bool ZERO, bool UPDATE>
+constexpr size_t sw_smem_bytes() {
+  return (size_t)sw_arrays<T, ZERO>() * kSwS * sizeof(T);
 }
 
 // one block per grid at its coarsest level (tile.level); a single-level grid adds its
-// correction to the FP64 iterate here
+// correction to the FP64 iterate here.  A level of at most one cell per thread keeps its stencil
+// in registers and the iterate in shared memory (the same iterates as the global-memory form).
+constexpr int kCoarseThreads = 1024;
+
 template <class T>
-__global__ void __launch_bounds__(512) kb_coarse(const Tile* __restrict__ tiles, const BLev<T>* __restrict__ lev, const BState* __restrict__ st,
-                          const BFine* __restrict__ fine) {
+__global__ void __launch_bounds__(kCoarseThreads, 1)
+    kb_coarse(const Tile* __restrict__ tiles, const BLev<T>* __restrict__ lev, const BState* __restrict__ st,
+              const BFine* __restrict__ fine) {
+  __shared__ T xs[2 * kCoarseThreads];
   const Tile tl = tiles[blockIdx.x];
   if (!st[tl.grid].active) return;
   const BLev<T>& B = lev[tl.grid * kMaxLev + tl.level];
   bool rb = true;
   for (int a = 0; a < B.L.ndim; ++a)
     if ((B.L.n[a] & 1) && B.L.bc[2 * a] == FLD_BC_PERIODIC) rb = false;
-  coarse_solve_block<T>(B.L, B.ncell, B.invd, B.r, B.x, B.tmp, rb ? 40 : 80, rb ? 1 : 0);
+  if (B.ncell <= (long long)blockDim.x) {
+    const int n = (int)B.ncell;
+    coarse_solve_small<T>(B.L, n, B.invd, B.r, xs, xs + n, rb ? 40 : 80, rb ? 1 : 0);
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) B.x[c] = xs[c];
+  } else {
+    coarse_solve_block<T>(B.L, B.ncell, B.invd, B.r, B.x, B.tmp, rb ? 40 : 80, rb ? 1 : 0);
+  }
   if (tl.level == 0) {
     __syncthreads();
     double* E = fine[tl.grid].E;
@@ -422,7 +630,10 @@ struct BatchedSolver::Impl {
     int off = 0, n = 0;
   };
   Range fine_r;
-  std::vector<Range> cell_r, smooth_r, restrict_r, prolong_r;  // per level
+  std::vector<Range> cell_r, smooth_r, restrict_r, prolong_r;  // per level (smooth_r: 3-D grids)
+  Tile2* tiles2_d = nullptr;  // tiles of the fused sweeps of 2-D grids
+  size_t tiles2_cap = 0;
+  std::vector<Range> sweep_r;  // per level, into tiles2_d
   Range coarse_r;
   int maxlev = 0;
   // graph
@@ -452,6 +663,7 @@ struct BatchedSolver::Impl {
     cudaFree(ctl_d);
     cudaFree(parts_d);
     cudaFree(tiles_d);
+    cudaFree(tiles2_d);
     cudaFree(scratch);
     if (st_pinned) cudaFreeHost(st_pinned);
     if (fine_pinned) cudaFreeHost(fine_pinned);
@@ -565,6 +777,9 @@ cudaError_t BatchedSolver::Impl::build_levels() {
       B.r = (T*)arena.take(n * es);
       B.tmp = (T*)arena.take(n * es);
       B.ncell = n;
+      B.f0 = make_fastdiv((unsigned)dims[i][l][0]);
+      B.f1 = make_fastdiv((unsigned)dims[i][l][1]);
+      B.fh = make_fastdiv((unsigned)((dims[i][l][0] + 1) / 2));
       if (!B.invd || !B.x || !B.r || !B.tmp) return cudaErrorMemoryAllocation;
     }
   }
@@ -616,14 +831,23 @@ cudaError_t BatchedSolver::Impl::build_tiles(int tile_cells) {
       if (l < (int)dims[g].size()) add_range(g, l, cells_of(dims[g][l]));
     cell_r[l].n = (int)t.size() - cell_r[l].off;
   }
+  std::vector<Tile2> t2;
+  sweep_r.assign(maxlev, {});
   for (int l = 0; l < maxlev; ++l) {
     smooth_r[l].off = (int)t.size();
+    sweep_r[l].off = (int)t2.size();
     for (int g = 0; g < ng; ++g)
       if (l < (int)dims[g].size() - 1) {
         const auto& n = dims[g][l];
-        add_range(g, l, (long long)((n[0] + 1) / 2) * n[1] * n[2]);
+        if (gd[g].ndim == 2) {
+          for (int j0 = 0; j0 < n[1]; j0 += kSwY)
+            for (int i0 = 0; i0 < n[0]; i0 += kSwX) t2.push_back({g, l, i0, j0});
+        } else {
+          add_range(g, l, (long long)((n[0] + 1) / 2) * n[1] * n[2]);
+        }
       }
     smooth_r[l].n = (int)t.size() - smooth_r[l].off;
+    sweep_r[l].n = (int)t2.size() - sweep_r[l].off;
     restrict_r[l].off = (int)t.size();
     for (int g = 0; g < ng; ++g)
       if (l < (int)dims[g].size() - 1) add_range(g, l, cells_of(dims[g][l + 1]));
@@ -644,6 +868,15 @@ cudaError_t BatchedSolver::Impl::build_tiles(int tile_cells) {
     tiles_cap = t.size();
   }
   if ((e = cudaMemcpy(tiles_d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if (t2.size() > tiles2_cap) {
+    cudaFree(tiles2_d);
+    tiles2_d = nullptr;
+    if ((e = cudaMalloc(&tiles2_d, t2.size() * sizeof(Tile2))) != cudaSuccess) return e;
+    tiles2_cap = t2.size();
+  }
+  if (!t2.empty() &&
+      (e = cudaMemcpy(tiles2_d, t2.data(), t2.size() * sizeof(Tile2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
   if ((size_t)fine_r.n > parts_cap) {
     cudaFree(parts_d);
     parts_d = nullptr;
@@ -666,8 +899,18 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
   for (int g = 0; g < ng; ++g) iter_cap = std::max(iter_cap, st_h[g].max_cycles);
   iter_cap += 1;
 
+  // the fused sweeps stage more than the default 48 KB of shared memory per block
+  cudaError_t e = cudaFuncSetAttribute(kb_sweep2d<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sw_smem_bytes<T, true, false>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_sweep2d<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sw_smem_bytes<T, false, false>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_sweep2d<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sw_smem_bytes<T, false, true>());
+  if (e != cudaSuccess) return e;
   cudaGraph_t graph;
-  cudaError_t e = cudaGraphCreate(&graph, 0);
+  e = cudaGraphCreate(&graph, 0);
   if (e != cudaSuccess) return e;
   e = cudaStreamBeginCaptureToGraph(cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) {
@@ -715,33 +958,61 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
     cudaStream_t b = body;
     note_launch(), kb_residual<T><<<fine_r.n, B, 0, b>>>(tl + fine_r.off, fine_d, lev, st_d, parts_d);
     note_launch(), kb_check<<<1, kCheckThreads, 0, b>>>(ng, parts_d, st_d, ctl_d, iter_cap, handle);
-    // V-cycle: levels down
+    // V-cycle.  3-D grids smooth with one launch per colour on x; 2-D grids with one fused launch
+    // per sweep, alternating x and tmp: pre_tmp[l] / post_tmp[l] record that their level-l iterate
+    // is in tmp after the pre- / post-smoothing (the first sweep, from zero, writes x).
+    std::vector<int> pre_tmp(maxlev, 0), post_tmp(maxlev, 0);
+    const Tile2* t2 = tiles2_d;
     for (int l = 0; l + 1 < maxlev; ++l) {
       const Range& sr = smooth_r[l];
-      if (!sr.n) continue;
+      const Range& wr = sweep_r[l];
+      if (!sr.n && !wr.n) continue;
+      int in_tmp = 0;
       for (int it = 0; it < nu1_; ++it) {
-        if (it == 0) note_launch(), kb_smooth<T, true, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
-        else note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
-        note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
+        if (sr.n) {
+          if (it == 0) note_launch(), kb_smooth<T, true, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+          else note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+          note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
+        }
+        if (wr.n) {
+          if (it == 0) {
+            note_launch(), kb_sweep2d<T, true, false><<<wr.n, B, sw_smem_bytes<T, true, false>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 0, 0);
+          } else {
+            note_launch(), kb_sweep2d<T, false, false><<<wr.n, B, sw_smem_bytes<T, false, false>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 0, in_tmp);
+            in_tmp ^= 1;
+          }
+        }
       }
-      note_launch(), kb_restrict<T><<<restrict_r[l].n, B, 0, b>>>(tl + restrict_r[l].off, lev, st_d);
+      pre_tmp[l] = in_tmp;
+      note_launch(), kb_restrict<T><<<restrict_r[l].n, B, 0, b>>>(tl + restrict_r[l].off, lev, st_d, pre_tmp[l]);
     }
-    note_launch(), kb_coarse<T><<<coarse_r.n, 512, 0, b>>>(tl + coarse_r.off, lev, st_d, fine_d);
+    note_launch(), kb_coarse<T><<<coarse_r.n, kCoarseThreads, 0, b>>>(tl + coarse_r.off, lev, st_d, fine_d);
     // levels up
     for (int l = maxlev - 2; l >= 0; --l) {
       const Range& sr = smooth_r[l];
-      if (!sr.n) continue;
-      note_launch(), kb_prolong<T><<<prolong_r[l].n, B, 0, b>>>(tl + prolong_r[l].off, lev, st_d);
+      const Range& wr = sweep_r[l];
+      if (!sr.n && !wr.n) continue;
+      note_launch(), kb_prolong<T><<<prolong_r[l].n, B, 0, b>>>(tl + prolong_r[l].off, lev, st_d, fine_d, pre_tmp[l],
+                                                               post_tmp[l + 1]);
+      int in_tmp = pre_tmp[l];
       for (int it = 0; it < nu2_; ++it) {
         bool last = (l == 0) && it == nu2_ - 1;
-        if (last) {
-          note_launch(), kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
-          note_launch(), kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
-        } else {
-          note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
-          note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+        if (sr.n) {
+          if (last) {
+            note_launch(), kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
+            note_launch(), kb_smooth<T, false, true><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+          } else {
+            note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
+            note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 0);
+          }
+        }
+        if (wr.n) {
+          if (last) note_launch(), kb_sweep2d<T, false, true><<<wr.n, B, sw_smem_bytes<T, false, true>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 1, in_tmp);
+          else note_launch(), kb_sweep2d<T, false, false><<<wr.n, B, sw_smem_bytes<T, false, false>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 1, in_tmp);
+          in_tmp ^= 1;
         }
       }
+      post_tmp[l] = in_tmp;
     }
     cudaGraph_t tmp = nullptr;
     e = cudaStreamEndCapture(b, &tmp);

@@ -259,16 +259,11 @@ __device__ __forceinline__ bool coeffs_cell_fast(const GridDev& g, const CoeffPh
 // D[a] is the cell-centred diffusion coefficient of axis a: the same array three times for the
 // scalar D of the paper, three arrays for a diagonal-tensor D.
 template <class TW>
-__device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const double* const (&D)[3], long long idx,
-                                           double* __restrict__ w0, double* __restrict__ w1, double* __restrict__ w2,
-                                           TW* __restrict__ t0, TW* __restrict__ t1, TW* __restrict__ t2,
-                                           float* __restrict__ l0 = nullptr, float* __restrict__ l1 = nullptr,
-                                           float* __restrict__ l2 = nullptr) {
-  int q[3];
-  q[0] = (int)(idx % g.n[0]);
-  long long r = idx / g.n[0];
-  q[1] = (int)(r % g.n[1]);
-  q[2] = (int)(r / g.n[1]);
+__device__ __forceinline__ void faces_cell_at(const GridDev& g, double dt, const double* const (&D)[3], const int (&q)[3],
+                                              long long idx, double* __restrict__ w0, double* __restrict__ w1,
+                                              double* __restrict__ w2, TW* __restrict__ t0, TW* __restrict__ t1,
+                                              TW* __restrict__ t2, float* __restrict__ l0 = nullptr,
+                                              float* __restrict__ l1 = nullptr, float* __restrict__ l2 = nullptr) {
   double Dc[3] = {0.0, 0.0, 0.0};
   double num[3] = {0, 0, 0}, den[3] = {1, 1, 1};
   bool pair[3] = {false, false, false};
@@ -317,6 +312,20 @@ __device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const do
       put(a, face_index(g.n, a, q[0], q[1], q[2], g.n[a]), wu);
     }
   }
+}
+
+template <class TW>
+__device__ __forceinline__ void faces_cell(const GridDev& g, double dt, const double* const (&D)[3], long long idx,
+                                           double* __restrict__ w0, double* __restrict__ w1, double* __restrict__ w2,
+                                           TW* __restrict__ t0, TW* __restrict__ t1, TW* __restrict__ t2,
+                                           float* __restrict__ l0 = nullptr, float* __restrict__ l1 = nullptr,
+                                           float* __restrict__ l2 = nullptr) {
+  int q[3];
+  q[0] = (int)(idx % g.n[0]);
+  long long r = idx / g.n[0];
+  q[1] = (int)(r % g.n[1]);
+  q[2] = (int)(r / g.n[1]);
+  faces_cell_at<TW>(g, dt, D, q, idx, w0, w1, w2, t0, t1, t2, l0, l1, l2);
 }
 
 }  // namespace fld

@@ -63,6 +63,17 @@ __device__ __forceinline__ void unflatten(const int n[3], long long idx, int& i,
   k = (int)(r / n[1]);
 }
 
+// The same for a level of fewer than 2^32 cells, with the divisions by n[0] and n[1] done by
+// multiplication (f0, f1 = make_fastdiv(n[0]), make_fastdiv(n[1])).
+__device__ __forceinline__ void unflatten32(unsigned idx, const FastDiv& f0, const FastDiv& f1, int& i, int& j,
+                                            int& k) {
+  const unsigned r = fast_div(idx, f0);
+  const unsigned kk = fast_div(r, f1);
+  i = (int)(idx - r * f0.d);
+  j = (int)(r - kk * f1.d);
+  k = (int)kk;
+}
+
 
 // Sum over the block (valid in thread 0); every thread of the block must call it.
 __device__ __forceinline__ double block_sum(double v) {
@@ -84,12 +95,10 @@ __device__ __forceinline__ double block_sum(double v) {
 // b = E_old + boundary constants (Dirichlet ghost value, Neumann gradient); the FP64 diagonal
 // of the outer operator and its inverse in T for the finest inner level.
 template <class T>
-__device__ __forceinline__ double fine_setup_cell(const LevelDev<double>& L, const GridDev& g,
-                                                  const double* __restrict__ E_old, long long idx,
-                                                  double* __restrict__ b, double* __restrict__ diag,
-                                                  T* __restrict__ invd) {
-  int i, j, k;
-  unflatten(g.n, idx, i, j, k);
+__device__ __forceinline__ double fine_setup_at(const LevelDev<double>& L, const GridDev& g,
+                                                const double* __restrict__ E_old, int i, int j, int k, long long idx,
+                                                double* __restrict__ b, double* __restrict__ diag,
+                                                T* __restrict__ invd) {
   double d = 1.0, cst = 0.0, wsum = 0.0;
   int face = 0;
   // boundary constants need to know which side each boundary face is on
@@ -115,16 +124,21 @@ __device__ __forceinline__ double fine_setup_cell(const LevelDev<double>& L, con
   return fma(2.0, wsum, 1.0);  // bound on the row's absolute sum: |diag| + sum |off-diagonal|
 }
 
+template <class T>
+__device__ __forceinline__ double fine_setup_cell(const LevelDev<double>& L, const GridDev& g,
+                                                  const double* __restrict__ E_old, long long idx,
+                                                  double* __restrict__ b, double* __restrict__ diag,
+                                                  T* __restrict__ invd) {
+  int i, j, k;
+  unflatten(g.n, idx, i, j, k);
+  return fine_setup_at<T>(L, g, E_old, i, j, k, idx, b, diag, invd);
+}
+
 // Coarse face `idx` of axis a (coarse face layout m = coarse dims with m[a] + 1): the mean of the
 // 2^(d-1) fine faces it covers, divided by 4 because dx doubles.
 template <class T>
-__device__ __forceinline__ T coarse_face_value(int a, int ndim, const int nf[3], const int m[3], long long idx,
-                                               const T* __restrict__ wf) {
-  int q[3];
-  q[0] = (int)(idx % m[0]);
-  long long r = idx / m[0];
-  q[1] = (int)(r % m[1]);
-  q[2] = (int)(r / m[1]);
+__device__ __forceinline__ T coarse_face_at(int a, int ndim, const int nf[3], const int (&q)[3],
+                                            const T* __restrict__ wf) {
   int mf[3] = {nf[0], nf[1], nf[2]};
   mf[a] += 1;
   T s = T(0);
@@ -143,16 +157,26 @@ __device__ __forceinline__ T coarse_face_value(int a, int ndim, const int nf[3],
   return s / (T)(4 * cnt);
 }
 
+template <class T>
+__device__ __forceinline__ T coarse_face_value(int a, int ndim, const int nf[3], const int m[3], long long idx,
+                                               const T* __restrict__ wf) {
+  int q[3];
+  q[0] = (int)(idx % m[0]);
+  long long r = idx / m[0];
+  q[1] = (int)(r % m[1]);
+  q[2] = (int)(r / m[1]);
+  return coarse_face_at<T>(a, ndim, nf, q, wf);
+}
+
 // r = b - A x in FP64 with the stored diagonal: r_c = b_c - d_c x_c + sum_f w_f x_nb (minus the
 // continuous-boundary terms), written in T for the inner V-cycle; returns acc + r^2.
 // x_out = x_in (the first iteration copies E_old into the iterate; later ones run in place,
 // x_out == x_in, where the store rewrites the value just read).
 template <class T>
-__device__ __forceinline__ double fma_residual_cell(const LevelDev<double>& L, const double* x_in, double* x_out,
-                                                    const double* __restrict__ b, const double* __restrict__ diag,
-                                                    T* __restrict__ r_out, long long idx, double acc) {
-  int i, j, k;
-  unflatten(L.n, idx, i, j, k);
+__device__ __forceinline__ double fma_residual_at(const LevelDev<double>& L, const double* x_in, double* x_out,
+                                                  const double* __restrict__ b, const double* __restrict__ diag,
+                                                  T* __restrict__ r_out, int i, int j, int k, long long idx,
+                                                  double acc) {
   double xc = x_in[idx];
   double s = fma(-diag[idx], xc, b[idx]);
   for_each_face(L, i, j, k, idx, [&](double w, int kind, long long nb) {
@@ -164,24 +188,23 @@ __device__ __forceinline__ double fma_residual_cell(const LevelDev<double>& L, c
   return fma(s, s, acc);
 }
 
+template <class T>
+__device__ __forceinline__ double fma_residual_cell(const LevelDev<double>& L, const double* x_in, double* x_out,
+                                                    const double* __restrict__ b, const double* __restrict__ diag,
+                                                    T* __restrict__ r_out, long long idx, double acc) {
+  int i, j, k;
+  unflatten(L.n, idx, i, j, k);
+  return fma_residual_at<T>(L, x_in, x_out, b, diag, r_out, i, j, k, idx, acc);
+}
+
 // Red-black Gauss-Seidel, thread t of one colour: x_c = (r_c + sum w x_nb) / diag on the cells
 // with (i+j+k) % 2 == color.  ZERO: the sweep starts from x = 0 (neighbours read as zero).
 // UPDATE (last sweep of the finest level): the colour's final correction is also added to the
 // FP64 iterate, x64_c += x_c.
 template <class T, bool ZERO, bool UPDATE>
-__device__ __forceinline__ void smooth_colour_cell(const LevelDev<T>& L, const T* __restrict__ invd,
-                                                   const T* __restrict__ r, T* __restrict__ x, int color, long long t,
-                                                   double* __restrict__ x64) {
-  int nxh = (L.n[0] + 1) >> 1;
-  long long rows = (long long)L.n[1] * L.n[2];
-  if (t >= (long long)nxh * rows) return;
-  int m = (int)(t % nxh);
-  long long row = t / nxh;
-  int j = (int)(row % L.n[1]);
-  int k = (int)(row / L.n[1]);
-  int i = 2 * m + ((color + j + k) & 1);
-  if (i >= L.n[0]) return;
-  long long idx = (long long)i + (long long)L.n[0] * row;
+__device__ __forceinline__ void smooth_at(const LevelDev<T>& L, const T* __restrict__ invd, const T* __restrict__ r,
+                                          T* __restrict__ x, int i, int j, int k, long long idx,
+                                          double* __restrict__ x64) {
   T v = r[idx];
   if (!ZERO) {
     // FP32 sweeps rebuild the diagonal from the face weights they read anyway (saves the 1/diag
@@ -208,14 +231,26 @@ __device__ __forceinline__ void smooth_colour_cell(const LevelDev<T>& L, const T
   if (UPDATE) x64[idx] += (double)v;
 }
 
+template <class T, bool ZERO, bool UPDATE>
+__device__ __forceinline__ void smooth_colour_cell(const LevelDev<T>& L, const T* __restrict__ invd,
+                                                   const T* __restrict__ r, T* __restrict__ x, int color, long long t,
+                                                   double* __restrict__ x64) {
+  int nxh = (L.n[0] + 1) >> 1;
+  long long rows = (long long)L.n[1] * L.n[2];
+  if (t >= (long long)nxh * rows) return;
+  int m = (int)(t % nxh);
+  long long row = t / nxh;
+  int j = (int)(row % L.n[1]);
+  int k = (int)(row / L.n[1]);
+  int i = 2 * m + ((color + j + k) & 1);
+  if (i >= L.n[0]) return;
+  smooth_at<T, ZERO, UPDATE>(L, invd, r, x, i, j, k, (long long)i + (long long)L.n[0] * row, x64);
+}
+
 // coarse rhs of coarse cell idx = average over its 2^d children of the fine residual r - A x
 template <class T>
-__device__ __forceinline__ T restrict_value(const LevelDev<T>& F, const T* __restrict__ rf, const T* __restrict__ xf,
-                                            const int nc[3], long long idx) {
-  int I = (int)(idx % nc[0]);
-  long long rr = idx / nc[0];
-  int J = (int)(rr % nc[1]);
-  int K = (int)(rr / nc[1]);
+__device__ __forceinline__ T restrict_at(const LevelDev<T>& F, const T* __restrict__ rf, const T* __restrict__ xf,
+                                         int I, int J, int K) {
   int o1max = F.ndim > 1 ? 2 : 1, o2max = F.ndim > 2 ? 2 : 1;
   T s = T(0);
   for (int o2 = 0; o2 < o2max; ++o2)
@@ -235,7 +270,24 @@ __device__ __forceinline__ T restrict_value(const LevelDev<T>& F, const T* __res
   return s / (T)(2 * o1max * o2max);
 }
 
+template <class T>
+__device__ __forceinline__ T restrict_value(const LevelDev<T>& F, const T* __restrict__ rf, const T* __restrict__ xf,
+                                            const int nc[3], long long idx) {
+  int I = (int)(idx % nc[0]);
+  long long rr = idx / nc[0];
+  int J = (int)(rr % nc[1]);
+  int K = (int)(rr / nc[1]);
+  return restrict_at<T>(F, rf, xf, I, J, K);
+}
+
 // x_f += x_c(parent): piecewise-constant prolongation of the coarse correction
+template <class T>
+__device__ __forceinline__ void prolong_at(int ndim, const T* __restrict__ xc, const int nc[3], T* __restrict__ xf,
+                                           int i, int j, int k, long long idx) {
+  int I = i >> 1, J = ndim > 1 ? j >> 1 : j, K = ndim > 2 ? k >> 1 : k;
+  xf[idx] += xc[(long long)I + (long long)nc[0] * ((long long)J + (long long)nc[1] * K)];
+}
+
 template <class T>
 __device__ __forceinline__ void prolong_cell(const int nf[3], int ndim, const T* __restrict__ xc, const int nc[3],
                                              T* __restrict__ xf, long long idx) {
@@ -243,8 +295,7 @@ __device__ __forceinline__ void prolong_cell(const int nf[3], int ndim, const T*
   long long r = idx / nf[0];
   int j = (int)(r % nf[1]);
   int k = (int)(r / nf[1]);
-  int I = i >> 1, J = ndim > 1 ? j >> 1 : j, K = ndim > 2 ? k >> 1 : k;
-  xf[idx] += xc[(long long)I + (long long)nc[0] * ((long long)J + (long long)nc[1] * K)];
+  prolong_at<T>(ndim, xc, nc, xf, i, j, k, idx);
 }
 
 // Coarsest level, executed by one whole block: x = 0, then `sweeps` red-black Gauss-Seidel
