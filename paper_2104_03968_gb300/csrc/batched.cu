@@ -83,7 +83,7 @@ struct BState {
   int max_cycles;
   int tile_begin;
   int tile_end;
-  int pad;
+  int f64res;  // the residual of this grid is evaluated in FP64 (else double-float with a bound)
   double bb;
   double rel;
   double rtol;
@@ -110,6 +110,7 @@ __global__ void kb_reset(int ng, BState* __restrict__ st, int* __restrict__ ctl)
     st[g].xiters = 0;
     st[g].xbis = 0;
     st[g].rel = 0.0;
+    st[g].f64res = 0;
   }
   if (g == 0) ctl[0] = ctl[1] = 0;
 }
@@ -248,28 +249,105 @@ __global__ void kb_bnorm(int ng, const double* __restrict__ parts, BState* __res
   st[g].bb = s;
 }
 
+// r = b - A x of one fine cell in FP64 (out of line: the fallback of the double-float path)
+static __device__ __noinline__ double residual_f64(const LevelDev<double>& L, const double* __restrict__ x,
+                                                   const double* __restrict__ b, const double* __restrict__ diag,
+                                                   int i, int j, int k, long long idx) {
+  double s = fma(-diag[idx], x[idx], b[idx]);
+  for_each_face(L, i, j, k, idx, [&](double w, int kind, long long nb) {
+    if (kind == kInterior) s = fma(w, x[nb], s);
+    else if (kind == kContinuous) s = fma(-w, x[nb], s);
+  });
+  return s;
+}
+
+// The same in double-float on the FP32 pipe (~16 splits and operations of relative error below
+// 2^-46 each, so the error is below 2^-41 times the sum of the terms' magnitudes, returned in mag
+// as that bound).  ok is false when an input lies outside the double-float window.
+__device__ __forceinline__ dfl residual_df(const LevelDev<double>& L, const double* __restrict__ x,
+                                           const double* __restrict__ b, const double* __restrict__ diag, int i,
+                                           int j, int k, long long idx, float& bound, bool& ok) {
+  dfl xc, bc, dc;
+  bool o1, o2, o3;
+  split_f64_try(x[idx], xc.hi, xc.lo, o1);
+  split_f64_try(b[idx], bc.hi, bc.lo, o2);
+  split_f64_try(diag[idx], dc.hi, dc.lo, o3);
+  ok = o1 && o2 && o3;
+  const dfl dx = df_mul(dc, xc);
+  dfl s = df_add(bc, df_neg(dx));
+  float mag = fabsf(bc.hi) + fabsf(dx.hi);
+  for_each_face(L, i, j, k, idx, [&](double w, int kind, long long nb) {
+    if (kind != kInterior && kind != kContinuous) return;
+    dfl wf, xn;
+    bool ow, ox;
+    split_f64_try(w, wf.hi, wf.lo, ow);
+    split_f64_try(x[nb], xn.hi, xn.lo, ox);
+    ok = ok && ow && ox;
+    const dfl p = df_mul(wf, xn);
+    s = df_add(s, kind == kInterior ? p : df_neg(p));
+    mag += fabsf(p.hi);
+  });
+  ok = ok && mag < 1e30f;
+  bound = 0x1p-41f * mag * 1.01f;  // 1.01: the FP32 sum of the magnitudes
+  return s;
+}
+
+// r = b - A x on the fine cells of a tile in T for the inner V-cycle.  parts[blk] = sum r^2 and,
+// in the double-float form (mixed precision, unless the grid fell back to FP64), parts[nt + blk] =
+// sum of the squared per-cell error bounds.
 template <class T>
-__global__ void kb_residual(const Tile* __restrict__ tiles, const BFine* __restrict__ fine, const BLev<T>* __restrict__ lev,
-                            const BState* __restrict__ st, double* __restrict__ parts) {
+__global__ void __launch_bounds__(256, 4)
+    kb_residual(const Tile* __restrict__ tiles, const BFine* __restrict__ fine, const BLev<T>* __restrict__ lev,
+                const BState* __restrict__ st, double* __restrict__ parts) {
   const Tile tl = tiles[blockIdx.x];
   if (!st[tl.grid].active) return;
   const BFine& f = fine[tl.grid];
   LevelDev<double> L = fine_level(f);
   const BLev<T>& L0 = lev[tl.grid * kMaxLev];
-  double acc = 0.0;
+  const bool use_df = sizeof(T) == sizeof(float) && !st[tl.grid].f64res;
+  double acc = 0.0, err = 0.0;
+  // the double-float form sums r^2 and bound^2 of its cells in FP32 (a tile gives a thread at most
+  // tile / blockDim cells; squares of values below 2^60 cannot overflow), then once in FP64
+  float facc = 0.0f, ferr = 0.0f;
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
     const unsigned idx = (unsigned)(tl.start + c);
     int i, j, k;
     unflatten32(idx, L0.f0, L0.f1, i, j, k);
-    acc = fma_residual_at<T>(L, f.E, f.E, f.b, f.diag, L0.r, i, j, k, idx, acc);
+    if (!use_df) {
+      acc = fma_residual_at<T>(L, f.E, f.E, f.b, f.diag, L0.r, i, j, k, idx, acc);
+      continue;
+    }
+    float bound;
+    bool ok;
+    const dfl s = residual_df(L, f.E, f.b, f.diag, i, j, k, idx, bound, ok);
+    if (ok && fabsf(s.hi) < 0x1p60f) {  // bound < 2^59 since mag < 1e30
+      L0.r[idx] = (T)(s.hi + s.lo);
+      facc = fmaf(s.hi, s.hi, facc);
+      ferr = fmaf(bound, bound, ferr);
+    } else {
+      const double r = residual_f64(L, f.E, f.b, f.diag, i, j, k, idx);
+      L0.r[idx] = (T)r;
+      acc = fma(r, r, acc);
+    }
   }
+  acc += (double)facc;
+  err += (double)ferr;
   acc = block_sum(acc);
   if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+  if (use_df) {
+    __syncthreads();  // block_sum's shared scratch is reused
+    err = block_sum(err);
+    if (threadIdx.x == 0) parts[gridDim.x + blockIdx.x] = err;
+  }
 }
 
-// One block: per-grid convergence decision, then the WHILE condition for the next pass.
+// One block: per-grid convergence decision, then the WHILE condition for the next pass.  A grid
+// whose residual was double-float (mixed, nt = the residual's tile count) converges when the
+// residual plus the bound on its error meets the tolerance, so the true residual does; while the
+// bound is above a quarter of the tolerance it could stall convergence, and the grid's later
+// residuals are FP64.
 __global__ void kb_check(int ng, const double* __restrict__ parts, BState* __restrict__ st, int* __restrict__ ctl,
-                         int iter_cap, cudaGraphConditionalHandle handle) {
+                         int iter_cap, int mixed, int nt, cudaGraphConditionalHandle handle) {
   __shared__ int nact;
   if (threadIdx.x == 0) nact = 0;
   __syncthreads();
@@ -280,11 +358,19 @@ __global__ void kb_check(int ng, const double* __restrict__ parts, BState* __res
     double rr = 0.0;
     for (int t = s.tile_begin; t < s.tile_end; ++t) rr += parts[t];
     double rel = s.bb > 0 ? sqrt(rr / s.bb) : sqrt(rr);
+    double bnd = 0.0;
+    if (mixed && !s.f64res) {
+      double ee = 0.0;
+      for (int t = s.tile_begin; t < s.tile_end; ++t) ee += parts[nt + t];
+      // 1.001 and 2^-18 rel: the FP32 partial sums of the squares (relative error below
+      // (tile / blockDim) 2^-24 <= 2^-19)
+      bnd = 1.001 * (s.bb > 0 ? sqrt(ee / s.bb) : sqrt(ee)) + 0x1p-18 * rel;
+    }
     s.rel = rel;
     if (!(rel == rel) || rel > 1e300) {
       s.active = 0;
       s.status = FLD_ERR_NONFINITE;
-    } else if (rel <= s.rtol) {
+    } else if (rel + bnd <= s.rtol) {
       s.active = 0;
       s.status = FLD_OK;
     } else if (s.cycles >= s.max_cycles) {
@@ -292,6 +378,7 @@ __global__ void kb_check(int ng, const double* __restrict__ parts, BState* __res
       s.status = FLD_ERR_NOT_CONVERGED;
     } else {
       s.cycles += 1;  // a V-cycle follows in this pass
+      if (bnd > 0.25 * s.rtol) s.f64res = 1;
       ++mine;
     }
   }
@@ -877,11 +964,11 @@ cudaError_t BatchedSolver::Impl::build_tiles(int tile_cells) {
   if (!t2.empty() &&
       (e = cudaMemcpy(tiles2_d, t2.data(), t2.size() * sizeof(Tile2), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
-  if ((size_t)fine_r.n > parts_cap) {
+  if (2 * (size_t)fine_r.n > parts_cap) {  // sums of r^2, then of the squared error bounds
     cudaFree(parts_d);
     parts_d = nullptr;
-    if ((e = cudaMalloc(&parts_d, fine_r.n * sizeof(double))) != cudaSuccess) return e;
-    parts_cap = fine_r.n;
+    if ((e = cudaMalloc(&parts_d, 2 * (size_t)fine_r.n * sizeof(double))) != cudaSuccess) return e;
+    parts_cap = 2 * (size_t)fine_r.n;
   }
   return cudaSuccess;
 }
@@ -957,7 +1044,8 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
   if (e == cudaSuccess) {
     cudaStream_t b = body;
     note_launch(), kb_residual<T><<<fine_r.n, B, 0, b>>>(tl + fine_r.off, fine_d, lev, st_d, parts_d);
-    note_launch(), kb_check<<<1, kCheckThreads, 0, b>>>(ng, parts_d, st_d, ctl_d, iter_cap, handle);
+    note_launch(), kb_check<<<1, kCheckThreads, 0, b>>>(ng, parts_d, st_d, ctl_d, iter_cap,
+                                                       sizeof(T) == sizeof(float) ? 1 : 0, fine_r.n, handle);
     // V-cycle.  3-D grids smooth with one launch per colour on x; 2-D grids with one fused launch
     // per sweep, alternating x and tmp: pre_tmp[l] / post_tmp[l] record that their level-l iterate
     // is in tmp after the pre- / post-smoothing (the first sweep, from zero, writes x).

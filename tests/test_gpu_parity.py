@@ -692,6 +692,31 @@ def test_step_batched_parity(ctx, precision):
         assert relerr(host(te), e2) < TOL
 
 
+def test_step_batched_mixed_certified_residual(ctx):
+    """Mixed batched residuals are double-float, with a bound on their error: a grid stops when the
+    residual plus the bound meets rtol, so the true relative residual of its diffusion solve is
+    below rtol.  With the exchange first the final E is the solve's result, and the oracle gives
+    the true residual from the exchanged state."""
+    from paper_2104_03968_gb300 import fld
+    rtol = 1e-9
+    cases = inputs.batched_2d(ngrids=6, nmin=64, nmax=160, seed=23)
+    params = [solver(c["phys"], rtol=rtol, precision="mixed", order="exchange_then_diffuse") for c in cases]
+    E = [dev(c["E"]) for c in cases]
+    infos = fld.step_batched(ctx, [c["grid"] for c in cases], params, [c["dt"] for c in cases],
+                             [dev(c["rho"]) for c in cases], [dev(c["eps"]) for c in cases], E)
+    for c, i, tE in zip(cases, infos, E):
+        assert i["status"] == 0 and i["cycles"] >= 1
+        p = c["phys"]
+        e1, E1, _ = oracle.exchange(p, c["dt"], c["rho"], oracle.opacity(p, c["rho"], c["eps"]), c["eps"], c["E"])
+        D = oracle.coeffs(c["grid"], p, E1, c["rho"], oracle.opacity(p, c["rho"], e1))
+        true = oracle.relres(c["grid"], c["dt"], D, E1, host(tE).reshape(E1.shape))
+        # the oracle's exchanged state differs from the GPU's at the 1e-12 level, which moves the
+        # residual by as much
+        assert true <= rtol * 1.01, (true, i)
+        # the reported residual is the double-float estimate of the true one
+        assert abs(i["rel_residual"] - true) <= 1e-3 * true + 1e-11, (true, i)
+
+
 def test_step_batched_mixed_dims_and_boundaries(ctx):
     """A batch mixing 2-D and 3-D grids, different boundary conditions and both step orders."""
     from paper_2104_03968_gb300 import fld
