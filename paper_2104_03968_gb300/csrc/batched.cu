@@ -468,7 +468,6 @@ __global__ void kb_prolong(const Tile* __restrict__ tiles, const BLev<T>* __rest
 // array and writes the other (x <-> tmp); the first sweep from zero reads no iterate and writes x.
 
 constexpr int kSwX = 64, kSwY = 32;  // cells of a tile
-constexpr int kSwW = kSwX + 4;       // staged row length (two cells each side)
 
 struct Tile2 {
   int grid;
@@ -514,9 +513,15 @@ __device__ __forceinline__ void sw_copy(T* smem, const T* gmem) {
 }
 __device__ __forceinline__ void sw_copy_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// staged arrays of a tile, each (kSwY + 4) x kSwW: the iterate, the right-hand side, the lower x-
-// and y-faces of each position, and 1/diag (the FP64 smoother, and the first sweep from zero)
-constexpr int kSwS = (kSwY + 4) * kSwW;
+// Staged arrays of a tile with a halo of H cells: each (kSwY + 2H) x (kSwX + 2H), holding the
+// iterate, the right-hand side, the lower x- and y-faces of each position, and 1/diag (the FP64
+// smoother, and the first sweep from zero).  H = 2 for a sweep; H = 3 for the last pre-sweep,
+// which also restricts its residual (below).
+template <int H>
+struct SwShape {
+  static constexpr int W = kSwX + 2 * H;  // staged row length
+  static constexpr int S = (kSwY + 2 * H) * W;
+};
 template <class T, bool ZERO>
 __host__ __device__ constexpr int sw_arrays() {
   return (ZERO || sizeof(T) == sizeof(double)) ? 5 : 4;
@@ -525,34 +530,61 @@ __host__ __device__ constexpr int sw_arrays() {
 // smooth_at for a 2-D cell at staged position e (global gi, gj): the upper faces are the lower
 // faces of the next positions, except on the last row / column, whose own upper face (index n)
 // is read from memory
-template <class T>
+template <class T, int W>
 __device__ __forceinline__ T sw_cell(const BLev<T>& B, const T* xs, const T* rs, const T* wxs, const T* wys,
                                      const T* is, int e, int gi, int gj) {
   const int n0 = B.L.n[0], n1 = B.L.n[1];
   T v = rs[e], d = T(1);
   const T wxu = gi < n0 - 1 ? wxs[e + 1] : B.L.w[0][n0 + (long long)(n0 + 1) * gj];
-  const T wyu = gj < n1 - 1 ? wys[e + kSwW] : B.L.w[1][gi + (long long)n0 * n1];
+  const T wyu = gj < n1 - 1 ? wys[e + W] : B.L.w[1][gi + (long long)n0 * n1];
   sw_face<T>(wxs[e], gi > 0, B.L.bc[0], xs[e - 1], xs[e + 1], v, d);
   sw_face<T>(wxu, gi < n0 - 1, B.L.bc[1], xs[e + 1], xs[e - 1], v, d);
-  sw_face<T>(wys[e], gj > 0, B.L.bc[2], xs[e - kSwW], xs[e + kSwW], v, d);
-  sw_face<T>(wyu, gj < n1 - 1, B.L.bc[3], xs[e + kSwW], xs[e - kSwW], v, d);
+  sw_face<T>(wys[e], gj > 0, B.L.bc[2], xs[e - W], xs[e + W], v, d);
+  sw_face<T>(wyu, gj < n1 - 1, B.L.bc[3], xs[e + W], xs[e - W], v, d);
   if constexpr (sizeof(T) == sizeof(float)) return __fdividef(v, d);
   else return v * is[e];
 }
 
+// (A x)_c of restrict_at's residual for a staged cell, its terms in for_each_face's order
+template <class T>
+__device__ __forceinline__ void sw_ax_face(T w, bool inner, int bc, T xv, T across, T inward, T& ax) {
+  if (inner || bc == FLD_BC_PERIODIC) ax += w * (xv - across);
+  else if (bc == FLD_BC_DIRICHLET) ax += w * xv;
+  else if (bc == FLD_BC_CONTINUOUS) ax += w * (inward - xv);
+}
+template <class T, int W>
+__device__ __forceinline__ T sw_ax(const BLev<T>& B, const T* xs, const T* wxs, const T* wys, int e, int gi, int gj) {
+  const int n0 = B.L.n[0], n1 = B.L.n[1];
+  const T xv = xs[e];
+  const T wxu = gi < n0 - 1 ? wxs[e + 1] : B.L.w[0][n0 + (long long)(n0 + 1) * gj];
+  const T wyu = gj < n1 - 1 ? wys[e + W] : B.L.w[1][gi + (long long)n0 * n1];
+  T ax = xv;
+  sw_ax_face<T>(wxs[e], gi > 0, B.L.bc[0], xv, xs[e - 1], xs[e + 1], ax);
+  sw_ax_face<T>(wxu, gi < n0 - 1, B.L.bc[1], xv, xs[e + 1], xs[e - 1], ax);
+  sw_ax_face<T>(wys[e], gj > 0, B.L.bc[2], xv, xs[e - W], xs[e + W], ax);
+  sw_ax_face<T>(wyu, gj < n1 - 1, B.L.bc[3], xv, xs[e + W], xs[e - W], ax);
+  return ax;
+}
+
 // ZERO: the sweep starts from x = 0 (writes x); otherwise it reads x (from_tmp = 0) or tmp and
-// writes the other.  UPDATE: the finest level's last sweep also adds the result to the FP64 iterate.
-// Dynamic shared memory: sw_arrays<T, ZERO>() * kSwS elements.
-template <class T, bool ZERO, bool UPDATE>
+// writes the other.  UPDATE: the finest level's last sweep also adds the result to the FP64
+// iterate.  RESTRICT (the last pre-sweep): the halo is three cells, colour c0 is updated two cells
+// around the tile and colour 1 - c0 one cell around it, so that every neighbour of a tile cell is
+// final; the block then forms the residual r - A x of its cells and writes the average of each
+// 2 x 2 block to the next level's right-hand side (restrict_at, term for term; tile origins and
+// the sizes of smoothed levels are even).  Dynamic shared memory: sw_smem_bytes().
+template <class T, bool ZERO, bool UPDATE, bool RESTRICT>
 __global__ void __launch_bounds__(256) kb_sweep2d(const Tile2* __restrict__ tiles, const BLev<T>* __restrict__ lev,
                                                   const BState* __restrict__ st, const BFine* __restrict__ fine,
                                                   int c0, int from_tmp) {
+  constexpr int H = RESTRICT ? 3 : 2;
+  constexpr int W = SwShape<H>::W, S = SwShape<H>::S;
   extern __shared__ __align__(16) unsigned char sw_smem[];
   T* xs = reinterpret_cast<T*>(sw_smem);
-  T* rs = xs + kSwS;
-  T* wxs = rs + kSwS;
-  T* wys = wxs + kSwS;
-  T* is = wys + kSwS;  // only with sw_arrays() == 5
+  T* rs = xs + S;
+  T* wxs = rs + S;
+  T* wys = wxs + S;
+  T* is = wys + S;  // only with sw_arrays() == 5
   constexpr bool kInvd = sw_arrays<T, ZERO>() == 5;
   const Tile2 tl = tiles[blockIdx.x];
   if (!st[tl.grid].active) return;
@@ -560,13 +592,13 @@ __global__ void __launch_bounds__(256) kb_sweep2d(const Tile2* __restrict__ tile
   const int n0 = B.L.n[0], n1 = B.L.n[1];
   const bool px = B.L.bc[0] == FLD_BC_PERIODIC, py = B.L.bc[2] == FLD_BC_PERIODIC;
   const int w = min(kSwX, n0 - tl.i0), h = min(kSwY, n1 - tl.j0);
-  const int nst = (h + 4) * kSwW;
+  const int nst = (h + 2 * H) * W;
   T* dst = (ZERO || from_tmp) ? B.x : B.tmp;
   const T* src = from_tmp ? B.tmp : B.x;
   for (int e = threadIdx.x; e < nst; e += blockDim.x) {
-    const int lj = e / kSwW, li = e - lj * kSwW;
+    const int lj = e / W, li = e - lj * W;
     int gi, gj;
-    if (li < w + 4 && sw_coord(tl.i0 + li - 2, n0, px, gi) && sw_coord(tl.j0 + lj - 2, n1, py, gj)) {
+    if (li < w + 2 * H && sw_coord(tl.i0 + li - H, n0, px, gi) && sw_coord(tl.j0 + lj - H, n1, py, gj)) {
       const long long idx = gi + (long long)n0 * gj;
       if (!ZERO) sw_copy(xs + e, src + idx);
       sw_copy(rs + e, B.r + idx);
@@ -579,36 +611,52 @@ __global__ void __launch_bounds__(256) kb_sweep2d(const Tile2* __restrict__ tile
   __syncthreads();
   // A smoothed level has even sizes, so wrapping keeps parities and the tile origin is even: in
   // staged row lj the cells of a colour are the staged columns li with li = colour + j0 + lj (mod 2).
-  // Each half-sweep walks only its colour's cells, kSwW / 2 per staged row.
+  // Each half-sweep walks only its colour's cells, W / 2 per staged row.
   for (int ph = 0; ph < 2; ++ph) {
     const int colour = ph ? 1 - c0 : c0;
-    const int m = ph ? 2 : 1;  // first staged row / column updated in this half-sweep
-    const int nrow = h + 4 - 2 * m;
-    for (int t = threadIdx.x; t < nrow * (kSwW / 2); t += blockDim.x) {
-      const int q = t / (kSwW / 2), lj = q + m;
-      const int li = 2 * (t - q * (kSwW / 2)) + ((colour + tl.j0 + lj) & 1);
-      if (li < m || li >= w + 4 - m) continue;
+    const int m = H - (ph ? (RESTRICT ? 1 : 0) : (RESTRICT ? 2 : 1));  // first staged row / column updated
+    const int nrow = h + 2 * H - 2 * m;
+    for (int t = threadIdx.x; t < nrow * (W / 2); t += blockDim.x) {
+      const int q = t / (W / 2), lj = q + m;
+      const int li = 2 * (t - q * (W / 2)) + ((colour + tl.j0 + lj) & 1);
+      if (li < m || li >= w + 2 * H - m) continue;
       int gi, gj;
-      if (!sw_coord(tl.i0 + li - 2, n0, px, gi) || !sw_coord(tl.j0 + lj - 2, n1, py, gj)) continue;
-      const int e = lj * kSwW + li;
-      xs[e] = (ZERO && ph == 0) ? rs[e] * is[e] : sw_cell<T>(B, xs, rs, wxs, wys, is, e, gi, gj);
+      if (!sw_coord(tl.i0 + li - H, n0, px, gi) || !sw_coord(tl.j0 + lj - H, n1, py, gj)) continue;
+      const int e = lj * W + li;
+      xs[e] = (ZERO && ph == 0) ? rs[e] * is[e] : sw_cell<T, W>(B, xs, rs, wxs, wys, is, e, gi, gj);
     }
     __syncthreads();
   }
   double* x64 = UPDATE ? fine[tl.grid].E : nullptr;
-  for (int e = threadIdx.x; e < h * kSwW; e += blockDim.x) {
-    const int lj = e / kSwW, li = e - lj * kSwW;
+  for (int e = threadIdx.x; e < h * W; e += blockDim.x) {
+    const int lj = e / W, li = e - lj * W;
     if (li >= w) continue;
     const long long idx = (tl.i0 + li) + (long long)n0 * (tl.j0 + lj);
-    const T v = xs[e + 2 * kSwW + 2];
+    const T v = xs[e + H * W + H];
     dst[idx] = v;
     if (UPDATE) x64[idx] += (double)v;
   }
+  if (RESTRICT) {
+    const BLev<T>& C = lev[tl.grid * kMaxLev + tl.level + 1];
+    const int wc = w >> 1, hc = h >> 1;
+    for (int t = threadIdx.x; t < hc * (kSwX / 2); t += blockDim.x) {
+      const int J = t / (kSwX / 2), I = t - J * (kSwX / 2);
+      if (I >= wc) continue;
+      T sum = T(0);
+      for (int o1 = 0; o1 < 2; ++o1)
+        for (int o0 = 0; o0 < 2; ++o0) {
+          const int li = 2 * I + o0, lj = 2 * J + o1;
+          const int e = (lj + H) * W + li + H;
+          sum += rs[e] - sw_ax<T, W>(B, xs, wxs, wys, e, tl.i0 + li, tl.j0 + lj);
+        }
+      C.r[(tl.i0 / 2 + I) + (long long)C.L.n[0] * (tl.j0 / 2 + J)] = sum / T(4);
+    }
+  }
 }
 
-template <class T, bool ZERO, bool UPDATE>
+template <class T, bool ZERO, bool UPDATE, bool RESTRICT>
 constexpr size_t sw_smem_bytes() {
-  return (size_t)sw_arrays<T, ZERO>() * kSwS * sizeof(T);
+  return (size_t)sw_arrays<T, ZERO>() * SwShape<RESTRICT ? 3 : 2>::S * sizeof(T);
 }
 
 // one block per grid at its coarsest level (tile.level); a single-level grid adds its
@@ -935,9 +983,9 @@ cudaError_t BatchedSolver::Impl::build_tiles(int tile_cells) {
       }
     smooth_r[l].n = (int)t.size() - smooth_r[l].off;
     sweep_r[l].n = (int)t2.size() - sweep_r[l].off;
-    restrict_r[l].off = (int)t.size();
+    restrict_r[l].off = (int)t.size();  // 2-D grids restrict inside their last pre-sweep
     for (int g = 0; g < ng; ++g)
-      if (l < (int)dims[g].size() - 1) add_range(g, l, cells_of(dims[g][l + 1]));
+      if (l < (int)dims[g].size() - 1 && gd[g].ndim != 2) add_range(g, l, cells_of(dims[g][l + 1]));
     restrict_r[l].n = (int)t.size() - restrict_r[l].off;
     prolong_r[l].off = (int)t.size();
     for (int g = 0; g < ng; ++g)
@@ -987,14 +1035,15 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
   iter_cap += 1;
 
   // the fused sweeps stage more than the default 48 KB of shared memory per block
-  cudaError_t e = cudaFuncSetAttribute(kb_sweep2d<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sw_smem_bytes<T, true, false>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kb_sweep2d<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sw_smem_bytes<T, false, false>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kb_sweep2d<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sw_smem_bytes<T, false, true>());
+  cudaError_t e = cudaSuccess;
+  auto allow = [&](const void* k, size_t bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  allow((const void*)kb_sweep2d<T, true, false, false>, sw_smem_bytes<T, true, false, false>());
+  allow((const void*)kb_sweep2d<T, false, false, false>, sw_smem_bytes<T, false, false, false>());
+  allow((const void*)kb_sweep2d<T, false, true, false>, sw_smem_bytes<T, false, true, false>());
+  allow((const void*)kb_sweep2d<T, true, false, true>, sw_smem_bytes<T, true, false, true>());
+  allow((const void*)kb_sweep2d<T, false, false, true>, sw_smem_bytes<T, false, false, true>());
   if (e != cudaSuccess) return e;
   cudaGraph_t graph;
   e = cudaGraphCreate(&graph, 0);
@@ -1063,16 +1112,29 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
           note_launch(), kb_smooth<T, false, false><<<sr.n, B, 0, b>>>(tl + sr.off, lev, st_d, fine_d, 1);
         }
         if (wr.n) {
-          if (it == 0) {
-            note_launch(), kb_sweep2d<T, true, false><<<wr.n, B, sw_smem_bytes<T, true, false>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 0, 0);
+          // the last pre-sweep also restricts the residual to level l + 1
+          const bool last = it == nu1_ - 1;
+          const Tile2* tw = t2 + wr.off;
+          if (it == 0 && last) {
+            note_launch(), kb_sweep2d<T, true, false, true>
+                               <<<wr.n, B, sw_smem_bytes<T, true, false, true>(), b>>>(tw, lev, st_d, fine_d, 0, 0);
+          } else if (it == 0) {
+            note_launch(), kb_sweep2d<T, true, false, false>
+                               <<<wr.n, B, sw_smem_bytes<T, true, false, false>(), b>>>(tw, lev, st_d, fine_d, 0, 0);
+          } else if (last) {
+            note_launch(), kb_sweep2d<T, false, false, true><<<wr.n, B, sw_smem_bytes<T, false, false, true>(), b>>>(
+                               tw, lev, st_d, fine_d, 0, in_tmp);
+            in_tmp ^= 1;
           } else {
-            note_launch(), kb_sweep2d<T, false, false><<<wr.n, B, sw_smem_bytes<T, false, false>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 0, in_tmp);
+            note_launch(), kb_sweep2d<T, false, false, false><<<wr.n, B, sw_smem_bytes<T, false, false, false>(), b>>>(
+                               tw, lev, st_d, fine_d, 0, in_tmp);
             in_tmp ^= 1;
           }
         }
       }
       pre_tmp[l] = in_tmp;
-      note_launch(), kb_restrict<T><<<restrict_r[l].n, B, 0, b>>>(tl + restrict_r[l].off, lev, st_d, pre_tmp[l]);
+      if (restrict_r[l].n)  // 3-D grids
+        note_launch(), kb_restrict<T><<<restrict_r[l].n, B, 0, b>>>(tl + restrict_r[l].off, lev, st_d, pre_tmp[l]);
     }
     note_launch(), kb_coarse<T><<<coarse_r.n, kCoarseThreads, 0, b>>>(tl + coarse_r.off, lev, st_d, fine_d);
     // levels up
@@ -1095,8 +1157,13 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
           }
         }
         if (wr.n) {
-          if (last) note_launch(), kb_sweep2d<T, false, true><<<wr.n, B, sw_smem_bytes<T, false, true>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 1, in_tmp);
-          else note_launch(), kb_sweep2d<T, false, false><<<wr.n, B, sw_smem_bytes<T, false, false>(), b>>>(t2 + wr.off, lev, st_d, fine_d, 1, in_tmp);
+          const Tile2* tw = t2 + wr.off;
+          if (last)
+            note_launch(), kb_sweep2d<T, false, true, false><<<wr.n, B, sw_smem_bytes<T, false, true, false>(), b>>>(
+                               tw, lev, st_d, fine_d, 1, in_tmp);
+          else
+            note_launch(), kb_sweep2d<T, false, false, false><<<wr.n, B, sw_smem_bytes<T, false, false, false>(), b>>>(
+                               tw, lev, st_d, fine_d, 1, in_tmp);
           in_tmp ^= 1;
         }
       }
