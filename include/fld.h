@@ -215,7 +215,13 @@ FLD_API fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_p
 /* fld_step on `ngrids` independent grids with their own sizes, parameters and time steps.
    grids, params and dt are HOST arrays of length ngrids; rho/eps/E are HOST arrays of DEVICE
    pointers; infos (may be NULL) receives one fld_info per grid.  Every grid must have ndim 2
-   or 3 and fewer than 2^31 cells (FLD_ERR_INVALID_ARG otherwise).  Synchronises. */
+   or 3 and fewer than 2^31 cells (FLD_ERR_INVALID_ARG otherwise).  Synchronises.
+   All grids share params[0].precision.  The batch autotunes its own sweep counts and tile size
+   on the first call for a batch shape (nu1 / nu2 of params are not used).  With
+   FLD_PREC_MIXED, each grid's fine residual is double-float with a bound on its error.  The
+   grid has converged when the residual plus the bound is at most its rtol, so the true residual
+   is too.  A grid whose bound exceeds rtol / 4 takes FP64 residuals from its next cycle on.
+   infos[g].rel_residual is the last residual computed, bound not included. */
 FLD_API fld_status fld_step_batched(fld_ctx* ctx, int ngrids, const fld_grid* grids,
                             const fld_params* params, const double* dt, const double* const* rho,
                             double* const* eps, double* const* E, fld_info* infos, void* stream);
