@@ -546,6 +546,76 @@ def test_table_opacity_bilinear_reproduces_nodes_and_planes():
     assert np.isclose(np.log10(k_out[0]), 0.3 * -16 - 0.8 * 6.5 + 1.0)
 
 
+def test_kramers_opacity_power_laws():
+    """Sect. 5.1's Kramers-like stand-in kappa = kappa0 rho^a T^b (T from the ideal-gas law of
+    Sect. 2): kappa(1, 1) = kappa0, doubling rho multiplies kappa by 2^a and doubling T by 2^b.
+    Two exponent pairs, so that exchanging a and b fails."""
+    for a, b in ((1.0, -3.5), (0.5, -2.5)):
+        phys = dict(inputs.code_units(), opacity="kramers", kappa0=7.0, kr_a=a, kr_b=b)
+        rho = np.array([1.0, 2.0, 1.0, 0.3, 0.6, 0.3])
+        T = np.array([1.0, 1.0, 2.0, 1.7, 1.7, 3.4])
+        kap = oracle.opacity(phys, rho, inputs.equilibrium_eps(phys, rho, T))
+        assert kap[0] == pytest.approx(7.0, rel=1e-15)
+        for lo, hi, f in ((0, 1, 2.0 ** a), (0, 2, 2.0 ** b), (3, 4, 2.0 ** a), (3, 5, 2.0 ** b)):
+            assert kap[hi] / kap[lo] == pytest.approx(f, rel=1e-14)
+
+
+def _free_streaming_gradient(col, E, bc_vals=(0.0, 0.0)):
+    """|dE/dr| at the cell centres recovered from the column D in the free-streaming limit:
+    with kappa rho -> 0 the flux D |grad E| tends to c E (Sect. 2.2), here to 1 - O(1/R) with
+    R ~ 1e13, so |grad E| = c E / D to ~1e-12."""
+    n = E.size
+    phys = dict(inputs.code_units(), c=2.0)
+    rho = np.full(n, 1e-7)
+    kap = np.full(n, 1e-7)
+    D = oracle.column_coeffs(col, phys, E, rho, kap, *bc_vals)
+    return phys["c"] * E / D
+
+
+def test_column_gradient_exact_on_quadratics():
+    """The 3-point non-uniform central difference that replaces the 5-point stencil of Sect. 3.2
+    on the stretched radial grid differentiates quadratics in r exactly at every interior cell,
+    whatever the spacing (swapping the two spacings breaks this on a stretched grid)."""
+    n = 24
+    col = _col(n, "spherical", ["continuous", "continuous"], 1.0, 4.0)
+    rf = col["r_faces"]
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    a, b, c2 = 5.0, -1.5, 0.9
+    E = a + b * rc + c2 * rc ** 2
+    g = _free_streaming_gradient(col, E)
+    exact = np.abs(b + 2 * c2 * rc)
+    assert np.allclose(g[1:-1], exact[1:-1], rtol=1e-9), np.abs(g / exact - 1).max()
+
+
+@pytest.mark.parametrize("bc", ["continuous", "luminosity", "neumann", "dirichlet"])
+def test_column_gradient_boundary_ghosts(bc):
+    """The column ends: the ghost cell sits one cell width beyond the end cell (mirrored in
+    width).  Continuous (and the luminosity face, whose D uses a linearly extrapolated ghost,
+    Sect. 5.2) extrapolates linearly, so a linear E has its exact gradient at both ends; a
+    Neumann ghost E_0 -/+ g h with g the exact slope, and a Dirichlet ghost holding the exact
+    value of a quadratic at the ghost centre, also give the exact gradient."""
+    n = 20
+    col = _col(n, "spherical", [bc, bc if bc != "luminosity" else "continuous"], 1.0, 5.0)
+    rf = col["r_faces"]
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    rg_lo = rc[0] - (rf[1] - rf[0])
+    rg_hi = rc[-1] + (rf[-1] - rf[-2])
+    if bc == "dirichlet":
+        a, b, c2 = 3.0, -0.4, 0.35
+        f = lambda r: a + b * r + c2 * r * r
+        df = lambda r: b + 2 * c2 * r
+        vals = (f(rg_lo), f(rg_hi))
+    else:
+        a, b = 2.0, 0.7
+        f = lambda r: a + b * r
+        df = lambda r: b + 0 * r
+        vals = (b, b) if bc == "neumann" else (0.0, 0.0)
+    E = f(rc)
+    g = _free_streaming_gradient(col, E, vals)
+    assert g[0] == pytest.approx(abs(df(rc[0])), rel=1e-9)
+    assert g[-1] == pytest.approx(abs(df(rc[-1])), rel=1e-9)
+
+
 # ----------------------------------------------------------------------------- IMEX midpoint
 
 def test_imex_midpoint_is_crank_nicolson_without_exchange():
