@@ -65,6 +65,46 @@ KERNEL_MODEL = {
 }
 
 
+GOLDEN_DT = os.path.join(ROOT, "tests", "golden", "explicit_dt.json")
+
+
+def stored_dt(key):
+    """Explicit diffusion limit of a full-size recipe's initial state, written by the oracle
+    (tests/golden/make_explicit_dt.py): the workloads' dt is a multiple of it."""
+    with open(GOLDEN_DT) as f:
+        table = json.load(f)
+    if key not in table:
+        raise SystemExit(f"no stored explicit limit for {key}; run tests/golden/make_explicit_dt.py")
+    return table[key]
+
+
+def host_cpu():
+    """CPU model and the cores this process may use."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:  # Arm hosts list no model name in /proc/cpuinfo; lscpu decodes the part number
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.strip().lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+            else os.cpu_count()}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -177,6 +217,10 @@ def oracle_sample(n: int, steps: int, rtol: float):
     from paper_2104_03968_gb300 import inputs
     case = inputs.lognormal_3d(n=n, seed=2)
     g, p = case["grid"], case["phys"]
+    # dt = 100x the explicit limit of this sample's initial state (the oracle's limited D)
+    D0 = oracle.coeffs(g, p, case["E"], case["rho"], oracle.opacity(p, case["rho"], case["eps"]))
+    inputs.with_explicit_dt(case, inputs.explicit_dt(D0, 1.0, 3))
+    del D0
     eps, E = case["eps"], case["E"]
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -197,7 +241,8 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             **host_cpu()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -205,7 +250,8 @@ def run_reference(args, world, rank):
 
 def workload_config(args, nu=None):
     """nu: the (nu1, nu2) the library's autotuner chose (reported by the solve), if known."""
-    cfg = {"workload": f"lognormal-density Kramers-opacity periodic grid {args.n}^3, dt = 100x explicit limit, "
+    cfg = {"workload": f"lognormal-density Kramers-opacity periodic grid {args.n}^3, dt = 100x the explicit limit "
+                       f"min(dx^2/(2 d D_cell)) with the initial state's Levermore-Pomraning D_cell, "
                        f"full FLD step (coeffs + multigrid diffusion to {args.rtol:g} + exchange)",
            "grid": [args.n] * 3, "cells": args.n ** 3, "rtol": args.rtol, "precision": args.precision,
            "multigrid": "FMG first cycle, V-cycles after; red-black Gauss-Seidel sweep counts autotuned",
@@ -302,7 +348,8 @@ def main():
 
     torch.cuda.set_device(local)
     ctx = fld.Context(local)
-    case = inputs.lognormal_3d(n=args.n, seed=2, device=f"cuda:{local}")
+    case = inputs.lognormal_3d(n=args.n, seed=2, device=f"cuda:{local}",
+                               dt_exp=stored_dt(f"lognormal_3d_{args.n}_seed2"))
     g, phys, dt = case["grid"], case["phys"], case["dt"]
     rho0, eps0, E0 = case["rho"], case["eps"], case["E"]
     ncell = args.n ** 3
@@ -383,7 +430,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         val, secs = oracle_sample(args.oracle_n, 1, args.rtol)
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one full step of the same recipe at {args.oracle_n}^3 ({secs:.1f} s, single thread)"}
+               "sample": f"one full step of the same recipe at {args.oracle_n}^3 ({secs:.1f} s, single thread)",
+               **host_cpu()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -419,7 +467,10 @@ def run_batched_workload(args):
     ctx = fld.Context(0)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     if args.workload == "batched2d":
-        cases = inputs.batched_2d(ngrids=args.ngrids, seed=3)
+        dtx = stored_dt("batched_2d_512_seed3")
+        if args.ngrids > len(dtx):
+            raise SystemExit(f"stored explicit limits cover {len(dtx)} batched grids")
+        cases = inputs.batched_2d(ngrids=args.ngrids, seed=3, dt_exp=dtx)
         grids = [c["grid"] for c in cases]
         params = [dict(c["phys"], precision=args.precision, rtol=args.rtol) for c in cases]
         dts = [c["dt"] for c in cases]
@@ -435,7 +486,10 @@ def run_batched_workload(args):
         desc = (f"{args.ngrids} independent periodic 2-D grids, n log-uniform in [64, 512], kappa0 = 10^U(-2,4), "
                 f"dt = 10^U(1,3) x explicit limit, one graph launch per step, rtol {args.rtol:g}")
     else:
-        case = inputs.wind_columns(ncol=args.ncol, ncell=2048, seed=4)
+        dtx = stored_dt("wind_columns_4096x2048_seed4")
+        if args.ncol > len(dtx):
+            raise SystemExit(f"stored explicit limits cover {len(dtx)} columns")
+        case = inputs.wind_columns(ncol=args.ncol, ncell=2048, seed=4, dt_exp=dtx[:args.ncol])
         p = dict(case["phys"], precision=args.precision)
         rf, vlo, vhi, dtt = dev(case["r_faces"]), dev(case["bc_lo"]), dev(case["bc_hi"]), dev(case["dt"])
         rho = dev(case["rho"])

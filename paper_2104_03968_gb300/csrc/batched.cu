@@ -307,7 +307,17 @@ __global__ void __launch_bounds__(256, 4)
   const bool use_df = sizeof(T) == sizeof(float) && !st[tl.grid].f64res;
   double acc = 0.0, err = 0.0;
   // the double-float form sums r^2 and bound^2 of its cells in FP32 (a tile gives a thread at most
-  // tile / blockDim cells; squares of values below 2^60 cannot overflow), then once in FP64
+  // tile / blockDim cells), then once in FP64.  Both are first scaled by 2^-e, 2^(e-1) <= rms(b) <
+  // 2^e, so that grids of any magnitude neither underflow nor overflow in the squares: relative to
+  // rms(b) a converging residual stays far above 2^-63 and the bounds near 2^-41.  Scaled values of
+  // 2^60 or more take the FP64 accumulator.
+  int e2 = 0;
+  if (use_df) {
+    const double bb = st[tl.grid].bb;
+    const double ncell = (double)f.g.n[0] * (double)f.g.n[1] * (double)f.g.n[2];
+    if (bb > 0.0) (void)frexp(sqrt(bb / ncell), &e2);
+  }
+  const float sc = ldexpf(1.0f, -e2);
   float facc = 0.0f, ferr = 0.0f;
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
     const unsigned idx = (unsigned)(tl.start + c);
@@ -320,18 +330,19 @@ __global__ void __launch_bounds__(256, 4)
     float bound;
     bool ok;
     const dfl s = residual_df(L, f.E, f.b, f.diag, i, j, k, idx, bound, ok);
-    if (ok && fabsf(s.hi) < 0x1p60f) {  // bound < 2^59 since mag < 1e30
+    const float hs = s.hi * sc, bs = bound * sc;
+    if (ok && fabsf(hs) < 0x1p60f && bs < 0x1p60f) {
       L0.r[idx] = (T)(s.hi + s.lo);
-      facc = fmaf(s.hi, s.hi, facc);
-      ferr = fmaf(bound, bound, ferr);
+      facc = fmaf(hs, hs, facc);
+      ferr = fmaf(bs, bs, ferr);
     } else {
       const double r = residual_f64(L, f.E, f.b, f.diag, i, j, k, idx);
       L0.r[idx] = (T)r;
       acc = fma(r, r, acc);
     }
   }
-  acc += (double)facc;
-  err += (double)ferr;
+  acc += ldexp((double)facc, 2 * e2);
+  err += ldexp((double)ferr, 2 * e2);
   acc = block_sum(acc);
   if (threadIdx.x == 0) parts[blockIdx.x] = acc;
   if (use_df) {

@@ -20,8 +20,15 @@ Recipes (numpy ``default_rng``; the seeds are the workloads' names):
 * ``heating_cooling``    uniform static gas out of radiative equilibrium.
 * ``thin_front``         1-D optically thin slab lit by an erf profile.
 
-The "explicit limit" is dx^2 / (2 d D_thick) with D_thick = c / (3 kappa rho), the
-optically thick diffusion coefficient; the flux limiter only lowers D below it.
+The "explicit limit" of the 3-D, batched 2-D and column workloads is the smallest explicit
+diffusion step of the initial state, dt_exp = min over cells of dx^2 / (2 d D_cell), with
+D_cell the flux-limited (Levermore-Pomraning) coefficient of that state.  This module holds no
+limiter, so the recipes take dt_exp (or D_cell) from the caller: the tests compute D_cell with
+the oracle, and the full-size workloads read dt_exp from a table written by a script that runs
+the oracle on these same recipes.  A recipe called without dt_exp returns dt = None.  The
+optically thick bound dx^2 / (2 d D_thick), D_thick = c / (3 min kappa rho), is kept as a
+secondary time scale (``dt_exp_thick``); the Gaussian pulse (R ~ 0, so the two agree) and the
+small brute-force grids of ``random_small`` use it.
 """
 from __future__ import annotations
 
@@ -82,6 +89,25 @@ def rad_temperature(phys: dict, E):
 def thick_explicit_dt(dx2_min, ndim: int, c: float, kr_min: float) -> float:
     """dx^2 / (2 d D_thick) with the largest optically thick D = c / (3 min(kappa rho))."""
     return float(dx2_min / (2.0 * ndim * c / (3.0 * kr_min)))
+
+
+def explicit_dt(D_cell, dx2, ndim: int) -> float:
+    """The explicit diffusion limit of a grid, min over cells of dx^2 / (2 d D_cell), from the
+    caller's cell-centred D (uniform spacing, dx2 = dx^2)."""
+    return float(dx2 / (2.0 * ndim * float(np.max(D_cell))))
+
+
+def column_explicit_dt(D_cell, r_faces) -> np.ndarray:
+    """Per column (rows of D_cell), min over cells of dr_i^2 / (2 D_i), dr_i the cell width."""
+    dr = np.diff(np.asarray(r_faces, dtype=np.float64))
+    return (dr[None, :] ** 2 / (2.0 * np.asarray(D_cell))).min(axis=1)
+
+
+def with_explicit_dt(case: dict, dt_exp) -> dict:
+    """Set a recipe's time step to its dt_factor times the given explicit limit(s)."""
+    case["dt_exp"] = dt_exp
+    case["dt"] = case["dt_factor"] * dt_exp
+    return case
 
 
 # ----------------------------------------------------------------------------- fields
@@ -177,23 +203,26 @@ def lognormal_fields(rng, shape, phys: dict, kappa0: float, sigma_ln: float = 1.
 
 
 def lognormal_3d(n: int = 128, seed: int = 1, kappa0: float = 1.0, dt_factor: float = 100.0,
-                 ndim: int = 3, limiter: str = "lp", device=None) -> dict:
-    """Lognormal density with Kramers opacity; periodic n^ndim (code units).  With a torch
-    ``device`` the fields are built there (same noise and recipe) and returned as tensors."""
+                 ndim: int = 3, limiter: str = "lp", device=None, dt_exp=None) -> dict:
+    """Lognormal density with Kramers opacity; periodic n^ndim (code units); dt = dt_factor x the
+    explicit limit dt_exp of the initial state (None: dt is None until ``with_explicit_dt``).
+    With a torch ``device`` the fields are built there (same noise and recipe) as tensors."""
     rng = np.random.default_rng(SEED_BASE + seed)
     shape = (n,) * ndim
     grid = periodic_grid(shape)
     phys = code_units(limiter)
     phys.update(opacity="kramers", kappa0=kappa0, kr_a=1.0, kr_b=-3.5)
     rho, eps, E, kr_min = lognormal_fields(rng, shape, phys, kappa0, device=device)
-    dt_exp = thick_explicit_dt(1.0, ndim, phys["c"], kr_min)
-    return {"name": f"lognormal_{ndim}d_{n}", "grid": grid, "phys": phys, "rho": rho, "eps": eps,
-            "E": E, "dt": dt_factor * dt_exp, "dt_exp": dt_exp}
+    case = {"name": f"lognormal_{ndim}d_{n}", "seed": seed, "grid": grid, "phys": phys, "rho": rho,
+            "eps": eps, "E": E, "dt_factor": dt_factor, "dt": None, "dt_exp": None,
+            "dt_exp_thick": thick_explicit_dt(1.0, ndim, phys["c"], kr_min)}
+    return case if dt_exp is None else with_explicit_dt(case, dt_exp)
 
 
 def batched_2d(ngrids: int = 512, seed: int = 3, nmin: int = 64, nmax: int = 512,
-               limiter: str = "lp") -> list:
-    """Independent square periodic 2-D grids of uneven size, opacity and time step."""
+               limiter: str = "lp", dt_exp=None) -> list:
+    """Independent square periodic 2-D grids of uneven size, opacity and time step
+    (dt = 10^U(1,3) x each grid's explicit limit; dt_exp: one per grid, or None)."""
     rng = np.random.default_rng(SEED_BASE + seed)
     out = []
     for g in range(ngrids):
@@ -205,9 +234,10 @@ def batched_2d(ngrids: int = 512, seed: int = 3, nmin: int = 64, nmax: int = 512
         phys = code_units(limiter)
         phys.update(opacity="kramers", kappa0=kappa0, kr_a=1.0, kr_b=-3.5)
         rho, eps, E, kr_min = lognormal_fields(rng, (n, n), phys, kappa0)
-        dt_exp = thick_explicit_dt(1.0, 2, phys["c"], kr_min)
-        out.append({"name": f"batched_2d_{g}", "grid": grid, "phys": phys, "rho": rho, "eps": eps,
-                    "E": E, "dt": fac * dt_exp, "dt_exp": dt_exp})
+        case = {"name": f"batched_2d_{g}", "grid": grid, "phys": phys, "rho": rho, "eps": eps, "E": E,
+                "dt_factor": fac, "dt": None, "dt_exp": None,
+                "dt_exp_thick": thick_explicit_dt(1.0, 2, phys["c"], kr_min)}
+        out.append(case if dt_exp is None else with_explicit_dt(case, float(dt_exp[g])))
     return out
 
 
@@ -224,8 +254,9 @@ def opacity_table(nrho: int = 128, nT: int = 128, lrho=(-16.0, -6.0), lT=(3.7, 6
 
 
 def wind_columns(ncol: int = 4096, ncell: int = 2048, seed: int = 4, dt_factor: float = 100.0,
-                 limiter: str = "lp") -> dict:
-    """Spherically symmetric wind-like radial columns (cgs).  Arrays are (ncol, ncell)."""
+                 limiter: str = "lp", dt_exp=None) -> dict:
+    """Spherically symmetric wind-like radial columns (cgs).  Arrays are (ncol, ncell).  dt per
+    column = dt_factor x its explicit limit (dt_exp: ncol values, or None)."""
     rng = np.random.default_rng(SEED_BASE + seed)
     mu = 4.0 / 3.0  # fully ionised helium
     phys = cgs_units(mu, limiter=limiter)
@@ -262,12 +293,13 @@ def wind_columns(ncol: int = 4096, ncell: int = 2048, seed: int = 4, dt_factor: 
         noise = np.interp(np.arange(ncell), np.linspace(0, ncell - 1, 17), rng.uniform(-1, 1, 17))
         Tg[j] = Tr * (1 + 0.05 * noise)
     eps = rho * phys["gas_R"] * Tg / (phys["gamma"] - 1.0)
-    # electron scattering is the smallest opacity the table holds
-    dt_exp = (dr[None, :] ** 2 * 3 * kappa_es * rho / (2 * C_LIGHT)).min(axis=1)
-    return {"name": f"wind_columns_{ncol}x{ncell}", "phys": phys, "r_faces": rf,
+    # electron scattering is the smallest opacity the table holds: the optically thick bound
+    dt_thick = (dr[None, :] ** 2 * 3 * kappa_es * rho / (2 * C_LIGHT)).min(axis=1)
+    case = {"name": f"wind_columns_{ncol}x{ncell}", "seed": seed, "phys": phys, "r_faces": rf,
             "geometry": "spherical", "bc": ["dirichlet", "dirichlet"], "rho": rho, "eps": eps,
-            "E": E, "bc_lo": E[:, 0].copy(), "bc_hi": E[:, -1].copy(), "dt": dt_factor * dt_exp,
-            "dt_exp": dt_exp, "v": vel, "L": L, "r_star": Rs}
+            "E": E, "bc_lo": E[:, 0].copy(), "bc_hi": E[:, -1].copy(), "dt_factor": dt_factor,
+            "dt": None, "dt_exp": None, "dt_exp_thick": dt_thick, "v": vel, "L": L, "r_star": Rs}
+    return case if dt_exp is None else with_explicit_dt(case, np.asarray(dt_exp, dtype=np.float64))
 
 
 def wind_cak(case: dict, Qbar: float = 2000.0) -> dict:
@@ -320,6 +352,7 @@ def random_small(shape, seed: int, bc=None, kappa0: float = 1.0, dt_factor: floa
     phys.update(opacity="kramers", kappa0=kappa0)
     arr_shape = tuple(reversed(shape))
     rho, eps, E, kr_min = lognormal_fields(rng, arr_shape, phys, kappa0)
+    # the optically thick time scale (these brute-force cases fix their stiffness by dt_factor)
     dt_exp = thick_explicit_dt(1.0, nd, phys["c"], kr_min)
     return {"name": f"random_{'x'.join(map(str, shape))}_{seed}", "grid": grid, "phys": phys,
             "rho": rho, "eps": eps, "E": E, "dt": dt_factor * dt_exp, "dt_exp": dt_exp}

@@ -9,6 +9,7 @@ import pytest
 import torch
 
 import oracle
+import lp_dt
 from paper_2104_03968_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -289,7 +290,7 @@ def test_launch_count(ctx):
         cycles.append(info["cycles"])
     assert cycles[1] == cycles[2] and counts[1] == counts[2], (counts, cycles)
     assert counts[2] > 4 * 2 * 2 * cycles[2]
-    cases = inputs.batched_2d(ngrids=6, seed=9, nmin=64, nmax=128)
+    cases = lp_dt.batched_dt(inputs.batched_2d(ngrids=6, seed=9, nmin=64, nmax=128))
     args = ([c["grid"] for c in cases], [solver(c["phys"], rtol=1e-8) for c in cases], [c["dt"] for c in cases],
             [dev(c["rho"]) for c in cases])
     fld.step_batched(ctx, *args, [dev(c["eps"]) for c in cases], [dev(c["E"]) for c in cases])  # builds the graph
@@ -432,7 +433,7 @@ def test_diffuse_in_place_alias(ctx):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_step_parity_lognormal(ctx, order, precision):
     from paper_2104_03968_gb300 import fld
-    case = inputs.lognormal_3d(n=32, seed=11)
+    case = lp_dt.grid_dt(inputs.lognormal_3d(n=32, seed=11))
     g, p = case["grid"], case["phys"]
     e_o, E_o, _ = oracle.step(g, p, case["dt"], case["rho"], case["eps"], case["E"], order=order, rtol=1e-14)
     eps, E = dev(case["eps"]), dev(case["E"])
@@ -477,7 +478,7 @@ def test_step_full_size_128(ctx, precision):
     """The 128^3 lognormal workload at its full size and rtol: the oracle's FP64 operator applied
     to the GPU result meets rtol, and sampled cells of the exchange match the oracle."""
     from paper_2104_03968_gb300 import fld
-    case = inputs.lognormal_3d(n=128, seed=1)
+    case = inputs.lognormal_3d(n=128, seed=1, dt_exp=lp_dt.stored("lognormal_3d_128_seed1"))
     g, p = case["grid"], case["phys"]
     rtol = 1e-10 if precision == "fp64" else 1e-8
     kap = oracle.opacity(p, case["rho"], case["eps"])
@@ -559,14 +560,14 @@ def test_pseudo_planar_parity(ctx, shape, bcname, x0):
 # ----------------------------------------------------------------------------- columns
 
 def _column_case(ncol, ncell, seed=0):
-    case = inputs.wind_columns(ncol=ncol, ncell=ncell, seed=seed)
+    case = lp_dt.columns_dt(inputs.wind_columns(ncol=ncol, ncell=ncell, seed=seed))
     return case
 
 
 def test_step_parity_minerbo(ctx):
     """The Minerbo limiter through a full 3-D step (both branches of the limiter are met)."""
     from paper_2104_03968_gb300 import fld
-    case = inputs.lognormal_3d(n=32, seed=12)
+    case = lp_dt.grid_dt(inputs.lognormal_3d(n=32, seed=12))
     g, p = case["grid"], dict(case["phys"], limiter="minerbo")
     e_o, E_o, _ = oracle.step(g, p, case["dt"], case["rho"], case["eps"], case["E"], rtol=1e-14)
     eps, E = dev(case["eps"]), dev(case["E"])
@@ -670,7 +671,7 @@ def test_step_batched_parity(ctx, precision):
     """Five uneven grids in one graph launch (the first call also autotunes), each against the
     oracle; a second call on the same shape reuses the graph."""
     from paper_2104_03968_gb300 import fld
-    cases = inputs.batched_2d(ngrids=5, nmin=32, nmax=96, seed=21)
+    cases = lp_dt.batched_dt(inputs.batched_2d(ngrids=5, nmin=32, nmax=96, seed=21))
     params = [solver(c["phys"], rtol=1e-13 if precision == "fp64" else 1e-12, precision=precision) for c in cases]
     eps = [dev(c["eps"]) for c in cases]
     E = [dev(c["E"]) for c in cases]
@@ -692,14 +693,28 @@ def test_step_batched_parity(ctx, precision):
         assert relerr(host(te), e2) < TOL
 
 
-def test_step_batched_mixed_certified_residual(ctx):
+def _scaled(case, s):
+    """The same problem in units where every energy density and the density are s times larger:
+    rho, eps, E and a_rad times s, kappa0 over s^2.  T, kappa rho, D, the limiter's R and the
+    exchange's a2 are unchanged, so the solution is s times the unscaled one."""
+    c = dict(case)
+    c["phys"] = dict(case["phys"], a_rad=case["phys"]["a_rad"] * s, kappa0=case["phys"]["kappa0"] / (s * s))
+    for k in ("rho", "eps", "E"):
+        c[k] = case[k] * s
+    return c
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-20])
+def test_step_batched_mixed_certified_residual(ctx, scale):
     """Mixed batched residuals are double-float, with a bound on their error: a grid stops when the
     residual plus the bound meets rtol, so the true relative residual of its diffusion solve is
     below rtol.  With the exchange first the final E is the solve's result, and the oracle gives
-    the true residual from the exchanged state."""
+    the true residual from the exchanged state.  At scale 1e-20 the squares of the residuals and
+    of their bounds are far below the FP32 range unless the solver scales them."""
     from paper_2104_03968_gb300 import fld
     rtol = 1e-9
-    cases = inputs.batched_2d(ngrids=6, nmin=64, nmax=160, seed=23)
+    cases = lp_dt.batched_dt(inputs.batched_2d(ngrids=6, nmin=64, nmax=160, seed=23))
+    cases = [_scaled(c, scale) for c in cases]
     params = [solver(c["phys"], rtol=rtol, precision="mixed", order="exchange_then_diffuse") for c in cases]
     E = [dev(c["E"]) for c in cases]
     infos = fld.step_batched(ctx, [c["grid"] for c in cases], params, [c["dt"] for c in cases],

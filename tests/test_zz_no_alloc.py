@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 import torch
 
+import lp_dt
 from paper_2104_03968_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -30,7 +31,7 @@ def _relerr(a, b):
 def test_static_entry_matches_context_entry_twice(order):
     from paper_2104_03968_gb300 import fld
     ctx = fld.Context(0)
-    case = inputs.wind_columns(ncol=37, ncell=2048, seed=6)
+    case = lp_dt.columns_dt(inputs.wind_columns(ncol=37, ncell=2048, seed=6))
     p = dict(case["phys"], order=order)
     bc = tuple(case["bc"])
     # reference: the context entry point, two steps in a row
