@@ -44,6 +44,11 @@ KERNEL_MODEL = {
     "wave_L0": {"bound": "hbm", "bytes_f32": 4 + 12 + 4 + 4, "bytes_f64": 8 + 24 + 8 + 8 + 8},
     "wave_L0_zero": {"bound": "hbm", "bytes_f32": 4 + 12 + 2 + 4, "bytes_f64": 8 + 24 + 8 + 8},
     "wave_L0_update": {"bound": "hbm", "bytes_f32": 4 + 12 + 4 + 4 + 16, "bytes_f64": 8 + 24 + 8 + 8 + 8 + 16},
+    # the tiled sweep of the mixed solver's finest 3-D level: r, the cell coefficient dc and x in,
+    # x out (16 B); from x = 0 no x in (12 B); the last sweep of a cycle also updates the FP64 iterate
+    "sweep_L0": {"bound": "hbm", "bytes_f32": 4 + 4 + 4 + 4, "bytes_f64": None},
+    "sweep_L0_zero": {"bound": "hbm", "bytes_f32": 4 + 4 + 4, "bytes_f64": None},
+    "sweep_L0_update": {"bound": "hbm", "bytes_f32": 4 + 4 + 4 + 4 + 16, "bytes_f64": None},
     "restrict_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 3 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 3 * 8 + 8 / 8},
     "prolong_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
     # first outer residual.  Mixed: one double-float pass that also builds the diagonal: weights hi
@@ -326,6 +331,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 2-D and column workloads")
     ap.add_argument("--workload", default="lognormal3d", choices=["lognormal3d", "batched2d", "columns"],
                     help="lognormal3d: the headline 512^3 grid; batched2d / columns: the batched workloads")
     ap.add_argument("--ngrids", type=int, default=512)
@@ -426,6 +432,11 @@ def main():
         e2e = {"value": world * ncell * args.steps / secs, "unit": UNIT, "h2d_bytes_per_step": 3 * ncell * 8,
                "d2h_bytes_per_step": 2 * ncell * 8}
 
+    # ---- the batched 2-D grids and the wind columns, mixed and FP64 (outside the headline's timing)
+    secondary = {}
+    if not args.no_batched:
+        secondary = secondary_workloads(torch, np, fld, inputs, ctx, args, peaks)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         val, secs = oracle_sample(args.oracle_n, 1, args.rtol)
@@ -446,7 +457,7 @@ def main():
                 "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in sorted(rep.items(), key=lambda kv: -kv[1][1])},
                 "cycles_per_step": [i["cycles"] for i in infos],
-                "rel_residual": [i["rel_residual"] for i in infos], **extra}
+                "rel_residual": [i["rel_residual"] for i in infos], **extra, **secondary}
         print(json.dumps(line), flush=True)
     ctx.close()
     barrier(world)
@@ -455,8 +466,107 @@ def main():
 
 # ----------------------------------------------------------------------------- batched workloads
 
+# Column step (one fused kernel per column): rho, eps, E in (24 B) and eps, E out (16 B) per cell.
+COLUMN_BYTES = 40
+
+
+def batched_inputs(torch, np, inputs, kind, ngrids, ncol):
+    """Device inputs of a secondary workload: 512 uneven periodic 2-D grids or the wind columns."""
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    if kind == "batched2d":
+        dtx = stored_dt("batched_2d_512_seed3")
+        if ngrids > len(dtx):
+            raise SystemExit(f"stored explicit limits cover {len(dtx)} batched grids")
+        cases = inputs.batched_2d(ngrids=ngrids, seed=3, dt_exp=dtx)
+        return {"kind": kind, "grids": [c["grid"] for c in cases], "phys": [c["phys"] for c in cases],
+                "dts": [c["dt"] for c in cases], "rho": [dev(c["rho"]) for c in cases],
+                "eps": [dev(c["eps"]) for c in cases], "E": [dev(c["E"]) for c in cases],
+                "cells": sum(int(c["rho"].size) for c in cases),
+                "desc": f"{ngrids} independent periodic 2-D grids, n log-uniform in [64, 512], kappa0 = 10^U(-2,4), "
+                        f"dt = 10^U(1,3) x each grid's explicit limit, one graph launch per step"}
+    dtx = stored_dt("wind_columns_4096x2048_seed4")
+    if ncol > len(dtx):
+        raise SystemExit(f"stored explicit limits cover {len(dtx)} columns")
+    case = inputs.wind_columns(ncol=ncol, ncell=2048, seed=4, dt_exp=dtx[:ncol])
+    return {"kind": kind, "phys": case["phys"], "bc": tuple(case["bc"]), "rf": dev(case["r_faces"]),
+            "vlo": dev(case["bc_lo"]), "vhi": dev(case["bc_hi"]), "dt": dev(case["dt"]), "rho": dev(case["rho"]),
+            "eps": dev(case["eps"]), "E": dev(case["E"]), "cells": int(case["rho"].size),
+            "desc": f"{ncol} spherical wind-like columns x 2048 cells, r = 1..100 R*, tabulated opacity, "
+                    f"dt = 100x each column's explicit limit, direct tridiagonal diffusion + exchange"}
+
+
+def time_batched(torch, fld, ctx, W, precision, rtol, steps, warmup, peaks):
+    """Warm-up, then `steps` timed steps of a secondary workload from its initial state, with the
+    device time of the library's traced scopes."""
+    if W["kind"] == "batched2d":
+        params = [dict(p, precision=precision, rtol=rtol) for p in W["phys"]]
+        eps = [t.clone() for t in W["eps"]]
+        E = [t.clone() for t in W["E"]]
+
+        def step():
+            return fld.step_batched(ctx, W["grids"], params, W["dts"], W["rho"], eps, E)
+    else:
+        p = dict(W["phys"], precision=precision)
+        eps, E = W["eps"].clone(), W["E"].clone()
+
+        def step():
+            return [fld.columns_step(ctx, W["rf"], "spherical", W["bc"], W["vlo"], W["vhi"], p, W["dt"], W["rho"],
+                                     eps, E)]
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    fld.trace_enable(ctx, True)
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    n0 = fld.launch_count()
+    t0.record(stream)
+    per_step = []
+    for _ in range(steps):
+        per_step.append(step())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    n1 = fld.launch_count()
+    fld.trace_enable(ctx, False)
+    rep = fld.trace_report(ctx)
+    ms = t0.elapsed_time(t1)
+    out = {"value": W["cells"] * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+           "gpu_launches": n1 - n0, "status": sorted({i["status"] for infos in per_step for i in infos}),
+           "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in rep.items()}}
+    if W["kind"] == "batched2d":
+        out["max_cycles_per_step"] = [max(i["cycles"] for i in infos) for infos in per_step]
+        out["mean_cycles_per_step"] = [sum(i["cycles"] for i in infos) / len(infos) for infos in per_step]
+    else:
+        name = "columns_mixed" if precision == "mixed" else "columns"
+        if name in rep:
+            launches, kms = rep[name]
+            achieved = COLUMN_BYTES * W["cells"] / (kms / launches * 1e-3) / 1e9
+            out["roofline"] = {"kernel": "k_columns", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                               "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                               "peak_source": peaks["source"] + " copy bandwidth", "traffic": None,
+                               "algorithmic_bytes_per_launch": COLUMN_BYTES * W["cells"],
+                               "note": "one fused kernel per step (coefficients, tridiagonal solve, exchange); "
+                                       "bound by FP64 arithmetic, not by HBM"}
+    return out
+
+
+def secondary_workloads(torch, np, fld, inputs, ctx, args, peaks):
+    """The batched 2-D grids and the wind columns, mixed and FP64, for the headline line."""
+    out = {}
+    for kind in ("batched2d", "columns"):
+        W = batched_inputs(torch, np, inputs, kind, args.ngrids, args.ncol)
+        res = {"config": {"workload": W["desc"], "cells": W["cells"], "rtol": args.rtol}}
+        for prec in ("mixed", "fp64"):
+            res[prec] = time_batched(torch, fld, ctx, W, prec, args.rtol, args.steps, args.warmup, peaks)
+        res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
+        out[kind] = res
+        del W
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_batched_workload(args):
-    """Secondary lines: many uneven 2-D grids in one graph launch, or many 1-D wind columns."""
+    """A line of its own for one secondary workload and precision."""
     import numpy as np
     import torch
 
@@ -465,68 +575,12 @@ def run_batched_workload(args):
     from paper_2104_03968_gb300 import fld, inputs
 
     ctx = fld.Context(0)
-    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
-    if args.workload == "batched2d":
-        dtx = stored_dt("batched_2d_512_seed3")
-        if args.ngrids > len(dtx):
-            raise SystemExit(f"stored explicit limits cover {len(dtx)} batched grids")
-        cases = inputs.batched_2d(ngrids=args.ngrids, seed=3, dt_exp=dtx)
-        grids = [c["grid"] for c in cases]
-        params = [dict(c["phys"], precision=args.precision, rtol=args.rtol) for c in cases]
-        dts = [c["dt"] for c in cases]
-        rhos = [dev(c["rho"]) for c in cases]
-        eps0 = [dev(c["eps"]) for c in cases]
-        E0 = [dev(c["E"]) for c in cases]
-        ncell = sum(int(c["rho"].size) for c in cases)
-        eps = [t.clone() for t in eps0]
-        E = [t.clone() for t in E0]
-
-        def step():
-            return fld.step_batched(ctx, grids, params, dts, rhos, eps, E)
-        desc = (f"{args.ngrids} independent periodic 2-D grids, n log-uniform in [64, 512], kappa0 = 10^U(-2,4), "
-                f"dt = 10^U(1,3) x explicit limit, one graph launch per step, rtol {args.rtol:g}")
-    else:
-        dtx = stored_dt("wind_columns_4096x2048_seed4")
-        if args.ncol > len(dtx):
-            raise SystemExit(f"stored explicit limits cover {len(dtx)} columns")
-        case = inputs.wind_columns(ncol=args.ncol, ncell=2048, seed=4, dt_exp=dtx[:args.ncol])
-        p = dict(case["phys"], precision=args.precision)
-        rf, vlo, vhi, dtt = dev(case["r_faces"]), dev(case["bc_lo"]), dev(case["bc_hi"]), dev(case["dt"])
-        rho = dev(case["rho"])
-        eps = dev(case["eps"])
-        E = dev(case["E"])
-        ncell = case["rho"].size
-
-        def step():
-            return [fld.columns_step(ctx, rf, "spherical", tuple(case["bc"]), vlo, vhi, p, dtt, rho, eps, E)]
-        desc = (f"{args.ncol} spherical wind-like columns x 2048 cells, r = 1..100 R*, tabulated opacity, "
-                f"direct tridiagonal diffusion + exchange, {args.precision}")
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    fld.trace_enable(ctx, True)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    n_before = fld.launch_count()
-    t0.record()
-    infos = []
-    for _ in range(args.steps):
-        infos = step()
-    t1.record()
-    torch.cuda.synchronize()
-    n_after = fld.launch_count()
-    fld.trace_enable(ctx, False)
-    rep = fld.trace_report(ctx)
-    ms = t0.elapsed_time(t1)
-    line = {"metric": f"{args.workload} cell-updates/s", "value": ncell * args.steps / (ms * 1e-3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.workload == "columns" or args.precision == "fp64" else "f64+f32",
-            "data": "synthetic", "config": {"workload": desc, "cells": int(ncell)},
-            "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in rep.items()},
-            "gpu_launches": n_after - n_before,
-            "status": sorted({i["status"] for i in infos}),
-            "max_cycles": max(i["cycles"] for i in infos)}
+    W = batched_inputs(torch, np, inputs, args.workload, args.ngrids, args.ncol)
+    r = time_batched(torch, fld, ctx, W, args.precision, args.rtol, args.steps, args.warmup, load_peaks())
+    line = {"metric": f"{args.workload} cell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": {"workload": W["desc"], "cells": W["cells"], "rtol": args.rtol}, **r}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0

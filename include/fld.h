@@ -120,12 +120,13 @@ typedef struct {
   int tn[2];
   double tlo[2], thi[2];
   /* solver */
-  int precision;   /* FLD_PREC_FP64: FP64 multigrid.  FLD_PREC_MIXED: FP32 V-cycles inside
-                      a defect-correction loop whose residuals, updates and norms are FP64-grade:
-                      double-float (pairs of floats, ~2^-46 relative) with a certified error
-                      bound, FP64 where values leave the double-float range or rtol < 1e-10.
-                      Both precisions compute the coefficients and the exchange in double-float
-                      with FP64 fallback per cell. */
+  int precision;   /* FLD_PREC_FP64: plain FP64 throughout -- the coefficients, the multigrid
+                      solve and the exchange's safeguarded Halley root (Sect. 3.3).
+                      FLD_PREC_MIXED: FP32 V-cycles inside a defect-correction loop whose
+                      residuals, updates and norms are FP64-grade: double-float (pairs of floats,
+                      ~2^-46 relative) with a certified error bound, FP64 where values leave the
+                      double-float range or rtol < 1e-10; the coefficients and the exchange in
+                      double-float with FP64 fallback per cell. */
   double rtol;     /* stop when ||b - A E||_2 / ||b||_2 <= rtol */
   int max_cycles;  /* outer iterations (one V-cycle each); 0 = 100 */
   int nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after coarse correction.  Both 0:
@@ -186,6 +187,23 @@ FLD_API fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_par
 FLD_API fld_status fld_diffuse_aniso(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
                              const double* const* D_axis, const double* E_old, double* E_new,
                              fld_info* info, void* stream);
+
+/* One red-black Gauss-Seidel sweep (both colours) of the smoother that the mixed-precision
+   multigrid runs on the finest level of 3-D grids (Sect. 3.4: a Gauss-Seidel smoother of the
+   backward-Euler operator of Eq. discdiff), exposed so that it can be checked on its own.  It
+   relaxes the dt-scaled correction equation x + dt (-div D grad x) = r in FP32:
+     x_c <- (r_c + sum_f w_f x_nb) / (1 + sum_f w_f),  w_f = dt D_f / dx_a^2,
+   with D_f the harmonic mean of the two cells' D (a non-periodic boundary face takes the interior
+   cell's D; Dirichlet, Neumann and linear-extrapolation faces as in fld_diffuse, with homogeneous
+   boundary values).  D_cell: DEVICE float64, N cells.  r, x_in, x_out: DEVICE float32, N cells,
+   x fastest; x_in NULL means x = 0 before the sweep; x_out must not overlap x_in.  The cells with
+   (i + j + k) % 2 == first_colour are updated first, then the others from their new values.
+   Supported grids: ndim 3, n[0] a multiple of 64, n[1] a multiple of 16, n[2] even and >= 4,
+   fewer than 2^31 cells (FLD_ERR_UNSUPPORTED otherwise).  Uses the context's scratch (allocated
+   on first use) for an FP32 copy of dt D / dx_0^2.  Asynchronous. */
+FLD_API fld_status fld_smooth_sweep(fld_ctx* ctx, const fld_grid* grid, double dt, const double* D_cell,
+                                    const float* r, const float* x_in, float* x_out, int first_colour,
+                                    void* stream);
 
 /* Point-implicit exchange (Sect. 3.3) on n independent cells, in place on eps and E.  kappa may
    be NULL, in which case it is evaluated from rho and eps with the opacity model of p.

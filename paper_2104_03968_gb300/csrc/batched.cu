@@ -1215,7 +1215,9 @@ cudaError_t BatchedSolver::Impl::upload(const fld_params* params, const double* 
     f.ph.gas_R = p.gas_R;
     f.ph.limiter = p.limiter;
     f.cdf = make_coeff_df(f.ph, f.g);
-    f.xp = make_exchange(p.c, p.a_rad, p.gamma, p.gas_R, dt[g], p.exch_maxit > 0 ? p.exch_maxit : 100);
+    const bool plain64 = params[0].precision == FLD_PREC_FP64;  // the batch shares one precision
+    if (plain64) f.cdf.ok = 0;  // FP64 coefficients in every cell
+    f.xp = make_exchange(p.c, p.a_rad, p.gamma, p.gas_R, dt[g], p.exch_maxit > 0 ? p.exch_maxit : 100, plain64);
     f.dt = dt[g];
     f.order = p.order;
     f.rho = rho[g];

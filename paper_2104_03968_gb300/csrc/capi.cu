@@ -15,6 +15,7 @@
 #include "columns.h"
 #include "kernels.h"
 #include "mg.h"
+#include "sweep3d.h"
 #include "trace.h"
 
 using namespace fld;
@@ -164,7 +165,8 @@ Opacity to_opacity(const fld_params* p) {
 }
 
 ExchangeParams to_exchange(const fld_params* p, double dt) {
-  return make_exchange(p->c, p->a_rad, p->gamma, p->gas_R, dt, p->exch_maxit > 0 ? p->exch_maxit : 100);
+  return make_exchange(p->c, p->a_rad, p->gamma, p->gas_R, dt, p->exch_maxit > 0 ? p->exch_maxit : 100,
+                       p->precision == FLD_PREC_FP64);
 }
 
 fld_status ensure_scratch(fld_ctx* ctx, long long ncell) {
@@ -332,7 +334,7 @@ fld_status fld_coeffs(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, c
   cudaStream_t s = (cudaStream_t)stream;
   GridDev g = to_dev(grid);
   cudaError_t e = launch_coeffs(g, to_opacity(p), p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, kappa_out, D_out,
-                                ctx->d_status, s);
+                                ctx->d_status, s, p->precision == FLD_PREC_FP64);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_coeffs launch");
   return FLD_OK;
 }
@@ -403,6 +405,42 @@ fld_status fld_diffuse_aniso(fld_ctx* ctx, const fld_grid* grid, const fld_param
   return diffuse_common(ctx, grid, p, dt, Dax, E_old, E_new, info, stream);
 }
 
+fld_status fld_smooth_sweep(fld_ctx* ctx, const fld_grid* grid, double dt, const double* D_cell, const float* r,
+                            const float* x_in, float* x_out, int first_colour, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_grid(ctx, grid);
+  if (st != FLD_OK) return st;
+  if (!D_cell || !r || !x_out) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell, r and x_out must be non-NULL");
+  if (x_in == x_out) return fail(ctx, FLD_ERR_INVALID_ARG, "x_out must not be x_in");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be positive and finite");
+  if (first_colour != 0 && first_colour != 1) return fail(ctx, FLD_ERR_INVALID_ARG, "first_colour must be 0 or 1");
+  if (grid->ndim != 3 || !sweep3d_eligible(grid->n[0], grid->n[1], grid->n[2]))
+    return fail(ctx, FLD_ERR_UNSUPPORTED,
+                "the tiled sweep needs a 3-D grid with n[0] %% 64 == 0, n[1] %% 16 == 0, n[2] even and >= 4");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const GridDev g = to_dev(grid);
+  if ((st = ensure_scratch(ctx, g.ncell)) != FLD_OK) return st;
+  float* dc = reinterpret_cast<float*>(ctx->kappa);  // FP32 in the FP64 scratch
+  cudaError_t e = launch_dcell32(g.ncell, dt * g.inv_dx2[0], D_cell, dc, s);
+  Sweep3dArgs a{};
+  a.nx = g.n[0];
+  a.ny = g.n[1];
+  a.nz = g.n[2];
+  for (int f = 0; f < 6; ++f) a.bc[f] = g.bc[f];
+  for (int ax = 0; ax < 3; ++ax) a.ra[ax] = (float)(g.inv_dx2[ax] / g.inv_dx2[0]);
+  a.dc = dc;
+  a.r = r;
+  a.xin = x_in;
+  a.xout = x_out;
+  a.x64 = nullptr;
+  a.c0 = first_colour;
+  if (e == cudaSuccess) e = launch_sweep3d(a, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_smooth_sweep launch");
+  return FLD_OK;
+}
+
 fld_status fld_exchange(fld_ctx* ctx, size_t n, const fld_params* p, double dt, const double* rho, const double* kappa,
                         double* eps, double* E, fld_info* info, void* stream) {
   if (!ctx) return FLD_ERR_INVALID_ARG;
@@ -463,7 +501,8 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
     if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
     e = cudaMemcpyAsync(Eh, E, bytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint copies");
-    e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status, s);
+    e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status, s,
+                      p->precision == FLD_PREC_FP64);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
     const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
     if ((st = run_diffuse(ctx, grid, p, 0.5 * dt, Dax, E, E, &ss, s)) != FLD_OK) return st;
@@ -477,7 +516,7 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
       if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
     }
     e = launch_coeffs(g, op, p->c, p->gamma, p->gas_R, p->limiter, E, rho, eps, ctx->kappa, ctx->D, ctx->d_status,
-                      s);
+                      s, p->precision == FLD_PREC_FP64);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
     const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
     if ((st = run_diffuse(ctx, grid, p, dt, Dax, E, E, &ss, s)) != FLD_OK) return st;
@@ -577,7 +616,7 @@ fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_params* p
     e = cudaStreamWaitEvent(s, ev[2 + i], 0);
     if (e == cudaSuccess)
       e = launch_coeffs_range(g, op, p->c, p->gamma, p->gas_R, p->limiter, dE, dr, de, ctx->kappa, ctx->D,
-                              ctx->d_status, first(i), first(i + 1) - first(i), s);
+                              ctx->d_status, first(i), first(i + 1) - first(i), s, p->precision == FLD_PREC_FP64);
   }
   if (e != cudaSuccess) return drain(cuda_fail(ctx, e, "coeffs launch"));
   SolveStats ss;

@@ -63,11 +63,13 @@ static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock -
 
 cudaError_t launch_coeffs_range(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
                                 int limiter, const double* E, const double* rho, const double* eps, double* kappa_out,
-                                double* D_out, unsigned* status, long long first, long long count, cudaStream_t s) {
+                                double* D_out, unsigned* status, long long first, long long count, cudaStream_t s,
+                                bool plain64) {
   if (count <= 0) return cudaSuccess;
   TraceScope ts("coeffs", s);
   CoeffPhys ph{op, c, gamma, gas_R, limiter};
-  const CoeffDf K = make_coeff_df(ph, g);
+  CoeffDf K = make_coeff_df(ph, g);
+  if (plain64) K.ok = 0;  // every cell takes the FP64 formula
   if (g.ncell < (1ll << 32) - kBlock)
     note_launch(),
         k_coeffs<<<blocks_for(count), kBlock, 0, s>>>(g, ph, K, make_fastdiv((unsigned)g.n[0]),
@@ -82,9 +84,10 @@ cudaError_t launch_coeffs_range(const GridDev& g, const Opacity& op, double c, d
 
 cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
                           int limiter, const double* E, const double* rho, const double* eps,
-                          double* kappa_out, double* D_out, unsigned* status, cudaStream_t s) {
+                          double* kappa_out, double* D_out, unsigned* status, cudaStream_t s, bool plain64) {
   if (g.ncell == 0) return cudaSuccess;
-  return launch_coeffs_range(g, op, c, gamma, gas_R, limiter, E, rho, eps, kappa_out, D_out, status, 0, g.ncell, s);
+  return launch_coeffs_range(g, op, c, gamma, gas_R, limiter, E, rho, eps, kappa_out, D_out, status, 0, g.ncell, s,
+                             plain64);
 }
 
 cudaError_t launch_faces(const GridDev& g, double dt, const double* const Dax[3], double* const w64[3],

@@ -76,6 +76,7 @@ struct ColArgs {
   double* Eout;
   double c, gamma, gas_R, sigma;
   int limiter, maxit;
+  int plain64;  // the FP64 precision: the exchange in FP64 arithmetic throughout
   Opacity op;
   int* info_iters;
   int* info_bisect;
@@ -237,10 +238,11 @@ __global__ void k_columns(ColArgs A) {
   const double vlo = A.v_lo ? A.v_lo[blockIdx.x] : 0.0, vhi = A.v_hi ? A.v_hi[blockIdx.x] : 0.0;
   const double *gl = A.geom, *gu = A.geom + n, *cm = A.geom + 2 * n, *cp = A.geom + 3 * n;
   const double hl = A.geom[4 * n], hr = A.geom[4 * n + 1], flo = A.geom[4 * n + 2], fhi = A.geom[4 * n + 3];
-  const ExchangeParams xp = make_exchange(A.c, 4.0 * A.sigma / A.c, A.gamma, A.gas_R, dtc, A.maxit);
-  const ExchangeParams xp1 = MODE == kColStepMidpoint
-                                 ? make_exchange(A.c, 4.0 * A.sigma / A.c, A.gamma, A.gas_R, 0.5 * dtc, A.maxit)
-                                 : xp;  // the first exchange stage
+  const ExchangeParams xp = make_exchange(A.c, 4.0 * A.sigma / A.c, A.gamma, A.gas_R, dtc, A.maxit, A.plain64 != 0);
+  const ExchangeParams xp1 =
+      MODE == kColStepMidpoint ? make_exchange(A.c, 4.0 * A.sigma / A.c, A.gamma, A.gas_R, 0.5 * dtc, A.maxit,
+                                               A.plain64 != 0)
+                               : xp;  // the first exchange stage
   int iters = 0, bis = 0;
   bool bad = false;
 
@@ -618,6 +620,7 @@ static ColArgs col_args(int ncell, const double* r_faces, int bc_lo, int bc_hi, 
   A.sigma = p.a_rad * p.c / 4.0;
   A.limiter = p.limiter;
   A.maxit = p.exch_maxit > 0 ? p.exch_maxit : 100;
+  A.plain64 = p.precision == FLD_PREC_FP64 ? 1 : 0;
   A.op.model = p.opacity;
   A.op.kappa0 = p.kappa0;
   A.op.kr_a = p.kr_a;

@@ -147,7 +147,7 @@ __device__ inline bool exchange_cell(const ExchangeParams& p, double r, double k
   const double cc = fma(a2 * u, E0, e0) * invS;
   const float af = (float)a, cf = (float)cc;
   double y;
-  if (af >= 1e-30f && af <= 1e30f && cf >= 1e-30f) {
+  if (!p.plain64 && af >= 1e-30f && af <= 1e30f && cf >= 1e-30f) {
     float r1;
     const float y32 = halley32(af, cf, iters, r1);
     // polish in double-float while a, cc and y keep their low parts normal floats, else in FP64

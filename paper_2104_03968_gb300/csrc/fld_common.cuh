@@ -47,6 +47,9 @@ struct ExchangeParams {
   // df_ok is 0 unless both are positive and finite
   float cdt_hi, cdt_lo, k4_hi, k4_lo;
   int cdt_e, k4_e, df_ok;
+  // 1: plain FP64 throughout (the FP64 solver's exchange): the FP64 safeguarded Halley iteration
+  // from its first step, no double-float path and no FP32 start
+  int plain64;
 };
 
 __host__ __device__ inline void mant_split(double v, float& hi, float& lo, int& e) {
@@ -72,6 +75,18 @@ __host__ __device__ inline ExchangeParams make_exchange(double c, double a_rad, 
   mant_split(p.cdt, p.cdt_hi, p.cdt_lo, p.cdt_e);
   mant_split(p.k4, p.k4_hi, p.k4_lo, p.k4_e);
   p.df_ok = p.cdt > 0.0 && p.cdt <= 1.7e308 && p.k4 > 0.0 && p.k4 <= 1.7e308 && p.cdt >= 2.3e-308 && p.k4 >= 2.3e-308;
+  p.plain64 = 0;
+  return p;
+}
+
+// The exchange constants of one call; plain64 selects the FP64 arithmetic of the FP64 solver.
+__host__ __device__ inline ExchangeParams make_exchange(double c, double a_rad, double gamma, double gas_R, double dt,
+                                                        int maxit, bool plain64) {
+  ExchangeParams p = make_exchange(c, a_rad, gamma, gas_R, dt, maxit);
+  if (plain64) {
+    p.plain64 = 1;
+    p.df_ok = 0;
+  }
   return p;
 }
 

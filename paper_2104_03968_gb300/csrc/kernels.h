@@ -7,13 +7,15 @@
 
 namespace fld {
 
+// plain64: the FP64 formula in every cell (the FP64 solver); else double-float with FP64 fallback
 cudaError_t launch_coeffs(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
                           int limiter, const double* E, const double* rho, const double* eps,
-                          double* kappa_out, double* D_out, unsigned* status, cudaStream_t s);
+                          double* kappa_out, double* D_out, unsigned* status, cudaStream_t s, bool plain64 = false);
 // the same for cells [first, first + count) only (the whole grid is the stencil's domain)
 cudaError_t launch_coeffs_range(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
                                 int limiter, const double* E, const double* rho, const double* eps, double* kappa_out,
-                                double* D_out, unsigned* status, long long first, long long count, cudaStream_t s);
+                                double* D_out, unsigned* status, long long first, long long count, cudaStream_t s,
+                                bool plain64 = false);
 
 // w64[a] (and w32[a] when non-null) receive the face weights of axis a (layout of fld_common.cuh);
 // with w32lo, w32 holds the truncated leading 24 bits of each weight and w32lo the remainder.

@@ -23,6 +23,7 @@
 #include "df.cuh"
 #include "mg_df.h"
 #include "mg_device.cuh"
+#include "sweep3d.h"
 #include "trace.h"
 
 namespace fld {
@@ -688,6 +689,17 @@ static bool wave_eligible(const GridDev& g, const std::array<int, 3>& n) {
          (long long)n[0] * (n[1] + 1) * n[2] < (1LL << 31) && (long long)n[0] * n[1] * (n[2] + 1) < (1LL << 31);
 }
 
+// The mixed solver's finest level takes the tiled sweep when it is 3-D, of a shape the tiles
+// cover, and at least 1 Mi cells (FLD_SWEEP3D_MIN_CELLS overrides the threshold; FLD_SWEEP3D=0
+// turns the tiled sweep off).
+static bool tiled_level(const GridDev& g, const std::array<int, 3>& n) {
+  const char* off = getenv("FLD_SWEEP3D");
+  if (off && off[0] == '0') return false;
+  const char* v = getenv("FLD_SWEEP3D_MIN_CELLS");
+  const long long min_cells = v ? std::max(0LL, atoll(v)) : (1LL << 20);
+  return g.ndim == 3 && cells3(n) >= min_cells && sweep3d_eligible(n[0], n[1], n[2]);
+}
+
 // Ticket order of the (half-sweep, plane) groups.  Half-sweep 1 trails half-sweep 0 by `skew`
 // positions.  On a periodic z axis the planes are visited folded (0, nz-1, 1, nz-2, ...), which
 // puts every pair of ring neighbours, the wrap-around pair included, within two positions.
@@ -764,6 +776,26 @@ cudaError_t Multigrid::wave_sweep(int l, bool zero, int c0, double* x64, cudaStr
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t Multigrid::tiled_sweep(bool zero, int c0, double* x64, cudaStream_t s) {
+  const std::array<int, 3>& n = dims_[0];
+  Sweep3dArgs a{};
+  a.nx = n[0];
+  a.ny = n[1];
+  a.nz = n[2];
+  for (int f = 0; f < 6; ++f) a.bc[f] = g_.bc[f];
+  for (int ax = 0; ax < 3; ++ax) a.ra[ax] = (float)(g_.inv_dx2[ax] / g_.inv_dx2[0]);
+  a.dc = dc32_;
+  a.r = (const float*)lv_[0].r;
+  a.xin = zero ? nullptr : (const float*)lv_[0].x;
+  a.xout = (float*)lv_[0].tmp;
+  a.x64 = x64;
+  a.c0 = c0;
+  cudaError_t e = launch_sweep3d(a, s);
+  std::swap(lv_[0].x, lv_[0].tmp);  // the iterate now lives in the other array
+  return e;
+}
+
 cudaError_t Multigrid::configure(const GridDev& g, int precision) {
   bool same = configured_ && precision == precision_ && g.ndim == g_.ndim;
   for (int a = 0; a < 3 && same; ++a) same = g.n[a] == g_.n[a];
@@ -799,6 +831,8 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
     for (int k = 0; k < 3; ++k) add(N * sizeof(float));                           // diag hi, lo; r lo
     add(sizeof(unsigned));
   }
+  const bool tiled = df && tiled_level(g, dims_[0]);
+  if (tiled) add(N * sizeof(float));  // dt D / dx_0^2 of the tiled sweep
   for (size_t l = 0; l < dims_.size(); ++l) {
     long long n = cells3(dims_[l]);
     if (l > 0 || precision == FLD_PREC_MIXED)
@@ -830,6 +864,8 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
     df_flag_ = (unsigned*)arena_.take(sizeof(unsigned));
     if (!dhi_ || !dlo_ || !rlo_ || !df_flag_) return cudaErrorMemoryAllocation;
   }
+  dc32_ = nullptr;
+  if (tiled && !(dc32_ = (float*)arena_.take(N * sizeof(float)))) return cudaErrorMemoryAllocation;
   lv_.assign(dims_.size(), LevelBuf{});
   for (size_t l = 0; l < dims_.size(); ++l) {
     long long n = cells3(dims_[l]);
@@ -861,6 +897,10 @@ cudaError_t Multigrid::fp64_operator(cudaStream_t s) {
     for (int a = 0; a < g_.ndim; ++a) w32[a] = (float*)lv_[0].w[a];
   cudaError_t e = launch_faces(g_, dt_, D_ax_, w64_, w32, dhi_ ? w32lo_ : nullptr, s);
   if (e != cudaSuccess) return e;
+  if (tiled_) {
+    e = launch_dcell32(g_.ncell, dt_ * g_.inv_dx2[0], D_ax_[0], dc32_, s);
+    if (e != cudaSuccess) return e;
+  }
   void* w64v[3] = {w64_[0], w64_[1], w64_[2]};
   LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
   {
@@ -890,6 +930,8 @@ cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const d
   for (int a = 0; a < g_.ndim; ++a) maxf = std::max(maxf, faces3(dims_[0], a));
   df_mode_ = sizeof(T) == sizeof(float) && dhi_ != nullptr && rtol >= 1e-10 && D_cell[1] == D_cell[0] &&
              D_cell[2] == D_cell[0] && maxf < (1LL << 31);
+  // the tiled finest-level sweep needs one scalar D (it forms the face means from dc32_)
+  tiled_ = sizeof(T) == sizeof(float) && dc32_ != nullptr && D_cell[1] == D_cell[0] && D_cell[2] == D_cell[0];
   cudaError_t e;
   if (df_mode_) {
     e = cudaMemsetAsync(df_flag_, 0, sizeof(unsigned), s);
@@ -898,7 +940,7 @@ cudaError_t Multigrid::setup_t(double dt, const double* const D_cell[3], const d
     float* w32[3] = {nullptr, nullptr, nullptr};
     for (int a = 0; a < g_.ndim; ++a) w32[a] = (float*)lv_[0].w[a];
     // the diagonal, 1/diag and b follow in the first residual's pass (solve_t)
-    e = launch_faces_df(g_, K, D_cell[0], w32, w32lo_, df_flag_, s);
+    e = launch_faces_df(g_, K, D_cell[0], w32, w32lo_, tiled_ ? dc32_ : nullptr, df_flag_, s);
     if (e != cudaSuccess) return e;
   } else {
     e = fp64_operator<T>(s);
@@ -1036,10 +1078,17 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
   long long nhalf = (long long)((n[0] + 1) / 2) * n[1] * n[2];
   unsigned gb = nblk(nhalf);
   const bool wave = wave_[l].order != nullptr;
+  const bool tiled = l == 0 && tiled_ && sizeof(T) == sizeof(float);
   // pre-smoothing (from a zero initial guess unless the caller set one): red, black, ...
   const char* sm_name = l == 0 ? "smooth_L0" : "smooth_Lc";
   for (int it = 0; it < nu1; ++it) {
     const bool zero = it == 0 && zero_init;
+    if (tiled) {
+      TraceScope ts(zero ? "sweep_L0_zero" : "sweep_L0", s);
+      cudaError_t e = tiled_sweep<T>(zero, 0, nullptr, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if (wave) {
       TraceScope ts(l == 0 ? (zero ? "wave_L0_zero" : "wave_L0") : "wave_Lc", s);
       cudaError_t e = wave_sweep<T>(l, zero, 0, nullptr, s);
@@ -1054,6 +1103,7 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     TraceScope ts(sm_name, s);
     note_launch(), k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 1);
   }
+  x = (T*)lv_[l].x;  // the tiled sweeps move the iterate between x and tmp
   const std::array<int, 3>& nc = dims_[l + 1];
   {
     TraceScope ts(l == 0 ? "restrict_L0" : "restrict_Lc", s);
@@ -1092,6 +1142,12 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
   // final correction to the FP64 iterate
   for (int it = 0; it < nu2; ++it) {
     bool last = x64 && it == nu2 - 1;
+    if (tiled) {
+      TraceScope ts(last ? "sweep_L0_update" : "sweep_L0", s);
+      cudaError_t e = tiled_sweep<T>(false, 1, last ? x64 : nullptr, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if (wave) {
       TraceScope ts(l == 0 ? (last ? "wave_L0_update" : "wave_L0") : "wave_Lc", s);
       cudaError_t e = wave_sweep<T>(l, false, 1, last ? x64 : nullptr, s);
@@ -1107,6 +1163,7 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     if (last) note_launch(), k_smooth<T, false, true><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0, x64);
     else note_launch(), k_smooth<T, false><<<gb, kBlock, 0, s>>>(L, invd, r, x, 0);
   }
+  x = (T*)lv_[l].x;
   if (x64 && nu2 == 0) {
     TraceScope ts("add_correction", s);
     note_launch(), k_add_correction<T><<<nblk(ncell), kBlock, 0, s>>>(ncell, x, x64);

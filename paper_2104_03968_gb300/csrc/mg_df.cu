@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256, 8) k_faces_df(GridDev g, DfConst K, const
                                                   float* __restrict__ w0, float* __restrict__ w1,
                                                   float* __restrict__ w2, float* __restrict__ l0,
                                                   float* __restrict__ l1, float* __restrict__ l2,
-                                                  unsigned* __restrict__ flag) {
+                                                  float* __restrict__ dc, unsigned* __restrict__ flag) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int rows = ny * nz;
   const bool per[3] = {g.bc[0] == FLD_BC_PERIODIC, g.bc[2] == FLD_BC_PERIODIC, g.bc[4] == FLD_BC_PERIODIC};
@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(256, 8) k_faces_df(GridDev g, DfConst K, const
         split_f64_scaled(Dc, sh, c.hi, c.lo, ok);
         if (!ok) bad = 1u;
       }
+      // the cell's own dt D / dx_0^2 in FP32, for the smoother that forms its face means on chip
+      if (dc) dc[idx] = scale2(c.hi * K.s_hi[0], sh);
       // x faces: lower face i of row (j, k), and face nx when this cell owns it
       {
         const dfl s{K.s_hi[0], K.s_lo[0]};
@@ -284,11 +286,12 @@ DfConst make_df_const(const GridDev& g, double dt) {
 }
 
 cudaError_t launch_faces_df(const GridDev& g, const DfConst& K, const double* D, float* const w[3],
-                            float* const wlo[3], unsigned* flag, cudaStream_t s) {
+                            float* const wlo[3], float* dc, unsigned* flag, cudaStream_t s) {
   TraceScope ts("faces", s);
   const int rows = g.n[1] * g.n[2];
   note_launch(),
-      k_faces_df<<<(unsigned)std::min(rows, 152 * 16), 256, 0, s>>>(g, K, D, w[0], w[1], w[2], wlo[0], wlo[1], wlo[2], flag);
+      k_faces_df<<<(unsigned)std::min(rows, 152 * 16), 256, 0, s>>>(g, K, D, w[0], w[1], w[2], wlo[0], wlo[1], wlo[2], dc,
+                                                                    flag);
   return cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ _SIGS = {
     "fld_photon_tiring_step": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_pseudo_planar_source": [P, P, P, ct.c_double, P, P, P, P, P, ct.c_int, P],
     "fld_pseudo_planar_step": [P, P, P, ct.c_double, ct.c_double, P, P, P, P, P],
+    "fld_smooth_sweep": [P, P, ct.c_double, P, P, P, P, ct.c_int, P],
 }
 
 
@@ -253,6 +254,23 @@ def diffuse(ctx: Context, grid: dict, params: dict, dt: float, D, E_old, out=Non
     if st and st != 4:
         ctx.check(st)
     return E_new, info.as_dict()
+
+
+def _fptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return ct.c_void_p(t.data_ptr())
+
+
+def smooth_sweep(ctx: Context, grid: dict, dt: float, D, r, x_in, x_out, first_colour: int = 0):
+    """One red-black Gauss-Seidel sweep of the mixed solver's FP32 smoother (Sect. 3.4) on a 3-D
+    grid: D float64, r / x_in / x_out float32 CUDA tensors (x_in None: start from zero)."""
+    g = grid_struct(grid)
+    ctx.check(ctx.lib.fld_smooth_sweep(ctx.h, ct.byref(g), float(dt), _dptr(D), _fptr(r), _fptr(x_in), _fptr(x_out),
+                                       int(first_colour), _stream()))
+    return x_out
 
 
 def diffuse_aniso(ctx: Context, grid: dict, params: dict, dt: float, D_axis, E_old, out=None):

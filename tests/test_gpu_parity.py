@@ -783,3 +783,121 @@ def test_not_converged_is_reported(ctx):
     D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
     out, info = fld.diffuse(ctx, g, solver(p, rtol=1e-14, max_cycles=1), case["dt"], dev(D), dev(case["E"]))
     assert info["status"] == 4 and info["cycles"] == 1
+
+# ----------------------------------------------------------------------------- tiled 3-D smoother
+
+def _gs_sweep(D, r, x, dt, dx, bc, first):
+    """One red-black Gauss-Seidel sweep of x + dt (-div D grad x) = r written from Sect. 3.4's
+    operator (harmonic-mean faces, homogeneous boundary faces), vectorised in FP64: each colour is
+    updated from the current values of the other.  Also returns, per cell, the magnitude M that
+    bounds an FP32 evaluation's error as a multiple of its unit roundoff: (|r| + sum |w x_nb| +
+    |x| (1 + sum |w|)) / |diag|, plus sum |w| M_nb / |diag| for the second colour, whose neighbours
+    carry the first colour's errors."""
+    codes = {"periodic": 0, "neumann": 1, "dirichlet": 2, "continuous": 3}
+    nz, ny, nx = D.shape
+    x = x.astype(np.float64).copy()
+    D = D.astype(np.float64)
+    M = np.zeros_like(x)
+    par = (np.arange(nx)[None, None, :] + np.arange(ny)[None, :, None] + np.arange(nz)[:, None, None]) & 1
+    for col in (first, 1 - first):
+        a = r.astype(np.float64).copy()
+        d = np.ones_like(a)
+        ma = np.abs(a)
+        wsum = np.ones_like(a)
+        mprop = np.zeros_like(a)
+        for ax_phys in range(3):
+            arr_ax = 2 - ax_phys
+            s = dt / dx[ax_phys] ** 2
+            n = D.shape[arr_ax]
+            idx = np.arange(n).reshape([-1 if q == arr_ax else 1 for q in range(3)])
+            for side in (0, 1):
+                shift = 1 if side == 0 else -1  # roll by +1 brings x[i-1] to position i
+                nb, Dn, mir = np.roll(x, shift, arr_ax), np.roll(D, shift, arr_ax), np.roll(x, -shift, arr_ax)
+                Mn, Mm = np.roll(M, shift, arr_ax), np.roll(M, -shift, arr_ax)
+                at_bnd = np.broadcast_to(idx == (0 if side == 0 else n - 1), D.shape)
+                kind = codes[bc[2 * ax_phys + side]]
+                w = s * 2 * D * Dn / (D + Dn)
+                pair = ~at_bnd if kind != 0 else np.ones_like(at_bnd)
+                a += np.where(pair, w * nb, 0.0)
+                d += np.where(pair, w, 0.0)
+                ma += np.where(pair, np.abs(w * nb), 0.0)
+                wsum += np.where(pair, w, 0.0)
+                mprop += np.where(pair, w * Mn, 0.0)
+                if kind == 2:
+                    d += np.where(at_bnd, s * D, 0.0)
+                    wsum += np.where(at_bnd, s * D, 0.0)
+                elif kind == 3:
+                    a -= np.where(at_bnd, s * D * mir, 0.0)
+                    d -= np.where(at_bnd, s * D, 0.0)
+                    ma += np.where(at_bnd, np.abs(s * D * mir), 0.0)
+                    wsum += np.where(at_bnd, s * D, 0.0)
+                    mprop += np.where(at_bnd, s * D * Mm, 0.0)
+        xn = a / d
+        Mc = (ma + np.abs(xn) * wsum + mprop) / np.abs(d)
+        x = np.where(par == col, xn, x)
+        M = np.where(par == col, Mc, M)
+    return x, M
+
+
+TILED_CASES = [((64, 16, 6), "periodic"), ((128, 32, 8), "mixed"), ((64, 48, 4), "dirichlet"),
+               ((192, 16, 10), "continuous"), ((64, 32, 8), "neumann")]
+
+
+@pytest.mark.parametrize("shape,bcname", TILED_CASES)
+@pytest.mark.parametrize("zero", [False, True])
+def test_tiled_sweep_matches_gauss_seidel(ctx, shape, bcname, zero):
+    """The finest-level smoother of the mixed solver on 3-D grids (one launch per sweep, tiles
+    staged in shared memory, face means formed on chip) is one red-black Gauss-Seidel sweep, for
+    both colour orders, with and without a starting iterate, on every boundary type."""
+    from paper_2104_03968_gb300 import fld
+    rng = np.random.default_rng(7 + len(bcname) + shape[2])
+    nx, ny, nz = shape
+    grid = {"ndim": 3, "n": list(shape), "dx": [1.0, 0.8, 1.3], "bc": BCS[bcname][0], "bc_val": [0.0] * 6}
+    D = 10 ** rng.uniform(-1, 1, (nz, ny, nx))
+    r = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    x0 = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    dt = 0.7
+    for first in (0, 1):
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+        fld.smooth_sweep(ctx, grid, dt, dev(D), torch.as_tensor(r, device="cuda"),
+                         None if zero else torch.as_tensor(x0, device="cuda"), out, first)
+        ref, M = _gs_sweep(D, r, np.zeros_like(x0) if zero else x0, dt, grid["dx"], grid["bc"], first)
+        got = out.cpu().numpy().astype(np.float64)
+        # FP32 inputs rounded once (dc), ~a dozen roundings per cell: 64 unit roundoffs of M
+        excess = np.abs(got - ref) / (64 * 2.0 ** -24 * M)
+        assert excess.max() <= 1.0, (first, excess.max(), relerr(got, ref))
+
+
+def test_tiled_sweep_rejects_unsupported_shapes(ctx):
+    from paper_2104_03968_gb300 import fld
+    grid = {"ndim": 3, "n": [48, 16, 8], "dx": [1.0] * 3, "bc": ["periodic"] * 6, "bc_val": [0.0] * 6}
+    z = torch.zeros((8, 16, 48), dtype=torch.float32, device="cuda")
+    with pytest.raises(fld.FldError) as e:
+        fld.smooth_sweep(ctx, grid, 1.0, torch.ones((8, 16, 48), dtype=torch.float64, device="cuda"), z, None,
+                         torch.empty_like(z))
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("shape,bcname", TILED_CASES)
+def test_tiled_solve_parity(monkeypatch, shape, bcname):
+    """Diffusion solves whose finest level uses the tiled sweep (forced onto these small grids)
+    meet the oracle's operator: its relative residual of the GPU result is at the solver's
+    tolerance, and where the operator is symmetric (no extrapolated boundary) the result equals
+    the oracle's CG solution."""
+    from paper_2104_03968_gb300 import fld
+    monkeypatch.setenv("FLD_SWEEP3D_MIN_CELLS", "0")
+    c = fld.Context(0)
+    try:
+        case = inputs.random_small(shape, seed=200 + shape[2], bc=BCS[bcname], dt_factor=100.0)
+        g, p = case["grid"], case["phys"]
+        kap = oracle.opacity(p, case["rho"], case["eps"])
+        D = oracle.coeffs(g, p, case["E"], case["rho"], kap)
+        out, info = fld.diffuse(c, g, solver(p, precision="mixed", rtol=1e-13), case["dt"], dev(D), dev(case["E"]))
+        assert info["status"] == 0
+        x = host(out).reshape(case["E"].shape)
+        assert oracle.relres(g, case["dt"], D, case["E"], x) < 2e-13
+        if bcname != "continuous":
+            ref = oracle.diffuse(g, case["dt"], D, case["E"], rtol=1e-14)
+            assert relerr(x, ref) < TOL
+    finally:
+        c.close()
