@@ -110,6 +110,22 @@ def host_cpu():
             else os.cpu_count()}
 
 
+def load_traffic(n: int, precision: str) -> dict:
+    """DRAM bytes per launch of each traced scope at n^3, from single-kernel ncu captures of a
+    smaller grid (profiles/traffic.json) scaled by the cells a launch processes.  A scope whose
+    kernel changed since its capture is absent there, so its traffic is reported as null."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    if t.get("precision") != precision:
+        return {}
+    scale = (n / t["captured_n"]) ** 3
+    return {k: v["dram_bytes_per_launch"] * scale for k, v in t.get("scopes", {}).items()}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -379,13 +395,7 @@ def main():
     barrier(world)
     ms, value = replica_throughput(world, ncell, args.steps, ms)
     launches = (n_after - n_before) * world
-    traffic = {}
-    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tdata = json.load(f)
-        if tdata.get("workload_n") == args.n and tdata.get("precision") == args.precision:
-            traffic = tdata.get("bytes_per_launch", {})
+    traffic = load_traffic(args.n, args.precision)
     peaks = load_peaks()
     roof = roofline(rep, ncell, args.precision, peaks, traffic)
     roof_hbm = roofline(rep, ncell, args.precision, peaks, traffic, bound="hbm")

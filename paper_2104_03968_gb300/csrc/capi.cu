@@ -413,6 +413,8 @@ fld_status fld_smooth_sweep(fld_ctx* ctx, const fld_grid* grid, double dt, const
   if (st != FLD_OK) return st;
   if (!D_cell || !r || !x_out) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell, r and x_out must be non-NULL");
   if (x_in == x_out) return fail(ctx, FLD_ERR_INVALID_ARG, "x_out must not be x_in");
+  if (((uintptr_t)r | (uintptr_t)x_in | (uintptr_t)x_out) & 15u)
+    return fail(ctx, FLD_ERR_INVALID_ARG, "r, x_in and x_out must start on 16-byte boundaries");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be positive and finite");
   if (first_colour != 0 && first_colour != 1) return fail(ctx, FLD_ERR_INVALID_ARG, "first_colour must be 0 or 1");
   if (grid->ndim != 3 || !sweep3d_eligible(grid->n[0], grid->n[1], grid->n[2]))

@@ -147,8 +147,8 @@ class Multigrid {
   bool rows_ok(int l) const;
   template <class T>
   cudaError_t wave_sweep(int l, bool zero, int c0, double* x64, cudaStream_t s);
-  // Tiled sweep of the mixed solver's finest 3-D level (sweep3d.cu): each cell's dt D / dx_0^2 in
-  // FP32, and whether this solve uses it (scalar D, eligible shape).  The sweep reads the iterate
+  // Tiled sweep of the mixed solver's finest 3-D level (sweep3d.cu): each cell's 1 / (dt D / dx_0^2)
+  // in FP32, and whether this solve uses it (scalar D, eligible shape).  The sweep reads the iterate
   // from lv_[0].x and writes lv_[0].tmp, then the two are swapped.
   float* dc32_ = nullptr;
   bool tiled_ = false;

@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(256, 8) k_faces_df(GridDev g, DfConst K, const
         split_f64_scaled(Dc, sh, c.hi, c.lo, ok);
         if (!ok) bad = 1u;
       }
-      // the cell's own dt D / dx_0^2 in FP32, for the smoother that forms its face means on chip
-      if (dc) dc[idx] = scale2(c.hi * K.s_hi[0], sh);
+      // the reciprocal of the cell's dt D / dx_0^2 in FP32, for the smoother that forms its face
+      // means on chip (inf where the product leaves the FP32 range downwards)
+      if (dc) dc[idx] = __frcp_rn(scale2(c.hi * K.s_hi[0], sh));
       // x faces: lower face i of row (j, k), and face nx when this cell owns it
       {
         const dfl s{K.s_hi[0], K.s_lo[0]};

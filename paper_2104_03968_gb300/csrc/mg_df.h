@@ -19,7 +19,7 @@ struct DfConst {
 DfConst make_df_const(const GridDev& g, double dt);
 
 // face weights w = dt D_f / dx^2 (harmonic-mean faces) as hi + lo floats, and (dc not null) each
-// cell's dt D / dx_0^2 in FP32; *flag |= 1 where a value left the double-float window
+// cell's 1 / (dt D / dx_0^2) in FP32; *flag |= 1 where a value left the double-float window
 cudaError_t launch_faces_df(const GridDev& g, const DfConst& K, const double* D, float* const w[3],
                             float* const wlo[3], float* dc, unsigned* flag, cudaStream_t s);
 

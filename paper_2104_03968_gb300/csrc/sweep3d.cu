@@ -2,20 +2,24 @@
 // discdiff, dt-scaled: (A x)_c = x_c + sum_faces w_f (x_c - x_nb)) on the FP32 finest level of a
 // 3-D grid, both colours in one pass over HBM.
 //
-// The face weights are not read from memory: the kernel stages the cell-centred coefficient
-// dc = dt D / dx_0^2 and forms each face's harmonic mean 2 dc_a dc_b / (dc_a + dc_b) (Sect. 3.4)
-// on chip, so a sweep moves r, dc and x in and x out (16 bytes per cell) instead of r, three face
-// arrays and x (24).
+// The face weights are not read from memory: the kernel stages each cell's reciprocal
+// coefficient ic = 1 / (dt D / dx_0^2) and forms the harmonic-mean weight of a face (Sect. 3.4) on
+// chip as w = 2 ra / (ic_a + ic_b), one reciprocal per face, so a sweep moves r, ic and x in and x
+// out (16 bytes per cell) instead of r, three face arrays and x (24).  A cell with D = 0 has
+// ic = inf and its faces weigh 0.
 //
 // Blocking: a block owns a 64 x 16 tile of the x-y plane and a run of z-planes (a z-chunk), and
 // marches through them.  At step s it updates the first colour on plane s (on the tile and one
 // cell around it) and the second colour on plane s - 1 (on the tile), so that every value the
-// second colour reads is final.  Planes of x and dc with a two-cell halo, and of r with a one-cell
-// halo, stay in a ring of shared-memory slots; cp.async fetches the planes of step s + 1 while
-// step s computes.  The cells around the tile are computed again by the neighbouring blocks from
-// the same inputs, so the sweep reads x from one array and writes another: no block waits for
-// another.  Periodic faces read the wrapped halo; Dirichlet, Neumann and linear-extrapolation
-// faces take the interior cell's coefficient, as in the FP64 operator.
+// second colour reads is final.  Planes of x and ic with a two-cell halo, and of r with a one-cell
+// halo, stay in a ring of shared-memory slots; 16-byte asynchronous copies (cp.async), two per
+// thread per staged plane, fetch the planes of the next two steps while step s computes.  The
+// cells around the tile are computed again by the neighbouring blocks from the same inputs, so the
+// sweep reads x from one array and writes another: no block waits for another.  Periodic faces
+// read the wrapped halo; Dirichlet, Neumann and linear-extrapolation faces take the interior cell's
+// coefficient, as in the FP64 operator.  Everything a thread needs for its cells (staged offsets,
+// its chunks to copy, its ring cells) is worked out once per tile, so the loop over planes spends
+// its instructions on the cells.
 #include <algorithm>
 
 #include "fld_common.cuh"
@@ -26,17 +30,18 @@ namespace fld {
 namespace {
 
 constexpr int TX = 64, TY = 16;        // tile of a plane
-constexpr int P = TX + 8;              // row pitch in shared memory: 4 cells each side (16-byte chunks)
-constexpr int RXR = TY + 4;            // rows of a staged x or dc plane (2 halo rows each side)
+constexpr int P = TX + 8;              // row pitch in shared memory: 4 cells each side (16-byte aligned)
+constexpr int RXR = TY + 4;            // rows of a staged x or ic plane (2 halo rows each side)
 constexpr int RRR = TY + 2;            // rows of a staged r plane (1 halo row each side)
 constexpr int CH = P / 4;              // 16-byte chunks per staged row
-constexpr int NXS = 5, NRS = 3;        // ring slots: x and dc planes s-2 .. s+2, r planes s-1 .. s+1
+constexpr int NXS = 6, NRS = 4;        // ring slots: x and ic planes s-2 .. s+3, r planes s-1 .. s+2
 constexpr int XPL = RXR * P, RPL = RRR * P;
 constexpr int kThreads = 256;
-constexpr int kXChunks = RXR * CH, kRChunks = RRR * CH;  // 360, 324: two per thread each
+constexpr int kXChunks = RXR * CH, kRChunks = RRR * CH;  // 360, 324: at most two per thread each
+constexpr int kRingHalf = TX + 2 + TY;  // 82 ring cells of each parity around the tile
 constexpr size_t kSmemBytes = (size_t)(2 * NXS * XPL + NRS * RPL) * sizeof(float);
-static_assert(kXChunks <= 2 * kThreads && kRChunks <= 2 * kThreads, "two chunks per thread");
 static_assert(P % 32 == 8, "the two-row lane mapping is conflict-free for a pitch of 8 mod 32");
+static_assert(kRingHalf <= kThreads && kXChunks <= 2 * kThreads && kRChunks <= 2 * kThreads, "thread shares");
 
 __device__ __forceinline__ void cp16(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -44,54 +49,59 @@ __device__ __forceinline__ void cp16(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// all but the most recent group complete
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// 2 a b / (a + b), 0 where both vanish
-__device__ __forceinline__ float hmean(float a, float b) {
-  const float s = a + b;
-  return s > 0.0f ? 2.0f * a * __fdividef(b, s) : 0.0f;
+// one hardware reciprocal (rcp.approx, about 1 ulp; 0 for inf): the smoother's arithmetic is FP32
+__device__ __forceinline__ float rcp_fast(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// One face of a cell next to a non-periodic boundary or away from it: the interior and periodic
-// faces pair the cell with the one across (xa, coefficient da); a Dirichlet face adds the cell's
+// Staged planes around the cell's plane: x and ic of the plane, below and above; r of the plane.
+struct Planes {
+  const float* x;
+  const float* c;
+  const float* xm;
+  const float* cm;
+  const float* xp;
+  const float* cp;
+  const float* r;  // indexed like x minus one row
+};
+
+// One face of a cell that may lie on a non-periodic face: interior and periodic faces pair the
+// cell with the one across (x xa, reciprocal coefficient ia); a Dirichlet face adds the cell's
 // own weight to the diagonal only; a Neumann face adds nothing; a linear-extrapolation face
 // (ghost 2 x_c - x_m) subtracts w x_m from the sum and w from the diagonal.
-__device__ __forceinline__ void face_b(bool inside, int bc, float dcen, float da, float xa, float xm, float ra,
+__device__ __forceinline__ void face_b(bool inside, int bc, float ic, float ia, float xa, float xm, float ra,
                                        float& a, float& d) {
   if (inside || bc == FLD_BC_PERIODIC) {
-    const float w = hmean(dcen, da) * ra;
+    const float w = 2.0f * ra * rcp_fast(ic + ia);
     a = fmaf(w, xa, a);
     d += w;
   } else if (bc == FLD_BC_DIRICHLET) {
-    d += dcen * ra;
+    d += ra * rcp_fast(ic);
   } else if (bc == FLD_BC_CONTINUOUS) {
-    const float w = dcen * ra;
+    const float w = ra * rcp_fast(ic);
     a = fmaf(-w, xm, a);
     d -= w;
   }
 }
 
-struct Planes {
-  const float* x;  // slot of the cell's plane
-  const float* d;
-  const float* xm; // slots of the planes below and above
-  const float* dm;
-  const float* xp;
-  const float* dp;
-  const float* r;  // r slot, indexed like x minus one row
-};
-
-// New value of the cell at staged offset o (row jj, column ii of the slot), global (i, j, k).
-// NOX: x is zero everywhere (the first colour of a sweep from zero).  BND: the cell may lie on a
-// non-periodic face, so the face kinds are checked; i, j must then be wrapped on periodic axes.
+// New value of the cell at staged offset o with right-hand side rv.  NOX: x is zero everywhere
+// (the first colour of a sweep from zero).  BND: the cell may lie on a non-periodic face, so the
+// face kinds are checked at its global (i, j, k) (wrapped on periodic axes); tr = 2 ra.
 template <bool NOX, bool BND>
-__device__ __forceinline__ float update(const Sweep3dArgs& A, const Planes& S, int o, int i, int j, int k) {
-  const float dcen = S.d[o];
-  float a = S.r[o - P];
+__device__ __forceinline__ float update(const Sweep3dArgs& A, const float tr[3], const Planes& S, int o, float rv,
+                                        int i, int j, int k) {
+  const float ic = S.c[o];
+  float a = rv;
   float d = 1.0f;
   if (!BND) {
-    const float w0 = hmean(dcen, S.d[o - 1]) * A.ra[0], w1 = hmean(dcen, S.d[o + 1]) * A.ra[0];
-    const float w2 = hmean(dcen, S.d[o - P]) * A.ra[1], w3 = hmean(dcen, S.d[o + P]) * A.ra[1];
-    const float w4 = hmean(dcen, S.dm[o]) * A.ra[2], w5 = hmean(dcen, S.dp[o]) * A.ra[2];
+    const float w0 = tr[0] * rcp_fast(ic + S.c[o - 1]), w1 = tr[0] * rcp_fast(ic + S.c[o + 1]);
+    const float w2 = tr[1] * rcp_fast(ic + S.c[o - P]), w3 = tr[1] * rcp_fast(ic + S.c[o + P]);
+    const float w4 = tr[2] * rcp_fast(ic + S.cm[o]), w5 = tr[2] * rcp_fast(ic + S.cp[o]);
     d += ((w0 + w1) + (w2 + w3)) + (w4 + w5);
     if (!NOX) {
       a = fmaf(w0, S.x[o - 1], a);
@@ -103,14 +113,14 @@ __device__ __forceinline__ float update(const Sweep3dArgs& A, const Planes& S, i
     }
   } else {
     const float z = 0.0f;
-    face_b(i > 0, A.bc[0], dcen, S.d[o - 1], NOX ? z : S.x[o - 1], NOX ? z : S.x[o + 1], A.ra[0], a, d);
-    face_b(i < A.nx - 1, A.bc[1], dcen, S.d[o + 1], NOX ? z : S.x[o + 1], NOX ? z : S.x[o - 1], A.ra[0], a, d);
-    face_b(j > 0, A.bc[2], dcen, S.d[o - P], NOX ? z : S.x[o - P], NOX ? z : S.x[o + P], A.ra[1], a, d);
-    face_b(j < A.ny - 1, A.bc[3], dcen, S.d[o + P], NOX ? z : S.x[o + P], NOX ? z : S.x[o - P], A.ra[1], a, d);
-    face_b(k > 0, A.bc[4], dcen, S.dm[o], NOX ? z : S.xm[o], NOX ? z : S.xp[o], A.ra[2], a, d);
-    face_b(k < A.nz - 1, A.bc[5], dcen, S.dp[o], NOX ? z : S.xp[o], NOX ? z : S.xm[o], A.ra[2], a, d);
+    face_b(i > 0, A.bc[0], ic, S.c[o - 1], NOX ? z : S.x[o - 1], NOX ? z : S.x[o + 1], A.ra[0], a, d);
+    face_b(i < A.nx - 1, A.bc[1], ic, S.c[o + 1], NOX ? z : S.x[o + 1], NOX ? z : S.x[o - 1], A.ra[0], a, d);
+    face_b(j > 0, A.bc[2], ic, S.c[o - P], NOX ? z : S.x[o - P], NOX ? z : S.x[o + P], A.ra[1], a, d);
+    face_b(j < A.ny - 1, A.bc[3], ic, S.c[o + P], NOX ? z : S.x[o + P], NOX ? z : S.x[o - P], A.ra[1], a, d);
+    face_b(k > 0, A.bc[4], ic, S.cm[o], NOX ? z : S.xm[o], NOX ? z : S.xp[o], A.ra[2], a, d);
+    face_b(k < A.nz - 1, A.bc[5], ic, S.cp[o], NOX ? z : S.xp[o], NOX ? z : S.xm[o], A.ra[2], a, d);
   }
-  return __fdividef(a, d);
+  return a * rcp_fast(d);
 }
 
 __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
@@ -118,55 +128,94 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
   return v < 0 ? 0 : (v >= n ? n - 1 : v);
 }
 
-// Cells of one colour on the tile of one plane, and (RING) on the ring of cells around it.  A warp
-// takes two rows of 32 cells, lanes 0-15 the colour's 16 cells of the first row and lanes 16-31
-// those of the second: with the pitch at 8 mod 32 the two halves fall on disjoint banks.
-template <bool NOX, bool RING>
-__device__ __forceinline__ void colour_pass(const Sweep3dArgs& A, const Planes& S, float* xs, int col, int i0, int j0,
-                                            int k, bool bnd) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kw = k < 0 ? k + A.nz : (k >= A.nz ? k - A.nz : k);
+// A thread's share of a tile.
+//  - Two tile tasks: task u of warp w takes rows 2 ((w + 8u) / 2) and 2 ((w + 8u) / 2) + 1, half
+//    (w + 8u) % 2 of each, lanes 0-15 the colour's 16 cells of the first row and lanes 16-31 those
+//    of the second (with the pitch at 8 mod 32 the two halves fall on disjoint banks).  The
+//    colour's cells of a row alternate parity with the plane: o0[u] is the staged offset for parity
+//    0 (column 2m), o0[u] + 1 for parity 1.
+//  - Threads 0..81 each own one ring cell of either parity class (iu + ju even or odd; 82 each:
+//    33 in the row below the tile, 33 above, 8 in each side column), so a colour pass on the ring
+//    occupies the first three warps only.
+//  - Each thread copies up to two 16-byte chunks of a staged x and ic plane and of an r plane:
+//    xg / rg are their in-plane source offsets (-1: none), xo / ro their offsets in a slot.  A chunk
+//    beyond a periodic face wraps; beyond a non-periodic one it is clamped into the grid (the
+//    boundary faces do not read it).
+struct Share {
+  int o0[2], row[2];
+  int ring_o[2], ring_i[2], ring_j[2];  // per parity class: staged offset, wrapped global (i, j)
+  int xg[2], xo[2], rg[2], ro[2];
+};
+
+__device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A, bool xper, bool yper) {
+  Share sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    const int task = warp + 8 * u;                  // 16 tasks: 8 row pairs x 2 halves of 32 cells
-    const int row = 2 * (task >> 1) + (lane >> 4);  // 0 .. 15
-    const int m = 16 * (task & 1) + (lane & 15);    // colour cell within the row, 0 .. 31
-    const int j = j0 + row;
-    const int q = (col + j + kw) & 1;
-    const int ii = 4 + 2 * m + q;
-    const int o = (2 + row) * P + ii;
-    const float v = bnd ? update<NOX, true>(A, S, o, i0 + ii - 4, j, kw) : update<NOX, false>(A, S, o, 0, 0, 0);
-    xs[o] = v;
+    const int task = warp + 8 * u;
+    sh.row[u] = 2 * (task >> 1) + (lane >> 4);        // 0 .. 15
+    const int m = 16 * (task & 1) + (lane & 15);      // colour cell within the row, 0 .. 31
+    sh.o0[u] = (2 + sh.row[u]) * P + 4 + 2 * m;
   }
-  if (RING) {
-    // 164 cells around the tile: rows j0-1 and j0+16 (66 cells each), columns i0-1 and i0+64
-    const int t = threadIdx.x;
-    if (t < 164) {
-      int ii, jj;
-      if (t < 66) ii = 3 + t, jj = 1;
-      else if (t < 132) ii = 3 + (t - 66), jj = RXR - 2;
-      else if (t < 148) ii = 3, jj = 2 + (t - 132);
-      else ii = P - 4, jj = 2 + (t - 148);
-      const int i = wrap_or_clamp(i0 + ii - 4, A.nx, A.bc[0] == FLD_BC_PERIODIC);
-      const int j = wrap_or_clamp(j0 + jj - 2, A.ny, A.bc[2] == FLD_BC_PERIODIC);
-      const int iu = i0 + ii - 4, ju = j0 + jj - 2;  // unwrapped: the parity of the staged position
-      if (((iu + ju + kw) & 1) == col) {
-        const int o = jj * P + ii;
-        // a ring cell outside a non-periodic face is a ghost position: computed, never read
-        const float v = bnd ? update<NOX, true>(A, S, o, i, j, kw) : update<NOX, false>(A, S, o, 0, 0, 0);
-        xs[o] = v;
-      }
-    }
+  // ring: with i0 and j0 even, the staged position (ii, jj) has parity (iu + ju) & 1 = (ii + jj) & 1
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int q = min(t, kRingHalf - 1);
+    int ii, jj;
+    if (q < TX / 2 + 1) ii = 3 + c + 2 * q, jj = 1;                             // row j0 - 1
+    else if (q < TX + 2) ii = 4 - c + 2 * (q - (TX / 2 + 1)), jj = RXR - 2;      // row j0 + 16
+    else if (q < TX + 2 + TY / 2) ii = 3, jj = 3 - c + 2 * (q - (TX + 2));       // column i0 - 1
+    else ii = P - 4, jj = 2 + c + 2 * (q - (TX + 2 + TY / 2));                   // column i0 + 64
+    sh.ring_o[c] = jj * P + ii;
+    sh.ring_i[c] = wrap_or_clamp(i0 + ii - 4, A.nx, xper);
+    sh.ring_j[c] = wrap_or_clamp(j0 + jj - 2, A.ny, yper);
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int tt = t + c * kThreads;
+    auto chunk = [&](int q, int jlo, int& g, int& o) {
+      const int jj = q / CH, cc = q % CH;
+      const int j = wrap_or_clamp(j0 + jlo + jj, A.ny, yper);
+      int i = i0 - 4 + 4 * cc;
+      i = xper ? (i < 0 ? i + A.nx : (i >= A.nx ? i - A.nx : i)) : min(max(i, 0), A.nx - 4);
+      g = j * A.nx + i;
+      o = jj * P + 4 * cc;
+    };
+    if (tt < kXChunks) chunk(tt, -2, sh.xg[c], sh.xo[c]);
+    else sh.xg[c] = -1, sh.xo[c] = 0;
+    if (tt < kRChunks) chunk(tt, -1, sh.rg[c], sh.ro[c]);
+    else sh.rg[c] = -1, sh.ro[c] = 0;
+  }
+  return sh;
+}
+
+// The cells of colour col on the tile of plane k (wrapped kw), and with RING on the ring around it
+// (a ring cell outside a non-periodic face is a ghost position: computed, never read).
+template <bool NOX, bool RING, bool BND>
+__device__ __forceinline__ void colour_pass(const Sweep3dArgs& A, const float tr[3], const Planes& S, float* xs,
+                                            const Share& sh, int col, int i0, int j0, int kw) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int j = j0 + sh.row[u];
+    const int o = sh.o0[u] + ((col + j + kw) & 1);
+    const float rv = S.r[o - P];
+    xs[o] = update<NOX, BND>(A, tr, S, o, rv, i0 + (o - (2 + sh.row[u]) * P) - 4, j, kw);
+  }
+  if (RING && threadIdx.x < kRingHalf) {
+    const bool c = ((col + kw) & 1) != 0;  // the class whose cells have this colour on plane kw
+    const int o = c ? sh.ring_o[1] : sh.ring_o[0];
+    xs[o] = update<NOX, BND>(A, tr, S, o, S.r[o - P], c ? sh.ring_i[1] : sh.ring_i[0],
+                             c ? sh.ring_j[1] : sh.ring_j[0], kw);
   }
 }
 
 template <bool ZERO, bool UPDATE>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep3d(Sweep3dArgs A, int lz, int tiles_x, int tiles_y,
+__global__ void __launch_bounds__(kThreads, 2) k_sweep3d(Sweep3dArgs A, int lz, int tiles_x, int tiles_y,
                                                          int nzchunk) {
   extern __shared__ __align__(16) float sm[];
   float* Xs = sm;
-  float* Ds = sm + NXS * XPL;
-  float* Rs = Ds + NXS * XPL;
+  float* Cs = sm + NXS * XPL;
+  float* Rs = Cs + NXS * XPL;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
   const size_t plane = (size_t)nx * ny;
   const bool xper = A.bc[0] == FLD_BC_PERIODIC, yper = A.bc[2] == FLD_BC_PERIODIC;
@@ -175,6 +224,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep3d(Sweep3dArgs A, int lz, 
   const int items = ntile * nzchunk;
   const int tid = threadIdx.x;
   const int c1 = A.c0 ^ 1;
+  const float tr[3] = {2.0f * A.ra[0], 2.0f * A.ra[1], 2.0f * A.ra[2]};
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     // consecutive items are neighbouring tiles of one z-chunk, so the blocks running together
     // share their halos through L2
@@ -182,70 +232,33 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep3d(Sweep3dArgs A, int lz, 
     const int i0 = (tile % tiles_x) * TX, j0 = (tile / tiles_x) * TY;
     const int k0 = zc * lz, k1 = min(nz, k0 + lz);
     const bool tile_bnd = (!xper && (i0 == 0 || i0 + TX == nx)) || (!yper && (j0 == 0 || j0 + TY == ny));
-    // per-thread 16-byte chunks of a staged plane: in-plane global offset and slot offset
-    int xg[2], xo[2], rg[2], ro[2];
-    bool xok[2], rok[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int t = tid + c * kThreads;
-      xok[c] = t < kXChunks;
-      rok[c] = t < kRChunks;
-      const int tx = xok[c] ? t : 0, tr = rok[c] ? t : 0;
-      {
-        const int jj = tx / CH, cc = tx % CH;
-        const int j = wrap_or_clamp(j0 - 2 + jj, ny, yper);
-        int i = i0 - 4 + 4 * cc;
-        i = xper ? (i < 0 ? i + nx : (i >= nx ? i - nx : i)) : min(max(i, 0), nx - 4);
-        xg[c] = j * nx + i;
-        xo[c] = jj * P + 4 * cc;
-      }
-      {
-        const int jj = tr / CH, cc = tr % CH;
-        const int j = wrap_or_clamp(j0 - 1 + jj, ny, yper);
-        int i = i0 - 4 + 4 * cc;
-        i = xper ? (i < 0 ? i + nx : (i >= nx ? i - nx : i)) : min(max(i, 0), nx - 4);
-        rg[c] = j * nx + i;
-        ro[c] = jj * P + 4 * cc;
-      }
-    }
+    const Share sh = make_share(i0, j0, A, xper, yper);
     auto valid = [&](int k) { return zper || (k >= 0 && k < nz); };
     auto wrapk = [&](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
-    auto xslot = [&](int k) { return (k - k0 + 2) % NXS; };
-    auto rslot = [&](int k) { return (k - k0 + 1) % NRS; };
-    auto load_xd = [&](int k) {
+    auto load_xc = [&](int k, int slot) {
       if (!valid(k)) return;
       const size_t pb = (size_t)wrapk(k) * plane;
-      const int s = xslot(k) * XPL;
+      float* xs = Xs + slot * XPL;
+      float* cs = Cs + slot * XPL;
 #pragma unroll
       for (int c = 0; c < 2; ++c)
-        if (xok[c]) {
-          if (!ZERO) cp16(Xs + s + xo[c], A.xin + pb + xg[c]);
-          cp16(Ds + s + xo[c], A.dc + pb + xg[c]);
+        if (sh.xg[c] >= 0) {
+          if (!ZERO) cp16(xs + sh.xo[c], A.xin + pb + sh.xg[c]);
+          cp16(cs + sh.xo[c], A.dc + pb + sh.xg[c]);
         }
     };
-    auto load_r = [&](int k) {
+    auto load_r = [&](int k, int slot) {
       if (!valid(k)) return;
       const size_t pb = (size_t)wrapk(k) * plane;
-      const int s = rslot(k) * RPL;
+      float* rs = Rs + slot * RPL;
 #pragma unroll
       for (int c = 0; c < 2; ++c)
-        if (rok[c]) cp16(Rs + s + ro[c], A.r + pb + rg[c]);
+        if (sh.rg[c] >= 0) cp16(rs + sh.ro[c], A.r + pb + sh.rg[c]);
     };
-    auto planes = [&](int k) {
-      Planes S;
-      S.x = Xs + xslot(k) * XPL;
-      S.d = Ds + xslot(k) * XPL;
-      S.xm = Xs + xslot(k - 1) * XPL;
-      S.dm = Ds + xslot(k - 1) * XPL;
-      S.xp = Xs + xslot(k + 1) * XPL;
-      S.dp = Ds + xslot(k + 1) * XPL;
-      S.r = Rs + rslot(k) * RPL;
-      return S;
-    };
-    auto store = [&](int k) {
+    auto store = [&](int k, int slot) {
       // the tile of plane k, both colours final: one float4 per thread
       const int row = tid >> 4, q4 = tid & 15;
-      const float4 v = *reinterpret_cast<const float4*>(Xs + xslot(k) * XPL + (2 + row) * P + 4 + 4 * q4);
+      const float4 v = *reinterpret_cast<const float4*>(Xs + slot * XPL + (2 + row) * P + 4 + 4 * q4);
       const size_t g = (size_t)wrapk(k) * plane + (size_t)(j0 + row) * nx + i0 + 4 * q4;
       *reinterpret_cast<float4*>(A.xout + g) = v;
       if (UPDATE) {
@@ -259,42 +272,66 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep3d(Sweep3dArgs A, int lz, 
         p[1] = b;
       }
     };
-    __syncthreads();  // the previous item's last reads of the slots are done
-    load_xd(k0 - 2);
-    load_xd(k0 - 1);
-    load_xd(k0);
-    load_r(k0 - 1);
-    cp_commit();
+    // slots: plane k0 - 2 + q of x and ic in slot q % NXS, plane k0 - 1 + q of r in slot q % NRS
     cp_wait_all();
+    __syncthreads();  // the previous item's last reads of the slots are done
+    load_xc(k0 - 2, 0);
+    load_xc(k0 - 1, 1);
+    load_xc(k0, 2);
+    load_r(k0 - 1, 0);
+    cp_commit();
+    // the planes of step k0 (in flight while step k0 - 1 computes)
+    load_xc(k0 + 1, 3);
+    load_r(k0, 1);
+    cp_commit();
+    cp_wait_prev();
     __syncthreads();
+    auto wrap_slot = [](int v, int n) { return v >= n ? v - n : (v < 0 ? v + n : v); };
+    int xs0 = 1, rs0 = 0;  // slots of plane s
     for (int s = k0 - 1; s <= k1; ++s) {
-      if (s + 2 <= k1 + 1) load_xd(s + 2);
-      if (s + 1 <= k1) load_r(s + 1);
+      const int xm2 = wrap_slot(xs0 - 2, NXS), xm1 = wrap_slot(xs0 - 1, NXS), xp1 = wrap_slot(xs0 + 1, NXS);
+      const int xp3 = wrap_slot(xs0 + 3, NXS);
+      const int rm1 = wrap_slot(rs0 - 1, NRS), rp2 = wrap_slot(rs0 + 2, NRS);
+      // the planes of step s + 2; those of step s + 1 are still in flight
+      if (s + 3 <= k1 + 1) load_xc(s + 3, xp3);
+      if (s + 2 <= k1) load_r(s + 2, rp2);
       cp_commit();
       // first colour on plane s, tile and ring (in place: it reads only second-colour cells)
       if (valid(s)) {
-        const Planes S = planes(s);
-        const bool bnd = tile_bnd || (!zper && (s == 0 || s == nz - 1));
-        colour_pass<ZERO, true>(A, S, Xs + xslot(s) * XPL, A.c0, i0, j0, s, bnd);
+        const Planes S{Xs + xs0 * XPL, Cs + xs0 * XPL, Xs + xm1 * XPL, Cs + xm1 * XPL,
+                       Xs + xp1 * XPL, Cs + xp1 * XPL, Rs + rs0 * RPL};
+        const int kw = wrapk(s);
+        if (tile_bnd || (!zper && (s == 0 || s == nz - 1)))
+          colour_pass<ZERO, true, true>(A, tr, S, Xs + xs0 * XPL, sh, A.c0, i0, j0, kw);
+        else
+          colour_pass<ZERO, true, false>(A, tr, S, Xs + xs0 * XPL, sh, A.c0, i0, j0, kw);
       }
-      if (s - 2 >= k0) store(s - 2);
+      if (s - 2 >= k0) store(s - 2, xm2);
       __syncthreads();
       // second colour on plane s - 1 (tile): its neighbours of the first colour are final
       if (s - 1 >= k0 && s - 1 < k1) {
-        const Planes S = planes(s - 1);
-        const bool bnd = tile_bnd || (!zper && (s - 1 == 0 || s - 1 == nz - 1));
-        colour_pass<false, false>(A, S, Xs + xslot(s - 1) * XPL, c1, i0, j0, s - 1, bnd);
+        const Planes S{Xs + xm1 * XPL, Cs + xm1 * XPL, Xs + xm2 * XPL, Cs + xm2 * XPL,
+                       Xs + xs0 * XPL, Cs + xs0 * XPL, Rs + rm1 * RPL};
+        const int kw = wrapk(s - 1);
+        if (tile_bnd || (!zper && (s - 1 == 0 || s - 1 == nz - 1)))
+          colour_pass<false, false, true>(A, tr, S, Xs + xm1 * XPL, sh, c1, i0, j0, kw);
+        else
+          colour_pass<false, false, false>(A, tr, S, Xs + xm1 * XPL, sh, c1, i0, j0, kw);
       }
-      cp_wait_all();
+      cp_wait_prev();  // the planes of step s + 1 have landed
       __syncthreads();
+      xs0 = xp1;
+      rs0 = wrap_slot(rs0 + 1, NRS);
     }
-    store(k1 - 1);
+    // the loop ended with xs0 = slot of plane k1 + 1
+    store(k1 - 1, wrap_slot(xs0 - 2, NXS));
   }
 }
 
-__global__ void k_dcell32(long long n, double scale, const double* __restrict__ D, float* __restrict__ dc) {
+// ic = 1 / (float)(scale D): the reciprocal coefficient the tiled sweep stages
+__global__ void k_dcell32(long long n, double scale, const double* __restrict__ D, float* __restrict__ ic) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dc[i] = (float)(scale * D[i]);
+  if (i < n) ic[i] = __frcp_rn((float)(scale * D[i]));
 }
 
 int g_blocks_per_sm = 0, g_sms = 0;
@@ -329,7 +366,7 @@ cudaError_t launch_sweep3d(const Sweep3dArgs& a, cudaStream_t s) {
   // (lz / (lz + 2)) and load balance over the resident blocks
   int lz = a.nz;
   double best = -1.0;
-  for (int c : {8, 16, 32, 64, 128, 256, 512}) {
+  for (int c : {4, 8, 16, 32, 64, 128, 256, 512}) {
     const int L = std::min(c, a.nz);
     const int nzc = (a.nz + L - 1) / L;
     const long long items = (long long)ntile * nzc;

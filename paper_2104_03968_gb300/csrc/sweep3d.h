@@ -10,7 +10,7 @@ struct Sweep3dArgs {
   int nx, ny, nz;
   int bc[6];
   float ra[3];          // dx_0^2 / dx_a^2: axis a's faces weigh harmonic(dc) * ra[a]
-  const float* dc;      // per cell, dt D_cell / dx_0^2 (FP32)
+  const float* dc;      // per cell, 1 / (dt D_cell / dx_0^2) (FP32; inf where D = 0)
   const float* r;       // right-hand side of the correction equation
   const float* xin;     // iterate before the sweep; nullptr: the sweep starts from x = 0
   float* xout;          // iterate after the sweep (a different array from xin)
@@ -22,10 +22,11 @@ struct Sweep3dArgs {
 // and >= 4, fewer than 2^31 cells.
 bool sweep3d_eligible(int nx, int ny, int nz);
 
-// One full sweep (both colours).  Asynchronous on s.
+// One full sweep (both colours).  Asynchronous on s.  Every array must start on a 16-byte boundary
+// (the planes are fetched in 16-byte copies).
 cudaError_t launch_sweep3d(const Sweep3dArgs& a, cudaStream_t s);
 
-// dc = (float)(dt D_cell / dx_0^2) per cell, from the FP64 D (the solver's FP64 set-up path).
+// dc = 1 / (float)(dt D_cell / dx_0^2) per cell, from the FP64 D (the solver's FP64 set-up path).
 cudaError_t launch_dcell32(long long ncell, double scale, const double* D, float* dc, cudaStream_t s);
 
 }  // namespace fld
