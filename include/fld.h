@@ -23,12 +23,20 @@
  *   - Arrays are caller-owned DEVICE memory, float64, contiguous, x fastest: cell (i,j,k)
  *     is element i + n[0]*(j + n[1]*k).  Column arrays are [column][cell].
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work
- *     is enqueued on it.  Calls that solve to a tolerance (fld_diffuse, fld_step,
- *     fld_step_batched) wait on the stream between multigrid cycles and return after the
- *     result is complete; the others return after enqueueing.
+ *     is enqueued on it, and calls return after enqueueing unless documented otherwise.
+ *     The solves (fld_diffuse, fld_diffuse_aniso, fld_step) keep their whole outer loop on
+ *     the device -- residual, convergence test and V-cycles in one CUDA graph whose
+ *     conditional nodes the device steers -- so they do not wait for the GPU either.  Their
+ *     outcome (status, cycles, residual, sweep counts) is written into *info in stream order:
+ *     keep `info` valid until the stream has passed the call, and read it after synchronising
+ *     the stream.  Two exceptions wait on the stream: the first solve of a grid configuration
+ *     with autotuned sweep counts (it times its candidates), and solves while per-kernel
+ *     tracing is on.  fld_step_batched and fld_step_host return with their results complete.
  *   - Inputs are never modified; eps and E are updated in place where documented.
- *   - Return value: FLD_OK, or an error code for an invalid argument, a CUDA error or a
- *     solve that did not reach rtol within max_cycles.  The message of the last error is
+ *   - Return value: FLD_OK, or an error code for an invalid argument or a CUDA error.  What
+ *     the device finds -- a solve that did not reach rtol within max_cycles, a non-positive
+ *     input met on the device, a non-finite residual -- is info->status of the asynchronous
+ *     calls (and the return value of the synchronous ones).  The message of the last error is
  *     available from fld_last_error().  No exception crosses the ABI.
  *   - A context is bound to one device and is not thread-safe; use one context per host
  *     thread.  It owns the multigrid hierarchy, scratch buffers and CUDA graphs and keeps
@@ -175,7 +183,8 @@ FLD_API fld_status fld_coeffs(fld_ctx* ctx, const fld_grid* grid, const fld_para
 /* Backward-Euler diffusion (Sect. 3.4, Eq. discdiff): solves
    E_new + dt*(-div D grad E_new) = E_old (with the boundary terms) to p->rtol.  D_cell is the
    cell-centred D from fld_coeffs; faces take its harmonic mean.  E_new may alias E_old.
-   `info` (may be NULL) receives cycles and the final relative residual.  Synchronises. */
+   `info` (may be NULL) receives the status, cycles and final relative residual in stream order.
+   Asynchronous (see the conventions above). */
 FLD_API fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
                        const double* D_cell, const double* E_old, double* E_new, fld_info* info,
                        void* stream);
@@ -183,7 +192,7 @@ FLD_API fld_status fld_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_par
 /* fld_diffuse with a diagonal-tensor D (the anisotropic variant Sect. 6 mentions: one diffusion
    coefficient per grid direction).  D_axis: host array of grid->ndim DEVICE pointers; D_axis[a]
    is the cell-centred D of axis a, and the faces of axis a take its harmonic mean.  Otherwise as
-   fld_diffuse (synchronises). */
+   fld_diffuse (asynchronous). */
 FLD_API fld_status fld_diffuse_aniso(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
                              const double* const* D_axis, const double* E_old, double* E_new,
                              fld_info* info, void* stream);
@@ -213,7 +222,9 @@ FLD_API fld_status fld_exchange(fld_ctx* ctx, size_t n, const fld_params* p, dou
 
 /* One full radiation-energy update in place on eps and E: coefficients from the state entering
    the diffusion stage (lagged D), diffusion, exchange; p->order selects the paper's order
-   (exchange first, Sect. 3.1) or diffusion first.  Synchronises. */
+   (exchange first, Sect. 3.1) or diffusion first.  Asynchronous: `info` (may be NULL) receives
+   the solve's outcome and the exchange's counters in stream order; its status is
+   FLD_ERR_NONPOSITIVE if rho, kappa or E <= 0 (or eps < 0) was met on the device. */
 FLD_API fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt,
                     const double* rho, double* eps, double* E, fld_info* info, void* stream);
 

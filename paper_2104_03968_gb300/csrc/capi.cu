@@ -229,15 +229,91 @@ fld_status read_status(fld_ctx* ctx, cudaStream_t s, unsigned* status, int* iter
   return FLD_OK;
 }
 
+// The outcome of a diffusion solve: known at once (the host-driven solve, which synchronises per
+// cycle: the first solve of a configuration, which autotunes, or a traced one), or pending in pinned
+// memory that the graph-driven solve writes when the stream passes it.
+struct DiffuseResult {
+  SolveStats ss;
+  const Multigrid::SolveOut* out = nullptr;
+};
+
+// Completes a pending result once the stream has passed the solve, and counts the kernels its
+// graph's loop ran.
+void resolve(DiffuseResult& r) {
+  if (!r.out) return;
+  r.ss.cycles = r.out->cycles;
+  r.ss.status = r.out->status;
+  r.ss.relres = r.out->relres;
+  note_launch(r.out->kernels);
+  r.out = nullptr;
+}
+
+void fill_info(fld_info* inf, const SolveStats& ss, const int* h_info) {
+  memset(inf, 0, sizeof(*inf));
+  inf->cycles = ss.cycles;
+  inf->rel_residual = ss.relres;
+  inf->status = ss.status;
+  inf->nu1 = ss.nu1;
+  inf->nu2 = ss.nu2;
+  inf->nu1_coarse = ss.nu1_coarse;
+  inf->nu2_coarse = ss.nu2_coarse;
+  if (h_info) {
+    inf->exch_max_iters = h_info[0];
+    inf->bisection_fallbacks = h_info[1];
+    if ((unsigned)h_info[2] & kStatNonpositive) inf->status = FLD_ERR_NONPOSITIVE;
+  }
+}
+
+// A stream host function: fills the caller's fld_info (may be null) when the stream reaches it.
+struct Delivery {
+  fld_info* dst;
+  DiffuseResult res;
+  const int* h_info;  // pinned exchange counters and status bits, or null
+};
+
+void CUDART_CB deliver(void* arg) {
+  Delivery* d = static_cast<Delivery*>(arg);
+  resolve(d->res);
+  if (d->dst) fill_info(d->dst, d->res.ss, d->h_info);
+  delete d;
+}
+
+fld_status enqueue_delivery(fld_ctx* ctx, fld_info* info, const DiffuseResult& r, const int* h_info, cudaStream_t s) {
+  if (!info && !r.out) return FLD_OK;
+  Delivery* d = new (std::nothrow) Delivery{info, r, h_info};
+  if (!d) return fail(ctx, FLD_ERR_CUDA, "out of host memory");
+  cudaError_t e = cudaLaunchHostFunc(s, deliver, d);
+  if (e != cudaSuccess) {
+    delete d;
+    return cuda_fail(ctx, e, "result delivery");
+  }
+  return FLD_OK;
+}
+
+// The status of a completed step, with its message.
+fld_status outcome(fld_ctx* ctx, const fld_info& inf) {
+  if (inf.status == FLD_ERR_NONPOSITIVE)
+    return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state");
+  if (inf.status != FLD_OK)
+    return fail(ctx, (fld_status)inf.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
+                inf.rel_residual, inf.cycles);
+  return FLD_OK;
+}
+
 fld_status run_diffuse(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* const D[3],
-                       const double* E_old, double* E_new, SolveStats* st, cudaStream_t s) {
+                       const double* E_old, double* E_new, DiffuseResult* r, cudaStream_t s) {
   GridDev g = to_dev(grid);
   cudaError_t e = ctx->mg.configure(g, p->precision);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid allocation");
   e = ctx->mg.setup(dt, D, E_old, p->rtol, ctx->d_status, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid setup");
   int maxc = p->max_cycles > 0 ? p->max_cycles : 100;
-  e = ctx->mg.solve(E_old, E_new, p->rtol, maxc, p->nu1, p->nu2, p->start == FLD_START_FMG, st, s);
+  const bool fmg = p->start == FLD_START_FMG;
+  r->out = nullptr;
+  if (ctx->mg.async_ready())
+    e = ctx->mg.solve_async(E_old, E_new, p->rtol, maxc, p->nu1, p->nu2, fmg, &r->ss, &r->out, s);
+  else
+    e = ctx->mg.solve(E_old, E_new, p->rtol, maxc, p->nu1, p->nu2, fmg, &r->ss, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "multigrid solve");
   return FLD_OK;
 }
@@ -346,23 +422,14 @@ fld_status diffuse_common(fld_ctx* ctx, const fld_grid* grid, const fld_params* 
                           void* stream) {
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  SolveStats ss;
-  fld_status st = run_diffuse(ctx, grid, p, dt, Dax, E_old, E_new, &ss, s);
+  DiffuseResult r;
+  fld_status st = run_diffuse(ctx, grid, p, dt, Dax, E_old, E_new, &r, s);
   if (st != FLD_OK) return st;
-  if (info) {
-    memset(info, 0, sizeof(*info));
-    info->cycles = ss.cycles;
-    info->rel_residual = ss.relres;
-    info->status = ss.status;
-    info->nu1 = ss.nu1;
-    info->nu2 = ss.nu2;
-    info->nu1_coarse = ss.nu1_coarse;
-    info->nu2_coarse = ss.nu2_coarse;
+  if (!r.out) {  // known already
+    if (info) fill_info(info, r.ss, nullptr);
+    return FLD_OK;
   }
-  if (ss.status != FLD_OK)
-    return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
-                ss.relres, ss.cycles);
-  return FLD_OK;
+  return enqueue_delivery(ctx, info, r, nullptr, s);
 }
 
 fld_status diffuse_checks(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, double dt, const double* E_old,
@@ -484,7 +551,7 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
   if ((st = reset_status(ctx, s)) != FLD_OK) return st;
   Opacity op = to_opacity(p);
   ExchangeParams xp = to_exchange(p, dt);
-  SolveStats ss;
+  DiffuseResult dr;
   cudaError_t e;
   if (p->order == FLD_ORDER_IMEX_MIDPOINT) {
     // Sect. 3.1, midpoint IMEX for the static-medium subsystem: exchange over dt/2 from u^n,
@@ -507,7 +574,7 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
                       p->precision == FLD_PREC_FP64);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
     const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
-    if ((st = run_diffuse(ctx, grid, p, 0.5 * dt, Dax, E, E, &ss, s)) != FLD_OK) return st;
+    if ((st = run_diffuse(ctx, grid, p, 0.5 * dt, Dax, E, E, &dr, s)) != FLD_OK) return st;
     e = launch_midpoint_combine(g.ncell, E0, eps0, Eh, E, eps, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "midpoint combine launch");
     e = launch_exchange(g.ncell, xp, op, rho, nullptr, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
@@ -521,32 +588,26 @@ fld_status fld_step(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, dou
                       s, p->precision == FLD_PREC_FP64);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coeffs launch");
     const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
-    if ((st = run_diffuse(ctx, grid, p, dt, Dax, E, E, &ss, s)) != FLD_OK) return st;
+    if ((st = run_diffuse(ctx, grid, p, dt, Dax, E, E, &dr, s)) != FLD_OK) return st;
     if (p->order == FLD_ORDER_DIFFUSE_THEN_EXCHANGE) {
       // eps is unchanged by the diffusion, so kappa^n from the coefficient stage is current
       e = launch_exchange(g.ncell, xp, op, rho, ctx->kappa, eps, E, ctx->d_info, ctx->d_info + 1, ctx->d_status, s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange launch");
     }
   }
-  unsigned sbits = 0;
-  fld_info tmp;
-  fld_info* inf = info ? info : &tmp;
-  memset(inf, 0, sizeof(*inf));
-  if ((st = read_status(ctx, s, &sbits, &inf->exch_max_iters, &inf->bisection_fallbacks)) != FLD_OK) return st;
-  inf->cycles = ss.cycles;
-  inf->rel_residual = ss.relres;
-  inf->status = ss.status;
-  inf->nu1 = ss.nu1;
-  inf->nu2 = ss.nu2;
-  inf->nu1_coarse = ss.nu1_coarse;
-  inf->nu2_coarse = ss.nu2_coarse;
-  if (sbits & kStatNonpositive) {
-    inf->status = FLD_ERR_NONPOSITIVE;
-    return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state");
+  // the exchange counters and status bits into pinned memory, then the outcome into *info, both in
+  // stream order: nothing here waits for the device
+  e = cudaMemcpyAsync(ctx->h_info, ctx->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_info + 2, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
+  if (!info && !dr.out) return FLD_OK;
+  Delivery* d = new (std::nothrow) Delivery{info, dr, ctx->h_info};
+  if (!d) return fail(ctx, FLD_ERR_CUDA, "out of host memory");
+  e = cudaLaunchHostFunc(s, deliver, d);
+  if (e != cudaSuccess) {
+    delete d;
+    return cuda_fail(ctx, e, "result delivery");
   }
-  if (ss.status != FLD_OK)
-    return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
-                ss.relres, ss.cycles);
   return FLD_OK;
 }
 
@@ -577,7 +638,9 @@ fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_params* p
     if (e == cudaSuccess) e = cudaMemcpyAsync(de, eps, n * cell, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dE, E, n * cell, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copies");
-    st = fld_step(ctx, grid, p, dt, dr, de, dE, info, stream);
+    fld_info tmp;
+    fld_info* inf = info ? info : &tmp;
+    st = fld_step(ctx, grid, p, dt, dr, de, dE, inf, stream);
     if (st == FLD_ERR_CUDA) return st;
     const std::string msg = ctx->err;
     e = cudaMemcpyAsync(eps, de, n * cell, cudaMemcpyDeviceToHost, s);
@@ -585,7 +648,8 @@ fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_params* p
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copies");
     ctx->err = msg;
-    return st;
+    if (st != FLD_OK) return st;
+    return outcome(ctx, *inf);
   }
   if ((st = ensure_scratch(ctx, n)) != FLD_OK) return st;
   if ((st = reset_status(ctx, s)) != FLD_OK) return st;
@@ -621,9 +685,9 @@ fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_params* p
                               ctx->d_status, first(i), first(i + 1) - first(i), s, p->precision == FLD_PREC_FP64);
   }
   if (e != cudaSuccess) return drain(cuda_fail(ctx, e, "coeffs launch"));
-  SolveStats ss;
+  DiffuseResult res;
   const double* const Dax[3] = {ctx->D, ctx->D, ctx->D};
-  if ((st = run_diffuse(ctx, grid, p, dt, Dax, dE, dE, &ss, s)) != FLD_OK) return drain(st);
+  if ((st = run_diffuse(ctx, grid, p, dt, Dax, dE, dE, &res, s)) != FLD_OK) return drain(st);
   // exchange slab by slab, each slab's eps and E copied back while the next ones are computed
   for (int i = 0; i < S && e == cudaSuccess; ++i) {
     const long long f = first(i), c = first(i + 1) - f;
@@ -637,26 +701,13 @@ fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_params* p
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
   if (e != cudaSuccess) return drain(cuda_fail(ctx, e, "exchange and device-to-host copies"));
-  unsigned sbits = 0;
+  // this call returns with the host arrays complete, so it waits here and reports the outcome
+  if ((st = read_status(ctx, s, nullptr, nullptr, nullptr)) != FLD_OK) return drain(st);
+  resolve(res);
   fld_info tmp;
   fld_info* inf = info ? info : &tmp;
-  memset(inf, 0, sizeof(*inf));
-  if ((st = read_status(ctx, s, &sbits, &inf->exch_max_iters, &inf->bisection_fallbacks)) != FLD_OK) return drain(st);
-  inf->cycles = ss.cycles;
-  inf->rel_residual = ss.relres;
-  inf->status = ss.status;
-  inf->nu1 = ss.nu1;
-  inf->nu2 = ss.nu2;
-  inf->nu1_coarse = ss.nu1_coarse;
-  inf->nu2_coarse = ss.nu2_coarse;
-  if (sbits & kStatNonpositive) {
-    inf->status = FLD_ERR_NONPOSITIVE;
-    return fail(ctx, FLD_ERR_NONPOSITIVE, "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state");
-  }
-  if (ss.status != FLD_OK)
-    return fail(ctx, (fld_status)ss.status, "diffusion solve stopped at relative residual %.3e after %d cycles",
-                ss.relres, ss.cycles);
-  return FLD_OK;
+  fill_info(inf, res.ss, ctx->h_info);
+  return outcome(ctx, *inf);
 }
 
 fld_status fld_radiation_terms(fld_ctx* ctx, const fld_grid* grid, const fld_params* p, const double* E,

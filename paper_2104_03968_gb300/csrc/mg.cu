@@ -28,6 +28,19 @@
 
 namespace fld {
 
+// Device state of the graph-driven solve (Multigrid::solve_async): the outer loop of solve_t kept
+// on the device.  pending: what the last residual was (the double-float first residual, an exact
+// residual, or a double-float update); kc_*: the kernels of each branch of the loop body.
+struct Multigrid::SolveDev {
+  double rtol, N;
+  int max_cycles, mixed, fmg_start, idx32;
+  int cycles, status, pending, updates, fp64_op;
+  float scale;
+  double rel, drift;
+  unsigned long long kernels;
+  unsigned long long kc_check, kc_fmg, kc_vcyc, kc_fp64, kc_add, kc_exact, kc_upd;
+};
+
 // ----------------------------------------------------------------------------- arena
 
 DeviceArena::~DeviceArena() { release(); }
@@ -247,8 +260,10 @@ __global__ void __launch_bounds__(256) k_residual_update(LevelDev<float> L, Leve
                                                          const float* __restrict__ dhi, const float* __restrict__ dlo,
                                                          const float* __restrict__ d, float* __restrict__ rhi,
                                                          float* __restrict__ rlo, double* __restrict__ x64, float scale,
-                                                         int nparts, double* __restrict__ parts) {
+                                                         const float* __restrict__ scale_p, int nparts,
+                                                         double* __restrict__ parts) {
   // 32-bit indices: the caller guarantees fewer than 2^31 cells and faces per axis
+  if (scale_p) scale = *scale_p;  // the graph-driven solve keeps the scale on the device
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
   const int rows = ny * nz, sy = nx, sz = nx * ny;
   float ss = 0.f, mm = 0.f;
@@ -649,6 +664,9 @@ static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / 
 Multigrid::~Multigrid() {
   drop_graphs();
   if (cap_stream_) cudaStreamDestroy(cap_stream_);
+  for (cudaStream_t b : body_s_)
+    if (b) cudaStreamDestroy(b);
+  if (out_h_) cudaFreeHost(out_h_);
   if (host_scal_) cudaFreeHost(host_scal_);
   if (tune_x_) cudaFree(tune_x_);
 }
@@ -656,6 +674,8 @@ Multigrid::~Multigrid() {
 void Multigrid::drop_graphs() {
   for (auto& g : graphs_) cudaGraphExecDestroy(g.exec);
   graphs_.clear();
+  if (sexec_) cudaGraphExecDestroy(sexec_);
+  sexec_ = nullptr;
 }
 
 static inline long long cells3(const std::array<int, 3>& n) { return (long long)n[0] * n[1] * n[2]; }
@@ -841,6 +861,7 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
     if (wave_eligible(g, dims_[l])) add(4 * (size_t)dims_[l][2] * sizeof(int));
   }
   add((2 + 2 * (size_t)dims_[0][2]) * sizeof(unsigned));
+  add(sizeof(SolveDev));
   cudaError_t e = arena_.reserve(bytes + 4096);
   if (e != cudaSuccess) return e;
   for (int a = 0; a < 3; ++a) w64_[a] = a < g.ndim ? (double*)arena_.take(faces3(dims_[0], a) * sizeof(double)) : nullptr;
@@ -883,6 +904,7 @@ cudaError_t Multigrid::configure(const GridDev& g, int precision) {
       if (!lv_[l].w[a]) return cudaErrorMemoryAllocation;
   }
   if (!b64_ || !diag64_ || !partials_ || !scal_) return cudaErrorMemoryAllocation;
+  if (!(sd_ = (SolveDev*)arena_.take(sizeof(SolveDev)))) return cudaErrorMemoryAllocation;
   e = configure_wave();
   if (e != cudaSuccess) return e;
   configured_ = true;
@@ -1274,16 +1296,16 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       float* rv = (float*)lv_[0].r;
       if (g_.ndim == 3)
         note_launch(),
-            k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
-                                                              partials_);
+            k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr,
+                                                              nparts_, partials_);
       else if (g_.ndim == 2)
         note_launch(),
-            k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
-                                                              partials_);
+            k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr,
+                                                              nparts_, partials_);
       else
         note_launch(),
-            k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nparts_,
-                                                              partials_);
+            k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr,
+                                                              nparts_, partials_);
       note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
       note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
     } else {
@@ -1434,6 +1456,366 @@ cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles
   tuned_.push_back({rtol, fmg_start ? 1.0 : 0.0, (double)c[0], (double)c[1], (double)c[2], (double)c[3]});
   for (int k = 0; k < 4; ++k) nu[k] = c[k];
   return cudaSuccess;
+}
+
+// ----------------------------------------------------------------------------- graph-driven solve
+//
+// The outer loop of solve_t with its decisions on the device.  The graph runs the first residual,
+// then a WHILE node whose body is: k_solve_check (one thread: evaluates the last residual exactly as
+// solve_t does and sets the conditions below and the loop's), then IF nodes for the full-multigrid
+// cycle, the V-cycle, the FP64 operator (the redo of a double-float set-up that left its window,
+// or the certification of an update), the addition of the correction to the FP64 iterate, the
+// exact residual and the double-float residual update.  Its last kernel writes the result into
+// pinned host memory.  Nothing on the host waits for a cycle.
+
+enum { kPendDf = 0, kPendExact = 1, kPendUpdate = 2 };
+
+struct SolveHandles {
+  cudaGraphConditionalHandle loop, fmg, vcyc, fp64, add, exact, upd;
+};
+
+__global__ void k_solve_init(Multigrid::SolveDev* S, double rtol, double N, int max_cycles, int mixed, int fmg_start,
+                             int idx32, int pending, int fp64_op, unsigned long long kernels) {
+  S->rtol = rtol;
+  S->N = N;
+  S->max_cycles = max_cycles;
+  S->mixed = mixed;
+  S->fmg_start = fmg_start;
+  S->idx32 = idx32;
+  S->cycles = 0;
+  S->status = FLD_ERR_NOT_CONVERGED;
+  S->pending = pending;
+  S->updates = 0;
+  S->fp64_op = fp64_op;
+  S->scale = 0.0f;
+  S->rel = 0.0;
+  S->drift = 0.0;
+  S->kernels = kernels;
+}
+
+__global__ void k_solve_check(Multigrid::SolveDev* S, const double* __restrict__ scal, const unsigned* df_flag,
+                              const unsigned* wave_err, SolveHandles h) {
+  constexpr double kDrift = 0x1p-42;  // as solve_t
+  int do_fmg = 0, do_v = 0, do_fp = 0, do_add = 0, do_exact = 0, do_upd = 0;
+  bool go = true;
+  const int pend = S->pending;
+  if (*wave_err) {
+    S->status = FLD_ERR_DEVICE_TIMEOUT;
+    go = false;
+  } else if (pend == kPendDf && df_flag && *df_flag) {
+    // a value left the double-float window: the FP64 operator, then an exact residual from the
+    // copy of E_old the set-up pass left in the iterate
+    do_fp = 1;
+    do_exact = 1;
+    S->fp64_op = 1;
+    S->pending = kPendExact;
+  } else {
+    const double N = S->N, bb = scal[1];
+    double rel, drift = S->drift;
+    if (pend == kPendDf) {
+      rel = bb > 0 ? sqrt(scal[0] / bb) : sqrt(scal[0]);
+      drift = kDrift * (bb > 0 ? sqrt(scal[2] / bb) : sqrt(scal[2]));
+      const double rms = sqrt(bb / N);
+      S->updates = rms * fmax(S->rtol, 1e-16) * 1e-3 >= 0x1p-76 && rms <= 0x1p90;
+      S->scale = (float)(1.0 / rms);
+    } else if (pend == kPendUpdate) {
+      rel = sqrt(scal[0] / N);
+      drift += kDrift * sqrt(scal[2] / N);
+    } else {
+      rel = bb > 0 ? sqrt(scal[0] / bb) : sqrt(scal[0]);
+      drift = 0.0;
+      if (S->cycles == 0 && S->mixed && bb > 0) {
+        const double rms = sqrt(bb / N);
+        S->updates = rms * fmax(S->rtol, 1e-16) * 1e-3 >= 0x1p-76 && rms <= 0x1p90 && S->idx32;
+        S->scale = (float)(1.0 / rms);
+      }
+    }
+    S->rel = rel;
+    S->drift = drift;
+    if (!(rel == rel) || rel > 1e300) {
+      S->status = FLD_ERR_NONFINITE;
+      go = false;
+    } else if (rel + drift <= S->rtol) {
+      S->status = FLD_OK;
+      go = false;
+    } else if (pend == kPendUpdate && rel <= S->rtol) {
+      // the estimate is converged but the bound does not certify it: an exact residual
+      do_exact = 1;
+      do_fp = S->mixed && !S->fp64_op;
+      S->fp64_op |= do_fp;
+      S->pending = kPendExact;
+    } else if (S->cycles >= S->max_cycles) {
+      S->status = FLD_ERR_NOT_CONVERGED;
+      go = false;
+    } else {
+      do_fmg = S->cycles == 0 && S->fmg_start;
+      do_v = !do_fmg;
+      S->cycles += 1;
+      if (S->updates) {
+        do_upd = 1;
+        S->pending = kPendUpdate;
+      } else {
+        do_add = 1;
+        do_exact = 1;
+        do_fp = S->mixed && !S->fp64_op;
+        S->fp64_op |= do_fp;
+        S->pending = kPendExact;
+      }
+    }
+  }
+  cudaGraphSetConditional(h.loop, go ? 1u : 0u);
+  cudaGraphSetConditional(h.fmg, (unsigned)do_fmg);
+  cudaGraphSetConditional(h.vcyc, (unsigned)do_v);
+  cudaGraphSetConditional(h.fp64, (unsigned)do_fp);
+  cudaGraphSetConditional(h.add, (unsigned)do_add);
+  cudaGraphSetConditional(h.exact, (unsigned)do_exact);
+  cudaGraphSetConditional(h.upd, (unsigned)do_upd);
+  S->kernels += S->kc_check + do_fmg * S->kc_fmg + do_v * S->kc_vcyc + do_fp * S->kc_fp64 + do_add * S->kc_add +
+                do_exact * S->kc_exact + do_upd * S->kc_upd;
+}
+
+__global__ void k_solve_done(const Multigrid::SolveDev* S, Multigrid::SolveOut* out) {
+  out->cycles = S->cycles;
+  out->status = S->status;
+  out->relres = S->rel;
+  out->kernels = S->kernels;  // the loop's kernels (the host counts the rest at launch)
+}
+
+// Adds a conditional node (type WHILE or IF, condition h) at the capture position of s and returns
+// its body graph.
+static cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                   cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t capg = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, &deps, &edata, &ndeps);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, capg, deps, edata, ndeps, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+template <class T>
+cudaError_t Multigrid::build_solve_graph(const SolveKey& k, cudaStream_t s0) {
+  if (sexec_) cudaGraphExecDestroy(sexec_);
+  sexec_ = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!cap_stream_) e = cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking);
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+    if (!body_s_[q]) e = cudaStreamCreateWithFlags(&body_s_[q], cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  // the state the capture changes on the host: restored afterwards
+  void* const x0 = lv_[0].x;
+  void* const t0 = lv_[0].tmp;
+  const bool fp64_op0 = fp64_op_;
+  const bool mixed = sizeof(T) == sizeof(float) && dhi_ != nullptr;
+  const bool df_first = mixed && df_mode_ && !fp64_op_;
+  long long maxf = g_.ncell;
+  for (int a = 0; a < g_.ndim; ++a) maxf = std::max(maxf, faces3(dims_[0], a));
+  const double* E_old = k.E_old;
+  double* x = k.E_new;
+  const int nu1 = k.nu[0], nu2 = k.nu[1];
+  const int tswaps = (tiled_ && sizeof(T) == sizeof(float)) ? nu1 + nu2 : 0;  // finest sweeps that swap x, tmp
+  void* const A = x0;  // where every branch leaves the correction d
+  void* const B = t0;
+  cudaGraph_t graph = nullptr;
+  e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return e;
+  cudaStream_t s = cap_stream_;
+  e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return e;
+  }
+  capturing_ = true;
+  unsigned long long kc[7] = {0, 0, 0, 0, 0, 0, 0};  // check, fmg, vcyc, fp64, add, exact, upd
+  const unsigned long long c0 = launch_count();
+  void* w64v[3] = {w64_[0], w64_[1], w64_[2]};
+  LevelDev<double> L64 = level_dev<double>(g_, dims_[0], w64v);
+  LevelDev<float> L32{}, L32lo{};
+  if (mixed) {
+    void* wlo[3] = {w32lo_[0], w32lo_[1], w32lo_[2]};
+    L32 = level_dev<float>(g_, dims_[0], lv_[0].w);
+    L32lo = level_dev<float>(g_, dims_[0], wlo);
+  }
+  auto exact_residual = [&](cudaStream_t b, const double* xin) {
+    if (mixed)
+      note_launch(), k_residual64_df<<<nparts_, kBlock, 0, b>>>(L64, xin, x, b64_, diag64_, (float*)lv_[0].r, rlo_,
+                                                                partials_);
+    else
+      note_launch(), k_residual64<T><<<nparts_, kBlock, 0, b>>>(L64, g_.ncell, xin, x, b64_, diag64_, (T*)lv_[0].r,
+                                                                partials_);
+    note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_, nparts_, scal_);
+  };
+  // pre-loop: the error word, the state and the first residual (the set-up ran before the graph)
+  e = cudaMemsetAsync(wave_ctl_, 0, sizeof(unsigned), s);
+  note_launch(), k_solve_init<<<1, 1, 0, s>>>(sd_, k.rtol, (double)g_.ncell, k.max_cycles, mixed ? 1 : 0, k.fmg,
+                                              maxf < (1LL << 31) ? 1 : 0, df_first ? kPendDf : kPendExact,
+                                              fp64_op_ ? 1 : 0, 0ull);
+  if (df_first) {
+    if (e == cudaSuccess)
+      e = launch_setup_res0_df(g_, make_df_const(g_, dt_), L32, L32lo, E_old, x != E_old ? x : nullptr, dhi_, dlo_,
+                               (float*)lv_[0].invd, (float*)lv_[0].r, rlo_, nparts_, partials_, scal_, df_flag_, s);
+  } else {
+    exact_residual(s, E_old);
+  }
+  const unsigned long long c_pre = launch_count() - c0 + 1;  // + k_solve_done
+  // the loop
+  cudaGraphConditionalHandle hloop;
+  cudaGraph_t bodyg = nullptr;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hloop, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = add_conditional(s, hloop, cudaGraphCondTypeWhile, &bodyg);
+  cudaStream_t b1 = body_s_[0], b2 = body_s_[1];
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b1, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    SolveHandles h{};
+    h.loop = hloop;
+    cudaGraphConditionalHandle* hs[6] = {&h.fmg, &h.vcyc, &h.fp64, &h.add, &h.exact, &h.upd};
+    for (int q = 0; q < 6 && e == cudaSuccess; ++q) e = cudaGraphConditionalHandleCreate(hs[q], bodyg, 0, 0);
+    unsigned long long c = launch_count();
+    if (e == cudaSuccess)
+      note_launch(), k_solve_check<<<1, 1, 0, b1>>>(sd_, scal_, df_first ? df_flag_ : nullptr, wave_ctl_, h);
+    kc[0] = launch_count() - c;
+    // one IF node per branch, its body captured on b2
+    auto branch = [&](cudaGraphConditionalHandle hh, int slot, auto&& fill) {
+      if (e != cudaSuccess) return;
+      cudaGraph_t ifg = nullptr;
+      e = add_conditional(b1, hh, cudaGraphCondTypeIf, &ifg);
+      if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b2, ifg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) return;
+      const unsigned long long cb = launch_count();
+      cudaError_t ef = fill(b2);
+      kc[slot] = launch_count() - cb;
+      cudaGraph_t tmp = nullptr;
+      e = cudaStreamEndCapture(b2, &tmp);
+      if (e == cudaSuccess) e = ef;
+    };
+    // full multigrid: the prolongation assigns into lv_[0].x, then nu1 + nu2 finest sweeps swap it
+    branch(h.fmg, 1, [&](cudaStream_t b) {
+      lv_[0].x = (tswaps % 2 == 0) ? A : B;
+      lv_[0].tmp = (tswaps % 2 == 0) ? B : A;
+      return fmg<T>(nu1, nu2, nullptr, b);
+    });
+    // V-cycle from zero: its first finest sweep writes lv_[0].tmp
+    branch(h.vcyc, 2, [&](cudaStream_t b) {
+      lv_[0].tmp = (tswaps % 2 == 1) ? A : B;
+      lv_[0].x = (tswaps % 2 == 1) ? B : A;
+      return vcycle<T>(0, nu1, nu2, nullptr, b, true);
+    });
+    if (e == cudaSuccess && lv_[0].x != A) e = cudaErrorInvalidValue;  // both branches end in A
+    branch(h.fp64, 3, [&](cudaStream_t b) { return fp64_operator<T>(b); });
+    branch(h.add, 4, [&](cudaStream_t b) {
+      note_launch(), k_add_correction<T><<<nblk(g_.ncell), kBlock, 0, b>>>(g_.ncell, (const T*)A, x);
+      return cudaGetLastError();
+    });
+    branch(h.exact, 5, [&](cudaStream_t b) {
+      exact_residual(b, x);
+      return cudaGetLastError();
+    });
+    branch(h.upd, 6, [&](cudaStream_t b) {
+      if (!mixed) return cudaSuccess;
+      const float* dv = (const float*)A;
+      float* rv = (float*)lv_[0].r;
+      const float* sp = &sd_->scale;
+      if (g_.ndim == 3)
+        note_launch(), k_residual_update<3><<<nparts_, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp,
+                                                                      nparts_, partials_);
+      else if (g_.ndim == 2)
+        note_launch(), k_residual_update<2><<<nparts_, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp,
+                                                                      nparts_, partials_);
+      else
+        note_launch(), k_residual_update<1><<<nparts_, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp,
+                                                                      nparts_, partials_);
+      note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_, nparts_, scal_);
+      note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_ + nparts_, nparts_, scal_ + 2);
+      return cudaGetLastError();
+    });
+    cudaGraph_t tmp = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b1, &tmp);
+    if (e == cudaSuccess) e = ee;
+  }
+  if (e == cudaSuccess) note_launch(), k_solve_done<<<1, 1, 0, s>>>(sd_, out_h_);
+  cudaGraph_t done = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(s, &done);
+  if (e == cudaSuccess) e = ee;
+  capturing_ = false;
+  unnote_launches(launch_count() - c0);  // captured, not run: the graph's last kernel counts what ran
+  lv_[0].x = x0;
+  lv_[0].tmp = t0;
+  fp64_op_ = fp64_op0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&sexec_, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    sexec_ = nullptr;
+    return e;
+  }
+  // the per-branch kernel counts, and the pre-loop's in the initial count
+  SolveDev init{};
+  init.kc_check = kc[0];
+  init.kc_fmg = kc[1];
+  init.kc_vcyc = kc[2];
+  init.kc_fp64 = kc[3];
+  init.kc_add = kc[4];
+  init.kc_exact = kc[5];
+  init.kc_upd = kc[6];
+  e = cudaMemcpyAsync(&sd_->kc_check, &init.kc_check, 7 * sizeof(unsigned long long), cudaMemcpyHostToDevice, s0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
+  pre_kernels_ = c_pre;
+  skey_ = k;
+  return e;
+}
+
+bool Multigrid::async_ready() const { return !tracer().on; }
+
+cudaError_t Multigrid::solve_async(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1,
+                                   int nu2, bool fmg_start, SolveStats* st, const SolveOut** out, cudaStream_t s) {
+  int nu[4] = {nu1 ? nu1 : 2, nu2 ? nu2 : 2, nu1 ? nu1 : 2, nu2 ? nu2 : 2};
+  if (nu1 == 0 && nu2 == 0) {
+    // the first solve of a configuration times candidate sweep counts (synchronises); later ones
+    // find them cached
+    cudaError_t e = autotune(E_old, rtol, max_cycles, fmg_start, nu, s);
+    if (e != cudaSuccess) return e;
+  }
+  nuc1_ = nu[2];
+  nuc2_ = nu[3];
+  st->nu1 = nu[0];
+  st->nu2 = nu[1];
+  st->nu1_coarse = nu[2];
+  st->nu2_coarse = nu[3];
+  if (!out_h_) {
+    cudaError_t e = cudaMallocHost(&out_h_, sizeof(SolveOut));
+    if (e != cudaSuccess) return e;
+  }
+  SolveKey k{};
+  k.E_old = E_old;
+  k.E_new = E_new;
+  for (int a = 0; a < 3; ++a) k.D[a] = D_ax_[a];
+  k.dt = dt_;
+  k.rtol = rtol;
+  k.max_cycles = max_cycles;
+  for (int q = 0; q < 4; ++q) k.nu[q] = nu[q];
+  k.fmg = fmg_start ? 1 : 0;
+  k.df = df_mode_ ? 1 : 0;
+  // whether the FP64 operator is already built (the autotuner's solves may have built it): a graph
+  // made for that state has no double-float set-up pass and reads the FP64 b and diagonal as they
+  // are, so it serves only calls that start in the same state
+  k.fp64op = fp64_op_ ? 1 : 0;
+  k.prec = precision_;
+  if (!sexec_ || !(k == skey_)) {
+    cudaError_t e = precision_ == FLD_PREC_MIXED ? build_solve_graph<float>(k, s) : build_solve_graph<double>(k, s);
+    if (e != cudaSuccess) return e;
+  }
+  note_launch(pre_kernels_);  // the pre-loop kernels; the loop's are added when the result is read
+  *out = out_h_;
+  return cudaGraphLaunch(sexec_, s);
 }
 
 cudaError_t Multigrid::solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,

@@ -67,6 +67,25 @@ class Multigrid {
   cudaError_t solve(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
                     bool fmg_start, SolveStats* st, cudaStream_t s);
 
+  // The result of a graph-driven solve, written by the graph's last kernel into pinned host memory:
+  // valid once the stream has passed the solve.  kernels: kernels the solve's graph ran.
+  struct SolveOut {
+    int cycles, status;
+    double relres;
+    unsigned long long kernels;
+  };
+  struct SolveDev;  // the graph-driven solve's device state (mg.cu)
+  // True when solve_async applies: per-kernel tracing (whose events are host bookkeeping) is off.
+  bool async_ready() const;
+  // The solve of `solve` with no host synchronisation per cycle: the whole outer loop (residuals,
+  // the convergence decision, V-cycles) is one CUDA graph whose conditional nodes the device steers,
+  // built on the first call for a configuration and these pointers, then replayed (the first solve
+  // of a configuration with autotuned sweep counts times its candidates first, which synchronises).
+  // *out receives the pinned result, valid after the stream passes the solve; st receives the sweep
+  // counts.
+  cudaError_t solve_async(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1, int nu2,
+                          bool fmg_start, SolveStats* st, const SolveOut** out, cudaStream_t s);
+
   int levels() const { return (int)dims_.size(); }
   const GridDev& grid() const { return g_; }
 
@@ -147,6 +166,29 @@ class Multigrid {
   bool rows_ok(int l) const;
   template <class T>
   cudaError_t wave_sweep(int l, bool zero, int c0, double* x64, cudaStream_t s);
+  // Graph-driven solve: device state (arena), pinned result, body capture streams and the graph of
+  // the last configuration with its key.
+  SolveDev* sd_ = nullptr;
+  SolveOut* out_h_ = nullptr;
+  cudaStream_t body_s_[2] = {nullptr, nullptr};
+  struct SolveKey {
+    const double* E_old;
+    double* E_new;
+    const double* D[3];
+    double dt, rtol;
+    int max_cycles, nu[4], fmg, df, fp64op, prec;
+    bool operator==(const SolveKey& o) const {
+      return E_old == o.E_old && E_new == o.E_new && D[0] == o.D[0] && D[1] == o.D[1] && D[2] == o.D[2] &&
+             dt == o.dt && rtol == o.rtol && max_cycles == o.max_cycles && nu[0] == o.nu[0] && nu[1] == o.nu[1] &&
+             nu[2] == o.nu[2] && nu[3] == o.nu[3] && fmg == o.fmg && df == o.df && fp64op == o.fp64op &&
+             prec == o.prec;
+    }
+  };
+  SolveKey skey_{};
+  cudaGraphExec_t sexec_ = nullptr;
+  unsigned long long pre_kernels_ = 0;  // kernels of the graph outside its loop
+  template <class T>
+  cudaError_t build_solve_graph(const SolveKey& k, cudaStream_t s);
   // Tiled sweep of the mixed solver's finest 3-D level (sweep3d.cu): each cell's 1 / (dt D / dx_0^2)
   // in FP32, and whether this solve uses it (scalar D, eligible shape).  The sweep reads the iterate
   // from lv_[0].x and writes lv_[0].tmp, then the two are swapped.

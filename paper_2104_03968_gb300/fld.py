@@ -243,17 +243,32 @@ def coeffs(ctx: Context, grid: dict, params: dict, E, rho, eps):
     return kappa, D
 
 
+def outcome(ctx: Context, info: Info, allow_unconverged: bool = True) -> dict:
+    """The outcome of an asynchronous call as a dict, once its stream has been synchronised; raises
+    FldError for a failed solve or invalid input (a solve that missed rtol only if
+    allow_unconverged is false)."""
+    d = info.as_dict()
+    st = d["status"]
+    if st and not (allow_unconverged and st == 4):
+        if st == 2:
+            msg = "rho, kappa or E <= 0 (or eps < 0) in the input or an intermediate state"
+        else:
+            msg = f"diffusion solve stopped at relative residual {d['rel_residual']:.3e} after {d['cycles']} cycles"
+        raise FldError(st, msg)
+    return d
+
+
 def diffuse(ctx: Context, grid: dict, params: dict, dt: float, D, E_old, out=None):
-    """Backward-Euler diffusion solve (Sect. 3.4) by multigrid.  Returns (E_new, info)."""
+    """Backward-Euler diffusion solve (Sect. 3.4) by multigrid.  Returns (E_new, info); the call is
+    asynchronous on torch's current stream, which this function synchronises to read info."""
     keep = []
     g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
     E_new = torch.empty_like(E_old) if out is None else out
     info = Info()
-    st = ctx.lib.fld_diffuse(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(D), _dptr(E_old), _dptr(E_new),
-                             ct.byref(info), _stream())
-    if st and st != 4:
-        ctx.check(st)
-    return E_new, info.as_dict()
+    ctx.check(ctx.lib.fld_diffuse(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(D), _dptr(E_old), _dptr(E_new),
+                                  ct.byref(info), _stream()))
+    torch.cuda.current_stream().synchronize()
+    return E_new, outcome(ctx, info)
 
 
 def _fptr(t: torch.Tensor | None):
@@ -282,11 +297,10 @@ def diffuse_aniso(ctx: Context, grid: dict, params: dict, dt: float, D_axis, E_o
     arr = (ct.c_void_p * len(D_axis))(*[d.data_ptr() for d in D_axis])
     E_new = torch.empty_like(E_old) if out is None else out
     info = Info()
-    st = ctx.lib.fld_diffuse_aniso(ctx.h, ct.byref(g), ct.byref(p), float(dt), ct.cast(arr, ct.c_void_p),
-                                   _dptr(E_old), _dptr(E_new), ct.byref(info), _stream())
-    if st and st != 4:
-        ctx.check(st)
-    return E_new, info.as_dict()
+    ctx.check(ctx.lib.fld_diffuse_aniso(ctx.h, ct.byref(g), ct.byref(p), float(dt), ct.cast(arr, ct.c_void_p),
+                                        _dptr(E_old), _dptr(E_new), ct.byref(info), _stream()))
+    torch.cuda.current_stream().synchronize()
+    return E_new, outcome(ctx, info)
 
 
 def exchange(ctx: Context, params: dict, dt: float, rho, eps, E, kappa=None) -> dict:
@@ -323,10 +337,15 @@ def _assign_back(host, tmp):
         host[...] = np.asarray(tmp).reshape(np.shape(host))
 
 
-def step(ctx: Context, grid: dict, params: dict, dt: float, rho, eps, E, allow_unconverged: bool = False) -> dict:
+def step(ctx: Context, grid: dict, params: dict, dt: float, rho, eps, E, allow_unconverged: bool = False,
+         sync: bool = True):
     """One full update in place on eps and E.  CUDA tensors are updated in place on the device;
     host arrays (numpy, or CPU tensors -- pinned ones let the copies overlap the kernels) go through
-    fld_step_host, which copies them in, steps and copies eps and E back into the same buffers."""
+    fld_step_host, which copies them in, steps and copies eps and E back into the same buffers.
+    On the device the call is asynchronous: with sync (the default) this function synchronises
+    torch's current stream and returns the outcome as a dict; without, it returns the Info that the
+    library fills in stream order (keep it until the stream is synchronised, then pass it to
+    ``outcome``)."""
     host = not (isinstance(E, torch.Tensor) and E.is_cuda)
     keep = []
     g, p = grid_struct(grid), params_struct(params, keep, _device_of(ctx))
@@ -341,12 +360,15 @@ def step(ctx: Context, grid: dict, params: dict, dt: float, rho, eps, E, allow_u
             _assign_back(eps, te)
         if tE is not None:
             _assign_back(E, tE)
-    else:
-        st = ctx.lib.fld_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(rho), _dptr(eps), _dptr(E),
-                              ct.byref(info), _stream())
-    if st and not (allow_unconverged and st == 4):
-        ctx.check(st)
-    return info.as_dict()
+        if st and not (allow_unconverged and st == 4):
+            ctx.check(st)
+        return info.as_dict()
+    ctx.check(ctx.lib.fld_step(ctx.h, ct.byref(g), ct.byref(p), float(dt), _dptr(rho), _dptr(eps), _dptr(E),
+                               ct.byref(info), _stream()))
+    if not sync:
+        return info
+    torch.cuda.current_stream().synchronize()
+    return outcome(ctx, info, allow_unconverged)
 
 
 def _copy_back(host, dev: torch.Tensor):

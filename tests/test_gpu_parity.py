@@ -775,6 +775,50 @@ def test_invalid_arguments_are_rejected(ctx):
     assert e.value.status == 2
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_steps_enqueued_back_to_back(ctx, precision):
+    """fld_step is asynchronous: two steps enqueued one after the other with no host wait between
+    them (the outcome of each arrives in its fld_info in stream order) give the oracle's two steps."""
+    from paper_2104_03968_gb300 import fld
+    case = lp_dt.grid_dt(inputs.lognormal_3d(n=32, seed=13))
+    g, p = case["grid"], solver(case["phys"], precision=precision, rtol=1e-13 if precision == "fp64" else 1e-12)
+    rho = dev(case["rho"])
+    # the first call of a configuration autotunes its sweep counts (that part synchronises)
+    fld.step(ctx, g, p, case["dt"], rho, dev(case["eps"]), dev(case["E"]))
+    eps, E = dev(case["eps"]), dev(case["E"])
+    infos = [fld.step(ctx, g, p, case["dt"], rho, eps, E, sync=False) for _ in range(2)]
+    torch.cuda.synchronize()
+    outs = [fld.outcome(ctx, i, allow_unconverged=False) for i in infos]
+    assert all(o["cycles"] >= 1 for o in outs), outs
+    e_o, E_o = case["eps"], case["E"]
+    for _ in range(2):
+        e_o, E_o, _ = oracle.step(g, case["phys"], case["dt"], case["rho"], e_o, E_o, rtol=1e-14)
+    assert relerr(host(E), E_o) < TOL and relerr(host(eps), e_o) < TOL
+
+
+def test_diffuse_same_arrays_new_contents(ctx):
+    """Solves that reuse one set of device arrays with new contents each time (the solver keeps its
+    CUDA graph while the arrays and parameters stay the same), crossing the double-float window
+    both ways: every result must meet rtol under the oracle's operator for its own inputs."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.random_small((48, 40, 32), seed=11, bc=BCS["periodic"], dt_factor=100.0)
+    g, p = case["grid"], case["phys"]
+    other = inputs.random_small((48, 40, 32), seed=12, bc=BCS["periodic"], dt_factor=100.0)
+    Ds = [oracle.coeffs(g, p, c["E"], c["rho"], oracle.opacity(p, c["rho"], c["eps"])) for c in (case, other)]
+    D_t, E_t = dev(Ds[0]), dev(case["E"])
+    out = torch.empty_like(E_t)
+    seq = [(0, case["E"]), (0, case["E"] * 1e30), (0, case["E"] * 2.0), (1, other["E"]), (0, case["E"] * 1e-25),
+           (1, other["E"] * 3.0)]
+    for which, E in seq:
+        D_t.copy_(torch.as_tensor(Ds[which]))
+        E_t.copy_(torch.as_tensor(E))
+        out.fill_(0.0)
+        _, info = fld.diffuse(ctx, g, solver(p, precision="mixed", rtol=1e-8), case["dt"], D_t, E_t, out=out)
+        assert info["status"] == 0, info
+        true = oracle.relres(g, case["dt"], Ds[which], E, host(out).reshape(E.shape))
+        assert true <= 1.01e-8, (which, float(np.abs(E).max()), true, info)
+
+
 def test_not_converged_is_reported(ctx):
     from paper_2104_03968_gb300 import fld
     case = inputs.random_small((64, 64), seed=2, dt_factor=300.0)
