@@ -52,17 +52,19 @@ KERNEL_MODEL = {
     "restrict_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 3 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 3 * 8 + 8 / 8},
     "prolong_L0": {"bound": "hbm", "bytes_f32": 2 * 4 + 4 / 8, "bytes_f64": 2 * 8 + 8 / 8},
     # first outer residual.  Mixed: one double-float pass that also builds the diagonal: weights hi
-    # and lo (24), E_old (8), the FP64 iterate's copy (8), diagonal hi and lo and 1/diag (12), r hi
-    # and lo (8).  FP64: r = b - d x + sum_6 w x_nb from w (24), x, b, diag (24), r (8)
-    "residual": {"bound": "hbm", "bytes_f32": 24 + 8 + 8 + 12 + 8, "bytes_f64": 24 + 24 + 8},
-    # mixed solver's double-float residual update r -= A d and x += d: d (4, neighbours from cache), r hi/lo
-    # in and out (16), weights hi and lo (24), diagonal hi and lo (8), the FP64 iterate (16)
+    # and lo (24), E_old (8; the step solves in place, so no copy into the FP64 iterate), diagonal
+    # hi and lo and 1/diag (12), r hi and lo (8).  FP64: r = b - d x + sum_6 w x_nb from w (24), x,
+    # b, diag (24), r (8)
+    "residual": {"bound": "hbm", "bytes_f32": 24 + 8 + 12 + 8, "bytes_f64": 24 + 24 + 8},
+    # mixed solver's double-float residual update r -= A d and x += d: d (4, neighbours from cache),
+    # r hi/lo in and out (16), weights hi and lo (24), diagonal hi and lo (8), the FP64 iterate (16)
     "residual_update": {"bound": "hbm", "bytes_f32": 4 + 16 + 24 + 8 + 16, "bytes_f64": 4 + 16 + 24 + 8 + 16},
     # E, rho, eps in; kappa and D out (double-float arithmetic on the FP32 pipe: issue-bound, far
     # below this bound)
     "coeffs": {"bound": "hbm", "bytes_f32": 40, "bytes_f64": 40},
-    # D in; weights out (mixed: hi and lo floats; FP64: doubles and their FP32 copies)
-    "faces": {"bound": "hbm", "bytes_f32": 8 + 24, "bytes_f64": 8 + 24 + 12},
+    # D in; weights out (mixed: hi and lo floats and the tiled sweep's cell coefficient; FP64:
+    # doubles and their FP32 copies)
+    "faces": {"bound": "hbm", "bytes_f32": 8 + 24 + 4, "bytes_f64": 8 + 24 + 12},
     # rho, kappa, eps, E in; eps, E out (double-float, issue-bound like coeffs)
     "exchange": {"bound": "hbm", "bytes_f32": 48, "bytes_f64": 48},
     # FP64 operator set-up: weights (24) and E_old (8) in; b, diag (16), 1/diag and diag hi/lo (12) out
@@ -347,6 +349,8 @@ def main():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--nu1", type=int, default=0, help="finest pre-sweeps (0 with --nu2 0: autotuned)")
+    ap.add_argument("--nu2", type=int, default=0, help="finest post-sweeps")
     ap.add_argument("--oracle-n", type=int, default=192, dest="oracle_n")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
@@ -380,6 +384,8 @@ def main():
     rho0, eps0, E0 = case["rho"], case["eps"], case["E"]
     ncell = args.n ** 3
     p = dict(phys, precision=args.precision, rtol=args.rtol)
+    if args.nu1 or args.nu2:
+        p.update(nu1=args.nu1, nu2=args.nu2)
 
     def fresh():
         return eps0.clone(), E0.clone()

@@ -1406,11 +1406,25 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
 
 cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles, bool fmg_start, int nu[4],
                                 cudaStream_t s) {
-  for (const auto& t : tuned_)
-    if (t[0] == rtol && t[1] == (fmg_start ? 1.0 : 0.0)) {
-      for (int k = 0; k < 4; ++k) nu[k] = (int)t[2 + k];
-      return cudaSuccess;
-    }
+  // (finest pre, finest post, coarser pre, coarser post)
+  static const int cand[kTuneCands][4] = {{2, 2, 2, 2}, {3, 3, 3, 3}, {4, 4, 2, 1}, {5, 3, 2, 1}, {4, 4, 2, 2},
+                                          {3, 3, 2, 1}, {4, 2, 2, 1}, {6, 4, 2, 1}, {2, 1, 2, 1}, {1, 1, 1, 1}};
+  size_t ti = tuned_.size();
+  for (size_t q = 0; q < tuned_.size(); ++q)
+    if (tuned_[q].rtol == rtol && tuned_[q].fmg == fmg_start) ti = q;
+  if (ti < tuned_.size() && tuned_[ti].rounds >= kTuneRounds) {
+    for (int k = 0; k < 4; ++k) nu[k] = cand[tuned_[ti].best][k];
+    return cudaSuccess;
+  }
+  // the first solve of a configuration is often not typical of the ones that follow (a time
+  // step's initial state differs from the states the stepping settles into), so the candidates are
+  // timed on the first kTuneRounds solves and chosen by their summed time
+  if (ti == tuned_.size()) {
+    Tuned t{};
+    t.rtol = rtol;
+    t.fmg = fmg_start;
+    tuned_.push_back(t);
+  }
   const size_t n = (size_t)g_.ncell;
   if (tune_cap_ < n) {
     if (tune_x_) cudaFree(tune_x_);
@@ -1420,16 +1434,14 @@ cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles
     if (e != cudaSuccess) return e;
     tune_cap_ = n;
   }
-  // (finest pre, finest post, coarser pre, coarser post)
-  static const int cand[][4] = {{2, 2, 2, 2}, {3, 3, 3, 3}, {4, 4, 2, 1}, {5, 3, 2, 1}, {4, 4, 2, 2}, {3, 3, 2, 1},
-                                {4, 2, 2, 1}, {6, 4, 2, 1}, {2, 1, 2, 1}, {1, 1, 1, 1}};
+  static const bool log = getenv("FLD_AUTOTUNE_LOG") != nullptr;  // each candidate's timing on stderr
   cudaEvent_t a, b;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   if (e != cudaSuccess) return e;
-  int best_k = 0;
-  float best = 1e30f;
-  for (int k = 0; k < (int)(sizeof(cand) / sizeof(cand[0])); ++k) {
+  float ms_k[kTuneCands];
+  bool ok_k[kTuneCands];
+  for (int k = 0; k < kTuneCands; ++k) {
     const int* c = cand[k];
     nuc1_ = c[2];
     nuc2_ = c[3];
@@ -1444,17 +1456,22 @@ cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles
     float ms = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
     if (e != cudaSuccess) break;
-    if (cs.status == FLD_OK && ms < best) {
-      best = ms;
-      best_k = k;
-    }
+    ms_k[k] = ms;
+    ok_k[k] = cs.status == FLD_OK;
+    if (log)
+      fprintf(stderr, "fld autotune: nu (%d,%d,%d,%d) %.3f ms, %d cycles, status %d, residual %.3e\n", c[0], c[1], c[2],
+              c[3], ms, cs.cycles, cs.status, cs.relres);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e != cudaSuccess) return e;
-  const int* c = cand[best_k];
-  tuned_.push_back({rtol, fmg_start ? 1.0 : 0.0, (double)c[0], (double)c[1], (double)c[2], (double)c[3]});
-  for (int k = 0; k < 4; ++k) nu[k] = c[k];
+  Tuned& t = tuned_[ti];
+  for (int k = 0; k < kTuneCands; ++k) t.sum[k] = ok_k[k] ? t.sum[k] + ms_k[k] : INFINITY;
+  t.rounds += 1;
+  t.best = 0;
+  for (int k = 1; k < kTuneCands; ++k)
+    if (t.sum[k] < t.sum[t.best]) t.best = k;
+  for (int k = 0; k < 4; ++k) nu[k] = cand[t.best][k];
   return cudaSuccess;
 }
 
@@ -1773,7 +1790,15 @@ cudaError_t Multigrid::build_solve_graph(const SolveKey& k, cudaStream_t s0) {
   return e;
 }
 
-bool Multigrid::async_ready() const { return !tracer().on; }
+// The graph-driven solve, unless the event tracer is on (its per-launch events are host-side
+// bookkeeping) or FLD_SOLVE_GRAPH=0 asks for the host-driven loop.
+bool Multigrid::async_ready() const {
+  static const bool off = [] {
+    const char* v = getenv("FLD_SOLVE_GRAPH");
+    return v && atoi(v) == 0;
+  }();
+  return !off && !tracer().on;
+}
 
 cudaError_t Multigrid::solve_async(const double* E_old, double* E_new, double rtol, int max_cycles, int nu1,
                                    int nu2, bool fmg_start, SolveStats* st, const SolveOut** out, cudaStream_t s) {

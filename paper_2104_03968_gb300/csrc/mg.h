@@ -115,7 +115,16 @@ class Multigrid {
 
   GridDev g_{};
   int precision_ = -1;
-  std::vector<std::array<double, 6>> tuned_;  // (rtol, fmg_start, nu1, nu2, coarser nu1, nu2)
+  // sweep-count tuning per (rtol, start): each candidate's solve time summed over the first
+  // kTuneRounds solves of the configuration (infinite once it failed to converge), then settled
+  static constexpr int kTuneCands = 10, kTuneRounds = 3;
+  struct Tuned {
+    double rtol;
+    bool fmg;
+    int rounds, best;
+    float sum[kTuneCands];
+  };
+  std::vector<Tuned> tuned_;
   int nuc1_ = 2, nuc2_ = 2;                   // sweep counts of the levels below the finest
   struct GraphEntry {
     int l, nu1, nu2, zero;

@@ -13,7 +13,11 @@
 // cell around it) and the second colour on plane s - 1 (on the tile), so that every value the
 // second colour reads is final.  Planes of x and ic with a two-cell halo, and of r with a one-cell
 // halo, stay in a ring of shared-memory slots; 16-byte asynchronous copies (cp.async), two per
-// thread per staged plane, fetch the planes of the next two steps while step s computes.  The
+// thread per staged plane, fetch the planes of the next step while step s computes.  With one step
+// of prefetch a block needs 73 KB of shared memory, so three blocks (24 warps) share an SM: more
+// warps to hide the shared-memory and reciprocal latencies measured faster than a second step of
+// prefetch at two blocks per SM.  A colour pass computes all its cells' values before it stores
+// any, so the loads of one cell do not wait behind the store of another.  The
 // cells around the tile are computed again by the neighbouring blocks from the same inputs, so the
 // sweep reads x from one array and writes another: no block waits for another.  Periodic faces
 // read the wrapped halo; Dirichlet, Neumann and linear-extrapolation faces take the interior cell's
@@ -34,7 +38,7 @@ constexpr int P = TX + 8;              // row pitch in shared memory: 4 cells ea
 constexpr int RXR = TY + 4;            // rows of a staged x or ic plane (2 halo rows each side)
 constexpr int RRR = TY + 2;            // rows of a staged r plane (1 halo row each side)
 constexpr int CH = P / 4;              // 16-byte chunks per staged row
-constexpr int NXS = 6, NRS = 4;        // ring slots: x and ic planes s-2 .. s+3, r planes s-1 .. s+2
+constexpr int NXS = 5, NRS = 3;        // ring slots: x and ic planes s-2 .. s+2, r planes s-1 .. s+1
 constexpr int XPL = RXR * P, RPL = RRR * P;
 constexpr int kThreads = 256;
 constexpr int kXChunks = RXR * CH, kRChunks = RRR * CH;  // 360, 324: at most two per thread each
@@ -49,8 +53,6 @@ __device__ __forceinline__ void cp16(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-// all but the most recent group complete
-__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // one hardware reciprocal (rcp.approx, about 1 ulp; 0 for inf): the smoother's arithmetic is FP32
 __device__ __forceinline__ float rcp_fast(float x) {
@@ -129,34 +131,31 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
 }
 
 // A thread's share of a tile.
-//  - Two tile tasks: task u of warp w takes rows 2 ((w + 8u) / 2) and 2 ((w + 8u) / 2) + 1, half
-//    (w + 8u) % 2 of each, lanes 0-15 the colour's 16 cells of the first row and lanes 16-31 those
-//    of the second (with the pitch at 8 mod 32 the two halves fall on disjoint banks).  The
-//    colour's cells of a row alternate parity with the plane: o0[u] is the staged offset for parity
-//    0 (column 2m), o0[u] + 1 for parity 1.
+//  - Two tile cells per colour pass: warp w, lanes 0-15 take row 2 (w / 2) and lanes 16-31 row
+//    2 (w / 2) + 1, half w % 2 of the row's 32 cells of the colour; the second cell is 8 rows below
+//    the first (with the pitch at 8 mod 32 the two half-warps fall on disjoint banks).  The
+//    colour's cells of a row alternate parity with the plane: o0 is the first cell's staged offset
+//    for parity 0 (column 2m), o0 + 1 for parity 1.
 //  - Threads 0..81 each own one ring cell of either parity class (iu + ju even or odd; 82 each:
 //    33 in the row below the tile, 33 above, 8 in each side column), so a colour pass on the ring
 //    occupies the first three warps only.
 //  - Each thread copies up to two 16-byte chunks of a staged x and ic plane and of an r plane:
-//    xg / rg are their in-plane source offsets (-1: none), xo / ro their offsets in a slot.  A chunk
-//    beyond a periodic face wraps; beyond a non-periodic one it is clamped into the grid (the
-//    boundary faces do not read it).
+//    xg / rg are their in-plane source offsets (-1: none), xo their offset in a slot (the same for
+//    the x and r chunks of one thread).  A chunk beyond a periodic face wraps; beyond a
+//    non-periodic one it is clamped into the grid (the boundary faces do not read it).
+// The share is kept small: with three blocks per SM a thread has at most 85 registers.
 struct Share {
-  int o0[2], row[2];
-  int ring_o[2], ring_i[2], ring_j[2];  // per parity class: staged offset, wrapped global (i, j)
-  int xg[2], xo[2], rg[2], ro[2];
+  int o0, row0;      // the first tile cell (parity-0 column); the second is 8 rows below
+  int ring_o[2];     // per parity class: staged offset
+  int xg[2], xo[2], rg[2];  // r chunks share the x chunks' slot offsets
 };
 
 __device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A, bool xper, bool yper) {
   Share sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int task = warp + 8 * u;
-    sh.row[u] = 2 * (task >> 1) + (lane >> 4);        // 0 .. 15
-    const int m = 16 * (task & 1) + (lane & 15);      // colour cell within the row, 0 .. 31
-    sh.o0[u] = (2 + sh.row[u]) * P + 4 + 2 * m;
-  }
+  sh.row0 = 2 * (warp >> 1) + (lane >> 4);        // 0 .. 7
+  const int m = 16 * (warp & 1) + (lane & 15);     // colour cell within the row, 0 .. 31
+  sh.o0 = (2 + sh.row0) * P + 4 + 2 * m;
   // ring: with i0 and j0 even, the staged position (ii, jj) has parity (iu + ju) & 1 = (ii + jj) & 1
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -167,8 +166,6 @@ __device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A
     else if (q < TX + 2 + TY / 2) ii = 3, jj = 3 - c + 2 * (q - (TX + 2));       // column i0 - 1
     else ii = P - 4, jj = 2 + c + 2 * (q - (TX + 2 + TY / 2));                   // column i0 + 64
     sh.ring_o[c] = jj * P + ii;
-    sh.ring_i[c] = wrap_or_clamp(i0 + ii - 4, A.nx, xper);
-    sh.ring_j[c] = wrap_or_clamp(j0 + jj - 2, A.ny, yper);
   }
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -183,8 +180,9 @@ __device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A
     };
     if (tt < kXChunks) chunk(tt, -2, sh.xg[c], sh.xo[c]);
     else sh.xg[c] = -1, sh.xo[c] = 0;
-    if (tt < kRChunks) chunk(tt, -1, sh.rg[c], sh.ro[c]);
-    else sh.rg[c] = -1, sh.ro[c] = 0;
+    int ro;
+    if (tt < kRChunks) chunk(tt, -1, sh.rg[c], ro);
+    else sh.rg[c] = -1;
   }
   return sh;
 }
@@ -194,23 +192,37 @@ __device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A
 template <bool NOX, bool RING, bool BND>
 __device__ __forceinline__ void colour_pass(const Sweep3dArgs& A, const float tr[3], const Planes& S, float* xs,
                                             const Share& sh, int col, int i0, int j0, int kw) {
+  float v[2];
+  int oo[2];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    const int j = j0 + sh.row[u];
-    const int o = sh.o0[u] + ((col + j + kw) & 1);
+    const int j = j0 + sh.row0 + 8 * u;
+    const int q = (col + j + kw) & 1;  // the same for both cells (8 rows apart)
+    const int o = sh.o0 + 8 * P * u + q;
     const float rv = S.r[o - P];
-    xs[o] = update<NOX, BND>(A, tr, S, o, rv, i0 + (o - (2 + sh.row[u]) * P) - 4, j, kw);
+    oo[u] = o;
+    v[u] = update<NOX, BND>(A, tr, S, o, rv, i0 + (sh.o0 - (2 + sh.row0) * P) - 4 + q, j, kw);
   }
+  float vr = 0.f;
+  int orr = 0;
   if (RING && threadIdx.x < kRingHalf) {
     const bool c = ((col + kw) & 1) != 0;  // the class whose cells have this colour on plane kw
-    const int o = c ? sh.ring_o[1] : sh.ring_o[0];
-    xs[o] = update<NOX, BND>(A, tr, S, o, S.r[o - P], c ? sh.ring_i[1] : sh.ring_i[0],
-                             c ? sh.ring_j[1] : sh.ring_j[0], kw);
+    orr = c ? sh.ring_o[1] : sh.ring_o[0];
+    int ri = 0, rj = 0;
+    if (BND) {  // the ring cell's global (i, j), wrapped on periodic axes
+      const int jj = orr / P, ii = orr - jj * P;
+      ri = wrap_or_clamp(i0 + ii - 4, A.nx, A.bc[0] == FLD_BC_PERIODIC);
+      rj = wrap_or_clamp(j0 + jj - 2, A.ny, A.bc[2] == FLD_BC_PERIODIC);
+    }
+    vr = update<NOX, BND>(A, tr, S, orr, S.r[orr - P], ri, rj, kw);
   }
+  xs[oo[0]] = v[0];
+  xs[oo[1]] = v[1];
+  if (RING && threadIdx.x < kRingHalf) xs[orr] = vr;
 }
 
 template <bool ZERO, bool UPDATE>
-__global__ void __launch_bounds__(kThreads, 2) k_sweep3d(Sweep3dArgs A, int lz, int tiles_x, int tiles_y,
+__global__ void __launch_bounds__(kThreads, 3) k_sweep3d(Sweep3dArgs A, int lz, int tiles_x, int tiles_y,
                                                          int nzchunk) {
   extern __shared__ __align__(16) float sm[];
   float* Xs = sm;
@@ -253,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep3d(Sweep3dArgs A, int lz, 
       float* rs = Rs + slot * RPL;
 #pragma unroll
       for (int c = 0; c < 2; ++c)
-        if (sh.rg[c] >= 0) cp16(rs + sh.ro[c], A.r + pb + sh.rg[c]);
+        if (sh.rg[c] >= 0) cp16(rs + sh.xo[c], A.r + pb + sh.rg[c]);
     };
     auto store = [&](int k, int slot) {
       // the tile of plane k, both colours final: one float4 per thread
@@ -280,21 +292,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep3d(Sweep3dArgs A, int lz, 
     load_xc(k0, 2);
     load_r(k0 - 1, 0);
     cp_commit();
-    // the planes of step k0 (in flight while step k0 - 1 computes)
-    load_xc(k0 + 1, 3);
-    load_r(k0, 1);
-    cp_commit();
-    cp_wait_prev();
+    cp_wait_all();
     __syncthreads();
     auto wrap_slot = [](int v, int n) { return v >= n ? v - n : (v < 0 ? v + n : v); };
     int xs0 = 1, rs0 = 0;  // slots of plane s
     for (int s = k0 - 1; s <= k1; ++s) {
       const int xm2 = wrap_slot(xs0 - 2, NXS), xm1 = wrap_slot(xs0 - 1, NXS), xp1 = wrap_slot(xs0 + 1, NXS);
-      const int xp3 = wrap_slot(xs0 + 3, NXS);
-      const int rm1 = wrap_slot(rs0 - 1, NRS), rp2 = wrap_slot(rs0 + 2, NRS);
-      // the planes of step s + 2; those of step s + 1 are still in flight
-      if (s + 3 <= k1 + 1) load_xc(s + 3, xp3);
-      if (s + 2 <= k1) load_r(s + 2, rp2);
+      const int xp2 = wrap_slot(xs0 + 2, NXS);
+      const int rm1 = wrap_slot(rs0 - 1, NRS), rp1 = wrap_slot(rs0 + 1, NRS);
+      // the planes step s + 1 adds (x and ic of plane s + 2, r of plane s + 1), in flight while
+      // step s computes
+      if (s + 2 <= k1 + 1) load_xc(s + 2, xp2);
+      if (s + 1 <= k1) load_r(s + 1, rp1);
       cp_commit();
       // first colour on plane s, tile and ring (in place: it reads only second-colour cells)
       if (valid(s)) {
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep3d(Sweep3dArgs A, int lz, 
         else
           colour_pass<false, false, false>(A, tr, S, Xs + xm1 * XPL, sh, c1, i0, j0, kw);
       }
-      cp_wait_prev();  // the planes of step s + 1 have landed
+      cp_wait_all();  // the planes of step s + 1 have landed
       __syncthreads();
       xs0 = xp1;
       rs0 = wrap_slot(rs0 + 1, NRS);
