@@ -16,8 +16,9 @@
 // drop out: their blocks return at once.  The loop is bounded: every grid stops after its
 // max_cycles, and the check kernel ends the loop after the largest max_cycles + 1 passes.
 //
-// Autotuning: on the first call for a batch shape, each (nu1, nu2, tile) candidate runs the
-// step on scratch copies of the state; the fastest is kept for that shape.
+// Autotuning: on the first three calls for a batch shape, each (nu1, nu2, tile) candidate runs
+// the step on scratch copies of the state; the candidate with the least summed time is kept for
+// that shape (the first step alone is not typical of the ones that follow).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -794,7 +795,10 @@ struct BatchedSolver::Impl {
   }
   cudaStream_t cap = nullptr, body = nullptr;
   int nu1 = 2, nu2 = 2;
-  bool tuned = false;
+  // autotune rounds done for this shape and each candidate's summed step time
+  static constexpr int kCands = 9, kTuneRounds = 3;
+  int tune_rounds = 0;
+  float tune_sum[kCands] = {};
   // autotune scratch
   double* scratch = nullptr;
   size_t scratch_cells = 0;
@@ -848,7 +852,8 @@ cudaError_t BatchedSolver::Impl::configure(int n, const fld_grid* grids, const f
   sig = s;
   ng = n;
   precision = params[0].precision;
-  tuned = false;
+  tune_rounds = 0;
+  for (float& t : tune_sum) t = 0.0f;
   dims.assign(n, {});
   gd.resize(n);
   maxlev = 0;
@@ -1258,8 +1263,9 @@ fld_status BatchedSolver::run(int ngrids, const fld_grid* grids, const fld_param
     GridDev d = grid_dev(grids[g]);
     I.fine_h[g].g = d;
   }
-  if (fresh) {
-    // autotune (nu1, nu2, tile) on scratch copies of the state, then keep the fastest
+  if (fresh || I.tune_rounds < Impl::kTuneRounds) {
+    // autotune (nu1, nu2, tile) on scratch copies of the state, then keep the candidate with the
+    // least time summed over the rounds so far
     size_t cells = 0;
     for (int g = 0; g < ngrids; ++g) cells += (size_t)I.gd[g].ncell;
     if (cells > I.scratch_cells) {
@@ -1278,13 +1284,14 @@ fld_status BatchedSolver::run(int ngrids, const fld_grid* grids, const fld_param
     struct Cand {
       int nu1, nu2, tile;
     };
-    const Cand cands[] = {{2, 2, 2048}, {1, 1, 2048}, {3, 3, 2048}, {2, 2, 8192}, {1, 1, 8192}};
-    float best = 1e30f;
-    Cand pick = cands[0];
+    const Cand cands[Impl::kCands] = {{2, 2, 2048}, {1, 1, 2048}, {3, 3, 2048}, {4, 4, 2048}, {4, 2, 2048},
+                                      {2, 2, 8192}, {3, 3, 8192}, {4, 4, 8192}, {1, 1, 8192}};
+    float ms_k[Impl::kCands] = {};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (const Cand& c : cands) {
+    for (int k = 0; k < Impl::kCands; ++k) {
+      const Cand& c = cands[k];
       if ((e = I.build_tiles(c.tile)) != cudaSuccess) break;
       if ((e = I.upload(params, dt, rho, se.data(), sE.data(), s)) != cudaSuccess) break;
       if ((e = I.build_graph_any(c.nu1, c.nu2)) != cudaSuccess) break;
@@ -1303,14 +1310,18 @@ fld_status BatchedSolver::run(int ngrids, const fld_grid* grids, const fld_param
         cudaEventElapsedTime(&ms, e0, e1);
       }
       if (e != cudaSuccess) break;
-      if (ms < best) {
-        best = ms;
-        pick = c;
-      }
+      ms_k[k] = ms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_err(e, "autotune");
+    int best = 0;
+    for (int k = 0; k < Impl::kCands; ++k) {
+      I.tune_sum[k] += ms_k[k];
+      if (I.tune_sum[k] < I.tune_sum[best]) best = k;
+    }
+    I.tune_rounds += 1;
+    const Cand pick = cands[best];
     if ((e = I.build_tiles(pick.tile)) != cudaSuccess) return cuda_err(e, "tiles");
     if ((e = I.upload(params, dt, rho, eps, E, s)) != cudaSuccess) return cuda_err(e, "upload");
     if ((e = I.build_graph_any(pick.nu1, pick.nu2)) != cudaSuccess) return cuda_err(e, "graph");
