@@ -1408,7 +1408,8 @@ cudaError_t Multigrid::autotune(const double* E_old, double rtol, int max_cycles
                                 cudaStream_t s) {
   // (finest pre, finest post, coarser pre, coarser post)
   static const int cand[kTuneCands][4] = {{2, 2, 2, 2}, {3, 3, 3, 3}, {4, 4, 2, 1}, {5, 3, 2, 1}, {4, 4, 2, 2},
-                                          {3, 3, 2, 1}, {4, 2, 2, 1}, {6, 4, 2, 1}, {2, 1, 2, 1}, {1, 1, 1, 1}};
+                                          {3, 3, 2, 1}, {4, 2, 2, 1}, {6, 4, 2, 1}, {2, 1, 2, 1}, {1, 1, 1, 1},
+                                          {6, 6, 2, 2}, {5, 5, 3, 3}};
   size_t ti = tuned_.size();
   for (size_t q = 0; q < tuned_.size(); ++q)
     if (tuned_[q].rtol == rtol && tuned_[q].fmg == fmg_start) ti = q;

@@ -117,7 +117,7 @@ class Multigrid {
   int precision_ = -1;
   // sweep-count tuning per (rtol, start): each candidate's solve time summed over the first
   // kTuneRounds solves of the configuration (infinite once it failed to converge), then settled
-  static constexpr int kTuneCands = 10, kTuneRounds = 3;
+  static constexpr int kTuneCands = 12, kTuneRounds = 3;
   struct Tuned {
     double rtol;
     bool fmg;
