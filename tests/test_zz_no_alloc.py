@@ -27,12 +27,13 @@ def _relerr(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse"])
-def test_static_entry_matches_context_entry_twice(order):
+@pytest.mark.parametrize("order", ["diffuse_then_exchange", "exchange_then_diffuse", "imex_midpoint"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_static_entry_matches_context_entry_twice(order, precision):
     from paper_2104_03968_gb300 import fld
     ctx = fld.Context(0)
     case = lp_dt.columns_dt(inputs.wind_columns(ncol=37, ncell=2048, seed=6))
-    p = dict(case["phys"], order=order)
+    p = dict(case["phys"], order=order, precision=precision)
     bc = tuple(case["bc"])
     # reference: the context entry point, two steps in a row
     eps_r, E_r = _dev(case["eps"]), _dev(case["E"])
@@ -52,6 +53,30 @@ def test_static_entry_matches_context_entry_twice(order):
     assert _relerr(E_s, E_r) < TOL
     assert _relerr(eps_s, eps_r) < TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_static_entry_matches_oracle(precision):
+    """One step of the allocation-free entry point against the oracle's column step, column by
+    column (the paper's order: exchange, then the implicit diffusion)."""
+    import oracle
+    from paper_2104_03968_gb300 import fld
+    case = lp_dt.columns_dt(inputs.wind_columns(ncol=5, ncell=2048, seed=7))
+    order = "exchange_then_diffuse"
+    p = dict(case["phys"], order=order, precision=precision)
+    bc = tuple(case["bc"])
+    rf, vlo, vhi, dt = (_dev(case[k]) for k in ("r_faces", "bc_lo", "bc_hi", "dt"))
+    eps, E = _dev(case["eps"]), _dev(case["E"])
+    info = fld.columns_step_static(rf, "spherical", bc, vlo, vhi, p, dt, _dev(case["rho"]), eps, E)
+    torch.cuda.synchronize()
+    assert info["status"] == 0
+    col = {"r_faces": case["r_faces"], "geometry": "spherical", "bc": case["bc"]}
+    for j in range(5):
+        e_o, E_o, _ = oracle.column_step(col, p, case["dt"][j], case["rho"][j], case["eps"][j], case["E"][j],
+                                         case["bc_lo"][j], case["bc_hi"][j], order=order)
+        got_E, got_e = E[j].cpu().numpy(), eps[j].cpu().numpy()
+        assert float(np.abs(got_E - E_o).max() / np.abs(E_o).max()) < TOL
+        assert float(np.abs(got_e - e_o).max() / np.abs(e_o).max()) < TOL
 
 
 def test_static_entry_rejects_oversized_columns():
