@@ -316,8 +316,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep3d(Sweep3dArgs A, int lz, 
           colour_pass<ZERO, true, false>(A, tr, S, Xs + xs0 * XPL, sh, A.c0, i0, j0, kw);
       }
       if (s - 2 >= k0) store(s - 2, xm2);
-      __syncthreads();
-      // second colour on plane s - 1 (tile): its neighbours of the first colour are final
+      // second colour on plane s - 1 (tile): its neighbours of the first colour are final.  No
+      // barrier is needed between the two passes: a thread's second-colour cell on plane s - 1 and
+      // its first-colour cell on plane s share their (i, j), so the one value the second pass reads
+      // from this step (the z+ neighbour) and the one the first pass reads from what the second
+      // overwrites (the z- neighbour) are the thread's own; everything else either pass reads was
+      // final at the last barrier, and the ring's second-colour cells are never written.
       if (s - 1 >= k0 && s - 1 < k1) {
         const Planes S{Xs + xm1 * XPL, Cs + xm1 * XPL, Xs + xm2 * XPL, Cs + xm2 * XPL,
                        Xs + xs0 * XPL, Cs + xs0 * XPL, Rs + rm1 * RPL};
