@@ -208,8 +208,10 @@ FLD_API fld_status fld_diffuse_aniso(fld_ctx* ctx, const fld_grid* grid, const f
    x fastest; x_in NULL means x = 0 before the sweep; x_out must not overlap x_in.  The cells with
    (i + j + k) % 2 == first_colour are updated first, then the others from their new values.
    Supported grids: ndim 3, n[0] a multiple of 64, n[1] a multiple of 16, n[2] even and >= 4,
-   fewer than 2^31 cells (FLD_ERR_UNSUPPORTED otherwise).  Uses the context's scratch (allocated
-   on first use) for an FP32 copy of dt D / dx_0^2.  Asynchronous. */
+   fewer than 2^31 cells (FLD_ERR_UNSUPPORTED otherwise); every array starts on a 16-byte boundary.
+   Uses the context's scratch (allocated on first use) for an FP32 copy of dt D / dx_0^2.
+   Synchronises the stream: FLD_ERR_DEVICE_TIMEOUT if a wait of the kernel for its staged planes
+   ran out of its bound (x_out is then unspecified). */
 FLD_API fld_status fld_smooth_sweep(fld_ctx* ctx, const fld_grid* grid, double dt, const double* D_cell,
                                     const float* r, const float* x_in, float* x_out, int first_colour,
                                     void* stream);

@@ -505,8 +505,14 @@ fld_status fld_smooth_sweep(fld_ctx* ctx, const fld_grid* grid, double dt, const
   a.xout = x_out;
   a.x64 = nullptr;
   a.c0 = first_colour;
+  a.err = ctx->d_status;  // set by a wait for staged planes that ran out of its bound
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = launch_sweep3d(a, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_info + 2, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_smooth_sweep launch");
+  if (ctx->h_info[2]) return fail(ctx, FLD_ERR_DEVICE_TIMEOUT, "fld_smooth_sweep: staged planes did not arrive in time");
   return FLD_OK;
 }
 

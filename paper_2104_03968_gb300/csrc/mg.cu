@@ -811,6 +811,7 @@ cudaError_t Multigrid::tiled_sweep(bool zero, int c0, double* x64, cudaStream_t 
   a.xout = (float*)lv_[0].tmp;
   a.x64 = x64;
   a.c0 = c0;
+  a.err = wave_ctl_;  // the solve loop turns a bounded wait that ran out into FLD_ERR_DEVICE_TIMEOUT
   cudaError_t e = launch_sweep3d(a, s);
   std::swap(lv_[0].x, lv_[0].tmp);  // the iterate now lives in the other array
   return e;

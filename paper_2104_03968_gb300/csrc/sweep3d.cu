@@ -8,23 +8,46 @@
 // out (16 bytes per cell) instead of r, three face arrays and x (24).  A cell with D = 0 has
 // ic = inf and its faces weigh 0.
 //
-// Blocking: a block owns a 64 x 16 tile of the x-y plane and a run of z-planes (a z-chunk), and
-// marches through them.  At step s it updates the first colour on plane s (on the tile and one
-// cell around it) and the second colour on plane s - 1 (on the tile), so that every value the
-// second colour reads is final.  Planes of x and ic with a two-cell halo, and of r with a one-cell
-// halo, stay in a ring of shared-memory slots; 16-byte asynchronous copies (cp.async), two per
-// thread per staged plane, fetch the planes of the next step while step s computes.  With one step
-// of prefetch a block needs 73 KB of shared memory, so three blocks (24 warps) share an SM: more
-// warps to hide the shared-memory and reciprocal latencies measured faster than a second step of
-// prefetch at two blocks per SM.  A colour pass computes all its cells' values before it stores
-// any, so the loads of one cell do not wait behind the store of another.  The
-// cells around the tile are computed again by the neighbouring blocks from the same inputs, so the
-// sweep reads x from one array and writes another: no block waits for another.  Periodic faces
-// read the wrapped halo; Dirichlet, Neumann and linear-extrapolation faces take the interior cell's
-// coefficient, as in the FP64 operator.  Everything a thread needs for its cells (staged offsets,
-// its chunks to copy, its ring cells) is worked out once per tile, so the loop over planes spends
-// its instructions on the cells.
+// Blocking: a block of 128 threads owns a 64 x 16 tile of the x-y plane and a run of z-planes (a
+// z-chunk), and marches through them.  At step s it updates the first colour on plane s (on the
+// tile and a one-cell ring around it) and the second colour on plane s - 1 (on the tile), so that
+// every value the second colour reads is final.
+//
+// Each thread owns a patch of 2 x 4 cells (two rows, four cells along x) at a fixed (i, j) and
+// keeps the patch's x and ic on planes s - 2 .. s + 1 in registers, so the neighbours along z,
+// along the strip and across the patch's two rows never go through shared memory.  A 16-byte
+// shared load brings the row above or below the patch, and the cells beyond the strip's ends come
+// from the neighbouring lane by a warp shuffle (from shared memory at the tile's border).  The
+// colours occupy alternate cells, and the second colour's cells on plane s - 1 sit at the same
+// patch positions as the first colour's on plane s; with z-chunks that start on even planes the
+// position class of each step of the plane loop (unrolled over the four register slots) and of
+// each colour order is fixed at compile time, so every register index is static.
+//
+// Shared memory holds four slots of staged x and ic planes (two-cell halo) and two of r planes
+// (one-cell halo; the second colour keeps the r of its cells in registers from the step before),
+// 57 KB per block, so four blocks share an SM within its registers (at most 128 per thread).
+// The planes are fetched one step ahead by tensor-memory-accelerator (TMA) box loads: one thread
+// issues one 72 x 20 (x, ic) or 72 x 18 (r) box per staged plane, completing on an mbarrier that
+// every thread waits on, with an iteration bound, at the end of the step.  Box
+// cells beyond a non-periodic face arrive as zeros and are only ever read by boundary faces, which
+// ignore them.  A box does not wrap, so tiles whose halo crosses a periodic face fetch their
+// planes with 16-byte asynchronous copies (cp.async) from the wrapped addresses instead.  After its
+// first-colour pass a thread writes its patch back to the plane's slot, where the next step's
+// second colour reads it; second-colour values go from registers straight to global memory.  The
+// ring's first-colour cells (82 per plane, threads 0..81) are computed from the slots with the same
+// function and operand order as the tile's cells, so they equal the neighbouring blocks' values
+// bit for bit, and the sweep reads x from one array and writes another: no block waits for another.
+// Periodic faces read the wrapped halo; Dirichlet, Neumann and linear-extrapolation faces take the
+// interior cell's coefficient, as in the FP64 operator, with the face terms summed in the same
+// order as on interior cells (grids with such faces run an instantiation that checks every cell).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 
 #include "fld_common.cuh"
 #include "sweep3d.h"
@@ -38,21 +61,63 @@ constexpr int P = TX + 8;              // row pitch in shared memory: 4 cells ea
 constexpr int RXR = TY + 4;            // rows of a staged x or ic plane (2 halo rows each side)
 constexpr int RRR = TY + 2;            // rows of a staged r plane (1 halo row each side)
 constexpr int CH = P / 4;              // 16-byte chunks per staged row
-constexpr int NXS = 5, NRS = 3;        // ring slots: x and ic planes s-2 .. s+2, r planes s-1 .. s+1
+constexpr int NS = 4;                  // slots: planes s - 1 .. s + 2 (s - 2 lives in registers only)
 constexpr int XPL = RXR * P, RPL = RRR * P;
-constexpr int kThreads = 256;
-constexpr int kXChunks = RXR * CH, kRChunks = RRR * CH;  // 360, 324: at most two per thread each
+constexpr int RPS = 1312;              // r slot stride: 128-byte aligned slots for the TMA
+constexpr int kThreads = 128;
+constexpr int kXChunks = RXR * CH, kRChunks = RRR * CH;  // 360, 324: at most three per thread each
 constexpr int kRingHalf = TX + 2 + TY;  // 82 ring cells of each parity around the tile
-constexpr size_t kSmemBytes = (size_t)(2 * NXS * XPL + NRS * RPL) * sizeof(float);
-static_assert(P % 32 == 8, "the two-row lane mapping is conflict-free for a pitch of 8 mod 32");
-static_assert(kRingHalf <= kThreads && kXChunks <= 2 * kThreads && kRChunks <= 2 * kThreads, "thread shares");
+constexpr int NR = 2;                  // r slots: planes s and s + 1 (the second colour keeps its r in registers)
+constexpr size_t kBarOffset = (size_t)(2 * NS * XPL + NR * RPS) * sizeof(float);
+constexpr size_t kSmemBytes = kBarOffset + 16;  // slots, then one mbarrier
+static_assert((XPL * 4) % 128 == 0 && (RPS * 4) % 128 == 0 && RPS >= RPL, "128-byte aligned TMA slots");
+static_assert(kRingHalf <= kThreads && kXChunks <= 3 * kThreads && kRChunks <= 3 * kThreads, "thread shares");
+static_assert(kThreads * 8 == TX * TY, "one 2 x 4 patch per thread");
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void cp16(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// the slots' generic-proxy accesses (loads, first-colour stores) before later TMA writes to them
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one arrival that also announces the bytes the step's TMA copies will deliver (0: none)
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// wait for the phase of the given parity to complete; false after the iteration bound
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// TMA box load of the map's box at (x, y, z) into dst, completing on bar
+__device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
 
 // one hardware reciprocal (rcp.approx, about 1 ulp; 0 for inf): the smoother's arithmetic is FP32
 __device__ __forceinline__ float rcp_fast(float x) {
@@ -61,68 +126,65 @@ __device__ __forceinline__ float rcp_fast(float x) {
   return y;
 }
 
-// Staged planes around the cell's plane: x and ic of the plane, below and above; r of the plane.
-struct Planes {
-  const float* x;
-  const float* c;
-  const float* xm;
-  const float* cm;
-  const float* xp;
-  const float* cp;
-  const float* r;  // indexed like x minus one row
-};
-
-// One face of a cell that may lie on a non-periodic face: interior and periodic faces pair the
-// cell with the one across (x xa, reciprocal coefficient ia); a Dirichlet face adds the cell's
-// own weight to the diagonal only; a Neumann face adds nothing; a linear-extrapolation face
-// (ghost 2 x_c - x_m) subtracts w x_m from the sum and w from the diagonal.
-__device__ __forceinline__ void face_b(bool inside, int bc, float ic, float ia, float xa, float xm, float ra,
-                                       float& a, float& d) {
-  if (inside || bc == FLD_BC_PERIODIC) {
-    const float w = 2.0f * ra * rcp_fast(ic + ia);
-    a = fmaf(w, xa, a);
-    d += w;
-  } else if (bc == FLD_BC_DIRICHLET) {
-    d += ra * rcp_fast(ic);
-  } else if (bc == FLD_BC_CONTINUOUS) {
-    const float w = ra * rcp_fast(ic);
-    a = fmaf(-w, xm, a);
-    d -= w;
-  }
+__device__ __forceinline__ void lds4(float* d, const float* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  d[0] = v.x, d[1] = v.y, d[2] = v.z, d[3] = v.w;
+}
+__device__ __forceinline__ void sts4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// New value of the cell at staged offset o with right-hand side rv.  NOX: x is zero everywhere
-// (the first colour of a sweep from zero).  BND: the cell may lie on a non-periodic face, so the
-// face kinds are checked at its global (i, j, k) (wrapped on periodic axes); tr = 2 ra.
-template <bool NOX, bool BND>
-__device__ __forceinline__ float update(const Sweep3dArgs& A, const float tr[3], const Planes& S, int o, float rv,
-                                        int i, int j, int k) {
-  const float ic = S.c[o];
-  float a = rv;
-  float d = 1.0f;
-  if (!BND) {
-    const float w0 = tr[0] * rcp_fast(ic + S.c[o - 1]), w1 = tr[0] * rcp_fast(ic + S.c[o + 1]);
-    const float w2 = tr[1] * rcp_fast(ic + S.c[o - P]), w3 = tr[1] * rcp_fast(ic + S.c[o + P]);
-    const float w4 = tr[2] * rcp_fast(ic + S.cm[o]), w5 = tr[2] * rcp_fast(ic + S.cp[o]);
-    d += ((w0 + w1) + (w2 + w3)) + (w4 + w5);
-    if (!NOX) {
-      a = fmaf(w0, S.x[o - 1], a);
-      a = fmaf(w1, S.x[o + 1], a);
-      a = fmaf(w2, S.x[o - P], a);
-      a = fmaf(w3, S.x[o + P], a);
-      a = fmaf(w4, S.xm[o], a);
-      a = fmaf(w5, S.xp[o], a);
-    }
-  } else {
-    const float z = 0.0f;
-    face_b(i > 0, A.bc[0], ic, S.c[o - 1], NOX ? z : S.x[o - 1], NOX ? z : S.x[o + 1], A.ra[0], a, d);
-    face_b(i < A.nx - 1, A.bc[1], ic, S.c[o + 1], NOX ? z : S.x[o + 1], NOX ? z : S.x[o - 1], A.ra[0], a, d);
-    face_b(j > 0, A.bc[2], ic, S.c[o - P], NOX ? z : S.x[o - P], NOX ? z : S.x[o + P], A.ra[1], a, d);
-    face_b(j < A.ny - 1, A.bc[3], ic, S.c[o + P], NOX ? z : S.x[o + P], NOX ? z : S.x[o - P], A.ra[1], a, d);
-    face_b(k > 0, A.bc[4], ic, S.cm[o], NOX ? z : S.xm[o], NOX ? z : S.xp[o], A.ra[2], a, d);
-    face_b(k < A.nz - 1, A.bc[5], ic, S.cp[o], NOX ? z : S.xp[o], NOX ? z : S.xm[o], A.ra[2], a, d);
+// One face's contribution: returns its diagonal term and adds its neighbour term to a.  Interior
+// and periodic faces pair the cell (reciprocal coefficient ic) with the one across (ia, value xa);
+// a Dirichlet face adds the cell's own weight to the diagonal only; a Neumann face adds nothing; a
+// linear-extrapolation face (ghost 2 x_c - x_m, xm the opposite neighbour) subtracts w x_m and w.
+template <bool NOX>
+__device__ __forceinline__ float face_term(bool pair, int bc, float t, float ra, float ic, float ia, float xa, float xm,
+                                           float& a) {
+  if (pair) {
+    const float w = t * rcp_fast(ic + ia);
+    if (!NOX) a = fmaf(w, xa, a);
+    return w;
   }
+  if (bc == FLD_BC_DIRICHLET) return ra * rcp_fast(ic);
+  if (bc == FLD_BC_CONTINUOUS) {
+    const float w = ra * rcp_fast(ic);
+    if (!NOX) a = fmaf(-w, xm, a);
+    return -w;
+  }
+  return 0.0f;
+}
+
+// New value of a cell from its right-hand side rv, its ic and its six neighbours' ic (cn) and x
+// (xn), faces ordered x-, x+, y-, y+, z-, z+.  NOX: x is zero everywhere (first colour of a sweep
+// from zero).  BND: bit f of bm marks face f as a non-periodic boundary face.  On a cell with no
+// boundary face both forms give the same bits.
+template <bool NOX, bool BND>
+__device__ __forceinline__ float cell(const Sweep3dArgs& A, const float tr[3], float rv, float ic, const float (&cn)[6],
+                                      const float (&xn)[6], unsigned bm) {
+  float a = rv, w[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (BND) {
+      w[f] = face_term<NOX>(!((bm >> f) & 1u), A.bc[f], tr[f >> 1], A.ra[f >> 1], ic, cn[f], xn[f], xn[f ^ 1], a);
+    } else {
+      w[f] = tr[f >> 1] * rcp_fast(ic + cn[f]);
+      if (!NOX) a = fmaf(w[f], xn[f], a);
+    }
+  }
+  const float d = 1.0f + (((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]));
   return a * rcp_fast(d);
+}
+
+__device__ __forceinline__ unsigned bnd_mask(const Sweep3dArgs& A, int i, int j, int k) {
+  unsigned m = 0u;
+  m |= (i == 0 && A.bc[0] != FLD_BC_PERIODIC) ? 1u : 0u;
+  m |= (i == A.nx - 1 && A.bc[1] != FLD_BC_PERIODIC) ? 2u : 0u;
+  m |= (j == 0 && A.bc[2] != FLD_BC_PERIODIC) ? 4u : 0u;
+  m |= (j == A.ny - 1 && A.bc[3] != FLD_BC_PERIODIC) ? 8u : 0u;
+  m |= (k == 0 && A.bc[4] != FLD_BC_PERIODIC) ? 16u : 0u;
+  m |= (k == A.nz - 1 && A.bc[5] != FLD_BC_PERIODIC) ? 32u : 0u;
+  return m;
 }
 
 __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
@@ -131,31 +193,23 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
 }
 
 // A thread's share of a tile.
-//  - Two tile cells per colour pass: warp w, lanes 0-15 take row 2 (w / 2) and lanes 16-31 row
-//    2 (w / 2) + 1, half w % 2 of the row's 32 cells of the colour; the second cell is 8 rows below
-//    the first (with the pitch at 8 mod 32 the two half-warps fall on disjoint banks).  The
-//    colour's cells of a row alternate parity with the plane: o0 is the first cell's staged offset
-//    for parity 0 (column 2m), o0 + 1 for parity 1.
+//  - Its patch: warp w, lanes 0-15 take rows 4 w and 4 w + 1, lanes 16-31 rows 4 w + 2 and
+//    4 w + 3; lane % 16 is the strip along x (four cells from column 4 (lane % 16)).  oA is the
+//    staged offset of the patch's first row in an x or ic slot (the second row: oA + P; r slots
+//    have one halo row fewer: oA - P).
 //  - Threads 0..81 each own one ring cell of either parity class (iu + ju even or odd; 82 each:
-//    33 in the row below the tile, 33 above, 8 in each side column), so a colour pass on the ring
-//    occupies the first three warps only.
-//  - Each thread copies up to two 16-byte chunks of a staged x and ic plane and of an r plane:
-//    xg / rg are their in-plane source offsets (-1: none), xo their offset in a slot (the same for
-//    the x and r chunks of one thread).  A chunk beyond a periodic face wraps; beyond a
-//    non-periodic one it is clamped into the grid (the boundary faces do not read it).
-// The share is kept small: with three blocks per SM a thread has at most 85 registers.
+//    33 in the row below the tile, 33 above, 8 in each side column).
 struct Share {
-  int o0, row0;      // the first tile cell (parity-0 column); the second is 8 rows below
-  int ring_o[2];     // per parity class: staged offset
-  int xg[2], xo[2], rg[2];  // r chunks share the x chunks' slot offsets
+  int oA, rowA, sx;
+  int ring_o[2];
 };
 
-__device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A, bool xper, bool yper) {
+__device__ __forceinline__ Share make_share() {
   Share sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
-  sh.row0 = 2 * (warp >> 1) + (lane >> 4);        // 0 .. 7
-  const int m = 16 * (warp & 1) + (lane & 15);     // colour cell within the row, 0 .. 31
-  sh.o0 = (2 + sh.row0) * P + 4 + 2 * m;
+  sh.rowA = 4 * warp + 2 * (lane >> 4);
+  sh.sx = lane & 15;
+  sh.oA = (2 + sh.rowA) * P + 4 + 4 * sh.sx;
   // ring: with i0 and j0 even, the staged position (ii, jj) has parity (iu + ju) & 1 = (ii + jj) & 1
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -167,9 +221,23 @@ __device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A
     else ii = P - 4, jj = 2 + c + 2 * (q - (TX + 2 + TY / 2));                   // column i0 + 64
     sh.ring_o[c] = jj * P + ii;
   }
+  return sh;
+}
+
+// cp.async staging of one tile (tiles whose halo wraps): each thread copies up to three 16-byte
+// chunks of a staged x and ic plane and of an r plane; xg / rg are their in-plane source offsets
+// (-1: none), xo their offsets in a slot (the same for the x and r chunks of one thread).  A chunk
+// beyond a periodic face wraps; beyond a non-periodic one it is clamped into the grid (the
+// boundary faces do not read it).
+struct Chunks {
+  int xg[3], xo[3], rg[3];
+};
+
+__device__ __forceinline__ Chunks make_chunks(int i0, int j0, const Sweep3dArgs& A, bool xper, bool yper) {
+  Chunks ch;
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int tt = t + c * kThreads;
+  for (int c = 0; c < 3; ++c) {
+    const int tt = threadIdx.x + c * kThreads;
     auto chunk = [&](int q, int jlo, int& g, int& o) {
       const int jj = q / CH, cc = q % CH;
       const int j = wrap_or_clamp(j0 + jlo + jj, A.ny, yper);
@@ -178,166 +246,349 @@ __device__ __forceinline__ Share make_share(int i0, int j0, const Sweep3dArgs& A
       g = j * A.nx + i;
       o = jj * P + 4 * cc;
     };
-    if (tt < kXChunks) chunk(tt, -2, sh.xg[c], sh.xo[c]);
-    else sh.xg[c] = -1, sh.xo[c] = 0;
+    if (tt < kXChunks) chunk(tt, -2, ch.xg[c], ch.xo[c]);
+    else ch.xg[c] = -1, ch.xo[c] = 0;
     int ro;
-    if (tt < kRChunks) chunk(tt, -1, sh.rg[c], ro);
-    else sh.rg[c] = -1;
+    if (tt < kRChunks) chunk(tt, -1, ch.rg[c], ro);
+    else ch.rg[c] = -1;
   }
-  return sh;
+  return ch;
 }
 
-// The cells of colour col on the tile of plane k (wrapped kw), and with RING on the ring around it
-// (a ring cell outside a non-periodic face is a ghost position: computed, never read).
-template <bool NOX, bool RING, bool BND>
-__device__ __forceinline__ void colour_pass(const Sweep3dArgs& A, const float tr[3], const Planes& S, float* xs,
-                                            const Share& sh, int col, int i0, int j0, int kw) {
-  float v[2];
-  int oo[2];
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int j = j0 + sh.row0 + 8 * u;
-    const int q = (col + j + kw) & 1;  // the same for both cells (8 rows apart)
-    const int o = sh.o0 + 8 * P * u + q;
-    const float rv = S.r[o - P];
-    oo[u] = o;
-    v[u] = update<NOX, BND>(A, tr, S, o, rv, i0 + (sh.o0 - (2 + sh.row0) * P) - 4 + q, j, kw);
+// Box maps of the staged arrays (x_in, ic: 72 x 20 x 1 boxes; r: 72 x 18 x 1), encoded on the host.
+struct Sweep3dMaps {
+  CUtensorMap x, c, r;
+};
+
+// One colour pass over a thread's patch on one plane: row A's cells at strip positions Q and
+// Q + 2, row B's at 1 - Q and 3 - Q.  xo/co: the plane's registers (row A 0..3, row B 4..7);
+// xm/cm, xp/cp: the planes below and above; xs, cs: the plane's slots (the rows above A and below
+// B, and the strip ends of the tile's border lanes); rs: its r slot.  The new values replace the
+// updated cells of xo.  Every x it reads is of the other colour, which this pass does not change.
+template <int Q, bool NOX, bool BND>
+__device__ __forceinline__ void patch_pass(const Sweep3dArgs& A, const float tr[3], const Share& sh, int i0, int j0,
+                                           int kw, const float* xs, const float* cs, const float (&ra)[4],
+                                           const float (&rb)[4], float (&xo)[8],
+                                           const float (&co)[8], const float (&xm)[8], const float (&cm)[8],
+                                           const float (&xp)[8], const float (&cp)[8]) {
+  const int oA = sh.oA, oB = oA + P;
+  float ca[4], cb[4], xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
+  lds4(ca, cs + oA - P);
+  lds4(cb, cs + oB + P);
+  if (!NOX) {
+    lds4(xa, xs + oA - P);
+    lds4(xb, xs + oB + P);
   }
-  float vr = 0.f;
-  int orr = 0;
-  if (RING && threadIdx.x < kRingHalf) {
-    const bool c = ((col + kw) & 1) != 0;  // the class whose cells have this colour on plane kw
-    orr = c ? sh.ring_o[1] : sh.ring_o[0];
-    int ri = 0, rj = 0;
-    if (BND) {  // the ring cell's global (i, j), wrapped on periodic axes
-      const int jj = orr / P, ii = orr - jj * P;
-      ri = wrap_or_clamp(i0 + ii - 4, A.nx, A.bc[0] == FLD_BC_PERIODIC);
-      rj = wrap_or_clamp(j0 + jj - 2, A.ny, A.bc[2] == FLD_BC_PERIODIC);
+  // Strip ends: row A needs its left neighbour for Q = 0 (right for Q = 1), row B the other side.
+  // The neighbouring strip belongs to the next lane of the 16-lane row group.
+  const unsigned full = 0xffffffffu;
+  float eAc, eBc, eAx = 0.f, eBx = 0.f;
+  if (Q == 0) {
+    eAc = __shfl_up_sync(full, co[3], 1, 16);
+    eBc = __shfl_down_sync(full, co[4], 1, 16);
+    if (!NOX) {
+      eAx = __shfl_up_sync(full, xo[3], 1, 16);
+      eBx = __shfl_down_sync(full, xo[4], 1, 16);
     }
-    vr = update<NOX, BND>(A, tr, S, orr, S.r[orr - P], ri, rj, kw);
+    if (sh.sx == 0) {
+      eAc = cs[oA - 1];
+      if (!NOX) eAx = xs[oA - 1];
+    }
+    if (sh.sx == 15) {
+      eBc = cs[oB + 4];
+      if (!NOX) eBx = xs[oB + 4];
+    }
+  } else {
+    eAc = __shfl_down_sync(full, co[0], 1, 16);
+    eBc = __shfl_up_sync(full, co[7], 1, 16);
+    if (!NOX) {
+      eAx = __shfl_down_sync(full, xo[0], 1, 16);
+      eBx = __shfl_up_sync(full, xo[7], 1, 16);
+    }
+    if (sh.sx == 15) {
+      eAc = cs[oA + 4];
+      if (!NOX) eAx = xs[oA + 4];
+    }
+    if (sh.sx == 0) {
+      eBc = cs[oB - 1];
+      if (!NOX) eBx = xs[oB - 1];
+    }
   }
-  xs[oo[0]] = v[0];
-  xs[oo[1]] = v[1];
-  if (RING && threadIdx.x < kRingHalf) xs[orr] = vr;
+  const int iA = i0 + 4 * sh.sx, jA = j0 + sh.rowA;
+  float v[4];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {  // row A
+    const int p = Q + 2 * u;
+    const float cn[6] = {p == 0 ? eAc : co[p > 0 ? p - 1 : 0], p == 3 ? eAc : co[p < 3 ? p + 1 : 3], ca[p],
+                         co[4 + p], cm[p], cp[p]};
+    const float xn[6] = {p == 0 ? eAx : xo[p > 0 ? p - 1 : 0], p == 3 ? eAx : xo[p < 3 ? p + 1 : 3], xa[p],
+                         xo[4 + p], xm[p], xp[p]};
+    const unsigned bm = BND ? bnd_mask(A, iA + p, jA, kw) : 0u;
+    v[u] = cell<NOX, BND>(A, tr, ra[p], co[p], cn, xn, bm);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {  // row B
+    const int p = 1 - Q + 2 * u;
+    const float cn[6] = {p == 0 ? eBc : co[4 + (p > 0 ? p - 1 : 0)], p == 3 ? eBc : co[4 + (p < 3 ? p + 1 : 3)], co[p],
+                         cb[p], cm[4 + p], cp[4 + p]};
+    const float xn[6] = {p == 0 ? eBx : xo[4 + (p > 0 ? p - 1 : 0)], p == 3 ? eBx : xo[4 + (p < 3 ? p + 1 : 3)], xo[p],
+                         xb[p], xm[4 + p], xp[4 + p]};
+    const unsigned bm = BND ? bnd_mask(A, iA + p, jA + 1, kw) : 0u;
+    v[2 + u] = cell<NOX, BND>(A, tr, rb[p], co[4 + p], cn, xn, bm);
+  }
+  xo[Q] = v[0];
+  xo[Q + 2] = v[1];
+  xo[4 + 1 - Q] = v[2];
+  xo[4 + 3 - Q] = v[3];
 }
 
-template <bool ZERO, bool UPDATE>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep3d(Sweep3dArgs A, int lz, int tiles_x, int tiles_y,
-                                                         int nzchunk) {
-  extern __shared__ __align__(16) float sm[];
+// First colour of plane kw on one ring cell (staged offset o), read entirely from the slots: x and
+// ic of the plane (xs, cs), below (xsm, csm) and above (xsp, csp); r from rs.
+template <bool NOX, bool BND>
+__device__ __noinline__ void ring_cell(const Sweep3dArgs& A, int i0, int j0, int o, int kw, float* xs, const float* cs,
+                                       const float* xsm, const float* csm, const float* xsp, const float* csp,
+                                       const float* rs) {
+  const float tr[3] = {2.0f * A.ra[0], 2.0f * A.ra[1], 2.0f * A.ra[2]};
+  const float cn[6] = {cs[o - 1], cs[o + 1], cs[o - P], cs[o + P], csm[o], csp[o]};
+  float xn[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (!NOX) {
+    xn[0] = xs[o - 1], xn[1] = xs[o + 1], xn[2] = xs[o - P], xn[3] = xs[o + P];
+    xn[4] = xsm[o], xn[5] = xsp[o];
+  }
+  unsigned bm = 0u;
+  if (BND) {  // the ring cell's global (i, j), wrapped on periodic axes
+    const int jj = o / P, ii = o - jj * P;
+    const int ri = wrap_or_clamp(i0 + ii - 4, A.nx, A.bc[0] == FLD_BC_PERIODIC);
+    const int rj = wrap_or_clamp(j0 + jj - 2, A.ny, A.bc[2] == FLD_BC_PERIODIC);
+    bm = bnd_mask(A, ri, rj, kw);
+  }
+  xs[o] = cell<NOX, BND>(A, tr, rs[o - P], cs[o], cn, xn, bm);
+}
+
+// The plane loop of one item (a tile's z-chunk), with the patch registers of planes s - 2 .. s + 1.
+// Plane p sits in slot (p - k0 + 2) % 4 of shared memory and of the registers.
+template <int C0, bool ZERO, bool UPDATE, bool BND>
+struct Sweeper {
+  const Sweep3dArgs& A;
+  const Sweep3dMaps& M;
+  const float* tr;
+  float* Xs;
+  float* Cs;
+  float* Rs;
+  uint64_t* bar;
+  const Share& sh;
+  const Chunks& ch;
+  int i0, j0, k0, k1;
+  bool zper, use_tma;
+  size_t plane;
+  float (&X)[NS][8];
+  float (&C)[NS][8];
+  float (&RK)[2][4];  // r of the cells the second colour updates on the plane just done, by step parity
+
+  __device__ __forceinline__ bool valid(int k) const { return zper || (k >= 0 && k < A.nz); }
+  __device__ __forceinline__ int wrapk(int k) const { return k < 0 ? k + A.nz : (k >= A.nz ? k - A.nz : k); }
+
+  // bytes the TMA boxes of x and ic of plane kx and r of plane kr deliver
+  __device__ __forceinline__ unsigned box_bytes(bool do_x, int kx, bool do_r, int kr) const {
+    return (do_x && valid(kx) ? (ZERO ? 1u : 2u) * (unsigned)(XPL * sizeof(float)) : 0u) +
+           (do_r && valid(kr) ? (unsigned)(RPL * sizeof(float)) : 0u);
+  }
+
+  // Fetch x and ic of plane kx into slot sx (if do_x) and r of plane kr into slot sr (if do_r):
+  // TMA boxes issued by thread 0 (after the step's mbar_expect), or every thread's cp.async chunks
+  // on a tile whose halo wraps (committed by the caller).  Planes outside a non-periodic z range
+  // are skipped.
+  __device__ __forceinline__ void issue(bool do_x, int kx, int sx, bool do_r, int kr, int sr) const {
+    do_x = do_x && valid(kx);
+    do_r = do_r && valid(kr);
+    if (use_tma) {
+      if (threadIdx.x != 0) return;
+      if (do_x) {
+        if (!ZERO) tma3(Xs + sx * XPL, &M.x, i0 - 4, j0 - 2, wrapk(kx), bar);
+        tma3(Cs + sx * XPL, &M.c, i0 - 4, j0 - 2, wrapk(kx), bar);
+      }
+      if (do_r) tma3(Rs + sr * RPS, &M.r, i0 - 4, j0 - 1, wrapk(kr), bar);
+      return;
+    }
+    const size_t px = (size_t)wrapk(kx) * plane, pr = (size_t)wrapk(kr) * plane;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (do_x && ch.xg[c] >= 0) {
+        if (!ZERO) cp16(Xs + sx * XPL + ch.xo[c], A.xin + px + ch.xg[c]);
+        cp16(Cs + sx * XPL + ch.xo[c], A.dc + px + ch.xg[c]);
+      }
+      if (do_r && ch.rg[c] >= 0) cp16(Rs + sr * RPS + ch.xo[c], A.r + pr + ch.rg[c]);
+    }
+  }
+
+  // one step's fetch: x and ic of plane kx into slot sx, r of plane kr into r slot sr
+  __device__ __forceinline__ void stage(bool do_x, int kx, int sx, bool do_r, int kr, int sr) const {
+    if (use_tma && threadIdx.x == 0) mbar_expect(bar, box_bytes(do_x, kx, do_r, kr));
+    issue(do_x, kx, sx, do_r, kr, sr);
+    if (!use_tma) cp_commit();
+  }
+
+  // the item's first fetch: x and ic of planes k0 - 2 .. k0 in slots 0..2, r of k0 - 1 in r slot 1
+  // (plane p's r slot is (p - k0 + 2) % 2)
+  __device__ __forceinline__ void stage_prologue() const {
+    if (use_tma && threadIdx.x == 0)
+      mbar_expect(bar, box_bytes(true, k0 - 2, false, 0) + box_bytes(true, k0 - 1, true, k0 - 1) +
+                           box_bytes(true, k0, false, 0));
+    issue(true, k0 - 2, 0, false, 0, 0);
+    issue(true, k0 - 1, 1, true, k0 - 1, 1);
+    issue(true, k0, 2, false, 0, 0);
+    if (!use_tma) cp_commit();
+  }
+
+  // End of a step: the staged planes have landed and every thread is done with the slots.  True
+  // (for the whole block) when a TMA wait ran out of its bound: the error word is set and the block
+  // leaves after giving the copies in flight a second bound.
+  __device__ __forceinline__ bool step_end(unsigned& phase) const {
+    if (!use_tma) {
+      cp_wait_all();
+      __syncthreads();
+      return false;
+    }
+    const int late = mbar_wait(bar, phase) ? 0 : 1;
+    fence_proxy_async();
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0 && A.err) atomicOr(A.err, 1u);
+      mbar_wait(bar, phase);
+      return true;
+    }
+    phase ^= 1u;
+    return false;
+  }
+
+  // registers of slot q <- the thread's patch of the plane staged in slot q
+  template <int Q>
+  __device__ __forceinline__ void load_patch() const {
+    if (ZERO) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) X[Q][c] = 0.f;
+    } else {
+      lds4(&X[Q][0], Xs + Q * XPL + sh.oA);
+      lds4(&X[Q][4], Xs + Q * XPL + sh.oA + P);
+    }
+    lds4(&C[Q][0], Cs + Q * XPL + sh.oA);
+    lds4(&C[Q][4], Cs + Q * XPL + sh.oA + P);
+  }
+
+  template <int Q>
+  __device__ __forceinline__ void store_plane(int k) const {
+    const size_t g = (size_t)wrapk(k) * plane + (size_t)(j0 + sh.rowA) * A.nx + i0 + 4 * sh.sx;
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const size_t gr = g + (size_t)row * A.nx;
+      const float* v = &X[Q][4 * row];
+      *reinterpret_cast<float4*>(A.xout + gr) = make_float4(v[0], v[1], v[2], v[3]);
+      if (UPDATE) {
+        double2* p = reinterpret_cast<double2*>(A.x64 + gr);
+        double2 a = p[0], b = p[1];
+        a.x += (double)v[0];
+        a.y += (double)v[1];
+        b.x += (double)v[2];
+        b.y += (double)v[3];
+        p[0] = a;
+        p[1] = b;
+      }
+    }
+  }
+
+  // Step s, with PH = (s - k0 + 1) % 4: the slots of planes s - 2 .. s + 2 and the patch position
+  // class (the first colour's row-A positions on plane s, (C0 + s) & 1 with k0 even) are fixed.
+  template <int PH>
+  __device__ __forceinline__ bool step(int s, unsigned& phase) const {
+    constexpr int SM1 = PH, S0 = (PH + 1) & 3, SP1 = (PH + 2) & 3, SP2 = (PH + 3) & 3, SM2 = SP2;
+    constexpr int R0 = (PH + 1) & 1, RP1 = PH & 1;  // r slots of planes s and s + 1
+    constexpr int Q = (C0 + 1 + PH) & 1;
+    // x and ic of plane s + 2 (up to k1 + 1) and r of plane s + 1 (up to k1) land while this step
+    // computes
+    stage(s + 2 <= k1 + 1, s + 2, SP2, s + 1 <= k1, s + 1, RP1);
+    if (s + 1 <= k1 + 1) load_patch<SP1>();
+    if (s <= k1 && valid(s)) {
+      const int kw = wrapk(s);
+      float ra[4], rb[4];
+      lds4(ra, Rs + R0 * RPS + sh.oA - P);
+      lds4(rb, Rs + R0 * RPS + sh.oA);
+      patch_pass<Q, ZERO, BND>(A, tr, sh, i0, j0, kw, Xs + S0 * XPL, Cs + S0 * XPL, ra, rb, X[S0], C[S0], X[SM1],
+                               C[SM1], X[SP1], C[SP1]);
+      // the r of this plane's second-colour cells (row A at 1 - Q, 3 - Q; row B at Q, Q + 2)
+      RK[PH & 1][0] = ra[1 - Q];
+      RK[PH & 1][1] = ra[3 - Q];
+      RK[PH & 1][2] = rb[Q];
+      RK[PH & 1][3] = rb[Q + 2];
+      sts4(Xs + S0 * XPL + sh.oA, &X[S0][0]);
+      sts4(Xs + S0 * XPL + sh.oA + P, &X[S0][4]);
+      if (threadIdx.x < kRingHalf) {
+        const int o = ((C0 + kw) & 1) ? sh.ring_o[1] : sh.ring_o[0];
+        ring_cell<ZERO, BND>(A, i0, j0, o, kw, Xs + S0 * XPL, Cs + S0 * XPL, Xs + SM1 * XPL, Cs + SM1 * XPL,
+                             Xs + SP1 * XPL, Cs + SP1 * XPL, Rs + R0 * RPS);
+      }
+    }
+    // second colour on plane s - 1: its cells sit at the same patch positions as the first
+    // colour's on plane s
+    if (s - 1 >= k0 && s - 1 < k1) {
+      // kept at the previous step: row A's cells at Q, Q + 2, row B's at 1 - Q, 3 - Q
+      const float* k = RK[(PH + 1) & 1];
+      float ra[4], rb[4];
+      ra[Q] = k[0], ra[Q + 2] = k[1], rb[1 - Q] = k[2], rb[3 - Q] = k[3];
+      ra[1 - Q] = ra[3 - Q] = rb[Q] = rb[Q + 2] = 0.f;
+      patch_pass<Q, false, BND>(A, tr, sh, i0, j0, wrapk(s - 1), Xs + SM1 * XPL, Cs + SM1 * XPL, ra, rb, X[SM1],
+                                C[SM1], X[SM2], C[SM2], X[S0], C[S0]);
+      store_plane<SM1>(s - 1);
+    }
+    return step_end(phase);
+  }
+};
+
+template <int C0, bool ZERO, bool UPDATE, bool BND>
+__global__ void __launch_bounds__(kThreads, 4) k_sweep3d(const __grid_constant__ Sweep3dArgs A,
+                                                         const __grid_constant__ Sweep3dMaps M, int lz, int tiles_x,
+                                                         int tiles_y, int nzchunk, int tma) {
+  extern __shared__ __align__(128) float sm[];
   float* Xs = sm;
-  float* Cs = sm + NXS * XPL;
-  float* Rs = Cs + NXS * XPL;
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const size_t plane = (size_t)nx * ny;
+  float* Cs = sm + NS * XPL;
+  float* Rs = Cs + NS * XPL;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sm) + kBarOffset);
+  const size_t plane = (size_t)A.nx * A.ny;
   const bool xper = A.bc[0] == FLD_BC_PERIODIC, yper = A.bc[2] == FLD_BC_PERIODIC;
   const bool zper = A.bc[4] == FLD_BC_PERIODIC;
   const int ntile = tiles_x * tiles_y;
   const int items = ntile * nzchunk;
-  const int tid = threadIdx.x;
-  const int c1 = A.c0 ^ 1;
   const float tr[3] = {2.0f * A.ra[0], 2.0f * A.ra[1], 2.0f * A.ra[2]};
+  const Share sh = make_share();
+  float X[NS][8], C[NS][8], RK[2][4];
+  if (threadIdx.x == 0) mbar_init(bar);
+  __syncthreads();
+  unsigned phase = 0;  // parity of the mbarrier phase the next wait is for
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     // consecutive items are neighbouring tiles of one z-chunk, so the blocks running together
     // share their halos through L2
     const int tile = item % ntile, zc = item / ntile;
     const int i0 = (tile % tiles_x) * TX, j0 = (tile / tiles_x) * TY;
-    const int k0 = zc * lz, k1 = min(nz, k0 + lz);
-    const bool tile_bnd = (!xper && (i0 == 0 || i0 + TX == nx)) || (!yper && (j0 == 0 || j0 + TY == ny));
-    const Share sh = make_share(i0, j0, A, xper, yper);
-    auto valid = [&](int k) { return zper || (k >= 0 && k < nz); };
-    auto wrapk = [&](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
-    auto load_xc = [&](int k, int slot) {
-      if (!valid(k)) return;
-      const size_t pb = (size_t)wrapk(k) * plane;
-      float* xs = Xs + slot * XPL;
-      float* cs = Cs + slot * XPL;
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-        if (sh.xg[c] >= 0) {
-          if (!ZERO) cp16(xs + sh.xo[c], A.xin + pb + sh.xg[c]);
-          cp16(cs + sh.xo[c], A.dc + pb + sh.xg[c]);
-        }
-    };
-    auto load_r = [&](int k, int slot) {
-      if (!valid(k)) return;
-      const size_t pb = (size_t)wrapk(k) * plane;
-      float* rs = Rs + slot * RPL;
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-        if (sh.rg[c] >= 0) cp16(rs + sh.xo[c], A.r + pb + sh.rg[c]);
-    };
-    auto store = [&](int k, int slot) {
-      // the tile of plane k, both colours final: one float4 per thread
-      const int row = tid >> 4, q4 = tid & 15;
-      const float4 v = *reinterpret_cast<const float4*>(Xs + slot * XPL + (2 + row) * P + 4 + 4 * q4);
-      const size_t g = (size_t)wrapk(k) * plane + (size_t)(j0 + row) * nx + i0 + 4 * q4;
-      *reinterpret_cast<float4*>(A.xout + g) = v;
-      if (UPDATE) {
-        double2* p = reinterpret_cast<double2*>(A.x64 + g);
-        double2 a = p[0], b = p[1];
-        a.x += (double)v.x;
-        a.y += (double)v.y;
-        b.x += (double)v.z;
-        b.y += (double)v.w;
-        p[0] = a;
-        p[1] = b;
-      }
-    };
-    // slots: plane k0 - 2 + q of x and ic in slot q % NXS, plane k0 - 1 + q of r in slot q % NRS
+    const int k0 = zc * lz, k1 = min(A.nz, k0 + lz);  // lz even: k0 even
+    // TMA boxes do not wrap: tiles whose halo crosses a periodic face stage with cp.async
+    const bool use_tma =
+        tma && !(xper && (i0 == 0 || i0 + TX == A.nx)) && !(yper && (j0 == 0 || j0 + TY == A.ny));
+    const Chunks ch = make_chunks(i0, j0, A, xper, yper);
+    const Sweeper<C0, ZERO, UPDATE, BND> W{A, M, tr, Xs, Cs, Rs, bar, sh, ch, i0, j0, k0, k1, zper, use_tma, plane,
+                                           X, C, RK};
     cp_wait_all();
+    fence_proxy_async();
     __syncthreads();  // the previous item's last reads of the slots are done
-    load_xc(k0 - 2, 0);
-    load_xc(k0 - 1, 1);
-    load_xc(k0, 2);
-    load_r(k0 - 1, 0);
-    cp_commit();
-    cp_wait_all();
-    __syncthreads();
-    auto wrap_slot = [](int v, int n) { return v >= n ? v - n : (v < 0 ? v + n : v); };
-    int xs0 = 1, rs0 = 0;  // slots of plane s
-    for (int s = k0 - 1; s <= k1; ++s) {
-      const int xm2 = wrap_slot(xs0 - 2, NXS), xm1 = wrap_slot(xs0 - 1, NXS), xp1 = wrap_slot(xs0 + 1, NXS);
-      const int xp2 = wrap_slot(xs0 + 2, NXS);
-      const int rm1 = wrap_slot(rs0 - 1, NRS), rp1 = wrap_slot(rs0 + 1, NRS);
-      // the planes step s + 1 adds (x and ic of plane s + 2, r of plane s + 1), in flight while
-      // step s computes
-      if (s + 2 <= k1 + 1) load_xc(s + 2, xp2);
-      if (s + 1 <= k1) load_r(s + 1, rp1);
-      cp_commit();
-      // first colour on plane s, tile and ring (in place: it reads only second-colour cells)
-      if (valid(s)) {
-        const Planes S{Xs + xs0 * XPL, Cs + xs0 * XPL, Xs + xm1 * XPL, Cs + xm1 * XPL,
-                       Xs + xp1 * XPL, Cs + xp1 * XPL, Rs + rs0 * RPL};
-        const int kw = wrapk(s);
-        if (tile_bnd || (!zper && (s == 0 || s == nz - 1)))
-          colour_pass<ZERO, true, true>(A, tr, S, Xs + xs0 * XPL, sh, A.c0, i0, j0, kw);
-        else
-          colour_pass<ZERO, true, false>(A, tr, S, Xs + xs0 * XPL, sh, A.c0, i0, j0, kw);
-      }
-      if (s - 2 >= k0) store(s - 2, xm2);
-      // second colour on plane s - 1 (tile): its neighbours of the first colour are final.  No
-      // barrier is needed between the two passes: a thread's second-colour cell on plane s - 1 and
-      // its first-colour cell on plane s share their (i, j), so the one value the second pass reads
-      // from this step (the z+ neighbour) and the one the first pass reads from what the second
-      // overwrites (the z- neighbour) are the thread's own; everything else either pass reads was
-      // final at the last barrier, and the ring's second-colour cells are never written.
-      if (s - 1 >= k0 && s - 1 < k1) {
-        const Planes S{Xs + xm1 * XPL, Cs + xm1 * XPL, Xs + xm2 * XPL, Cs + xm2 * XPL,
-                       Xs + xs0 * XPL, Cs + xs0 * XPL, Rs + rm1 * RPL};
-        const int kw = wrapk(s - 1);
-        if (tile_bnd || (!zper && (s - 1 == 0 || s - 1 == nz - 1)))
-          colour_pass<false, false, true>(A, tr, S, Xs + xm1 * XPL, sh, c1, i0, j0, kw);
-        else
-          colour_pass<false, false, false>(A, tr, S, Xs + xm1 * XPL, sh, c1, i0, j0, kw);
-      }
-      cp_wait_all();  // the planes of step s + 1 have landed
-      __syncthreads();
-      xs0 = xp1;
-      rs0 = wrap_slot(rs0 + 1, NRS);
+    W.stage_prologue();
+    if (W.step_end(phase)) return;
+    W.template load_patch<0>();
+    W.template load_patch<1>();
+    const int nsteps = k1 - k0 + 2;  // s = k0 - 1 .. k1
+    for (int t = 0; t < nsteps; t += 4) {
+      const int s = k0 - 1 + t;
+      if (W.template step<0>(s, phase)) return;
+      if (t + 1 < nsteps && W.template step<1>(s + 1, phase)) return;
+      if (t + 2 < nsteps && W.template step<2>(s + 2, phase)) return;
+      if (t + 3 < nsteps && W.template step<3>(s + 3, phase)) return;
     }
-    // the loop ended with xs0 = slot of plane k1 + 1
-    store(k1 - 1, wrap_slot(xs0 - 2, NXS));
   }
 }
 
@@ -347,7 +598,44 @@ __global__ void k_dcell32(long long n, double scale, const double* __restrict__ 
   if (i < n) ic[i] = __frcp_rn((float)(scale * D[i]));
 }
 
+using SweepKernel = void (*)(const Sweep3dArgs, const Sweep3dMaps, int, int, int, int, int);
+
+// the instantiations, indexed by c0 + 2 zero + 4 update + 8 bnd
+template <int I>
+constexpr SweepKernel kernel_at() {
+  return k_sweep3d<I & 1, ((I >> 1) & 1) != 0, ((I >> 2) & 1) != 0, ((I >> 3) & 1) != 0>;
+}
+const SweepKernel kKernels[16] = {kernel_at<0>(),  kernel_at<1>(),  kernel_at<2>(),  kernel_at<3>(),
+                                  kernel_at<4>(),  kernel_at<5>(),  kernel_at<6>(),  kernel_at<7>(),
+                                  kernel_at<8>(),  kernel_at<9>(),  kernel_at<10>(), kernel_at<11>(),
+                                  kernel_at<12>(), kernel_at<13>(), kernel_at<14>(), kernel_at<15>()};
+
 int g_blocks_per_sm = 0, g_sms = 0;
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda); nullptr where unavailable, in
+// which case every tile stages with cp.async
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// a map of an nx x ny x nz FP32 array whose boxes are 72 x rows x 1 (zero fill beyond the array)
+bool encode_box(CUtensorMap& m, const float* base, int nx, int ny, int nz, int rows) {
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)P, (cuuint32_t)rows, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -363,20 +651,18 @@ cudaError_t launch_sweep3d(const Sweep3dArgs& a, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    const void* ks[4] = {(const void*)k_sweep3d<false, false>, (const void*)k_sweep3d<true, false>,
-                         (const void*)k_sweep3d<false, true>, (const void*)k_sweep3d<true, true>};
-    for (int q = 0; q < 4 && e == cudaSuccess; ++q)
-      e = cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    for (int q = 0; q < 16 && e == cudaSuccess; ++q)
+      e = cudaFuncSetAttribute((const void*)kKernels[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     int b = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep3d<false, false>, kThreads, kSmemBytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)kKernels[0], kThreads, kSmemBytes);
     if (e != cudaSuccess) return e;
     g_blocks_per_sm = std::max(1, b);
   }
   const int tiles_x = a.nx / TX, tiles_y = a.ny / TY, ntile = tiles_x * tiles_y;
   const int resident = g_blocks_per_sm * g_sms;
-  // z-chunk length: the candidate with the best product of useful planes per staged plane
-  // (lz / (lz + 2)) and load balance over the resident blocks
+  // z-chunk length (even, so that chunks start on even planes): the candidate with the best product
+  // of useful planes per staged plane (lz / (lz + 2)) and load balance over the resident blocks
   int lz = a.nz;
   double best = -1.0;
   for (int c : {4, 8, 16, 32, 64, 128, 256, 512}) {
@@ -392,11 +678,24 @@ cudaError_t launch_sweep3d(const Sweep3dArgs& a, cudaStream_t s) {
   const int items = ntile * nzchunk;
   const unsigned grid = (unsigned)std::min(items, resident);
   const bool zero = a.xin == nullptr, upd = a.x64 != nullptr;
+  bool bnd = false;
+  for (int f = 0; f < 6; ++f) bnd = bnd || a.bc[f] != FLD_BC_PERIODIC;
+  // TMA box maps of this launch's arrays (FLD_SWEEP3D_TMA=0: cp.async staging for every tile)
+  static const bool tma_env = [] {
+    const char* v = getenv("FLD_SWEEP3D_TMA");
+    return !(v && v[0] == '0');
+  }();
+  Sweep3dMaps M;
+  memset(&M, 0, sizeof(M));
+  int tma = 0;
+  if (tma_env && encode_fn()) {
+    const bool ok = encode_box(M.c, a.dc, a.nx, a.ny, a.nz, RXR) && encode_box(M.r, a.r, a.nx, a.ny, a.nz, RRR) &&
+                    (zero || encode_box(M.x, a.xin, a.nx, a.ny, a.nz, RXR));
+    tma = ok ? 1 : 0;
+  }
+  const int q = (a.c0 & 1) + 2 * (zero ? 1 : 0) + 4 * (upd ? 1 : 0) + 8 * (bnd ? 1 : 0);
   note_launch();
-  if (zero && upd) k_sweep3d<true, true><<<grid, kThreads, kSmemBytes, s>>>(a, lz, tiles_x, tiles_y, nzchunk);
-  else if (zero) k_sweep3d<true, false><<<grid, kThreads, kSmemBytes, s>>>(a, lz, tiles_x, tiles_y, nzchunk);
-  else if (upd) k_sweep3d<false, true><<<grid, kThreads, kSmemBytes, s>>>(a, lz, tiles_x, tiles_y, nzchunk);
-  else k_sweep3d<false, false><<<grid, kThreads, kSmemBytes, s>>>(a, lz, tiles_x, tiles_y, nzchunk);
+  kKernels[q]<<<grid, kThreads, kSmemBytes, s>>>(a, M, lz, tiles_x, tiles_y, nzchunk, tma);
   return cudaGetLastError();
 }
 

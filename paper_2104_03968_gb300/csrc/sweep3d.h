@@ -16,6 +16,7 @@ struct Sweep3dArgs {
   float* xout;          // iterate after the sweep (a different array from xin)
   double* x64;          // if set, each cell's new value is also added to this FP64 array
   int c0;               // the first half-sweep updates the cells with (i + j + k) & 1 == c0
+  unsigned* err;        // if set, a wait for staged planes that ran out of its bound ORs 1 into it
 };
 
 // Levels the tiled sweep takes: 3-D, nx a multiple of 64 (and at least 64), ny of 16, nz even
@@ -23,7 +24,7 @@ struct Sweep3dArgs {
 bool sweep3d_eligible(int nx, int ny, int nz);
 
 // One full sweep (both colours).  Asynchronous on s.  Every array must start on a 16-byte boundary
-// (the planes are fetched in 16-byte copies).
+// (the planes are fetched in 16-byte copies and TMA boxes).
 cudaError_t launch_sweep3d(const Sweep3dArgs& a, cudaStream_t s);
 
 // dc = 1 / (float)(dt D_cell / dx_0^2) per cell, from the FP64 D (the solver's FP64 set-up path).
