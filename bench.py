@@ -113,9 +113,10 @@ def host_cpu():
 
 
 def load_traffic(n: int, precision: str) -> dict:
-    """DRAM bytes per launch of each traced scope at n^3, from single-kernel ncu captures of a
-    smaller grid (profiles/traffic.json) scaled by the cells a launch processes.  A scope whose
-    kernel changed since its capture is absent there, so its traffic is reported as null."""
+    """DRAM bytes per launch of each traced scope at n^3, from single-kernel ncu captures
+    (profiles/traffic.json; a scope's own captured_n, else the file's) scaled by the cells a launch
+    processes.  A scope whose kernel changed since its capture is absent there, so its traffic is
+    reported as null."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -124,8 +125,8 @@ def load_traffic(n: int, precision: str) -> dict:
         return {}
     if t.get("precision") != precision:
         return {}
-    scale = (n / t["captured_n"]) ** 3
-    return {k: v["dram_bytes_per_launch"] * scale for k, v in t.get("scopes", {}).items()}
+    return {k: v["dram_bytes_per_launch"] * (n / v.get("captured_n", t["captured_n"])) ** 3
+            for k, v in t.get("scopes", {}).items()}
 
 
 def load_peaks():

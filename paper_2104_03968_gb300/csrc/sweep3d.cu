@@ -563,9 +563,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep3d(const __grid_constant__
   __syncthreads();
   unsigned phase = 0;  // parity of the mbarrier phase the next wait is for
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    // consecutive items are neighbouring tiles of one z-chunk, so the blocks running together
-    // share their halos through L2
-    const int tile = item % ntile, zc = item / ntile;
+    // consecutive items are the z-chunks of one tile, then those of the next tile along x: the
+    // blocks running together cover a few rows of tiles through the whole depth (measured at 512^3:
+    // 0.532 ms per sweep, against 0.586 ms with the tiles of one z-chunk consecutive)
+    const int tile = item / nzchunk, zc = item % nzchunk;
     const int i0 = (tile % tiles_x) * TX, j0 = (tile / tiles_x) * TY;
     const int k0 = zc * lz, k1 = min(A.nz, k0 + lz);  // lz even: k0 even
     // TMA boxes do not wrap: tiles whose halo crosses a periodic face stage with cp.async
