@@ -28,6 +28,19 @@ __host__ inline void unnote_launches(unsigned long long n) {
 }
 __host__ inline unsigned long long launch_count() { return g_kernel_launches.load(std::memory_order_relaxed); }
 
+// Grid size for kernels that walk rows block-cyclically: at most cap blocks, and no more than the
+// device keeps resident at once (blocks of kBlock threads of kernel fn), so that all of them
+// advance through the rows in one front and the neighbouring rows and planes a block re-reads are
+// the ones its neighbours fetched just before (a grid twice the resident size splits the rows in
+// two fronts far apart, and the re-reads then miss in L2).
+__host__ inline int front_grid(const void* fn, int cap, size_t smem = 0) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem) != cudaSuccess || per_sm <= 0)
+    return cap;
+  return per_sm * sms < cap ? per_sm * sms : cap;
+}
+
 struct GridDev {
   int n[3];
   int ndim;

@@ -933,8 +933,9 @@ cudaError_t Multigrid::fp64_operator(cudaStream_t s) {
   }
   {
     TraceScope ts("norm_b", s);
-    note_launch(), k_sumsq<<<nparts_, kBlock, 0, s>>>(b64_, g_.ncell, partials_);
-    note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_ + 1);
+    const int gs = front_grid((const void*)k_sumsq, nparts_);
+    note_launch(), k_sumsq<<<gs, kBlock, 0, s>>>(b64_, g_.ncell, partials_);
+    note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, gs, scal_ + 1);
   }
   fp64_op_ = true;
   return cudaGetLastError();
@@ -1132,7 +1133,7 @@ cudaError_t Multigrid::vcycle_direct(int l, int nu1, int nu2, double* x64, cudaS
     TraceScope ts(l == 0 ? "restrict_L0" : "restrict_Lc", s);
     if (rows_ok(l)) {
       const int crows = nc[1] * nc[2];
-      const unsigned gr = (unsigned)std::min(crows, 152 * 16);
+      const unsigned gr = (unsigned)front_grid((const void*)k_restrict_rows<T, 3>, std::min(crows, 152 * 16));
       if (g_.ndim == 3) note_launch(),
           k_restrict_rows<T, 3><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
       else note_launch(), k_restrict_rows<T, 2><<<gr, kBlock, 0, s>>>(L, r, x, nc[1], crows, (T*)lv_[l + 1].r);
@@ -1268,6 +1269,10 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
     L32lo = level_dev<float>(g_, dims_[0], wlo);
   }
   const double N = (double)g_.ncell;
+  // one front of resident blocks for the row-walking residual kernels
+  const int gu = front_grid((const void*)k_residual_update<3>, nparts_);
+  const int gx = mixed ? front_grid((const void*)k_residual64_df, nparts_)
+                       : front_grid((const void*)k_residual64<T>, nparts_);
   // the FP64 iterate lives in E_new; the first residual copies E_old into it
   const double* x_in = E_old;
   double* x = E_new;
@@ -1297,18 +1302,18 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
       float* rv = (float*)lv_[0].r;
       if (g_.ndim == 3)
         note_launch(),
-            k_residual_update<3><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr,
-                                                              nparts_, partials_);
+            k_residual_update<3><<<gu, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr, gu,
+                                                         partials_);
       else if (g_.ndim == 2)
         note_launch(),
-            k_residual_update<2><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr,
-                                                              nparts_, partials_);
+            k_residual_update<2><<<gu, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr, gu,
+                                                         partials_);
       else
         note_launch(),
-            k_residual_update<1><<<nparts_, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr,
-                                                              nparts_, partials_);
-      note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
-      note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_ + nparts_, nparts_, scal_ + 2);
+            k_residual_update<1><<<gu, kBlock, 0, s>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, scale, nullptr, gu,
+                                                         partials_);
+      note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, gu, scal_);
+      note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_ + gu, gu, scal_ + 2);
     } else {
       TraceScope ts("residual", s);
       df_res = mixed && df_mode_ && !fp64_op_ && cycles == 0;
@@ -1326,11 +1331,11 @@ cudaError_t Multigrid::solve_t(const double* E_old, double* E_new, double rtol, 
         }
         if (mixed)
           note_launch(),
-              k_residual64_df<<<nparts_, kBlock, 0, s>>>(L64, x_in, x, b64_, diag64_, (float*)lv_[0].r, rlo_, partials_);
+              k_residual64_df<<<gx, kBlock, 0, s>>>(L64, x_in, x, b64_, diag64_, (float*)lv_[0].r, rlo_, partials_);
         else
-          note_launch(), k_residual64<T><<<nparts_, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r,
-                                                                    partials_);
-        note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, nparts_, scal_);
+          note_launch(), k_residual64<T><<<gx, kBlock, 0, s>>>(L64, g_.ncell, x_in, x, b64_, diag64_, (T*)lv_[0].r,
+                                                               partials_);
+        note_launch(), k_reduce<<<1, 1024, 0, s>>>(partials_, gx, scal_);
       }
     }
     cudaError_t e = cudaMemcpyAsync(host_scal_, scal_, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1665,14 +1670,17 @@ cudaError_t Multigrid::build_solve_graph(const SolveKey& k, cudaStream_t s0) {
     L32 = level_dev<float>(g_, dims_[0], lv_[0].w);
     L32lo = level_dev<float>(g_, dims_[0], wlo);
   }
+  const int gu = front_grid((const void*)k_residual_update<3>, nparts_);
+  const int gx = mixed ? front_grid((const void*)k_residual64_df, nparts_)
+                       : front_grid((const void*)k_residual64<T>, nparts_);
   auto exact_residual = [&](cudaStream_t b, const double* xin) {
     if (mixed)
-      note_launch(), k_residual64_df<<<nparts_, kBlock, 0, b>>>(L64, xin, x, b64_, diag64_, (float*)lv_[0].r, rlo_,
-                                                                partials_);
+      note_launch(), k_residual64_df<<<gx, kBlock, 0, b>>>(L64, xin, x, b64_, diag64_, (float*)lv_[0].r, rlo_,
+                                                           partials_);
     else
-      note_launch(), k_residual64<T><<<nparts_, kBlock, 0, b>>>(L64, g_.ncell, xin, x, b64_, diag64_, (T*)lv_[0].r,
-                                                                partials_);
-    note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_, nparts_, scal_);
+      note_launch(), k_residual64<T><<<gx, kBlock, 0, b>>>(L64, g_.ncell, xin, x, b64_, diag64_, (T*)lv_[0].r,
+                                                           partials_);
+    note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_, gx, scal_);
   };
   // pre-loop: the error word, the state and the first residual (the set-up ran before the graph)
   e = cudaMemsetAsync(wave_ctl_, 0, sizeof(unsigned), s);
@@ -1745,16 +1753,16 @@ cudaError_t Multigrid::build_solve_graph(const SolveKey& k, cudaStream_t s0) {
       float* rv = (float*)lv_[0].r;
       const float* sp = &sd_->scale;
       if (g_.ndim == 3)
-        note_launch(), k_residual_update<3><<<nparts_, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp,
-                                                                      nparts_, partials_);
+        note_launch(), k_residual_update<3><<<gu, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp, gu,
+                                                                 partials_);
       else if (g_.ndim == 2)
-        note_launch(), k_residual_update<2><<<nparts_, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp,
-                                                                      nparts_, partials_);
+        note_launch(), k_residual_update<2><<<gu, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp, gu,
+                                                                 partials_);
       else
-        note_launch(), k_residual_update<1><<<nparts_, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp,
-                                                                      nparts_, partials_);
-      note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_, nparts_, scal_);
-      note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_ + nparts_, nparts_, scal_ + 2);
+        note_launch(), k_residual_update<1><<<gu, kBlock, 0, b>>>(L32, L32lo, dhi_, dlo_, dv, rv, rlo_, x, 0.f, sp, gu,
+                                                                 partials_);
+      note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_, gu, scal_);
+      note_launch(), k_reduce<<<1, 1024, 0, b>>>(partials_ + gu, gu, scal_ + 2);
       return cudaGetLastError();
     });
     cudaGraph_t tmp = nullptr;
