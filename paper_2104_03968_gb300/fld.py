@@ -281,7 +281,9 @@ def _fptr(t: torch.Tensor | None):
 
 def smooth_sweep(ctx: Context, grid: dict, dt: float, D, r, x_in, x_out, first_colour: int = 0):
     """One red-black Gauss-Seidel sweep of the mixed solver's FP32 smoother (Sect. 3.4) on a 3-D
-    grid: D float64, r / x_in / x_out float32 CUDA tensors (x_in None: start from zero)."""
+    grid: D float64, r / x_in / x_out float32 CUDA tensors (x_in None: start from zero).
+    Synchronises the stream (FLD_ERR_DEVICE_TIMEOUT if the kernel's wait for staged planes ran out
+    of its bound)."""
     g = grid_struct(grid)
     ctx.check(ctx.lib.fld_smooth_sweep(ctx.h, ct.byref(g), float(dt), _dptr(D), _fptr(r), _fptr(x_in), _fptr(x_out),
                                        int(first_colour), _stream()))
