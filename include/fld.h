@@ -252,6 +252,8 @@ FLD_API fld_status fld_step_host(fld_ctx* ctx, const fld_grid* grid, const fld_p
    FLD_PREC_MIXED, each grid's fine residual is double-float with a bound on its error.  The
    grid has converged when the residual plus the bound is at most its rtol, so the true residual
    is too.  A grid whose bound exceeds rtol / 4 takes FP64 residuals from its next cycle on.
+   A grid with no linear-extrapolation face (a symmetric operator) runs conjugate gradients
+   preconditioned by the V-cycle as its outer loop; the others add each V-cycle's correction.
    infos[g].rel_residual is the last residual computed, bound not included. */
 FLD_API fld_status fld_step_batched(fld_ctx* ctx, int ngrids, const fld_grid* grids,
                             const fld_params* params, const double* dt, const double* const* rho,

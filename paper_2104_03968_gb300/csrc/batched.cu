@@ -21,6 +21,7 @@
 // that shape (the first step alone is not typical of the ones that follow).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 
@@ -58,6 +59,7 @@ struct BFine {
   double* diag;
   double* D;
   double* kappa;
+  double* p;  // search direction of the conjugate-gradient outer loop (FP64, fine cells)
   const double* rho;
   double* eps;
   double* E;
@@ -85,6 +87,8 @@ struct BState {
   int tile_begin;
   int tile_end;
   int f64res;  // the residual of this grid is evaluated in FP64 (else double-float with a bound)
+  int pcg;     // the outer loop is preconditioned conjugate gradients (symmetric operator)
+  double rz, beta, alpha;  // its r.z of the last cycle and step coefficients
   double bb;
   double rel;
   double rtol;
@@ -112,6 +116,7 @@ __global__ void kb_reset(int ng, BState* __restrict__ st, int* __restrict__ ctl)
     st[g].xbis = 0;
     st[g].rel = 0.0;
     st[g].f64res = 0;
+    st[g].rz = st[g].beta = st[g].alpha = 0.0;
   }
   if (g == 0) ctl[0] = ctl[1] = 0;
 }
@@ -409,7 +414,8 @@ __global__ void kb_smooth(const Tile* __restrict__ tiles, const BLev<T>* __restr
   const Tile tl = tiles[blockIdx.x];
   if (!st[tl.grid].active) return;
   const BLev<T>& B = lev[tl.grid * kMaxLev + tl.level];
-  double* x64 = UPDATE ? fine[tl.grid].E : nullptr;
+  // a conjugate-gradient grid takes the V-cycle's result as its preconditioned residual instead
+  double* x64 = UPDATE && !st[tl.grid].pcg ? fine[tl.grid].E : nullptr;
   for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
     // thread t of the colour: half-row position m, row (j, k); the tile list covers exactly
     // ((n[0] + 1) / 2) n[1] n[2] threads
@@ -464,6 +470,124 @@ __global__ void kb_prolong(const Tile* __restrict__ tiles, const BLev<T>* __rest
     int i, j, k;
     unflatten32(idx, F.f0, F.f1, i, j, k);
     prolong_at<T>(F.L.ndim, xc, C.L.n, xf, i, j, k, idx);
+  }
+}
+
+// ----------------------------------------------------------------------------- conjugate gradients
+//
+// On a grid with no linear-extrapolation face the operator A of Eq. discdiff (harmonic-mean faces,
+// Dirichlet, Neumann or periodic boundaries) is symmetric positive definite, and its outer loop runs
+// preconditioned conjugate gradients with the V-cycle as the preconditioner: z = V(r),
+// beta = (r.z) / (r.z)_previous (0 on the grid's first cycle), p = z + beta p,
+// alpha = (r.z) / (p.A p), x += alpha p.  The r of each pass is the true residual b - A x
+// (kb_residual), so the convergence test and its error bound are those of the plain loop, and a
+// cycle costs one more application of A.  Grids with such a face keep the plain loop x += z.
+
+// where a grid's level-0 V-cycle result is: in tmp for 2-D grids whose fused sweeps left it there
+template <class T>
+__device__ __forceinline__ const T* vcycle_out(const BFine& f, const BLev<T>& L0, int z2d_tmp) {
+  return (f.g.ndim == 2 && f.nlev > 1 && z2d_tmp) ? L0.tmp : L0.x;
+}
+
+// parts[blk] = sum of r z over the tile (0 for the tiles of other grids)
+template <class T>
+__global__ void kb_pcg_rz(const Tile* __restrict__ tiles, const BFine* __restrict__ fine,
+                          const BLev<T>* __restrict__ lev, const BState* __restrict__ st, double* __restrict__ parts,
+                          int z2d_tmp) {
+  const Tile tl = tiles[blockIdx.x];
+  double acc = 0.0;
+  if (st[tl.grid].active && st[tl.grid].pcg) {
+    const BLev<T>& L0 = lev[tl.grid * kMaxLev];
+    const T* z = vcycle_out(fine[tl.grid], L0, z2d_tmp);
+    for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+      const long long idx = tl.start + c;
+      acc = fma((double)L0.r[idx], (double)z[idx], acc);
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+}
+
+// one block: each conjugate-gradient grid's r.z and beta
+__global__ void kb_pcg_beta(int ng, const double* __restrict__ parts, BState* __restrict__ st) {
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    BState& s = st[g];
+    if (!s.active || !s.pcg) continue;
+    double rz = 0.0;
+    for (int t = s.tile_begin; t < s.tile_end; ++t) rz += parts[t];
+    s.beta = (s.cycles <= 1 || !(s.rz > 0.0) || !(rz == rz)) ? 0.0 : rz / s.rz;
+    s.rz = rz;
+  }
+}
+
+// p = z + beta p (p = z where beta is 0: p holds the previous step's direction); parts[blk] =
+// sum of p (A p) over the tile, A in FP64 from the fine weights and diagonal
+template <class T>
+__global__ void kb_pcg_dir(const Tile* __restrict__ tiles, const BFine* __restrict__ fine,
+                           const BLev<T>* __restrict__ lev, const BState* __restrict__ st, int z2d_tmp) {
+  const Tile tl = tiles[blockIdx.x];
+  const BState& s = st[tl.grid];
+  if (!s.active || !s.pcg) return;
+  const BFine& f = fine[tl.grid];
+  const T* z = vcycle_out(f, lev[tl.grid * kMaxLev], z2d_tmp);
+  const double beta = s.beta;
+  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+    const long long idx = tl.start + c;
+    f.p[idx] = beta == 0.0 ? (double)z[idx] : fma(beta, f.p[idx], (double)z[idx]);
+  }
+}
+
+template <class T>
+__global__ void kb_pcg_ap(const Tile* __restrict__ tiles, const BFine* __restrict__ fine,
+                          const BLev<T>* __restrict__ lev, const BState* __restrict__ st,
+                          double* __restrict__ parts) {
+  const Tile tl = tiles[blockIdx.x];
+  double acc = 0.0;
+  if (st[tl.grid].active && st[tl.grid].pcg) {
+    const BFine& f = fine[tl.grid];
+    const BLev<T>& L0 = lev[tl.grid * kMaxLev];
+    const LevelDev<double> L = fine_level(f);
+    const double* __restrict__ p = f.p;
+    for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+      const unsigned idx = (unsigned)(tl.start + c);
+      int i, j, k;
+      unflatten32(idx, L0.f0, L0.f1, i, j, k);
+      const double pc = p[idx];
+      double ap = f.diag[idx] * pc;
+      for_each_face(L, i, j, k, (long long)idx, [&](double w, int kind, long long nb) {
+        if (kind == kInterior) ap = fma(-w, p[nb], ap);
+        else if (kind == kContinuous) ap = fma(w, p[nb], ap);
+      });
+      acc = fma(pc, ap, acc);
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+}
+
+// one block: alpha = r.z / p.A p (1 where p.A p is not positive: the plain correction)
+__global__ void kb_pcg_alpha(int ng, const double* __restrict__ parts, BState* __restrict__ st) {
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    BState& s = st[g];
+    if (!s.active || !s.pcg) continue;
+    double pap = 0.0;
+    for (int t = s.tile_begin; t < s.tile_end; ++t) pap += parts[t];
+    const double a = s.rz / pap;
+    s.alpha = (pap > 0.0 && a == a && a > 0.0 && a < 1e300) ? a : 1.0;
+  }
+}
+
+// x += alpha p
+__global__ void kb_pcg_x(const Tile* __restrict__ tiles, const BFine* __restrict__ fine,
+                         const BState* __restrict__ st) {
+  const Tile tl = tiles[blockIdx.x];
+  const BState& s = st[tl.grid];
+  if (!s.active || !s.pcg) return;
+  const BFine& f = fine[tl.grid];
+  const double a = s.alpha;
+  for (long long c = threadIdx.x; c < tl.count; c += blockDim.x) {
+    const long long idx = tl.start + c;
+    f.E[idx] = fma(a, f.p[idx], f.E[idx]);
   }
 }
 
@@ -639,14 +763,14 @@ __global__ void __launch_bounds__(256) kb_sweep2d(const Tile2* __restrict__ tile
     }
     __syncthreads();
   }
-  double* x64 = UPDATE ? fine[tl.grid].E : nullptr;
+  double* x64 = UPDATE && !st[tl.grid].pcg ? fine[tl.grid].E : nullptr;
   for (int e = threadIdx.x; e < h * W; e += blockDim.x) {
     const int lj = e / W, li = e - lj * W;
     if (li >= w) continue;
     const long long idx = (tl.i0 + li) + (long long)n0 * (tl.j0 + lj);
     const T v = xs[e + H * W + H];
     dst[idx] = v;
-    if (UPDATE) x64[idx] += (double)v;
+    if (UPDATE && x64) x64[idx] += (double)v;
   }
   if (RESTRICT) {
     const BLev<T>& C = lev[tl.grid * kMaxLev + tl.level + 1];
@@ -783,6 +907,7 @@ struct BatchedSolver::Impl {
   std::vector<Range> sweep_r;  // per level, into tiles2_d
   Range coarse_r;
   int maxlev = 0;
+  bool pcg_any = false;  // some grid of the batch runs the conjugate-gradient outer loop
   // graph
   cudaGraphExec_t exec = nullptr;
   // kernels of one graph replay: those outside the WHILE node, and those of one pass of its body
@@ -887,7 +1012,7 @@ cudaError_t BatchedSolver::Impl::build_levels() {
   for (int i = 0; i < ng; ++i) {
     long long N = cells_of(dims[i][0]);
     for (int a = 0; a < gd[i].ndim; ++a) add(faces_of(dims[i][0], a) * 8);
-    for (int k = 0; k < 4; ++k) add(N * 8);  // b, diag, D, kappa
+    for (int k = 0; k < 5; ++k) add(N * 8);  // b, diag, D, kappa, p
     for (size_t l = 0; l < dims[i].size(); ++l) {
       long long n = cells_of(dims[i][l]);
       if (l > 0 || es == 4)
@@ -910,7 +1035,8 @@ cudaError_t BatchedSolver::Impl::build_levels() {
     f.diag = (double*)arena.take(N * 8);
     f.D = (double*)arena.take(N * 8);
     f.kappa = (double*)arena.take(N * 8);
-    if (!f.b || !f.diag || !f.D || !f.kappa) return cudaErrorMemoryAllocation;
+    f.p = (double*)arena.take(N * 8);
+    if (!f.b || !f.diag || !f.D || !f.kappa || !f.p) return cudaErrorMemoryAllocation;
     for (size_t l = 0; l < dims[i].size(); ++l) {
       BLev<T>& B = lev_h[(size_t)i * kMaxLev + l];
       long long n = cells_of(dims[i][l]);
@@ -966,10 +1092,21 @@ cudaError_t BatchedSolver::Impl::build_tiles(int tile_cells) {
   };
   // fine cells, grouped by grid (contiguous per grid for the segmented reductions)
   fine_r.off = 0;
+  // conjugate gradients on the grids whose operator is symmetric (no linear-extrapolation face);
+  // FLD_BATCHED_PCG=0 keeps the plain defect correction everywhere
+  static const bool pcg_env = [] {
+    const char* v = getenv("FLD_BATCHED_PCG");
+    return !(v && v[0] == '0');
+  }();
+  pcg_any = false;
   for (int g = 0; g < ng; ++g) {
     st_h[g].tile_begin = (int)t.size();
     add_range(g, 0, cells_of(dims[g][0]));
     st_h[g].tile_end = (int)t.size();
+    bool sym = pcg_env;
+    for (int f = 0; f < 2 * gd[g].ndim; ++f) sym = sym && gd[g].bc[f] != FLD_BC_CONTINUOUS;
+    st_h[g].pcg = sym ? 1 : 0;
+    pcg_any = pcg_any || sym;
   }
   fine_r.n = (int)t.size();
   cell_r.assign(maxlev, {});
@@ -1184,6 +1321,16 @@ cudaError_t BatchedSolver::Impl::build_graph(int nu1_, int nu2_) {
         }
       }
       post_tmp[l] = in_tmp;
+    }
+    if (pcg_any) {  // the conjugate-gradient update of the grids that use it (kb_pcg_*)
+      const int z2d = post_tmp[0];
+      const Tile* tf = tl + fine_r.off;
+      note_launch(), kb_pcg_rz<T><<<fine_r.n, B, 0, b>>>(tf, fine_d, lev, st_d, parts_d, z2d);
+      note_launch(), kb_pcg_beta<<<1, kCheckThreads, 0, b>>>(ng, parts_d, st_d);
+      note_launch(), kb_pcg_dir<T><<<fine_r.n, B, 0, b>>>(tf, fine_d, lev, st_d, z2d);
+      note_launch(), kb_pcg_ap<T><<<fine_r.n, B, 0, b>>>(tf, fine_d, lev, st_d, parts_d);
+      note_launch(), kb_pcg_alpha<<<1, kCheckThreads, 0, b>>>(ng, parts_d, st_d);
+      note_launch(), kb_pcg_x<<<fine_r.n, B, 0, b>>>(tf, fine_d, st_d);
     }
     cudaGraph_t tmp = nullptr;
     e = cudaStreamEndCapture(b, &tmp);

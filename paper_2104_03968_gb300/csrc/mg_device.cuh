@@ -228,7 +228,7 @@ __device__ __forceinline__ void smooth_at(const LevelDev<T>& L, const T* __restr
     v *= invd[idx];
   }
   x[idx] = v;
-  if (UPDATE) x64[idx] += (double)v;
+  if (UPDATE && x64) x64[idx] += (double)v;
 }
 
 template <class T, bool ZERO, bool UPDATE>
