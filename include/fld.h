@@ -216,6 +216,15 @@ FLD_API fld_status fld_smooth_sweep(fld_ctx* ctx, const fld_grid* grid, double d
                                     const float* r, const float* x_in, float* x_out, int first_colour,
                                     void* stream);
 
+/* Opacity of n independent cells (Sect. 2: T from the ideal-gas law; Sect. 5.1: the tabulated
+   opacity, here a bilinear table in log10 rho and log10 T on log10 kappa, clamped to its edges; or
+   the constant / Kramers-like models of p).  rho, eps, kappa: DEVICE float64, n cells.  With
+   p->precision == FLD_PREC_MIXED the table's two logarithms and its power of ten are evaluated in
+   double-float arithmetic (relative error ~1e-14), as the mixed column step does; otherwise in
+   FP64.  Asynchronous. */
+FLD_API fld_status fld_opacity(fld_ctx* ctx, size_t n, const fld_params* p, const double* rho, const double* eps,
+                               double* kappa, void* stream);
+
 /* Point-implicit exchange (Sect. 3.3) on n independent cells, in place on eps and E.  kappa may
    be NULL, in which case it is evaluated from rho and eps with the opacity model of p.
    Asynchronous; `info` (may be NULL) is filled after a stream synchronisation. */

@@ -844,21 +844,7 @@ GridDev grid_dev(const fld_grid& g) {
   return d;
 }
 
-Opacity opacity_of(const fld_params& p) {
-  Opacity o{};
-  o.model = p.opacity;
-  o.kappa0 = p.kappa0;
-  o.kr_a = p.kr_a;
-  o.kr_b = p.kr_b;
-  o.table = p.table;
-  o.tn0 = p.tn[0];
-  o.tn1 = p.tn[1];
-  o.tlo0 = p.tlo[0];
-  o.tlo1 = p.tlo[1];
-  o.thi0 = p.thi[0];
-  o.thi1 = p.thi[1];
-  return o;
-}
+Opacity opacity_of(const fld_params& p) { return make_opacity(p); }
 
 long long cells_of(const std::array<int, 3>& n) { return (long long)n[0] * n[1] * n[2]; }
 

@@ -148,21 +148,7 @@ GridDev to_dev(const fld_grid* g) {
   return d;
 }
 
-Opacity to_opacity(const fld_params* p) {
-  Opacity o{};
-  o.model = p->opacity;
-  o.kappa0 = p->kappa0;
-  o.kr_a = p->kr_a;
-  o.kr_b = p->kr_b;
-  o.table = p->table;
-  o.tn0 = p->tn[0];
-  o.tn1 = p->tn[1];
-  o.tlo0 = p->tlo[0];
-  o.tlo1 = p->tlo[1];
-  o.thi0 = p->thi[0];
-  o.thi1 = p->thi[1];
-  return o;
-}
+Opacity to_opacity(const fld_params* p) { return make_opacity(*p); }
 
 ExchangeParams to_exchange(const fld_params* p, double dt) {
   return make_exchange(p->c, p->a_rad, p->gamma, p->gas_R, dt, p->exch_maxit > 0 ? p->exch_maxit : 100,
@@ -513,6 +499,20 @@ fld_status fld_smooth_sweep(fld_ctx* ctx, const fld_grid* grid, double dt, const
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_smooth_sweep launch");
   if (ctx->h_info[2]) return fail(ctx, FLD_ERR_DEVICE_TIMEOUT, "fld_smooth_sweep: staged planes did not arrive in time");
+  return FLD_OK;
+}
+
+fld_status fld_opacity(fld_ctx* ctx, size_t n, const fld_params* p, const double* rho, const double* eps,
+                       double* kappa, void* stream) {
+  if (!ctx) return FLD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  fld_status st = check_params(ctx, p, false);
+  if (st != FLD_OK) return st;
+  if (n > 0 && (!rho || !eps || !kappa)) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and kappa must be non-NULL");
+  DeviceGuard dg(ctx->device);
+  cudaError_t e = launch_opacity((long long)n, to_opacity(p), p->gamma, p->gas_R, p->precision == FLD_PREC_MIXED, rho,
+                                 eps, kappa, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fld_opacity launch");
   return FLD_OK;
 }
 

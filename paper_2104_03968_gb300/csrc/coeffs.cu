@@ -6,6 +6,7 @@
 //
 // FP64 throughout: D enters the operator whose residual is checked in FP64.
 #include "coeffs.cuh"
+#include "dfmath.cuh"
 #include "kernels.h"
 #include "trace.h"
 
@@ -60,6 +61,24 @@ __global__ void k_faces(GridDev g, double dt, DAxes D, double* __restrict__ w0,
 }
 
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <bool MIXED>
+__global__ void k_opacity(long long n, const __grid_constant__ Opacity op, double gamma, double gas_R,
+                          const double* __restrict__ rho, const double* __restrict__ eps, double* __restrict__ kappa) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double rh = rho[i], T = temperature(gamma, gas_R, rh, eps[i]);
+  kappa[i] = (MIXED && op.model == FLD_OPACITY_TABLE) ? opacity_table_df(op, rh, T) : opacity(op, rh, T);
+}
+
+cudaError_t launch_opacity(long long n, const Opacity& op, double gamma, double gas_R, bool mixed, const double* rho,
+                           const double* eps, double* kappa, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  if (mixed) k_opacity<true><<<blocks_for(n), kBlock, 0, s>>>(n, op, gamma, gas_R, rho, eps, kappa);
+  else k_opacity<false><<<blocks_for(n), kBlock, 0, s>>>(n, op, gamma, gas_R, rho, eps, kappa);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_coeffs_range(const GridDev& g, const Opacity& op, double c, double gamma, double gas_R,
                                 int limiter, const double* E, const double* rho, const double* eps, double* kappa_out,

@@ -18,6 +18,7 @@
 #include <string>
 
 #include "columns.h"
+#include "dfmath.cuh"
 #include "exchange.cuh"
 #include "trace.h"
 
@@ -211,6 +212,14 @@ __device__ __forceinline__ void chunk_solve_f32(int t, int P, int m, const float
   }
 }
 
+// kappa of a cell: the mixed precision takes the table's logarithms and power of ten in
+// double-float (dfmath.cuh), the FP64 precision opacity() as it is
+template <bool MIXED>
+__device__ __forceinline__ double col_opacity(const Opacity& o, double rho, double T) {
+  if (MIXED && o.model == FLD_OPACITY_TABLE) return opacity_table_df(o, rho, T);
+  return opacity(o, rho, T);
+}
+
 template <int MODE, bool MIXED>
 __global__ void k_columns(ColArgs A) {
   extern __shared__ double sm[];
@@ -276,7 +285,7 @@ __global__ void k_columns(ColArgs A) {
   if (MODE == kColStepExchangeFirst || MODE == kColStepMidpoint) {
     for (int i = s0; i < s1; ++i) {
       double e = se[i], E = sx[i];
-      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
+      double k = col_opacity<MIXED>(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
       if (exchange_cell_fast(xp1, sr[i], k, e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
@@ -290,7 +299,7 @@ __global__ void k_columns(ColArgs A) {
   if (MODE != kColDiffuse) {
     for (int i = s0; i < s1; ++i) {
       double e = sx[i], rh = sr[i];
-      double k = opacity(A.op, rh, temperature(A.gamma, A.gas_R, rh, se[i])) + (cak ? sq[i] : 0.0);
+      double k = col_opacity<MIXED>(A.op, rh, temperature(A.gamma, A.gas_R, rh, se[i])) + (cak ? sq[i] : 0.0);
       sk[i] = k;
       if (!(e > 0.0) || !(rh > 0.0) || !(k > 0.0) || !(se[i] >= 0.0)) bad = true;
       double em, ep;
@@ -510,7 +519,7 @@ __global__ void k_columns(ColArgs A) {
     for (int i = s0; i < s1; ++i) {
       double E = fma(2.0, sx[i] - sh[i], A.Ein[base + i]);
       double e = A.eps[base + i];
-      double k = opacity(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
+      double k = col_opacity<MIXED>(A.op, sr[i], temperature(A.gamma, A.gas_R, sr[i], e)) + (cak ? sq[i] : 0.0);
       if (exchange_cell_fast(xp, sr[i], k, e, E, iters, bis)) {
         se[i] = e;
         sx[i] = E;
@@ -621,17 +630,7 @@ static ColArgs col_args(int ncell, const double* r_faces, int bc_lo, int bc_hi, 
   A.limiter = p.limiter;
   A.maxit = p.exch_maxit > 0 ? p.exch_maxit : 100;
   A.plain64 = p.precision == FLD_PREC_FP64 ? 1 : 0;
-  A.op.model = p.opacity;
-  A.op.kappa0 = p.kappa0;
-  A.op.kr_a = p.kr_a;
-  A.op.kr_b = p.kr_b;
-  A.op.table = p.table;
-  A.op.tn0 = p.tn[0];
-  A.op.tn1 = p.tn[1];
-  A.op.tlo0 = p.tlo[0];
-  A.op.tlo1 = p.tlo[1];
-  A.op.thi0 = p.thi[0];
-  A.op.thi1 = p.thi[1];
+  A.op = make_opacity(p);
   return A;
 }
 

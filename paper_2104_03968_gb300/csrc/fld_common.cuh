@@ -109,7 +109,28 @@ struct Opacity {
   const double* table;
   int tn0, tn1;
   double tlo0, tlo1, thi0, thi1;
+  double su0, su1;  // (tn - 1) / (thi - tlo) per axis: table cells per decade
 };
+
+// the Opacity of a parameter set (every path builds it here, so that the derived table scales
+// are always set)
+__host__ inline Opacity make_opacity(const fld_params& p) {
+  Opacity o{};
+  o.model = p.opacity;
+  o.kappa0 = p.kappa0;
+  o.kr_a = p.kr_a;
+  o.kr_b = p.kr_b;
+  o.table = p.table;
+  o.tn0 = p.tn[0];
+  o.tn1 = p.tn[1];
+  o.tlo0 = p.tlo[0];
+  o.tlo1 = p.tlo[1];
+  o.thi0 = p.thi[0];
+  o.thi1 = p.thi[1];
+  o.su0 = o.thi0 > o.tlo0 ? (o.tn0 - 1) / (o.thi0 - o.tlo0) : 0.0;
+  o.su1 = o.thi1 > o.tlo1 ? (o.tn1 - 1) / (o.thi1 - o.tlo1) : 0.0;
+  return o;
+}
 
 // device status word: bit flags OR-ed by kernels, read back by the host
 enum : unsigned { kStatNonpositive = 1u, kStatNonfinite = 2u };

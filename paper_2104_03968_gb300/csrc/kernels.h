@@ -17,6 +17,11 @@ cudaError_t launch_coeffs_range(const GridDev& g, const Opacity& op, double c, d
                                 double* D_out, unsigned* status, long long first, long long count, cudaStream_t s,
                                 bool plain64 = false);
 
+// kappa per cell from rho and eps (gas law for T); mixed: the table model's logarithms and power
+// of ten in double-float (dfmath.cuh), else opacity() in FP64
+cudaError_t launch_opacity(long long n, const Opacity& op, double gamma, double gas_R, bool mixed, const double* rho,
+                           const double* eps, double* kappa, cudaStream_t s);
+
 // w64[a] (and w32[a] when non-null) receive the face weights of axis a (layout of fld_common.cuh);
 // with w32lo, w32 holds the truncated leading 24 bits of each weight and w32lo the remainder.
 // Dax[a]: cell-centred D of axis a (the same pointer three times for a scalar D).

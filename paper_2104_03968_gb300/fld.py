@@ -76,6 +76,7 @@ _SIGS = {
     "fld_coeffs": [P, P, P, P, P, P, P, P, P],
     "fld_diffuse": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_exchange": [P, ct.c_size_t, P, ct.c_double, P, P, P, P, P, P],
+    "fld_opacity": [P, ct.c_size_t, P, P, P, P, P],
     "fld_step": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_step_host": [P, P, P, ct.c_double, P, P, P, P, P],
     "fld_step_batched": [P, ct.c_int, P, P, P, P, P, P, P, P],
@@ -313,6 +314,17 @@ def exchange(ctx: Context, params: dict, dt: float, rho, eps, E, kappa=None) -> 
     ctx.check(ctx.lib.fld_exchange(ctx.h, E.numel(), ct.byref(p), float(dt), _dptr(rho), _dptr(kappa), _dptr(eps),
                                    _dptr(E), ct.byref(info), _stream()))
     return info.as_dict()
+
+
+def opacity(ctx: Context, params: dict, rho, eps, out=None):
+    """kappa per cell from rho and eps (CUDA float64 tensors) with the opacity model of params
+    (the table's logarithms in double-float with precision "mixed")."""
+    keep = []
+    p = params_struct(params, keep, _device_of(ctx))
+    if out is None:
+        out = rho.new_empty(rho.shape)
+    ctx.check(ctx.lib.fld_opacity(ctx.h, rho.numel(), ct.byref(p), _dptr(rho), _dptr(eps), _dptr(out), _stream()))
+    return out
 
 
 def _host_buffer(a, writable: bool):

@@ -99,6 +99,29 @@ def test_coeffs_unit_scales(ctx, scaling, limiter):
     assert np.abs(host(D).reshape(D_o.shape) / D_o - 1).max() < 1e-12
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_opacity_table_over_its_range(ctx, precision):
+    """The tabulated opacity (bilinear in log10 rho, log10 T on log10 kappa, clamped at the edges)
+    over and beyond the table's range: the mixed precision's double-float logarithms and power
+    of ten, and the FP64 ones, against the oracle."""
+    from paper_2104_03968_gb300 import fld
+    case = inputs.wind_columns(ncol=2, ncell=64)
+    p = dict(case["phys"], precision=precision)
+    rng = np.random.default_rng(11)
+    n = 200000
+    lrho = rng.uniform(-17.0, -5.0, n)   # the table covers -16 .. -6
+    lT = rng.uniform(3.5, 6.8, n)        # and 3.7 .. 6.5
+    # grid nodes and cell midpoints of the table exactly, where the interpolation weights are 0 or 1/2
+    lrho[:128] = np.linspace(-16.0, -6.0, 128)
+    lT[128:256] = np.linspace(3.7, 6.5, 128)
+    rho = 10.0 ** lrho
+    T = 10.0 ** lT
+    eps = rho * p["gas_R"] * T / (p["gamma"] - 1.0)  # T = (gamma - 1) eps / (rho gas_R)
+    kap_o = oracle.opacity(case["phys"], rho, eps)
+    kap = host(fld.opacity(ctx, p, dev(rho), dev(eps)))
+    assert np.abs(kap / kap_o - 1).max() < 1e-13
+
+
 def test_coeffs_table_opacity(ctx):
     from paper_2104_03968_gb300 import fld
     case = inputs.wind_columns(ncol=4, ncell=64)
