@@ -12,6 +12,7 @@
 // T = double is the plain FP64 solver; T = float gives the mixed form whose smoother,
 // restriction and prolongation run in FP32 while the residual, update and norm stay FP64.
 #include <algorithm>
+#include <cstdint>
 #include <array>
 #include <cstdio>
 #include <cstdlib>
@@ -809,12 +810,16 @@ cudaError_t Multigrid::tiled_sweep(bool zero, int c0, double* x64, cudaStream_t 
   a.r = (const float*)lv_[0].r;
   a.xin = zero ? nullptr : (const float*)lv_[0].x;
   a.xout = (float*)lv_[0].tmp;
-  a.x64 = x64;
+  // the sweep adds its result to x64 in 16-byte accesses; other alignments add it afterwards
+  const bool aligned = ((uintptr_t)x64 & 15u) == 0;
+  a.x64 = aligned ? x64 : nullptr;
   a.c0 = c0;
   a.err = wave_ctl_;  // the solve loop turns a bounded wait that ran out into FLD_ERR_DEVICE_TIMEOUT
   cudaError_t e = launch_sweep3d(a, s);
   std::swap(lv_[0].x, lv_[0].tmp);  // the iterate now lives in the other array
-  return e;
+  if (e == cudaSuccess && x64 && !aligned)
+    note_launch(), k_add_correction<T><<<nblk(g_.ncell), kBlock, 0, s>>>(g_.ncell, (const T*)lv_[0].x, x64);
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 cudaError_t Multigrid::configure(const GridDev& g, int precision) {
