@@ -1,5 +1,5 @@
-// Many independent grids advanced in one graph launch (the benchmark spec's batching of uneven
-// grids; the per-grid mathematics is that of fld_step: Sect. 2.2 coefficients, Sect. 3.4
+// Many independent grids of uneven sizes, opacities and time steps advanced in one graph launch
+// (the per-grid mathematics is that of fld_step: Sect. 2.2 coefficients, Sect. 3.4
 // multigrid diffusion, Sect. 3.3 exchange).
 //
 // Design: every kernel of the single-grid path exists here in a level-synchronous batched
