@@ -140,22 +140,28 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons, one sample every `interval_ms`, each stamped with
+    the host's monotonic clock when it arrives.  The sampler starts before the warm-up (nvidia-smi
+    takes a few hundred ms to deliver its first line), and `window()` brackets the timed region:
+    the summary covers the samples that arrived inside it."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, interval_ms: int = 50):
         self.device = device
+        self.interval_ms = interval_ms
         self.proc = None
-        self.lines = []
+        self.lines = []  # (monotonic seconds, line)
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
+                                          "-lms", str(self.interval_ms), "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -163,33 +169,51 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def begin(self):
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        # two intervals, so that the first sample after a window shorter than one has arrived
+        time.sleep(2 * self.interval_ms * 1e-3)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
+        return self.summary(self.lines, self.t0, self.t1, self.interval_ms)
+
+    @classmethod
+    def summary(cls, lines, t0, t1, interval_ms) -> dict:
+        """Median SM clock, maximum clock and the throttle reasons seen, over the samples that
+        arrived in [t0, t1]; when the window is shorter than one interval and holds none, over the
+        first sample after t0 (`"window": "next sample"`)."""
+        rows = []
+        for t, ln in lines:
+            parts = [q.strip() for q in ln.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                rows.append((t, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        sm.sort()
-        med = sm[len(sm) // 2] if sm else None
-        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        lo = t0 if t0 is not None else -math.inf
+        hi = t1 if t1 is not None else math.inf
+        inside = [r for r in rows if lo <= r[0] <= hi]
+        note = "timed region"
+        if not inside:
+            later = [r for r in rows if r[0] >= lo]
+            inside, note = later[:1], "next sample"
+        sm = sorted(r[1] for r in inside)
+        reasons = sorted({nm for r in inside for nm, v in zip(cls.REASONS, r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": inside[-1][2] if inside else None,
+                "reasons": reasons, "samples": len(sm), "interval_ms": interval_ms, "window": note}
 
 
 def dist_setup():
@@ -393,14 +417,16 @@ def main():
 
     # ---- main arm: warm-up, then exactly K timed steps
     eps, E = fresh()
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         fld.step(ctx, g, p, dt, rho0, eps, E)
-    clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
-    clocks.start()
     n_before = fld.launch_count()
+    clocks.begin()
     ms, infos, _ = timed_steps(torch, fld, ctx, g, p, dt, rho0, eps, E, args.steps)
+    clocks.end()
     n_after = fld.launch_count()
     clk = clocks.stop()
     barrier(world)
