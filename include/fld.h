@@ -33,6 +33,10 @@
  *     with autotuned sweep counts (it times its candidates), and solves while per-kernel
  *     tracing is on.  fld_step_batched and fld_step_host return with their results complete.
  *   - Inputs are never modified; eps and E are updated in place where documented.
+ *   - Empty batches are valid: n == 0 cells (fld_opacity, fld_exchange), ncol == 0 columns and
+ *     ngrids == 0 grids launch nothing and return FLD_OK once the scalar arguments have passed
+ *     their checks; the data arrays may then be NULL, and an info is zeroed (status FLD_OK).
+ *     A grid (fld_grid) has at least one cell per axis.
  *   - Return value: FLD_OK, or an error code for an invalid argument or a CUDA error.  What
  *     the device finds -- a solve that did not reach rtol within max_cycles, a non-positive
  *     input met on the device, a non-finite residual -- is info->status of the asynchronous

@@ -508,7 +508,8 @@ fld_status fld_opacity(fld_ctx* ctx, size_t n, const fld_params* p, const double
   ctx->err.clear();
   fld_status st = check_params(ctx, p, false);
   if (st != FLD_OK) return st;
-  if (n > 0 && (!rho || !eps || !kappa)) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and kappa must be non-NULL");
+  if (n == 0) return FLD_OK;
+  if (!rho || !eps || !kappa) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and kappa must be non-NULL");
   DeviceGuard dg(ctx->device);
   cudaError_t e = launch_opacity((long long)n, to_opacity(p), p->gamma, p->gas_R, p->precision == FLD_PREC_MIXED, rho,
                                  eps, kappa, (cudaStream_t)stream);
@@ -523,7 +524,11 @@ fld_status fld_exchange(fld_ctx* ctx, size_t n, const fld_params* p, double dt, 
   fld_status st = check_params(ctx, p, false);
   if (st != FLD_OK) return st;
   if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, FLD_ERR_INVALID_ARG, "dt must be > 0");
-  if (n > 0 && (!rho || !eps || !E)) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and E must be non-NULL");
+  if (n == 0) {
+    if (info) memset(info, 0, sizeof(*info));
+    return FLD_OK;
+  }
+  if (!rho || !eps || !E) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and E must be non-NULL");
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = reset_status(ctx, s)) != FLD_OK) return st;
@@ -886,8 +891,11 @@ fld_status fld_columns_step(fld_ctx* ctx, int ncol, int ncell, const double* r_f
   std::string err;
   st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);
   if (st != FLD_OK) return fail(ctx, st, "%s", err.c_str());
+  if (ncol == 0) {
+    if (info) memset(info, 0, sizeof(*info));
+    return FLD_OK;
+  }
   if (!rho || !eps || !E) return fail(ctx, FLD_ERR_INVALID_ARG, "rho, eps and E must be non-NULL");
-  if (ncol == 0) return FLD_OK;
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = reset_status(ctx, s)) != FLD_OK) return st;
@@ -915,8 +923,8 @@ fld_status fld_columns_diffuse(fld_ctx* ctx, int ncol, int ncell, const double* 
   std::string err;
   st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);
   if (st != FLD_OK) return fail(ctx, st, "%s", err.c_str());
-  if (!D_cell || !E_old || !E_new) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell, E_old and E_new must be non-NULL");
   if (ncol == 0) return FLD_OK;
+  if (!D_cell || !E_old || !E_new) return fail(ctx, FLD_ERR_INVALID_ARG, "D_cell, E_old and E_new must be non-NULL");
   DeviceGuard dg(ctx->device);
   if ((st = ensure_geom(ctx, ncell)) != FLD_OK) return st;
   cudaError_t e = launch_columns_diffuse(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, *p, dt, D_cell,

@@ -560,14 +560,15 @@ fld_status columns_validate(int ncol, int ncell, const double* r_faces, int geom
     *err = buf;
     return ncell > kColumnMaxCells ? FLD_ERR_UNSUPPORTED : FLD_ERR_INVALID_ARG;
   }
-  if (!r_faces) return bad("r_faces is NULL");
   if (geometry != FLD_GEOM_CARTESIAN && geometry != FLD_GEOM_SPHERICAL) return bad("unknown geometry");
   for (int bc : {bc_lo, bc_hi})
     if (bc != FLD_BC_DIRICHLET && bc != FLD_BC_NEUMANN && bc != FLD_BC_CONTINUOUS && bc != FLD_BC_LUMINOSITY)
       return bad("column boundaries must be Dirichlet, Neumann, continuous or (inner) luminosity");
   if (bc_hi == FLD_BC_LUMINOSITY) return bad("the luminosity boundary is for the inner face only");
+  if (ncol == 0) return FLD_OK;  // an empty batch reads no array
   if ((bc_lo != FLD_BC_CONTINUOUS && !v_lo) || (bc_hi != FLD_BC_CONTINUOUS && !v_hi))
     return bad("v_lo / v_hi are required for Dirichlet, Neumann and luminosity boundaries");
+  if (!r_faces) return bad("r_faces is NULL");
   if (!dt) return bad("dt is NULL");
   return FLD_OK;
 }
@@ -722,7 +723,7 @@ extern "C" fld_status fld_columns_step_static(int ncol, int ncell, const double*
   std::string err;
   fld_status st = columns_validate(ncol, ncell, r_faces, geometry, bc_lo, bc_hi, v_lo, v_hi, dt, &err);
   if (st != FLD_OK) return st;
-  if (!static_params_ok(p) || !rho || !eps || !E) return FLD_ERR_INVALID_ARG;
+  if (!static_params_ok(p) || (ncol > 0 && (!rho || !eps || !E))) return FLD_ERR_INVALID_ARG;
   if (info) memset(info, 0, sizeof(*info));
   if (ncol == 0) return FLD_OK;
   double* scratch = nullptr;

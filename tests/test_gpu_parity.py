@@ -824,6 +824,33 @@ def test_invalid_arguments_are_rejected(ctx):
     assert e.value.status == 2
 
 
+def test_empty_batches_launch_nothing(ctx):
+    """Zero cells, zero columns and zero grids are valid calls: FLD_OK, no kernel launched, the
+    data arrays may be NULL (an empty tensor's data pointer), the info zeroed."""
+    from paper_2104_03968_gb300 import fld
+    case = _column_case(2, 64)
+    p = solver(case["phys"])
+    empty = torch.empty(0, dtype=torch.float64, device="cuda")
+    n0 = fld.launch_count()
+    info = fld.exchange(ctx, p, 1.0, empty, empty.clone(), empty.clone())
+    assert info["status"] == 0 and info["exch_max_iters"] == 0
+    assert fld.opacity(ctx, dict(p, precision="mixed"), empty, empty.clone()).numel() == 0
+    assert fld.step_batched(ctx, [], [], [], [], [], []) == []
+    no_col = torch.empty((0, 64), dtype=torch.float64, device="cuda")
+    for precision in ("fp64", "mixed"):
+        info = fld.columns_step(ctx, case["r_faces"], "spherical", tuple(case["bc"]), case["bc_lo"][:0],
+                                case["bc_hi"][:0], dict(p, precision=precision), case["dt"][:0], no_col,
+                                no_col.clone(), no_col.clone())
+        assert info["status"] == 0
+    out = fld.columns_diffuse(ctx, case["r_faces"], "spherical", tuple(case["bc"]), case["bc_lo"][:0],
+                              case["bc_hi"][:0], p, case["dt"][:0], no_col, no_col.clone())
+    assert out.shape == (0, 64)
+    info = fld.columns_step_static(dev(case["r_faces"]), "spherical", tuple(case["bc"]), empty, empty.clone(), p,
+                                   empty.clone(), no_col, no_col.clone(), no_col.clone())
+    assert info["status"] == 0
+    assert fld.launch_count() == n0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_steps_enqueued_back_to_back(ctx, precision):
     """fld_step is asynchronous: two steps enqueued one after the other with no host wait between
