@@ -243,14 +243,15 @@ def batched_2d(ngrids: int = 512, seed: int = 3, nmin: int = 64, nmax: int = 512
 
 def opacity_table(nrho: int = 128, nT: int = 128, lrho=(-16.0, -6.0), lT=(3.7, 6.5)):
     """Synthetic log10 kappa table: electron scattering + Kramers + an iron-like bump at
-    log T = 5.3.  Rows are log10 rho, columns log10 T."""
+    log T = 5.3.  Rows are log10 rho, columns log10 T.  Returns (table, tlo, thi) with the
+    parameters' convention: tlo = [lowest log10 rho, lowest log10 T], thi = the highest."""
     lr = np.linspace(lrho[0], lrho[1], nrho)
     lt = np.linspace(lT[0], lT[1], nT)
     R, T = np.meshgrid(10.0 ** lr, 10.0 ** lt, indexing="ij")
     kK = 0.2 / (1e-10 * (1e5) ** -3.5)
     bump = 1.0 * np.exp(-(np.log10(T) - 5.3) ** 2 / (2 * 0.15 ** 2)) * (R / 1e-10) ** 0.25
     kap = 0.2 + kK * R * T ** -3.5 + bump
-    return np.ascontiguousarray(np.log10(kap)), list(lrho), list(lT)
+    return np.ascontiguousarray(np.log10(kap)), [lrho[0], lT[0]], [lrho[1], lT[1]]
 
 
 def wind_columns(ncol: int = 4096, ncell: int = 2048, seed: int = 4, dt_factor: float = 100.0,
