@@ -142,3 +142,20 @@ def test_gaussian_pulse_setup():
     assert c["E"].max() == pytest.approx(1e-6 + math.exp(-0.5 / 32), rel=1e-14)  # centre at (32, 32), 2 sigma^2 = 32
     assert i in {(31, 31), (31, 32), (32, 31), (32, 32)}
     assert c["dt_exp"] == pytest.approx(750.0) and c["dt"] == pytest.approx(7500.0)
+
+
+def test_wind_table_reproduces_its_opacity_law_at_the_nodes():
+    """The wind recipe's table, read through the oracle's lookup with the recipe's parameters,
+    gives back electron scattering + Kramers + the bump at log T = 5.3 at every node: the ranges
+    reach the lookup in the parameters' order (rows log10 rho over [-16, -6], columns log10 T over
+    [3.7, 6.5])."""
+    import oracle
+    phys = inputs.wind_columns(ncol=1, ncell=16)["phys"]
+    lr, lt = np.linspace(-16.0, -6.0, 128), np.linspace(3.7, 6.5, 128)
+    rng = np.random.default_rng(3)
+    i, j = rng.integers(0, 128, 64), rng.integers(0, 128, 64)
+    rho, T = 10.0 ** lr[i], 10.0 ** lt[j]
+    kap = oracle.opacity(phys, rho, inputs.equilibrium_eps(phys, rho, T))
+    kK = 0.2 / (1e-10 * 1e5 ** -3.5)  # the Kramers term is 0.2 at rho = 1e-10, T = 1e5
+    law = 0.2 + kK * rho * T ** -3.5 + np.exp(-(np.log10(T) - 5.3) ** 2 / (2 * 0.15 ** 2)) * (rho / 1e-10) ** 0.25
+    assert np.abs(kap / law - 1).max() < 1e-9
